@@ -1,0 +1,184 @@
+/*
+ * lh.h - C ABI of the B300-native implicit high-order Lagrangian hydrodynamics library.
+ *
+ * The library evaluates, matrix-free and sum-factorised on tensor-product quad/hex
+ * elements, the stage residual of the implicit time step of the paper
+ * "Implicit Lagrangian Hydrodynamics with High-Order Finite Elements" (arxiv 2609.16424)
+ * and its Jacobian actions, and drives the Newton-Krylov solve of that stage.
+ *
+ * Discretisation (paper Sec. 2.1): kinematic space Q_k (continuous, order 1 <= k <= 4)
+ * for position x and velocity v, thermodynamic space Q_{k-1} (discontinuous) for the
+ * specific internal energy e.  Readings of points the paper leaves open: H1 basis =
+ * Lagrange at Gauss-Lobatto points, L2 basis = Lagrange at Gauss-Legendre points,
+ * quadrature = Gauss-Legendre with 2k points per direction (or lh_mesh_desc.quad_1d).
+ *
+ * State vectors (all double unless stated):  U = [ x | v | e ]
+ *   x, v : dim components, each all N_V H1 nodes of the (k n_0 + 1) x (k n_1 + 1)
+ *          [x (k n_2 + 1)] lattice, x-fastest;                       length dim*N_V each
+ *   e    : element-major, element e = e0 + n_0 (e1 + n_1 e2), then its k^dim dofs
+ *          x-fastest;                                                 length N_E = NE k^dim
+ *   n = 2 dim N_V + N_E unknowns.
+ *
+ * Stage residual (paper Sec. 3.5, Eq. (21), at w = u + tau k), mass-weighted form that
+ * matches the blocks of Eq. (23):
+ *   R_x = k_x - w_v
+ *   R_v = M_V k_v + F(w) . 1         rows of fixed normal velocity (bc_mask): R_v = k_v
+ *   R_e = M_E k_e - F(w)^T w_v - b(w)
+ * with M_V, M_E, F from Eq. (7), the stress of Eqs. (11), (13)-(20), rho = rho0 detJ0 /
+ * detJ at quadrature points, and b the optional Taylor-Green energy source.
+ *
+ * Conventions:
+ *  - Vector arguments are DEVICE pointers owned by the caller unless stated otherwise.
+ *  - Work is queued on the mesh's stream (lh_mesh_desc.stream / lh_set_stream); calls
+ *    that return host scalars synchronise that stream.
+ *  - No exception crosses the ABI.  Failures return a status; lh_last_error(mesh)
+ *    returns a message for the last failing call on that mesh.
+ */
+#ifndef LH_H
+#define LH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lh_mesh lh_mesh;
+
+typedef enum {
+  LH_OK = 0,
+  LH_EINVAL = 1,      /* invalid argument (NULL pointer, unsupported order/dim, ...) */
+  LH_ECUDA = 2,       /* a CUDA runtime call failed */
+  LH_ENOMEM = 3,      /* device allocation failed */
+  LH_ETANGLED = 4,    /* a quadrature point has det J <= 0 */
+  LH_ENOCONV = 5,     /* Newton did not reach its tolerance; state left unchanged */
+  LH_ENONFINITE = 6   /* a residual norm is NaN or Inf */
+} lh_status;
+
+typedef enum {
+  LH_FP64 = 0,        /* double in, double out, double arithmetic */
+  LH_FP32 = 1         /* float in, float out, float arithmetic (state gathered in double) */
+} lh_prec;
+
+/* Mesh and model description.  Call lh_mesh_desc_init first to get the defaults. */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int n[3];                /* elements per direction (n[2] ignored for dim 2) */
+  double lo[3], hi[3];     /* box corners */
+  int order;               /* H1 order k, 1..4 (L2 order k-1) */
+  int quad_1d;             /* Gauss points per direction; 0 -> 2k (only 2k is supported) */
+  const double* rho0;      /* HOST array [NE] of initial densities, or NULL -> rho0_value */
+  const double* gamma;     /* HOST array [NE] of adiabatic indices, or NULL -> gamma_value */
+  double rho0_value;       /* default 1.0 */
+  double gamma_value;      /* default 1.4 */
+  unsigned bc_mask;        /* bit 2c+s: v_c = 0 on the face of axis c at low (s=0) / high
+                              (s=1) end; default all faces */
+  int visc;                /* smooth artificial viscosity mu_imp (Eq. (13)) on/off; default 1 */
+  double q1, q2, psi0;     /* Eq. (13), (17); defaults 0.5, 1.0, 0.5 */
+  double eps_e;            /* Eq. (19); default 1e-6 */
+  double h0;               /* Eq. (14) initial length scale; <= 0 -> (|Omega0| / NE)^(1/dim) */
+  double h_coarse;         /* Eq. (18) coarse length scale; <= 0 -> h0 */
+  int tg_source;           /* Taylor-Green manufactured energy source (dim 2); default 0 */
+  void* stream;            /* cudaStream_t for all work; NULL = legacy default stream */
+} lh_mesh_desc;
+
+/* Fill *desc with the defaults listed above (unit box, dim 3, 4^3 elements, order 2). */
+void lh_mesh_desc_init(lh_mesh_desc* desc);
+
+/* Create a mesh: builds the 1D bases and quadrature, copies materials to the device and
+ * allocates the mesh's work buffers (element scratch, reduction partials).  Memory owned
+ * by the mesh is released by lh_mesh_destroy.  Writes *out = NULL on failure. */
+lh_status lh_mesh_create(const lh_mesh_desc* desc, lh_mesh** out);
+lh_status lh_mesh_destroy(lh_mesh* mesh);
+
+/* Host array out[6] = { NE, N_V, N_E, n, NQ (quadrature points), dim }. */
+lh_status lh_sizes(const lh_mesh* mesh, long long* out);
+
+/* Change the stream used by all later calls on this mesh. */
+lh_status lh_set_stream(lh_mesh* mesh, void* stream);
+
+/* x0: device [dim*N_V]; writes the undeformed node positions of the box. */
+lh_status lh_initial_nodes(lh_mesh* mesh, double* x0);
+
+/* Stage residual R(k; tau, u) of Eq. (21).  u, k, r: device [n] double.  r may not alias
+ * u or k.  If min_detj (HOST pointer) is non-NULL the call synchronises and stores the
+ * minimum over quadrature points of det J at w (the line-search test of Sec. 3.5). */
+lh_status lh_residual(lh_mesh* mesh, const double* u, const double* k, double tau,
+                      double* r, double* min_detj);
+
+/* Jacobian action out = (dR/dk)(u, k; tau) dk of Eq. (22), matrix-free (paper Sec. 3.1,
+ * Eq. (10): transfers B, G unchanged, only the quadrature-point kernel differentiated).
+ * dk and out are device [n] arrays of double (LH_FP64) or float (LH_FP32); u and k are
+ * double.  With LH_FP32 the state is gathered and re-centred per element in double,
+ * then all arithmetic runs in float. */
+lh_status lh_jvp(lh_mesh* mesh, const double* u, const double* k, double tau,
+                 const void* dk, void* out, lh_prec prec);
+
+/* Transpose action out = (dR/dk)^T y (paper Sec. 3.1: transpose actions share the
+ * gather-apply-scatter structure).  LH_FP64 only; y, out device [n] double. */
+lh_status lh_jtvp(lh_mesh* mesh, const double* u, const double* k, double tau,
+                  const void* y, void* out, lh_prec prec);
+
+/* Mass matrices of Eq. (7) (constant in time since rho detJ = rho0 detJ0).
+ * which = 0: H1 mass M_V applied to each of the dim components, f/out device [dim*N_V];
+ * which = 1: L2 mass M_E (block diagonal), f/out device [N_E]. */
+lh_status lh_mass_apply(lh_mesh* mesh, int which, const double* f, double* out);
+
+/* Solve M z = rhs.  which = 0: M_V, Jacobi-preconditioned CG per component to relative
+ * tolerance rtol (maxit iterations); which = 1: M_E by the exact per-element inverse
+ * (rtol, maxit ignored).  *iters (HOST, may be NULL) receives the CG iterations used.
+ * Synchronises.  Returns LH_ENOCONV if CG stopped at maxit above tolerance. */
+lh_status lh_mass_solve(lh_mesh* mesh, int which, const double* rhs, double* sol,
+                        double rtol, int maxit, int* iters);
+
+/* Explicit time step estimate used to set "CFL multiple" time steps (reading: the
+ * paper's first-step CFL refers to an estimate it does not print):
+ *   dt = min_q h_min,q / (c_s,q + mu_q / (rho_q h_min,q)),  h_min,q = sigma_min(J_q) / k.
+ * u device [n]; *dt (HOST).  Synchronises. */
+lh_status lh_dt_estimate(lh_mesh* mesh, const double* u, double* dt);
+
+/* Kinetic 1/2 v^T M_V v and internal 1^T M_E e energies of state u (HOST outputs). */
+lh_status lh_energies(lh_mesh* mesh, const double* u, double* kinetic, double* internal);
+
+typedef struct {
+  double newton_rtol;      /* ||R|| <= rtol ||R^0|| stops; default 1e-10 */
+  double newton_atol;      /* ... or ||R|| <= atol; default 0 */
+  double gmres_rtol;       /* relative tolerance of each linear solve; default 1e-12 */
+  int newton_maxit;        /* default 20 */
+  int gmres_maxit;         /* total GMRES iterations per linear solve; default 60 */
+  int restart;             /* GMRES restart length (<= 64); default 30 */
+  int max_halvings;        /* line-search halvings of the Newton step; default 10 */
+  lh_prec jvp_prec;        /* precision of the J.w inside GMRES; default LH_FP64 */
+} lh_newton_opts;
+
+typedef struct {
+  int newton_its;          /* Newton iterations taken */
+  int gmres_its_total;     /* GMRES iterations over all linear solves */
+  int backtracks;          /* line-search halvings */
+  int residual_evals;      /* residual evaluations (incl. line-search trials) */
+  int jvp_evals;           /* Jacobian actions */
+  double r0, rfinal;       /* ||R|| at the initial guess and at exit */
+  double min_detj;         /* min det J at the accepted stage state */
+} lh_step_stats;
+
+void lh_newton_opts_init(lh_newton_opts* opts);
+
+/* One implicit midpoint step (paper Sec. 4.1, SD2): tau = dt/2, solve R(k; tau, u) = 0
+ * by inexact Newton-GMRES (right preconditioner diag(I, diag(M_V)^-1, M_E^-1), a
+ * stand-in for the block-diagonal AMG of Eq. (23)) with the det J line search of Sec.
+ * 3.5, then u <- u + dt k.  u: device [n] in/out.  k_prev: device [n] initial guess on
+ * entry and the converged k on exit, or NULL (zero initial guess).  Synchronises.
+ * On LH_ENOCONV / LH_ETANGLED / LH_ENONFINITE u and k_prev are left unchanged. */
+lh_status lh_newton_step(lh_mesh* mesh, double* u, double* k_prev, double dt,
+                         const lh_newton_opts* opts, lh_step_stats* stats);
+
+/* Message for the last failing call on mesh (or a global message if mesh is NULL). */
+const char* lh_last_error(const lh_mesh* mesh);
+
+/* Measurement helper: throughput (TFLOP/s, HOST *tflops) of independent FMA chains on
+ * every SM of the current device; prec LH_FP64 or LH_FP32.  Used as the roofline
+ * denominator of FP64/FP32-pipe-bound kernels.  Synchronises the device. */
+lh_status lh_probe_fma(int prec, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LH_H */

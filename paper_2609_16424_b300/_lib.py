@@ -1,0 +1,70 @@
+"""ctypes declarations of the C ABI in include/lh.h (argument marshalling only)."""
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblh.so")
+
+LH_OK, LH_EINVAL, LH_ECUDA, LH_ENOMEM, LH_ETANGLED, LH_ENOCONV, LH_ENONFINITE = range(7)
+LH_FP64, LH_FP32 = 0, 1
+STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "LH_ETANGLED",
+                5: "LH_ENOCONV", 6: "LH_ENONFINITE"}
+
+# every symbol include/lh.h declares
+SYMBOLS = ["lh_mesh_desc_init", "lh_mesh_create", "lh_mesh_destroy", "lh_sizes", "lh_set_stream",
+           "lh_initial_nodes", "lh_residual", "lh_jvp", "lh_jtvp", "lh_mass_apply", "lh_mass_solve",
+           "lh_dt_estimate", "lh_energies", "lh_newton_opts_init", "lh_newton_step", "lh_last_error",
+           "lh_probe_fma"]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("order", C.c_int), ("quad_1d", C.c_int),
+                ("rho0", C.POINTER(C.c_double)), ("gamma", C.POINTER(C.c_double)),
+                ("rho0_value", C.c_double), ("gamma_value", C.c_double), ("bc_mask", C.c_uint),
+                ("visc", C.c_int), ("q1", C.c_double), ("q2", C.c_double), ("psi0", C.c_double),
+                ("eps_e", C.c_double), ("h0", C.c_double), ("h_coarse", C.c_double),
+                ("tg_source", C.c_int), ("stream", C.c_void_p)]
+
+
+class NewtonOpts(C.Structure):
+    _fields_ = [("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("gmres_rtol", C.c_double),
+                ("newton_maxit", C.c_int), ("gmres_maxit", C.c_int), ("restart", C.c_int),
+                ("max_halvings", C.c_int), ("jvp_prec", C.c_int)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("newton_its", C.c_int), ("gmres_its_total", C.c_int), ("backtracks", C.c_int),
+                ("residual_evals", C.c_int), ("jvp_evals", C.c_int), ("r0", C.c_double),
+                ("rfinal", C.c_double), ("min_detj", C.c_double)]
+
+
+def load(path=LIB_PATH):
+    """Load liblh.so and declare the signatures.  Raises OSError if it is missing."""
+    lib = C.CDLL(path)
+    vp, dp, ip, llp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_longlong)
+    i, d = C.c_int, C.c_double
+    sig = {
+        "lh_mesh_desc_init": (None, [C.POINTER(MeshDesc)]),
+        "lh_mesh_create": (i, [C.POINTER(MeshDesc), C.POINTER(vp)]),
+        "lh_mesh_destroy": (i, [vp]),
+        "lh_sizes": (i, [vp, llp]),
+        "lh_set_stream": (i, [vp, vp]),
+        "lh_initial_nodes": (i, [vp, vp]),
+        "lh_residual": (i, [vp, vp, vp, d, vp, dp]),
+        "lh_jvp": (i, [vp, vp, vp, d, vp, vp, i]),
+        "lh_jtvp": (i, [vp, vp, vp, d, vp, vp, i]),
+        "lh_mass_apply": (i, [vp, i, vp, vp]),
+        "lh_mass_solve": (i, [vp, i, vp, vp, d, i, ip]),
+        "lh_dt_estimate": (i, [vp, vp, dp]),
+        "lh_energies": (i, [vp, vp, dp, dp]),
+        "lh_newton_opts_init": (None, [C.POINTER(NewtonOpts)]),
+        "lh_newton_step": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(StepStats)]),
+        "lh_last_error": (C.c_char_p, [vp]),
+        "lh_probe_fma": (i, [i, dp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib

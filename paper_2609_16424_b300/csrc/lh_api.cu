@@ -1,0 +1,626 @@
+// C ABI of the library (include/lh.h): mesh set-up, operator calls, mass solves and the
+// Newton-GMRES implicit midpoint step (paper Sec. 3.5 and Sec. 4.1).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+#include "lh_internal.h"
+#include "lh_kernels.h"
+
+using namespace lh;
+
+namespace {
+
+std::string g_err;   // message for failures that have no mesh
+
+lh_status fail(lh_mesh* m, lh_status st, const std::string& msg) {
+  if (m) m->err = msg; else g_err = msg;
+  return st;
+}
+
+#define LH_CK(m, call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e__ = (call);                                                              \
+    if (e__ != cudaSuccess)                                                                \
+      return fail(m, LH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__));      \
+  } while (0)
+
+// ---- 1D rules and bases on [0, 1] (host, double) -------------------------------------
+// Legendre P_n and P_n' at x in [-1, 1] by the three-term recurrence.
+void legendre(int n, double x, double& p, double& dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) { p = 1.0; dp = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  p = p1;
+  dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+// n-point Gauss-Legendre on [0, 1]: roots of P_n by Newton from Chebyshev-like guesses
+void gauss(int n, std::vector<double>& z, std::vector<double>& w) {
+  z.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double x = -std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(n, x, p, dp);
+      const double dx = p / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-17) break;
+    }
+    double p, dp;
+    legendre(n, x, p, dp);
+    z[i] = 0.5 * (x + 1.0);
+    w[i] = 1.0 / ((1.0 - x * x) * dp * dp);     // 2 / ((1-x^2) P'^2) scaled by 1/2
+  }
+}
+
+// n-point Gauss-Lobatto on [0, 1]: end points and the roots of P'_{n-1}, found by Newton
+// on P'_{n-1} with P''_{n-1} from Legendre's equation
+void lobatto(int n, std::vector<double>& z) {
+  z.assign(n, 0.0);
+  const int m = n - 1;
+  z[0] = 0.0;
+  z[n - 1] = 1.0;
+  for (int i = 1; i < n - 1; ++i) {
+    double x = -std::cos(M_PI * i / m);
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(m, x, p, dp);
+      const double ddp = (2.0 * x * dp - m * (m + 1.0) * p) / (1.0 - x * x);
+      const double dx = dp / ddp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-17) break;
+    }
+    z[i] = 0.5 * (x + 1.0);
+  }
+}
+
+double lagr(const std::vector<double>& z, int j, double t) {
+  double v = 1.0;
+  for (size_t l = 0; l < z.size(); ++l)
+    if ((int)l != j) v *= (t - z[l]) / (z[j] - z[l]);
+  return v;
+}
+
+double lagr_d(const std::vector<double>& z, int j, double t) {
+  double s = 0.0;
+  for (size_t l = 0; l < z.size(); ++l) {
+    if ((int)l == j) continue;
+    double v = 1.0 / (z[j] - z[l]);
+    for (size_t i = 0; i < z.size(); ++i)
+      if ((int)i != j && i != l) v *= (t - z[i]) / (z[j] - z[i]);
+    s += v;
+  }
+  return s;
+}
+
+// device table: [B (QxD) | G (QxD) | Bl (QxL) | w (Q) | zh (D) | zl (L)]
+std::vector<double> build_tables(int K) {
+  const int D = K + 1, L = K, Q = 2 * K;
+  std::vector<double> zq, wq, zh, zl, wl;
+  gauss(Q, zq, wq);
+  lobatto(D, zh);
+  gauss(L, zl, wl);
+  std::vector<double> t;
+  for (int q = 0; q < Q; ++q)
+    for (int a = 0; a < D; ++a) t.push_back(lagr(zh, a, zq[q]));
+  for (int q = 0; q < Q; ++q)
+    for (int a = 0; a < D; ++a) t.push_back(lagr_d(zh, a, zq[q]));
+  for (int q = 0; q < Q; ++q)
+    for (int j = 0; j < L; ++j) t.push_back(lagr(zl, j, zq[q]));
+  for (int q = 0; q < Q; ++q) t.push_back(wq[q]);
+  for (int a = 0; a < D; ++a) t.push_back(zh[a]);
+  for (int j = 0; j < L; ++j) t.push_back(zl[j]);
+  return t;
+}
+
+lh_status ensure_work(lh_mesh* m, int restart) {
+  const long long n = m->n;
+  const long long need = (long long)(restart + 1) * n + 8 * n;
+  if (m->d_work && m->work_len >= need) return LH_OK;
+  if (m->d_work) cudaFree(m->d_work);
+  if (m->d_fwork) cudaFree(m->d_fwork);
+  m->d_work = nullptr;
+  m->d_fwork = nullptr;
+  if (cudaMalloc(&m->d_work, sizeof(double) * need) != cudaSuccess)
+    return fail(m, LH_ENOMEM, "cannot allocate Newton-GMRES workspace");
+  if (cudaMalloc(&m->d_fwork, sizeof(float) * 2 * n) != cudaSuccess)
+    return fail(m, LH_ENOMEM, "cannot allocate FP32 workspace");
+  m->work_len = need;
+  m->restart_alloc = restart;
+  return LH_OK;
+}
+
+// ||x||_2^2 into a host double (synchronises)
+lh_status dot_host(lh_mesh* m, const double* a, const double* b, long long n, double* out) {
+  LH_CK(m, launch_mdot(m->stream, a, 1, 0, b, n, m->d_part, m->d_scalar));
+  LH_CK(m, cudaMemcpyAsync(out, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  return LH_OK;
+}
+
+lh_status apply_jvp(lh_mesh* m, const double* u, const double* k, double tau, const double* z, double* w,
+                    lh_prec prec) {
+  if (prec == LH_FP32) {
+    float* fz = m->d_fwork;
+    float* fw = m->d_fwork + m->n;
+    LH_CK(m, launch_to_f32(m->stream, z, fz, m->n));
+    LH_CK(m, launch_jvp_f32(m->P, m->stream, u, k, tau, fz, reinterpret_cast<float*>(m->d_ev), fw));
+    LH_CK(m, launch_to_f64(m->stream, fw, w, m->n));
+  } else {
+    LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, w));
+  }
+  return LH_OK;
+}
+
+// residual + min detJ (host) in one call
+lh_status residual_min(lh_mesh* m, const double* u, const double* k, double tau, double* r, double* mindet) {
+  LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r));
+  LH_CK(m, launch_min(m->stream, m->d_blockmin, m->nblocks_elem, m->d_scalar + 1));
+  LH_CK(m, cudaMemcpyAsync(mindet, m->d_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  return LH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lh_mesh_desc_init(lh_mesh_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->dim = 3;
+  d->n[0] = d->n[1] = d->n[2] = 4;
+  d->hi[0] = d->hi[1] = d->hi[2] = 1.0;
+  d->order = 2;
+  d->rho0_value = 1.0;
+  d->gamma_value = 1.4;
+  d->bc_mask = 0x3f;
+  d->visc = 1;
+  d->q1 = 0.5;
+  d->q2 = 1.0;
+  d->psi0 = 0.5;
+  d->eps_e = 1e-6;
+}
+
+void lh_newton_opts_init(lh_newton_opts* o) {
+  if (!o) return;
+  o->newton_rtol = 1e-10;
+  o->newton_atol = 0.0;
+  o->gmres_rtol = 1e-12;
+  o->newton_maxit = 20;
+  o->gmres_maxit = 60;
+  o->restart = 30;
+  o->max_halvings = 10;
+  o->jvp_prec = LH_FP64;
+}
+
+lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
+  if (!out) return fail(nullptr, LH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(nullptr, LH_EINVAL, "desc is NULL");
+  if (d->dim != 2 && d->dim != 3) return fail(nullptr, LH_EINVAL, "dim must be 2 or 3");
+  if (d->order < 1 || d->order > 4) return fail(nullptr, LH_EINVAL, "order must be in 1..4");
+  if (d->quad_1d != 0 && d->quad_1d != 2 * d->order)
+    return fail(nullptr, LH_EINVAL, "only 2k Gauss points per direction are supported");
+  for (int c = 0; c < d->dim; ++c) {
+    if (d->n[c] < 1) return fail(nullptr, LH_EINVAL, "element counts must be >= 1");
+    if (!(d->hi[c] > d->lo[c])) return fail(nullptr, LH_EINVAL, "box must have hi > lo");
+  }
+  if (d->visc && !(d->psi0 > 0.0 && d->psi0 < 1.0)) return fail(nullptr, LH_EINVAL, "psi0 must be in (0, 1)");
+  if (!(d->eps_e > 0.0)) return fail(nullptr, LH_EINVAL, "eps_e must be > 0");
+  if (d->tg_source && d->dim != 2) return fail(nullptr, LH_EINVAL, "the Taylor-Green source is 2D");
+
+  lh_mesh* m = new (std::nothrow) lh_mesh();
+  if (!m) return fail(nullptr, LH_ENOMEM, "host allocation failed");
+  m->desc = *d;
+  m->stream = reinterpret_cast<cudaStream_t>(d->stream);
+  ElemParams& P = m->P;
+  const int dim = d->dim, K = d->order;
+  P.dim = dim;
+  P.K = K;
+  P.n0 = d->n[0];
+  P.n1 = d->n[1];
+  P.n2 = dim == 3 ? d->n[2] : 1;
+  P.N0 = K * P.n0 + 1;
+  P.N1 = K * P.n1 + 1;
+  P.N2 = dim == 3 ? K * P.n2 + 1 : 1;
+  P.NE = (long long)P.n0 * P.n1 * P.n2;
+  P.NV = (long long)P.N0 * P.N1 * P.N2;
+  long long nl = 1, nd = 1, nq = 1;
+  for (int c = 0; c < dim; ++c) {
+    nl *= K;
+    nd *= K + 1;
+    nq *= 2 * K;
+  }
+  P.NEd = P.NE * nl;
+  double vol = 1.0;
+  P.detJ0 = 1.0;
+  for (int c = 0; c < 3; ++c) {
+    P.lo[c] = c < dim ? d->lo[c] : 0.0;
+    P.h[c] = c < dim ? (d->hi[c] - d->lo[c]) / d->n[c] : 1.0;
+    if (c < dim) {
+      vol *= d->hi[c] - d->lo[c];
+      P.detJ0 *= P.h[c];
+    }
+  }
+  P.h0 = d->h0 > 0 ? d->h0 : std::pow(vol / (double)P.NE, 1.0 / dim);
+  P.inv_hc = 1.0 / (d->h_coarse > 0 ? d->h_coarse : P.h0);
+  P.q1 = d->q1;
+  P.q2 = d->q2;
+  P.scoef = 2.0 * std::atanh(1.0 - 2.0 * d->psi0);
+  P.eps2 = d->eps_e * d->eps_e;
+  P.visc = d->visc;
+  P.tg = d->tg_source;
+  P.bc = d->bc_mask;
+  m->n = 2LL * dim * P.NV + P.NEd;
+  m->NQ = P.NE * nq;
+
+  std::vector<double> rho(P.NE), gam(P.NE);
+  for (long long e = 0; e < P.NE; ++e) {
+    rho[e] = d->rho0 ? d->rho0[e] : d->rho0_value;
+    gam[e] = d->gamma ? d->gamma[e] : d->gamma_value;
+    if (!(rho[e] > 0.0) || !(gam[e] > 1.0)) {
+      delete m;
+      return fail(nullptr, LH_EINVAL, "rho0 must be > 0 and gamma > 1");
+    }
+  }
+  const std::vector<double> tab = build_tables(K);
+  m->nblocks_elem = elem_grid(P);
+  const long long evn = P.NE * 2 * dim * nd;
+  bool ok = cudaMalloc(&m->d_rho0, sizeof(double) * P.NE) == cudaSuccess &&
+            cudaMalloc(&m->d_gamma, sizeof(double) * P.NE) == cudaSuccess &&
+            cudaMalloc(&m->d_tab, sizeof(double) * tab.size()) == cudaSuccess &&
+            cudaMalloc(&m->d_ev, sizeof(double) * evn) == cudaSuccess &&
+            cudaMalloc(&m->d_part, sizeof(double) * kRedBlocks * 72) == cudaSuccess &&
+            cudaMalloc(&m->d_scalar, sizeof(double) * 256) == cudaSuccess &&
+            cudaMalloc(&m->d_diagMv, sizeof(double) * P.NV) == cudaSuccess &&
+            cudaMalloc(&m->d_invMe, sizeof(double) * P.NEd) == cudaSuccess &&
+            cudaMalloc(&m->d_blockmin, sizeof(double) * (m->nblocks_elem + 1)) == cudaSuccess;
+  if (!ok) {
+    lh_mesh_destroy(m);
+    return fail(nullptr, LH_ENOMEM, "device allocation failed in lh_mesh_create");
+  }
+  P.rho0 = m->d_rho0;
+  P.gamma = m->d_gamma;
+  P.tab = m->d_tab;
+  cudaError_t e = cudaMemcpyAsync(m->d_rho0, rho.data(), sizeof(double) * P.NE, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_gamma, gam.data(), sizeof(double) * P.NE, cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = launch_setup(P, m->stream, m->d_ev, m->d_diagMv, m->d_invMe);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) {
+    lh_mesh_destroy(m);
+    return fail(nullptr, LH_ECUDA, std::string("lh_mesh_create: ") + cudaGetErrorString(e));
+  }
+  *out = m;
+  return LH_OK;
+}
+
+lh_status lh_mesh_destroy(lh_mesh* m) {
+  if (!m) return LH_OK;
+  double* bufs[] = {m->d_rho0, m->d_gamma, m->d_tab, m->d_ev, m->d_part, m->d_scalar,
+                    m->d_diagMv, m->d_invMe, m->d_blockmin, m->d_work};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  if (m->d_fwork) cudaFree(m->d_fwork);
+  delete m;
+  return LH_OK;
+}
+
+lh_status lh_sizes(const lh_mesh* m, long long* out) {
+  if (!m || !out) return fail(nullptr, LH_EINVAL, "NULL argument to lh_sizes");
+  out[0] = m->P.NE;
+  out[1] = m->P.NV;
+  out[2] = m->P.NEd;
+  out[3] = m->n;
+  out[4] = m->NQ;
+  out[5] = m->P.dim;
+  return LH_OK;
+}
+
+lh_status lh_set_stream(lh_mesh* m, void* stream) {
+  if (!m) return fail(nullptr, LH_EINVAL, "mesh is NULL");
+  m->stream = reinterpret_cast<cudaStream_t>(stream);
+  return LH_OK;
+}
+
+lh_status lh_initial_nodes(lh_mesh* m, double* x0) {
+  if (!m || !x0) return fail(m, LH_EINVAL, "NULL argument to lh_initial_nodes");
+  LH_CK(m, launch_initial_nodes(m->P, m->stream, x0));
+  return LH_OK;
+}
+
+lh_status lh_residual(lh_mesh* m, const double* u, const double* k, double tau, double* r, double* min_detj) {
+  if (!m || !u || !k || !r) return fail(m, LH_EINVAL, "NULL argument to lh_residual");
+  if (r == u || r == k) return fail(m, LH_EINVAL, "r must not alias u or k");
+  if (min_detj) return residual_min(m, u, k, tau, r, min_detj);
+  LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r));
+  return LH_OK;
+}
+
+lh_status lh_jvp(lh_mesh* m, const double* u, const double* k, double tau, const void* dk, void* out,
+                 lh_prec prec) {
+  if (!m || !u || !k || !dk || !out) return fail(m, LH_EINVAL, "NULL argument to lh_jvp");
+  if (dk == out) return fail(m, LH_EINVAL, "out must not alias dk");
+  if (prec == LH_FP64) {
+    LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, static_cast<const double*>(dk), m->d_ev,
+                            static_cast<double*>(out)));
+  } else if (prec == LH_FP32) {
+    LH_CK(m, launch_jvp_f32(m->P, m->stream, u, k, tau, static_cast<const float*>(dk),
+                            reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out)));
+  } else {
+    return fail(m, LH_EINVAL, "lh_jvp: unsupported precision");
+  }
+  return LH_OK;
+}
+
+lh_status lh_jtvp(lh_mesh* m, const double* u, const double* k, double tau, const void* y, void* out,
+                  lh_prec prec) {
+  if (!m || !u || !k || !y || !out) return fail(m, LH_EINVAL, "NULL argument to lh_jtvp");
+  if (prec != LH_FP64) return fail(m, LH_EINVAL, "lh_jtvp supports LH_FP64 only");
+  if (y == out) return fail(m, LH_EINVAL, "out must not alias y");
+  LH_CK(m, launch_jtvp(m->P, m->stream, u, k, tau, static_cast<const double*>(y), m->d_ev,
+                       static_cast<double*>(out)));
+  return LH_OK;
+}
+
+lh_status lh_mass_apply(lh_mesh* m, int which, const double* f, double* out) {
+  if (!m || !f || !out) return fail(m, LH_EINVAL, "NULL argument to lh_mass_apply");
+  if (which == 0) {
+    LH_CK(m, launch_mass_h1(m->P, m->stream, f, m->d_ev, out));
+  } else if (which == 1) {
+    LH_CK(m, launch_mass_l2(m->P, m->stream, f, out));
+  } else {
+    return fail(m, LH_EINVAL, "which must be 0 (H1) or 1 (L2)");
+  }
+  return LH_OK;
+}
+
+lh_status lh_mass_solve(lh_mesh* m, int which, const double* rhs, double* sol, double rtol, int maxit,
+                        int* iters) {
+  if (!m || !rhs || !sol) return fail(m, LH_EINVAL, "NULL argument to lh_mass_solve");
+  if (iters) *iters = 0;
+  if (which == 1) {
+    LH_CK(m, launch_mul(m->stream, rhs, m->d_invMe, sol, m->P.NEd));
+    LH_CK(m, cudaStreamSynchronize(m->stream));
+    return LH_OK;
+  }
+  if (which != 0) return fail(m, LH_EINVAL, "which must be 0 (H1) or 1 (L2)");
+  lh_status st = ensure_work(m, m->restart_alloc > 0 ? m->restart_alloc : 30);
+  if (st != LH_OK) return st;
+  const long long n = (long long)m->P.dim * m->P.NV;
+  double* r = m->d_work;
+  double* z = r + n;
+  double* p = z + n;
+  double* Ap = p + n;
+  LH_CK(m, cudaMemsetAsync(sol, 0, sizeof(double) * n, m->stream));
+  LH_CK(m, cudaMemcpyAsync(r, rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+  LH_CK(m, launch_jacobi_h1(m->stream, m->P.NV, m->P.dim, m->d_diagMv, r, z));
+  LH_CK(m, cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->stream));
+  double rz, bb, pAp, rr;
+  if ((st = dot_host(m, r, z, n, &rz)) != LH_OK) return st;
+  if ((st = dot_host(m, r, r, n, &bb)) != LH_OK) return st;
+  if (bb == 0.0) return LH_OK;
+  int it = 0;
+  bool conv = false;
+  for (; it < maxit; ++it) {
+    LH_CK(m, launch_mass_h1(m->P, m->stream, p, m->d_ev, Ap));
+    if ((st = dot_host(m, p, Ap, n, &pAp)) != LH_OK) return st;
+    const double alpha = rz / pAp;
+    LH_CK(m, launch_axpby(m->stream, alpha, p, 1.0, sol, n));
+    LH_CK(m, launch_axpby(m->stream, -alpha, Ap, 1.0, r, n));
+    if ((st = dot_host(m, r, r, n, &rr)) != LH_OK) return st;
+    if (std::sqrt(rr) <= rtol * std::sqrt(bb)) {
+      conv = true;
+      ++it;
+      break;
+    }
+    LH_CK(m, launch_jacobi_h1(m->stream, m->P.NV, m->P.dim, m->d_diagMv, r, z));
+    double rz_new;
+    if ((st = dot_host(m, r, z, n, &rz_new)) != LH_OK) return st;
+    LH_CK(m, launch_axpby(m->stream, 1.0, z, rz_new / rz, p, n));
+    rz = rz_new;
+  }
+  if (iters) *iters = it;
+  return conv ? LH_OK : fail(m, LH_ENOCONV, "lh_mass_solve: CG reached maxit");
+}
+
+lh_status lh_dt_estimate(lh_mesh* m, const double* u, double* dt) {
+  if (!m || !u || !dt) return fail(m, LH_EINVAL, "NULL argument to lh_dt_estimate");
+  LH_CK(m, launch_dt_estimate(m->P, m->stream, u, m->d_blockmin));
+  LH_CK(m, launch_min(m->stream, m->d_blockmin, m->nblocks_elem, m->d_scalar + 2));
+  LH_CK(m, cudaMemcpyAsync(dt, m->d_scalar + 2, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  return LH_OK;
+}
+
+lh_status lh_energies(lh_mesh* m, const double* u, double* kinetic, double* internal) {
+  if (!m || !u || !kinetic || !internal) return fail(m, LH_EINVAL, "NULL argument to lh_energies");
+  lh_status st = ensure_work(m, m->restart_alloc > 0 ? m->restart_alloc : 30);
+  if (st != LH_OK) return st;
+  const long long n1 = (long long)m->P.dim * m->P.NV;
+  double* t = m->d_work;
+  LH_CK(m, launch_mass_h1(m->P, m->stream, u + n1, m->d_ev, t));
+  double kv;
+  if ((st = dot_host(m, u + n1, t, n1, &kv)) != LH_OK) return st;
+  *kinetic = 0.5 * kv;
+  LH_CK(m, launch_mass_l2(m->P, m->stream, u + 2 * n1, t));
+  LH_CK(m, launch_mdot(m->stream, t, 1, 0, nullptr, m->P.NEd, m->d_part, m->d_scalar));
+  LH_CK(m, cudaMemcpyAsync(internal, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  return LH_OK;
+}
+
+lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const lh_newton_opts* opts_in,
+                         lh_step_stats* stats) {
+  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_newton_step");
+  lh_newton_opts o;
+  if (opts_in) o = *opts_in; else lh_newton_opts_init(&o);
+  if (o.restart < 1 || o.restart > 64) return fail(m, LH_EINVAL, "restart must be in 1..64");
+  if (o.jvp_prec != LH_FP64 && o.jvp_prec != LH_FP32) return fail(m, LH_EINVAL, "unsupported jvp_prec");
+  if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
+  lh_status st = ensure_work(m, o.restart);
+  if (st != LH_OK) return st;
+  lh_step_stats S;
+  std::memset(&S, 0, sizeof(S));
+  const long long n = m->n;
+  const int mres = o.restart;
+  cudaStream_t s = m->stream;
+  double* V = m->d_work;                      // (mres + 1) x n Krylov basis
+  double* k = V + (long long)(mres + 1) * n;  // Newton iterate
+  double* r = k + n;                          // residual at k
+  double* dk = r + n;                         // Newton correction
+  double* z = dk + n;                         // preconditioned vector
+  double* w = z + n;                          // operator output
+  double* kt = w + n;                         // trial iterate
+  double* rt = kt + n;                        // residual at the trial
+  double* dh = m->d_scalar + 8;               // device Hessenberg column (2 x 64 + 1)
+  const double tau = 0.5 * dt;
+
+  if (k_prev) {
+    LH_CK(m, cudaMemcpyAsync(k, k_prev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
+  }
+  double mind, nr2;
+  if ((st = residual_min(m, u, k, tau, r, &mind)) != LH_OK) return st;
+  ++S.residual_evals;
+  if (!(mind > 0.0) && k_prev) {   // a tangled initial guess: restart from k = 0
+    LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
+    if ((st = residual_min(m, u, k, tau, r, &mind)) != LH_OK) return st;
+    ++S.residual_evals;
+  }
+  if (!(mind > 0.0)) return fail(m, LH_ETANGLED, "lh_newton_step: det J <= 0 at the initial guess");
+  if ((st = dot_host(m, r, r, n, &nr2)) != LH_OK) return st;
+  double nr = std::sqrt(nr2);
+  if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite residual");
+  S.r0 = nr;
+  bool conv = nr <= std::fmax(o.newton_rtol * S.r0, o.newton_atol);
+  std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), g(mres + 1), hcol(2 * 64 + 2);
+  for (int it = 0; it < o.newton_maxit && !conv; ++it) {
+    // ---- GMRES(m), right preconditioned, on J dk = -r, dk0 = 0
+    LH_CK(m, cudaMemsetAsync(dk, 0, sizeof(double) * n, s));
+    double beta = nr, beta0 = nr;
+    LH_CK(m, launch_axpby(s, -1.0 / beta, r, 0.0, V, n));
+    int total = 0;
+    bool lin_done = false;
+    while (!lin_done) {
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int j = 0;
+      for (; j < mres && total < o.gmres_maxit; ++j) {
+        double* vj = V + (long long)j * n;
+        LH_CK(m, launch_precond(s, m->P, m->d_diagMv, m->d_invMe, vj, z));
+        if ((st = apply_jvp(m, u, k, tau, z, w, o.jvp_prec)) != LH_OK) return st;
+        ++S.jvp_evals;
+        // classical Gram-Schmidt, twice
+        LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, m->d_part, dh));
+        LH_CK(m, launch_gemv_sub(s, V, j + 1, n, dh, w, n));
+        LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, m->d_part, dh + 64));
+        LH_CK(m, launch_gemv_sub(s, V, j + 1, n, dh + 64, w, n));
+        LH_CK(m, launch_mdot(s, w, 1, 0, w, n, m->d_part, dh + 128));
+        LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * 129, cudaMemcpyDeviceToHost, s));
+        LH_CK(m, cudaStreamSynchronize(s));
+        const double hn = std::sqrt(hcol[128]);
+        for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = hcol[i] + hcol[64 + i];
+        H[(size_t)(j + 1) * mres + j] = hn;
+        if (hn > 0.0) LH_CK(m, launch_axpby(s, 1.0 / hn, w, 0.0, V + (long long)(j + 1) * n, n));
+        for (int i = 0; i < j; ++i) {   // previous Givens rotations
+          const double a = H[(size_t)i * mres + j], b = H[(size_t)(i + 1) * mres + j];
+          H[(size_t)i * mres + j] = cs[i] * a + sn[i] * b;
+          H[(size_t)(i + 1) * mres + j] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = H[(size_t)j * mres + j], b = H[(size_t)(j + 1) * mres + j];
+        const double rad = std::hypot(a, b);
+        cs[j] = rad > 0 ? a / rad : 1.0;
+        sn[j] = rad > 0 ? b / rad : 0.0;
+        H[(size_t)j * mres + j] = rad;
+        H[(size_t)(j + 1) * mres + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        ++total;
+        if (std::fabs(g[j + 1]) <= o.gmres_rtol * beta0 || hn == 0.0) {
+          ++j;
+          lin_done = true;
+          break;
+        }
+      }
+      // y = H^-1 g (upper triangular j x j), dk += P^-1 V y
+      std::vector<double> y(j);
+      for (int i = j - 1; i >= 0; --i) {
+        double sum = g[i];
+        for (int l = i + 1; l < j; ++l) sum -= H[(size_t)i * mres + l] * y[l];
+        y[i] = sum / H[(size_t)i * mres + i];
+      }
+      LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+      LH_CK(m, launch_gemv(s, V, j, n, dh, 0.0, w, n));
+      LH_CK(m, launch_precond(s, m->P, m->d_diagMv, m->d_invMe, w, z));
+      LH_CK(m, launch_axpby(s, 1.0, z, 1.0, dk, n));
+      if (lin_done || total >= o.gmres_maxit) break;
+      // restart: r_lin = -r - J dk
+      if ((st = apply_jvp(m, u, k, tau, dk, w, o.jvp_prec)) != LH_OK) return st;
+      ++S.jvp_evals;
+      LH_CK(m, launch_axpby(s, -1.0, r, -1.0, w, n));   // w = -r - J dk
+      double b2;
+      if ((st = dot_host(m, w, w, n, &b2)) != LH_OK) return st;
+      beta = std::sqrt(b2);
+      if (beta <= o.gmres_rtol * beta0) break;
+      LH_CK(m, launch_axpby(s, 1.0 / beta, w, 0.0, V, n));
+    }
+    S.gmres_its_total += total;
+    // ---- backtracking line search on det J > 0 (Sec. 3.5)
+    double lam = 1.0;
+    bool accepted = false;
+    for (int hlv = 0; hlv <= o.max_halvings; ++hlv) {
+      LH_CK(m, cudaMemcpyAsync(kt, k, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      LH_CK(m, launch_axpby(s, lam, dk, 1.0, kt, n));
+      if ((st = residual_min(m, u, kt, tau, rt, &mind)) != LH_OK) return st;
+      ++S.residual_evals;
+      if (mind > 0.0) {
+        accepted = true;
+        break;
+      }
+      lam *= 0.5;
+      ++S.backtracks;
+    }
+    if (!accepted) return fail(m, LH_ETANGLED, "lh_newton_step: line search could not keep det J > 0");
+    std::swap(k, kt);
+    std::swap(r, rt);
+    if ((st = dot_host(m, r, r, n, &nr2)) != LH_OK) return st;
+    nr = std::sqrt(nr2);
+    if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite residual");
+    S.min_detj = mind;
+    ++S.newton_its;
+    conv = nr <= std::fmax(o.newton_rtol * S.r0, o.newton_atol);
+  }
+  S.rfinal = nr;
+  if (S.min_detj == 0.0) S.min_detj = mind;
+  if (stats) *stats = S;
+  if (!conv) return fail(m, LH_ENOCONV, "lh_newton_step: Newton did not converge");
+  LH_CK(m, launch_axpby(s, dt, k, 1.0, u, n));
+  if (k_prev) LH_CK(m, cudaMemcpyAsync(k_prev, k, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  LH_CK(m, cudaStreamSynchronize(s));
+  return LH_OK;
+}
+
+const char* lh_last_error(const lh_mesh* m) { return m ? m->err.c_str() : g_err.c_str(); }
+
+lh_status lh_probe_fma(int prec, double* tflops) {
+  if (!tflops) return fail(nullptr, LH_EINVAL, "tflops is NULL");
+  if (prec != LH_FP64 && prec != LH_FP32) return fail(nullptr, LH_EINVAL, "prec must be LH_FP64 or LH_FP32");
+  cudaError_t e = launch_probe_fma(prec, tflops);
+  if (e != cudaSuccess) return fail(nullptr, LH_ECUDA, std::string("lh_probe_fma: ") + cudaGetErrorString(e));
+  return LH_OK;
+}
+
+}  // extern "C"

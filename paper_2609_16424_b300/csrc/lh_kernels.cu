@@ -1,0 +1,915 @@
+// Element kernels (residual, tangent, adjoint, mass) and node-centric H1 assembly.
+//
+// Operator decomposition of paper Sec. 2.2, Eq. (8), A = P^T G^T B^T D B G P, with P = I
+// on one GPU.  Element kernels fuse G (gather from the node lattice by index arithmetic),
+// B (sum-factorised contractions, lh_contract.cuh), D (quadrature-point kernel, lh_qp.cuh)
+// and B^T; they write element vectors of the H1 rows to a scratch buffer and L2 rows
+// (element-local, G = I) directly.  G^T is a separate node-centric kernel that sums the
+// up to 2^dim element contributions of each node in a fixed order (deterministic, no
+// atomics).
+#include <cfloat>
+#include "lh_internal.h"
+#include "lh_kernels.h"
+#include "lh_qp.cuh"
+#include "lh_contract.cuh"
+
+namespace lh {
+
+// ---- 1D table layout in the device table buffer (built by the host at mesh creation)
+template <int K>
+struct Tab {
+  static constexpr int D = K + 1, L = K, Q = 2 * K;
+  static constexpr int B = 0, G = Q * D, BL = 2 * Q * D, W = 2 * Q * D + Q * L;
+  static constexpr int SMEM = 2 * Q * D + Q * L + Q;           // entries staged in shared memory
+};
+
+// Per-element shared-memory plan (units of T).
+template <int DIM, int K, int NCH, int NCV, int NCL, int NCO>
+struct Plan {
+  using C = Cfg<DIM, K>;
+  using SC = H1Scratch<DIM, K, NCH>;
+  static constexpr int IN = NCH * C::ND + NCV * C::ND + NCL * C::NL;
+  static constexpr int T1 = SC::T1;
+  static constexpr int T2 = SC::T2;
+  static constexpr int SF = (DIM + 1) * (NCO > 1 ? NCO : 1) * C::NQ;
+  static constexpr int PER = IN + T1 + T2 + SF;
+  static constexpr int HEAD = ((Tab<K>::SMEM + C::THREADS + 1) / 2) * 2;   // tables + reduction
+  static constexpr size_t bytes(size_t szT) { return szT * (size_t)(HEAD + C::EPB * PER); }
+};
+
+struct ElemIdx {
+  long long e;
+  int ex, ey, ez;
+  bool valid;
+};
+
+template <int DIM, int K>
+__device__ __forceinline__ ElemIdx elem_index(const ElemParams& P) {
+  using C = Cfg<DIM, K>;
+  ElemIdx r;
+  const int eb = threadIdx.x / C::NQ;
+  r.e = (long long)blockIdx.x * C::EPB + eb;
+  r.valid = r.e < P.NE;
+  const long long e = r.valid ? r.e : 0;
+  r.ex = (int)(e % P.n0);
+  r.ey = (int)((e / P.n0) % P.n1);
+  r.ez = DIM == 3 ? (int)(e / ((long long)P.n0 * P.n1)) : 0;
+  return r;
+}
+
+// global lattice node of local H1 node a of element (ex, ey, ez)
+template <int DIM, int K>
+__device__ __forceinline__ long long node_of(const ElemParams& P, const ElemIdx& E, int a) {
+  constexpr int D = K + 1;
+  const int a0 = a % D, a1 = (a / D) % D, a2 = a / (D * D);
+  const long long i0 = (long long)E.ex * K + a0, i1 = (long long)E.ey * K + a1;
+  if constexpr (DIM == 2) return i0 + (long long)P.N0 * i1;
+  const long long i2 = (long long)E.ez * K + a2;
+  return i0 + (long long)P.N0 * (i1 + (long long)P.N1 * i2);
+}
+
+template <int DIM, int K, class T>
+__device__ __forceinline__ QpC<T> qp_consts(const ElemParams& P, const ElemIdx& E, const T* sW, int lt) {
+  constexpr int Q = 2 * K;
+  QpC<T> c;
+  const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+  T a = sW[q0] * sW[q1];
+  if constexpr (DIM == 3) a *= sW[q2];
+  c.alpha = a;
+  const double rho0 = E.valid ? P.rho0[E.e] : 1.0;
+  const double gam = E.valid ? P.gamma[E.e] : 1.4;
+  c.mq = T(rho0 * P.detJ0) * a;
+  c.inv_detJ0 = T(1.0 / P.detJ0);
+  c.gm1 = T(gam - 1.0);
+  c.ggm1 = T(gam * (gam - 1.0));
+  c.h0 = T(P.h0);
+  c.inv_hc = T(P.inv_hc);
+  c.q1 = T(P.q1);
+  c.q2 = T(P.q2);
+  c.scoef = T(P.scoef);
+  c.eps2 = T(P.eps2);
+  c.visc = P.visc != 0;
+  return c;
+}
+
+// true if velocity component comp of lattice node nd is fixed (v.n = 0 on a masked face)
+template <int DIM>
+__device__ __forceinline__ bool fixed_node(const ElemParams& P, long long nd, int comp) {
+  long long ic;
+  int Nc;
+  if (comp == 0) {
+    ic = nd % P.N0;
+    Nc = P.N0;
+  } else if (comp == 1) {
+    ic = (nd / P.N0) % P.N1;
+    Nc = P.N1;
+  } else {
+    ic = nd / ((long long)P.N0 * P.N1);
+    Nc = P.N2;
+  }
+  const bool lo = ((P.bc >> (2 * comp)) & 1u) && ic == 0;
+  const bool hi = ((P.bc >> (2 * comp + 1)) & 1u) && ic == Nc - 1;
+  return lo || hi;
+}
+
+template <class T>
+__device__ __forceinline__ void load_tables(const ElemParams& P, T* s, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = T(P.tab[i]);
+}
+
+// min over the block (thread 0 holds the result); red has blockDim.x entries
+__device__ __forceinline__ double block_min(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 1; s < (int)blockDim.x; s <<= 1) {
+    const int i = threadIdx.x;
+    double o = DBL_MAX;
+    if ((i % (2 * s)) == 0 && i + s < (int)blockDim.x) o = red[i + s];
+    __syncthreads();
+    if ((i % (2 * s)) == 0) red[i] = fmin(red[i], o);
+    __syncthreads();
+  }
+  return red[0];
+}
+
+// =====================================================================================
+// Residual: H1 rows (M_V k_v + F(w).1) to the element scratch, L2 rows
+// (M_E k_e - F(w)^T w_v - b) directly, per-block min det J.
+template <int DIM, int K>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk, double tau,
+           double* __restrict__ ev, double* __restrict__ Re, double* __restrict__ blockmin) {
+  using C = Cfg<DIM, K>;
+  constexpr int D = C::D, Q = C::Q, ND = C::ND, NL = C::NL, NQ = C::NQ;
+  constexpr int NCH = 2 * DIM;
+  using PL = Plan<DIM, K, NCH, DIM, 2, DIM>;
+  using TB = Tab<K>;
+  extern __shared__ double smem[];
+  double* sB = smem + TB::B;
+  double* sG = smem + TB::G;
+  double* sBl = smem + TB::BL;
+  double* sW = smem + TB::W;
+  double* red = smem + TB::SMEM;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  double* s_h = smem + PL::HEAD + eb * PL::PER;   // [2 DIM][ND]: w_x, w_v
+  double* s_kv = s_h + NCH * ND;                  // [DIM][ND]: k_v
+  double* s_l = s_kv + DIM * ND;                  // [2][NL]: w_e, k_e
+  double* t1 = s_l + 2 * NL;
+  double* t2 = t1 + PL::T1;
+  double* sf = t2 + PL::T2;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  for (int i = lt; i < NCH * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    double v = 0.0;
+    if (E.valid) {
+      const long long g = comp * P.NV + node_of<DIM, K>(P, E, a);
+      v = u[g] + tau * kk[g];
+    }
+    s_h[i] = v;
+  }
+  for (int i = lt; i < DIM * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    s_kv[i] = E.valid ? kk[(DIM + comp) * P.NV + node_of<DIM, K>(P, E, a)] : 0.0;
+  }
+  for (int i = lt; i < NL; i += NQ) {
+    double we = 0.0, ke = 0.0;
+    if (E.valid) {
+      const long long g = 2 * DIM * P.NV + E.e * NL + i;
+      ke = kk[g];
+      we = u[g] + tau * ke;
+    }
+    s_l[i] = we;
+    s_l[NL + i] = ke;
+  }
+  __syncthreads();
+  double hv[NCH], hg[NCH][DIM];
+  h1_fwd<DIM, K, NCH>(s_h, t1, t2, sB, sG, lt, hv, hg);
+  double kvq[DIM];
+  l2_fwd<DIM, K, DIM, double, D>(s_kv, t1, t2, sB, lt, kvq);
+  double lq[2];
+  l2_fwd<DIM, K, 2>(s_l, t1, t2, sBl, lt, lq);
+
+  const QpC<double> c = qp_consts<DIM, K, double>(P, E, sW, lt);
+  double J[DIM][DIM], Gv[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      J[i][r] = hg[i][r];
+      Gv[i][r] = hg[DIM + i][r];
+    }
+  if (!E.valid) {
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) J[i][i] = 1.0;   // keep the idle lanes finite
+  }
+  double So[DIM][DIM], Eo, detJ;
+  qp_forward<DIM>(J, Gv, lq[0], c, So, Eo, detJ);
+  double fval[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) fval[i] = c.mq * kvq[i];
+  double g = c.mq * lq[1] - Eo;
+  if constexpr (DIM == 2) {
+    if (P.tg) g -= c.alpha * detJ * tg_source<double, double>(hv[0], hv[1]);
+  }
+  h1_bwd<DIM, K, DIM>(fval, So, sf, t1, t2, sB, sG, lt, s_h);
+  if (E.valid)
+    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
+  double gv[1] = {g};
+  l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
+  if (E.valid)
+    for (int i = lt; i < NL; i += NQ) Re[E.e * NL + i] = s_l[i];
+  const double m = block_min(E.valid ? detJ : DBL_MAX, red);
+  if (threadIdx.x == 0) blockmin[blockIdx.x] = m;
+}
+
+// =====================================================================================
+// Jacobian action (tangent of the residual along dw = tau dk, plus the mass terms).
+// State gathered in double; in float mode positions are re-centred on the element's
+// first node before rounding so that J keeps full float accuracy.
+template <int DIM, int K, class T>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_jvp(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk, double tau,
+      const T* __restrict__ dk, T* __restrict__ ev, T* __restrict__ oute) {
+  using C = Cfg<DIM, K>;
+  constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ;
+  constexpr int NCH = 4 * DIM;   // w_x, w_v, dk_x, dk_v
+  using PL = Plan<DIM, K, NCH, 0, 2, DIM>;
+  using TB = Tab<K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  T* sB = smem + TB::B;
+  T* sG = smem + TB::G;
+  T* sBl = smem + TB::BL;
+  T* sW = smem + TB::W;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  T* s_h = smem + PL::HEAD + eb * PL::PER;
+  T* s_l = s_h + NCH * ND;
+  T* t1 = s_l + 2 * NL;
+  T* t2 = t1 + PL::T1;
+  T* sf = t2 + PL::T2;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  // element origin for the re-centring of positions
+  double org[DIM];
+#pragma unroll
+  for (int cc = 0; cc < DIM; ++cc) {
+    org[cc] = 0.0;
+    if (E.valid && sizeof(T) < sizeof(double)) {
+      const long long g = cc * P.NV + node_of<DIM, K>(P, E, 0);
+      org[cc] = u[g] + tau * kk[g];
+    }
+  }
+  for (int i = lt; i < NCH * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    T v = T(0);
+    if (E.valid) {
+      const long long nd = node_of<DIM, K>(P, E, a);
+      if (comp < 2 * DIM) {
+        const long long g = comp * P.NV + nd;
+        double w = u[g] + tau * kk[g];
+        if (comp < DIM) w -= org[comp];
+        v = T(w);
+      } else {
+        v = dk[(comp - 2 * DIM) * P.NV + nd];
+      }
+    }
+    s_h[i] = v;
+  }
+  for (int i = lt; i < NL; i += NQ) {
+    T we = T(0), de = T(0);
+    if (E.valid) {
+      const long long g = 2 * DIM * P.NV + E.e * NL + i;
+      we = T(u[g] + tau * kk[g]);
+      de = dk[g];
+    }
+    s_l[i] = we;
+    s_l[NL + i] = de;
+  }
+  __syncthreads();
+  T hv[NCH], hg[NCH][DIM];
+  h1_fwd<DIM, K, NCH>(s_h, t1, t2, sB, sG, lt, hv, hg);
+  T lq[2];
+  l2_fwd<DIM, K, 2>(s_l, t1, t2, sBl, lt, lq);
+
+  const QpC<T> c = qp_consts<DIM, K, T>(P, E, sW, lt);
+  const T tf = T(tau);
+  Dual<T> J[DIM][DIM], Gv[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      J[i][r] = Dual<T>(hg[i][r], tf * hg[2 * DIM + i][r]);
+      Gv[i][r] = Dual<T>(hg[DIM + i][r], tf * hg[3 * DIM + i][r]);
+    }
+  if (!E.valid) {
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) J[i][i] = Dual<T>(T(1), T(0));
+  }
+  Dual<T> So[DIM][DIM], Eo, detJ;
+  qp_forward<DIM>(J, Gv, Dual<T>(lq[0], tf * lq[1]), c, So, Eo, detJ);
+  T fval[DIM], fgrad[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    fval[i] = c.mq * hv[3 * DIM + i];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) fgrad[i][r] = So[i][r].d;
+  }
+  T g = c.mq * lq[1] - Eo.d;
+  if constexpr (DIM == 2) {
+    if (P.tg) {
+      const Dual<T> xq(T(org[0]) + hv[0], tf * hv[2 * DIM + 0]);
+      const Dual<T> yq(T(org[1]) + hv[1], tf * hv[2 * DIM + 1]);
+      const Dual<T> ws = c.alpha * detJ * tg_source<Dual<T>, T>(xq, yq);
+      g -= ws.d;
+    }
+  }
+  h1_bwd<DIM, K, DIM>(fval, fgrad, sf, t1, t2, sB, sG, lt, s_h);
+  if (E.valid)
+    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
+  T gv[1] = {g};
+  l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
+  if (E.valid)
+    for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = s_l[i];
+}
+
+// =====================================================================================
+// Transpose action: adjoint of the element residual map, contributions to the x and v
+// rows in the element scratch ([e][2 DIM][ND]), e rows directly.
+template <int DIM, int K>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_jtvp(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk, double tau,
+       const double* __restrict__ y, double* __restrict__ ev, double* __restrict__ oute) {
+  using C = Cfg<DIM, K>;
+  constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ;
+  constexpr int NCH = 3 * DIM;   // w_x, w_v, y_v (fixed rows masked)
+  using PL = Plan<DIM, K, NCH, 0, 2, 2 * DIM>;
+  using TB = Tab<K>;
+  extern __shared__ double smem[];
+  double* sB = smem + TB::B;
+  double* sG = smem + TB::G;
+  double* sBl = smem + TB::BL;
+  double* sW = smem + TB::W;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  double* s_h = smem + PL::HEAD + eb * PL::PER;
+  double* s_l = s_h + NCH * ND;
+  double* t1 = s_l + 2 * NL;
+  double* t2 = t1 + PL::T1;
+  double* sf = t2 + PL::T2;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  for (int i = lt; i < NCH * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    double v = 0.0;
+    if (E.valid) {
+      const long long nd = node_of<DIM, K>(P, E, a);
+      if (comp < 2 * DIM) {
+        const long long g = comp * P.NV + nd;
+        v = u[g] + tau * kk[g];
+      } else {
+        const int cc = comp - 2 * DIM;
+        v = fixed_node<DIM>(P, nd, cc) ? 0.0 : y[(DIM + cc) * P.NV + nd];
+      }
+    }
+    s_h[i] = v;
+  }
+  for (int i = lt; i < NL; i += NQ) {
+    double we = 0.0, ye = 0.0;
+    if (E.valid) {
+      const long long g = 2 * DIM * P.NV + E.e * NL + i;
+      we = u[g] + tau * kk[g];
+      ye = y[g];
+    }
+    s_l[i] = we;
+    s_l[NL + i] = ye;
+  }
+  __syncthreads();
+  double hv[NCH], hg[NCH][DIM];
+  h1_fwd<DIM, K, NCH>(s_h, t1, t2, sB, sG, lt, hv, hg);
+  double lq[2];
+  l2_fwd<DIM, K, 2>(s_l, t1, t2, sBl, lt, lq);
+
+  const QpC<double> c = qp_consts<DIM, K, double>(P, E, sW, lt);
+  double J[DIM][DIM], Gv[DIM][DIM], Sb[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      J[i][r] = hg[i][r];
+      Gv[i][r] = hg[DIM + i][r];
+      Sb[i][r] = hg[2 * DIM + i][r];
+    }
+  if (!E.valid) {
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) J[i][i] = 1.0;
+  }
+  const double Eb = -lq[1];
+  double detb = 0.0, xb[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) xb[i] = 0.0;
+  if constexpr (DIM == 2) {
+    if (P.tg) {   // -alpha det(J) s(x_q) in the e rows
+      double A[DIM][DIM];
+      const double det = det_adj<DIM>(J, A);
+      const double wb = -lq[1];
+      detb = wb * c.alpha * tg_source<double, double>(hv[0], hv[1]);
+      double sx, sy;
+      tg_source_grad<double>(hv[0], hv[1], sx, sy);
+      xb[0] = wb * c.alpha * det * sx;
+      xb[1] = wb * c.alpha * det * sy;
+    }
+  }
+  double Jb[DIM][DIM], Gvb[DIM][DIM], eb_ = 0.0;
+  qp_adjoint<DIM>(J, Gv, lq[0], c, Sb, Eb, detb, Jb, Gvb, eb_);
+  double fval[2 * DIM], fgrad[2 * DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    fval[i] = tau * xb[i];
+    fval[DIM + i] = c.mq * hv[2 * DIM + i];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      fgrad[i][r] = tau * Jb[i][r];
+      fgrad[DIM + i][r] = tau * Gvb[i][r];
+    }
+  }
+  const double g = c.mq * lq[1] + tau * eb_;
+  h1_bwd<DIM, K, 2 * DIM>(fval, fgrad, sf, t1, t2, sB, sG, lt, s_h);
+  if (E.valid)
+    for (int i = lt; i < 2 * DIM * ND; i += NQ) ev[E.e * (2 * DIM * ND) + i] = s_h[i];
+  double gv[1] = {g};
+  l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
+  if (E.valid)
+    for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = s_l[i];
+}
+
+// =====================================================================================
+// H1 mass: element vectors of M_V f for NC = DIM components (f component-major [DIM][NV]).
+template <int DIM, int K>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_mass_h1(ElemParams P, const double* __restrict__ f, double* __restrict__ ev) {
+  using C = Cfg<DIM, K>;
+  constexpr int D = C::D, ND = C::ND, NQ = C::NQ;
+  using PL = Plan<DIM, K, DIM, 0, 0, DIM>;
+  using TB = Tab<K>;
+  extern __shared__ double smem[];
+  double* sB = smem + TB::B;
+  double* sW = smem + TB::W;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  double* s_h = smem + PL::HEAD + eb * PL::PER;
+  double* t1 = s_h + DIM * ND;
+  double* t2 = t1 + PL::T1;
+  double* sf = t2 + PL::T2;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  for (int i = lt; i < DIM * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    s_h[i] = E.valid ? f[comp * P.NV + node_of<DIM, K>(P, E, a)] : 0.0;
+  }
+  __syncthreads();
+  double fq[DIM];
+  l2_fwd<DIM, K, DIM, double, D>(s_h, t1, t2, sB, lt, fq);
+  const QpC<double> c = qp_consts<DIM, K, double>(P, E, sW, lt);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) fq[i] *= c.mq;
+  l2_bwd<DIM, K, DIM, double, D>(fq, sf, t1, t2, sB, lt, s_h);
+  if (E.valid)
+    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
+}
+
+// L2 mass: out = M_E g (element-local, no assembly)
+template <int DIM, int K>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_mass_l2(ElemParams P, const double* __restrict__ gin, double* __restrict__ out) {
+  using C = Cfg<DIM, K>;
+  constexpr int NL = C::NL, NQ = C::NQ;
+  using PL = Plan<DIM, K, 1, 0, 0, 1>;
+  using TB = Tab<K>;
+  extern __shared__ double smem[];
+  double* sBl = smem + TB::BL;
+  double* sW = smem + TB::W;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  double* s_l = smem + PL::HEAD + eb * PL::PER;
+  double* t1 = s_l + C::ND;
+  double* t2 = t1 + PL::T1;
+  double* sf = t2 + PL::T2;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  for (int i = lt; i < NL; i += NQ) s_l[i] = E.valid ? gin[E.e * NL + i] : 0.0;
+  __syncthreads();
+  double gq[1];
+  l2_fwd<DIM, K, 1>(s_l, t1, t2, sBl, lt, gq);
+  const QpC<double> c = qp_consts<DIM, K, double>(P, E, sW, lt);
+  gq[0] *= c.mq;
+  l2_bwd<DIM, K, 1>(gq, sf, t1, t2, sBl, lt, s_l);
+  if (E.valid)
+    for (int i = lt; i < NL; i += NQ) out[E.e * NL + i] = s_l[i];
+}
+
+// =====================================================================================
+// Explicit time-step estimate per block: min_q h_min / (c_s + mu / (rho h_min)),
+// h_min = sigma_min(J) / K.
+template <int DIM>
+__device__ __forceinline__ double sigma_min(const double (&J)[DIM][DIM]) {
+  // smallest eigenvalue of the symmetric J^T J, then its square root
+  double M[DIM][DIM];
+  for (int i = 0; i < DIM; ++i)
+    for (int j = 0; j < DIM; ++j) {
+      double s = 0;
+      for (int r = 0; r < DIM; ++r) s += J[r][i] * J[r][j];
+      M[i][j] = s;
+    }
+  if constexpr (DIM == 2) {
+    const double tr = M[0][0] + M[1][1];
+    const double dd = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    const double disc = sqrt(fmax(0.25 * tr * tr - dd, 0.0));
+    return sqrt(fmax(0.5 * tr - disc, 0.0));
+  } else {
+    // eigenvalues of a symmetric 3x3 matrix by the trigonometric solution of its
+    // characteristic cubic (Smith 1961)
+    const double p1 = M[0][1] * M[0][1] + M[0][2] * M[0][2] + M[1][2] * M[1][2];
+    const double q = (M[0][0] + M[1][1] + M[2][2]) / 3.0;
+    const double p2 = (M[0][0] - q) * (M[0][0] - q) + (M[1][1] - q) * (M[1][1] - q) +
+                      (M[2][2] - q) * (M[2][2] - q) + 2.0 * p1;
+    const double p = sqrt(p2 / 6.0);
+    if (p <= 1e-300) return sqrt(fmax(q, 0.0));
+    double Bm[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Bm[i][j] = (M[i][j] - (i == j ? q : 0.0)) / p;
+    const double detB = Bm[0][0] * (Bm[1][1] * Bm[2][2] - Bm[1][2] * Bm[2][1]) -
+                        Bm[0][1] * (Bm[1][0] * Bm[2][2] - Bm[1][2] * Bm[2][0]) +
+                        Bm[0][2] * (Bm[1][0] * Bm[2][1] - Bm[1][1] * Bm[2][0]);
+    const double r = fmin(fmax(0.5 * detB, -1.0), 1.0);
+    const double phi = acos(r) / 3.0;
+    const double lmin = q + 2.0 * p * cos(phi + 2.0 * 3.14159265358979323846 / 3.0);
+    return sqrt(fmax(lmin, 0.0));
+  }
+}
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_dt_estimate(ElemParams P, const double* __restrict__ u, double* __restrict__ blockmin) {
+  using C = Cfg<DIM, K>;
+  constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ;
+  constexpr int NCH = 2 * DIM;
+  using PL = Plan<DIM, K, NCH, 0, 1, 1>;
+  using TB = Tab<K>;
+  extern __shared__ double smem[];
+  double* sB = smem + TB::B;
+  double* sG = smem + TB::G;
+  double* sBl = smem + TB::BL;
+  double* sW = smem + TB::W;
+  double* red = smem + TB::SMEM;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  double* s_h = smem + PL::HEAD + eb * PL::PER;
+  double* s_l = s_h + NCH * ND;
+  double* t1 = s_l + NL;
+  double* t2 = t1 + PL::T1;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  for (int i = lt; i < NCH * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    s_h[i] = E.valid ? u[comp * P.NV + node_of<DIM, K>(P, E, a)] : 0.0;
+  }
+  for (int i = lt; i < NL; i += NQ) s_l[i] = E.valid ? u[2 * DIM * P.NV + E.e * NL + i] : 0.0;
+  __syncthreads();
+  double hv[NCH], hg[NCH][DIM];
+  h1_fwd<DIM, K, NCH>(s_h, t1, t2, sB, sG, lt, hv, hg);
+  double lq[1];
+  l2_fwd<DIM, K, 1>(s_l, t1, t2, sBl, lt, lq);
+  const QpC<double> c = qp_consts<DIM, K, double>(P, E, sW, lt);
+  double J[DIM][DIM], Gv[DIM][DIM];
+  for (int i = 0; i < DIM; ++i)
+    for (int r = 0; r < DIM; ++r) {
+      J[i][r] = hg[i][r];
+      Gv[i][r] = hg[DIM + i][r];
+    }
+  if (!E.valid)
+    for (int i = 0; i < DIM; ++i) J[i][i] = 1.0;
+  double A[DIM][DIM];
+  const double det = det_adj<DIM>(J, A);
+  const double rho = c.mq / (c.alpha * det);
+  const double e = lq[0];
+  const double ep = 0.5 * (e + sqrt(e * e + c.eps2));
+  const double cs = sqrt(c.ggm1 * ep);
+  double mu = 0.0;
+  if (c.visc) {
+    double Lv[DIM][DIM];
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        double s = 0;
+        for (int r = 0; r < DIM; ++r) s += Gv[i][r] * A[r][j] / det;
+        Lv[i][j] = s;
+      }
+    const double h = c.h0 * root_dim<DIM>(det * c.inv_detJ0);
+    double div = 0;
+    for (int i = 0; i < DIM; ++i) div += Lv[i][i];
+    const double dv = h * div;
+    const double ds = 2.0 * c.inv_hc * h * cs;
+    const double ab = sqrt(dv * dv + ds * ds);
+    const double psi = 0.5 + 0.5 * tanh((-dv - c.scoef * ds) / (2.0 * ds));
+    mu = rho * h * (c.q2 * ab + c.q1 * cs * psi);
+  }
+  const double hmin = sigma_min<DIM>(J) / K;
+  const double dt = hmin / (cs + mu / (rho * hmin));
+  const double m = block_min(E.valid ? dt : DBL_MAX, red);
+  if (threadIdx.x == 0) blockmin[blockIdx.x] = m;
+}
+
+// =====================================================================================
+// Node-centric G^T: sum of the element contributions of lattice node nd, component comp,
+// from an element scratch laid out [e][ncomp][ND], in a fixed order.
+template <int DIM, int K, class T>
+__device__ __forceinline__ T gather_node(const ElemParams& P, const T* __restrict__ ev, int ncomp, int comp,
+                                         long long nd) {
+  constexpr int D = K + 1, ND = Cfg<DIM, K>::ND;
+  int ic[3];
+  ic[0] = (int)(nd % P.N0);
+  ic[1] = (int)((nd / P.N0) % P.N1);
+  ic[2] = DIM == 3 ? (int)(nd / ((long long)P.N0 * P.N1)) : 0;
+  const int nel[3] = {P.n0, P.n1, P.n2};
+  int el[3][2], loc[3][2], cnt[3];
+  for (int d = 0; d < 3; ++d) {
+    cnt[d] = 0;
+    if (d >= DIM) {
+      el[d][0] = 0;
+      loc[d][0] = 0;
+      cnt[d] = 1;
+      continue;
+    }
+    const int q = ic[d] / K, r = ic[d] % K;
+    if (r == 0) {
+      if (q >= 1) { el[d][cnt[d]] = q - 1; loc[d][cnt[d]] = K; ++cnt[d]; }
+      if (q < nel[d]) { el[d][cnt[d]] = q; loc[d][cnt[d]] = 0; ++cnt[d]; }
+    } else {
+      el[d][0] = q;
+      loc[d][0] = r;
+      cnt[d] = 1;
+    }
+  }
+  T s = T(0);
+  for (int k2 = 0; k2 < cnt[2]; ++k2)
+    for (int k1 = 0; k1 < cnt[1]; ++k1)
+      for (int k0 = 0; k0 < cnt[0]; ++k0) {
+        const long long e = el[0][k0] + (long long)P.n0 * (el[1][k1] + (long long)P.n1 * el[2][k2]);
+        const int a = loc[0][k0] + D * (loc[1][k1] + D * loc[2][k2]);
+        s += ev[(e * ncomp + comp) * ND + a];
+      }
+  return s;
+}
+
+// R_x = k_x - w_v; R_v = sum of element rows, or k_v on fixed rows
+template <int DIM, int K>
+__global__ void k_assemble_residual(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk,
+                                    double tau, const double* __restrict__ ev, double* __restrict__ r) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= DIM * P.NV) return;
+  const int comp = (int)(i / P.NV);
+  const long long nd = i % P.NV;
+  const long long iv = DIM * P.NV + i;
+  r[i] = kk[i] - (u[iv] + tau * kk[iv]);
+  r[iv] = fixed_node<DIM>(P, nd, comp) ? kk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd);
+}
+
+template <int DIM, int K, class T>
+__global__ void k_assemble_jvp(ElemParams P, const T* __restrict__ dk, double tau, const T* __restrict__ ev,
+                               T* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= DIM * P.NV) return;
+  const int comp = (int)(i / P.NV);
+  const long long nd = i % P.NV;
+  const long long iv = DIM * P.NV + i;
+  out[i] = dk[i] - T(tau) * dk[iv];
+  out[iv] = fixed_node<DIM>(P, nd, comp) ? dk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd);
+}
+
+template <int DIM, int K>
+__global__ void k_assemble_jtvp(ElemParams P, const double* __restrict__ y, double tau,
+                                const double* __restrict__ ev, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= DIM * P.NV) return;
+  const int comp = (int)(i / P.NV);
+  const long long nd = i % P.NV;
+  const long long iv = DIM * P.NV + i;
+  out[i] = y[i] + gather_node<DIM, K>(P, ev, 2 * DIM, comp, nd);
+  double s = -tau * y[i] + gather_node<DIM, K>(P, ev, 2 * DIM, DIM + comp, nd);
+  if (fixed_node<DIM>(P, nd, comp)) s += y[iv];
+  out[iv] = s;
+}
+
+template <int DIM, int K>
+__global__ void k_assemble_sum(ElemParams P, const double* __restrict__ ev, int ncomp, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ncomp * P.NV) return;
+  const int comp = (int)(i / P.NV);
+  out[i] = gather_node<DIM, K>(P, ev, ncomp, comp, i % P.NV);
+}
+
+// diagonal of M_V, element part: rho0 detJ0 prod_d sum_q w_q B(q, a_d)^2
+template <int DIM, int K>
+__global__ void k_diag_mv_elem(ElemParams P, double* __restrict__ ev) {
+  constexpr int D = K + 1, Q = 2 * K, ND = Cfg<DIM, K>::ND;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.NE * ND) return;
+  const long long e = i / ND;
+  const int a = (int)(i % ND);
+  const int ad[3] = {a % D, (a / D) % D, a / (D * D)};
+  double prod = P.rho0[e] * P.detJ0;
+  for (int d = 0; d < DIM; ++d) {
+    double s = 0;
+    for (int q = 0; q < Q; ++q) {
+      const double b = P.tab[Tab<K>::B + q * D + ad[d]];
+      s += P.tab[Tab<K>::W + q] * b * b;
+    }
+    prod *= s;
+  }
+  ev[i] = prod;
+}
+
+// inverse of the L2 mass: Lagrange basis at the K Gauss points is orthogonal under
+// exact integration, so M_E is diagonal, entry rho0 detJ0 sum_q alpha_q phi_j(q)^2
+template <int DIM, int K>
+__global__ void k_inv_me(ElemParams P, double* __restrict__ inv) {
+  constexpr int L = K, Q = 2 * K, NL = Cfg<DIM, K>::NL;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.NE * NL) return;
+  const long long e = i / NL;
+  const int j = (int)(i % NL);
+  const int jd[3] = {j % L, (j / L) % L, j / (L * L)};
+  double prod = P.rho0[e] * P.detJ0;
+  for (int d = 0; d < DIM; ++d) {
+    double s = 0;
+    for (int q = 0; q < Q; ++q) {
+      const double b = P.tab[Tab<K>::BL + q * L + jd[d]];
+      s += P.tab[Tab<K>::W + q] * b * b;
+    }
+    prod *= s;
+  }
+  inv[i] = 1.0 / prod;
+}
+
+template <int DIM, int K>
+__global__ void k_initial_nodes(ElemParams P, double* __restrict__ x0) {
+  constexpr int D = K + 1;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.NV) return;
+  const int ic[3] = {(int)(i % P.N0), (int)((i / P.N0) % P.N1), DIM == 3 ? (int)(i / ((long long)P.N0 * P.N1)) : 0};
+  const int nel[3] = {P.n0, P.n1, P.n2};
+  const double* zh = P.tab + Tab<K>::W + 2 * K;    // H1 nodes follow the weights
+  for (int d = 0; d < DIM; ++d) {
+    int el = ic[d] / K;
+    if (el >= nel[d]) el = nel[d] - 1;
+    const int a = ic[d] - el * K;
+    x0[d * P.NV + i] = P.lo[d] + P.h[d] * (el + zh[a]);
+  }
+  (void)D;
+}
+
+// =====================================================================================
+// launchers
+// raise the dynamic shared-memory limit once per kernel (the plan size is fixed per kernel)
+template <auto KERN>
+static cudaError_t prep(size_t bytes) {
+  static bool done = false;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  return cudaSuccess;
+}
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <int DIM, int K>
+struct Launch {
+  using C = Cfg<DIM, K>;
+  static unsigned grid(const ElemParams& P) { return (unsigned)((P.NE + C::EPB - 1) / C::EPB); }
+
+  static cudaError_t residual(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                              double* ev, double* Re, double* bmin, double* r) {
+    using PL = Plan<DIM, K, 2 * DIM, DIM, 2, DIM>;
+    const size_t by = PL::bytes(sizeof(double));
+    cudaError_t e = prep<k_residual<DIM, K>>(by);
+    if (e != cudaSuccess) return e;
+    k_residual<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, ev, Re, bmin);
+    k_assemble_residual<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, u, k, tau, ev, r);
+    return cudaGetLastError();
+  }
+  template <class T>
+  static cudaError_t jvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                         const T* dk, T* ev, T* out) {
+    using PL = Plan<DIM, K, 4 * DIM, 0, 2, DIM>;
+    const size_t by = PL::bytes(sizeof(T));
+    cudaError_t e = prep<k_jvp<DIM, K, T>>(by);
+    if (e != cudaSuccess) return e;
+    k_jvp<DIM, K, T><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, dk, ev, out + 2 * DIM * P.NV);
+    k_assemble_jvp<DIM, K, T><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    return cudaGetLastError();
+  }
+  static cudaError_t jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                          const double* y, double* ev, double* out) {
+    using PL = Plan<DIM, K, 3 * DIM, 0, 2, 2 * DIM>;
+    const size_t by = PL::bytes(sizeof(double));
+    cudaError_t e = prep<k_jtvp<DIM, K>>(by);
+    if (e != cudaSuccess) return e;
+    k_jtvp<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, y, ev, out + 2 * DIM * P.NV);
+    k_assemble_jtvp<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, y, tau, ev, out);
+    return cudaGetLastError();
+  }
+  static cudaError_t mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out) {
+    using PL = Plan<DIM, K, DIM, 0, 0, DIM>;
+    const size_t by = PL::bytes(sizeof(double));
+    cudaError_t e = prep<k_mass_h1<DIM, K>>(by);
+    if (e != cudaSuccess) return e;
+    k_mass_h1<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, f, ev);
+    k_assemble_sum<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, ev, DIM, out);
+    return cudaGetLastError();
+  }
+  static cudaError_t mass_l2(const ElemParams& P, cudaStream_t s, const double* g, double* out) {
+    using PL = Plan<DIM, K, 1, 0, 0, 1>;
+    const size_t by = PL::bytes(sizeof(double));
+    cudaError_t e = prep<k_mass_l2<DIM, K>>(by);
+    if (e != cudaSuccess) return e;
+    k_mass_l2<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, g, out);
+    return cudaGetLastError();
+  }
+  static cudaError_t dt_estimate(const ElemParams& P, cudaStream_t s, const double* u, double* bmin) {
+    using PL = Plan<DIM, K, 2 * DIM, 0, 1, 1>;
+    const size_t by = PL::bytes(sizeof(double));
+    cudaError_t e = prep<k_dt_estimate<DIM, K>>(by);
+    if (e != cudaSuccess) return e;
+    k_dt_estimate<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, bmin);
+    return cudaGetLastError();
+  }
+  static cudaError_t setup(const ElemParams& P, cudaStream_t s, double* ev, double* diag, double* invme) {
+    k_diag_mv_elem<DIM, K><<<nblk(P.NE * C::ND, 256), 256, 0, s>>>(P, ev);
+    k_assemble_sum<DIM, K><<<nblk(P.NV, 256), 256, 0, s>>>(P, ev, 1, diag);
+    k_inv_me<DIM, K><<<nblk(P.NE * C::NL, 256), 256, 0, s>>>(P, invme);
+    return cudaGetLastError();
+  }
+  static cudaError_t initial_nodes(const ElemParams& P, cudaStream_t s, double* x0) {
+    k_initial_nodes<DIM, K><<<nblk(P.NV, 256), 256, 0, s>>>(P, x0);
+    return cudaGetLastError();
+  }
+};
+
+#define LH_DISPATCH(P, CALL)                                             \
+  switch ((P).dim * 10 + (P).K) {                                        \
+    case 21: return Launch<2, 1>::CALL;                                  \
+    case 22: return Launch<2, 2>::CALL;                                  \
+    case 23: return Launch<2, 3>::CALL;                                  \
+    case 24: return Launch<2, 4>::CALL;                                  \
+    case 31: return Launch<3, 1>::CALL;                                  \
+    case 32: return Launch<3, 2>::CALL;                                  \
+    case 33: return Launch<3, 3>::CALL;                                  \
+    case 34: return Launch<3, 4>::CALL;                                  \
+    default: return cudaErrorInvalidValue;                               \
+  }
+
+cudaError_t launch_residual(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                            double* ev, double* bmin, double* r) {
+  double* Re = r + 2 * P.dim * P.NV;
+  LH_DISPATCH(P, residual(P, s, u, k, tau, ev, Re, bmin, r))
+}
+cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                           const double* dk, double* ev, double* out) {
+  LH_DISPATCH(P, template jvp<double>(P, s, u, k, tau, dk, ev, out))
+}
+cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                           const float* dk, float* ev, float* out) {
+  LH_DISPATCH(P, template jvp<float>(P, s, u, k, tau, dk, ev, out))
+}
+cudaError_t launch_jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                        const double* y, double* ev, double* out) {
+  LH_DISPATCH(P, jtvp(P, s, u, k, tau, y, ev, out))
+}
+cudaError_t launch_mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out) {
+  LH_DISPATCH(P, mass_h1(P, s, f, ev, out))
+}
+cudaError_t launch_mass_l2(const ElemParams& P, cudaStream_t s, const double* g, double* out) {
+  LH_DISPATCH(P, mass_l2(P, s, g, out))
+}
+cudaError_t launch_dt_estimate(const ElemParams& P, cudaStream_t s, const double* u, double* bmin) {
+  LH_DISPATCH(P, dt_estimate(P, s, u, bmin))
+}
+cudaError_t launch_setup(const ElemParams& P, cudaStream_t s, double* ev, double* diag, double* invme) {
+  LH_DISPATCH(P, setup(P, s, ev, diag, invme))
+}
+cudaError_t launch_initial_nodes(const ElemParams& P, cudaStream_t s, double* x0) {
+  LH_DISPATCH(P, initial_nodes(P, s, x0))
+}
+unsigned elem_grid(const ElemParams& P) {
+  switch (P.dim * 10 + P.K) {
+    case 21: return Launch<2, 1>::grid(P);
+    case 22: return Launch<2, 2>::grid(P);
+    case 23: return Launch<2, 3>::grid(P);
+    case 24: return Launch<2, 4>::grid(P);
+    case 31: return Launch<3, 1>::grid(P);
+    case 32: return Launch<3, 2>::grid(P);
+    case 33: return Launch<3, 3>::grid(P);
+    case 34: return Launch<3, 4>::grid(P);
+    default: return 0;
+  }
+}
+
+}  // namespace lh

@@ -1,0 +1,200 @@
+"""Python view of a mesh and its operators (argument marshalling over include/lh.h)."""
+import ctypes as C
+
+import torch
+
+from . import _lib
+from . import lib as _L
+
+
+class LHError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def newton_opts(**kw):
+    """lh_newton_opts with the library defaults, overridden by keyword arguments
+    (newton_rtol, newton_atol, gmres_rtol, newton_maxit, gmres_maxit, restart,
+    max_halvings, jvp_prec in {'fp64', 'fp32'})."""
+    o = _lib.NewtonOpts()
+    _L.lh_newton_opts_init(C.byref(o))
+    for key, val in kw.items():
+        if key == "jvp_prec":
+            val = {"fp64": _lib.LH_FP64, "fp32": _lib.LH_FP32}.get(val, val)
+        setattr(o, key, val)
+    return o
+
+
+def probe_fma(prec="fp64"):
+    """Measured FMA-pipe throughput (TFLOP/s) of the current device."""
+    out = C.c_double()
+    st = _L.lh_probe_fma(_lib.LH_FP64 if prec == "fp64" else _lib.LH_FP32, C.byref(out))
+    if st != _lib.LH_OK:
+        raise LHError(st, _L.lh_last_error(None).decode())
+    return out.value
+
+
+class Mesh:
+    """Box mesh of quads (dim 2) or hexes (dim 3) with Q_k - Q_{k-1} spaces.
+
+    rho0 and gamma may be scalars or per-element sequences (element order x-fastest).
+    All vector arguments are CUDA tensors in the layout of include/lh.h.
+    """
+
+    def __init__(self, dim, n, lo, hi, order, rho0=1.0, gamma=1.4, bc_mask=None, visc=True,
+                 q1=0.5, q2=1.0, psi0=0.5, eps_e=1e-6, h0=0.0, h_coarse=0.0, tg_source=False,
+                 device=None):
+        self.device = torch.device(device or "cuda")
+        d = _lib.MeshDesc()
+        _L.lh_mesh_desc_init(C.byref(d))
+        d.dim = dim
+        for c in range(dim):
+            d.n[c] = int(n[c])
+            d.lo[c] = float(lo[c])
+            d.hi[c] = float(hi[c])
+        d.order = order
+        ne = 1
+        for c in range(dim):
+            ne *= int(n[c])
+        keep = []
+        for name, val in (("rho0", rho0), ("gamma", gamma)):
+            if hasattr(val, "__len__"):
+                arr = (C.c_double * ne)(*[float(x) for x in val])
+                keep.append(arr)
+                setattr(d, name, C.cast(arr, C.POINTER(C.c_double)))
+            else:
+                setattr(d, name + "_value", float(val))
+        d.bc_mask = (1 << (2 * dim)) - 1 if bc_mask is None else int(bc_mask)
+        d.visc = int(bool(visc))
+        d.q1, d.q2, d.psi0, d.eps_e = q1, q2, psi0, eps_e
+        d.h0, d.h_coarse = h0, h_coarse
+        d.tg_source = int(bool(tg_source))
+        with torch.cuda.device(self.device):
+            d.stream = torch.cuda.current_stream().cuda_stream
+            h = C.c_void_p()
+            st = _L.lh_mesh_create(C.byref(d), C.byref(h))
+        if st != _lib.LH_OK:
+            raise LHError(st, _L.lh_last_error(None).decode())
+        self._h = h
+        s = (C.c_longlong * 6)()
+        self._check(_L.lh_sizes(self._h, s))
+        self.NE, self.NV, self.NEd, self.n, self.NQ, self.dim = (int(x) for x in s)
+        self.order = order
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _L.lh_mesh_destroy(h)
+            self._h = None
+
+    # -- helpers ---------------------------------------------------------------------
+    def _check(self, st):
+        if st != _lib.LH_OK:
+            raise LHError(st, _L.lh_last_error(self._h).decode())
+
+    def _stream(self):
+        _L.lh_set_stream(self._h, C.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+
+    def _vec(self, t, name, dtype=torch.float64, n=None):
+        n = self.n if n is None else n
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()
+                and t.numel() == n):
+            raise ValueError(f"{name}: expected a contiguous CUDA {dtype} tensor of {n} entries")
+        return t
+
+    def new(self, dtype=torch.float64):
+        return torch.empty(self.n, dtype=dtype, device=self.device)
+
+    # -- operators -------------------------------------------------------------------------
+    def initial_nodes(self):
+        x0 = torch.empty(self.dim * self.NV, dtype=torch.float64, device=self.device)
+        self._stream()
+        self._check(_L.lh_initial_nodes(self._h, _ptr(x0)))
+        return x0
+
+    def residual(self, u, k, tau, out=None, min_detj=False):
+        """R(k; tau, u) (Eq. (21)); with min_detj=True also returns min det J at w."""
+        self._vec(u, "u")
+        self._vec(k, "k")
+        out = self.new() if out is None else self._vec(out, "out")
+        self._stream()
+        md = C.c_double()
+        self._check(_L.lh_residual(self._h, _ptr(u), _ptr(k), float(tau), _ptr(out),
+                                   C.byref(md) if min_detj else None))
+        return (out, md.value) if min_detj else out
+
+    def jvp(self, u, k, tau, dk, out=None):
+        """(dR/dk) dk; float64 dk -> FP64 kernel, float32 dk -> FP32 kernel."""
+        self._vec(u, "u")
+        self._vec(k, "k")
+        prec = _lib.LH_FP32 if dk.dtype == torch.float32 else _lib.LH_FP64
+        self._vec(dk, "dk", dk.dtype)
+        out = self.new(dk.dtype) if out is None else self._vec(out, "out", dk.dtype)
+        self._stream()
+        self._check(_L.lh_jvp(self._h, _ptr(u), _ptr(k), float(tau), _ptr(dk), _ptr(out), prec))
+        return out
+
+    def jtvp(self, u, k, tau, y, out=None):
+        """(dR/dk)^T y (FP64)."""
+        self._vec(u, "u")
+        self._vec(k, "k")
+        self._vec(y, "y")
+        out = self.new() if out is None else self._vec(out, "out")
+        self._stream()
+        self._check(_L.lh_jtvp(self._h, _ptr(u), _ptr(k), float(tau), _ptr(y), _ptr(out), _lib.LH_FP64))
+        return out
+
+    def mass_apply(self, which, f):
+        n = self.dim * self.NV if which == 0 else self.NEd
+        self._vec(f, "f", n=n)
+        out = torch.empty(n, dtype=torch.float64, device=self.device)
+        self._stream()
+        self._check(_L.lh_mass_apply(self._h, int(which), _ptr(f), _ptr(out)))
+        return out
+
+    def mass_solve(self, which, rhs, rtol=1e-12, maxit=500):
+        n = self.dim * self.NV if which == 0 else self.NEd
+        self._vec(rhs, "rhs", n=n)
+        sol = torch.empty(n, dtype=torch.float64, device=self.device)
+        its = C.c_int()
+        self._stream()
+        self._check(_L.lh_mass_solve(self._h, int(which), _ptr(rhs), _ptr(sol), float(rtol), int(maxit),
+                                     C.byref(its)))
+        return sol, its.value
+
+    def dt_estimate(self, u):
+        self._vec(u, "u")
+        dt = C.c_double()
+        self._stream()
+        self._check(_L.lh_dt_estimate(self._h, _ptr(u), C.byref(dt)))
+        return dt.value
+
+    def energies(self, u):
+        self._vec(u, "u")
+        ke, ie = C.c_double(), C.c_double()
+        self._stream()
+        self._check(_L.lh_energies(self._h, _ptr(u), C.byref(ke), C.byref(ie)))
+        return ke.value, ie.value
+
+    def newton_step(self, u, k_prev, dt, opts=None, **kw):
+        """One implicit midpoint step in place on u (and k_prev, if given).  Returns the
+        step statistics as a dict; raises LHError (state unchanged) on failure."""
+        self._vec(u, "u")
+        if k_prev is not None:
+            self._vec(k_prev, "k_prev")
+        o = opts if opts is not None else newton_opts(**kw)
+        stats = _lib.StepStats()
+        self._stream()
+        st = _L.lh_newton_step(self._h, _ptr(u), _ptr(k_prev) if k_prev is not None else None, float(dt),
+                               C.byref(o), C.byref(stats))
+        out = {f: getattr(stats, f) for f, _ in _lib.StepStats._fields_}
+        if st != _lib.LH_OK:
+            err = LHError(st, _L.lh_last_error(self._h).decode())
+            err.stats = out
+            raise err
+        return out

@@ -1,0 +1,131 @@
+"""GPU parity against the oracle: residual, Jacobian actions, mass operators.
+
+Sizes span several thread blocks with a ragged last block (elements per block: 32 for
+2D Q1, 8 for 2D Q2, 2 for 3D Q2, 1 for 3D Q3/Q4).  Tolerances: FP64 residual and
+FP64 J.w relative L2 <= 1e-12 / 1e-11 per block (x, v, e rows) against the oracle's
+residual and its complex-step derivative; FP32 J.w <= 2e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lh_synth
+from lhcase import Case
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    (2, (7, 5), 1, True, False),
+    (2, (7, 5), 2, True, False),
+    (2, (5, 3), 2, False, True),      # Taylor-Green source, no viscosity
+    (2, (4, 3), 3, True, False),
+    (2, (3, 2), 4, True, False),
+    (3, (5, 4, 3), 1, True, False),
+    (3, (3, 3, 3), 2, True, False),
+    (3, (2, 2, 1), 3, True, False),
+    (3, (1, 1, 2), 4, True, False),
+]
+IDS = [f"d{c[0]}_n{'x'.join(map(str, c[1]))}_k{c[2]}{'_visc' if c[3] else ''}{'_tg' if c[4] else ''}" for c in CASES]
+
+
+@pytest.fixture(scope="module", params=CASES, ids=IDS)
+def case(request):
+    dim, n, k, visc, tg = request.param
+    return Case(dim, n, k, seed=11, visc=visc, tg=tg)
+
+
+def test_initial_nodes(case):
+    x0 = case.gm.initial_nodes().cpu().numpy()
+    assert np.abs(x0 - case.hyd.x0.ravel()).max() <= 1e-14
+
+
+def test_residual_parity(case):
+    kk = lh_synth.normal_vector(case.gm.n, 3, 0.1)
+    tau = 0.01
+    ref, detj = case.hyd.residual(case.u, kk, tau, return_detj=True)
+    got, md = case.gm.residual(case.dev(case.u), case.dev(kk), tau, min_detj=True)
+    rel = case.rel_blocks(got.cpu().numpy(), ref)
+    assert max(rel) <= 1e-12, rel
+    assert abs(md - detj.min()) <= 1e-13 * abs(detj.min())
+
+
+def test_jvp_fp64_parity(case):
+    kk = lh_synth.normal_vector(case.gm.n, 4, 0.1)
+    dk = lh_synth.normal_vector(case.gm.n, 5)
+    tau = 0.02
+    ref = case.hyd.jvp_complex_step(case.u, kk, tau, dk)
+    got = case.gm.jvp(case.dev(case.u), case.dev(kk), tau, case.dev(dk)).cpu().numpy()
+    rel = case.rel_blocks(got, ref)
+    assert max(rel) <= 1e-11, rel
+
+
+def test_jvp_fp32_parity(case):
+    kk = lh_synth.normal_vector(case.gm.n, 4, 0.1)
+    dk = lh_synth.normal_vector(case.gm.n, 5)
+    tau = 0.02
+    ref = case.hyd.jvp_complex_step(case.u, kk, tau, dk.astype(np.float32).astype(np.float64))
+    got = case.gm.jvp(case.dev(case.u), case.dev(kk), tau, case.dev(dk, torch.float32)).double().cpu().numpy()
+    rel = case.rel_blocks(got, ref)
+    assert max(rel) <= 2e-5, rel
+
+
+def test_jtvp_dot_product(case):
+    """<J dk, y> = <dk, J^T y> for the GPU tangent and adjoint kernels."""
+    kk = lh_synth.normal_vector(case.gm.n, 6, 0.1)
+    dk = lh_synth.normal_vector(case.gm.n, 7)
+    y = lh_synth.normal_vector(case.gm.n, 8)
+    tau = 0.03
+    u = case.dev(case.u)
+    Jdk = case.gm.jvp(u, case.dev(kk), tau, case.dev(dk)).cpu().numpy()
+    JTy = case.gm.jtvp(u, case.dev(kk), tau, case.dev(y)).cpu().numpy()
+    a, b = float(Jdk @ y), float(dk @ JTy)
+    scale = np.linalg.norm(Jdk) * np.linalg.norm(y)
+    assert abs(a - b) <= 1e-13 * scale, (a, b)
+
+
+@pytest.mark.parametrize("dim,n,k,tg", [(2, (2, 2), 2, False), (2, (2, 1), 2, True), (3, (1, 1, 1), 2, False)])
+def test_jtvp_dense_jacobian(dim, n, k, tg):
+    """J^T y from the GPU adjoint against the oracle's dense complex-step Jacobian."""
+    c = Case(dim, n, k, seed=21, visc=not tg, tg=tg)
+    kk = lh_synth.normal_vector(c.gm.n, 9, 0.1)
+    y = lh_synth.normal_vector(c.gm.n, 10)
+    tau = 0.05
+    Jd = c.hyd.jacobian(c.u, kk, tau)
+    got = c.gm.jtvp(c.dev(c.u), c.dev(kk), tau, c.dev(y)).cpu().numpy()
+    rel = c.rel_blocks(got, Jd.T @ y)
+    assert max(rel) <= 1e-12, rel
+    # and every column of J against the GPU tangent
+    u, kd = c.dev(c.u), c.dev(kk)
+    for j in range(0, c.gm.n, max(1, c.gm.n // 25)):
+        e = np.zeros(c.gm.n)
+        e[j] = 1.0
+        col = c.gm.jvp(u, kd, tau, c.dev(e)).cpu().numpy()
+        assert np.linalg.norm(col - Jd[:, j]) <= 1e-12 * max(1.0, np.linalg.norm(Jd[:, j]))
+
+
+def test_mass_operators(case):
+    m = case.hyd.m
+    f = lh_synth.normal_vector(case.nx, 12).reshape(m.d, m.NV)
+    ref = case.hyd.apply_mass_v(f).ravel()
+    got = case.gm.mass_apply(0, case.dev(f.ravel())).cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    g = lh_synth.normal_vector(m.NEd, 13).reshape(m.NE, m.NL)
+    ref = case.hyd.apply_mass_e(g).ravel()
+    got = case.gm.mass_apply(1, case.dev(g.ravel())).cpu().numpy()
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    # solves: M_V by Jacobi-CG, M_E by its exact (diagonal) inverse
+    Mv = case.hyd.mass_v_dense()
+    rhs = lh_synth.normal_vector(case.nx, 14)
+    sol, its = case.gm.mass_solve(0, case.dev(rhs), rtol=1e-13, maxit=1000)
+    ref = np.linalg.solve(Mv, rhs.reshape(m.d, m.NV).T).T.ravel()
+    assert its > 0 and np.linalg.norm(sol.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+    rhs_e = lh_synth.normal_vector(m.NEd, 15)
+    sol_e, _ = case.gm.mass_solve(1, case.dev(rhs_e))
+    ref_e = np.linalg.solve(case.hyd.mass_e_elem(), rhs_e.reshape(m.NE, m.NL, 1)).ravel()
+    assert np.linalg.norm(sol_e.cpu().numpy() - ref_e) <= 1e-12 * np.linalg.norm(ref_e)
+
+
+def test_energies(case):
+    ke, ie = case.gm.energies(case.dev(case.u))
+    assert abs(ke - case.hyd.kinetic_energy(case.u)) <= 1e-13 * abs(ke)
+    assert abs(ie - case.hyd.internal_energy(case.u)) <= 1e-13 * abs(ie)
