@@ -1,0 +1,462 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit Lagrangian hydrodynamics hot path on B300.
+
+One step = one implicit midpoint Newton-GMRES step (residual, Jacobian actions inside
+GMRES, preconditioner, Gram-Schmidt, line search, update) on the 3D point-blast
+workload: [0,1]^3, 24^3 hexes, Q2-Q1, gamma 1.4, smooth viscosity, walls, state after a
+few implicit steps from the corner deposit, dt = 2 x the explicit estimate.
+
+value = unknowns x (residual + Jacobian-action evaluations) per second of step time
+(GDoF/s of J.w & residual over the whole step), the chosen form = FP64 residual with
+an FP32 Jacobian action.  Also reported: the plain FP64 step, standalone operator
+throughputs, the roofline of the dominant kernel and the CPU oracle baseline.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"name": "blast3d_24_q2q1", "dim": 3, "n": (24, 24, 24), "k": 2, "gamma": 1.4, "energy": 0.25,
+            "develop_steps": 3, "cfl": 2.0}
+NEWTON = {"newton_rtol": 1e-8, "gmres_rtol": 1e-4, "gmres_maxit": 200, "restart": 30, "newton_maxit": 20}
+L2_FLUSH_BYTES = 512 << 20
+
+
+def sf_macs(dim, k):
+    """Multiply-adds of the sum-factorised contractions per element and field component."""
+    D, Q = k + 1, 2 * k
+    if dim == 3:
+        grad = 2 * D ** 3 * Q + 3 * D ** 2 * Q ** 2 + 3 * D * Q ** 3
+        valgrad = 2 * D ** 3 * Q + 3 * D ** 2 * Q ** 2 + 4 * D * Q ** 3
+
+        def val(N):
+            return N ** 3 * Q + N ** 2 * Q ** 2 + N * Q ** 3
+    else:
+        grad = 2 * D ** 2 * Q + 2 * D * Q ** 2
+        valgrad = 2 * D ** 2 * Q + 3 * D * Q ** 2
+
+        def val(N):
+            return N ** 2 * Q + N * Q ** 2
+    return grad, valgrad, val
+
+
+def flops_per_element(dim, k, kind, visc=True):
+    """Algorithmic FLOPs per element: contractions (2 per multiply-add, minimal factorised
+    forms) + quadrature-point kernel (exact count of its code, lh_qp_flops) + per-point glue."""
+    import ctypes as C
+    import paper_2609_16424_b300 as lh
+    grad, valgrad, val = sf_macs(dim, k)
+    nq = (2 * k) ** dim
+    qk = {"residual": 0, "jvp": 1, "jvp_rec": 1, "jtvp": 2}[kind]
+    ops = C.c_longlong()
+    lh.lib.lh_qp_flops(dim, qk, int(visc), C.byref(ops))
+    if kind == "residual":
+        macs = 2 * dim * grad + dim * val(k + 1) + 2 * val(k) + dim * valgrad + val(k)
+        glue = dim + 2 + 3
+    elif kind == "jvp":
+        macs = 3 * dim * grad + dim * valgrad + 2 * val(k) + dim * valgrad + val(k)
+        glue = 2 * dim * dim + 1 + dim + 2 + 3
+    elif kind == "jvp_rec":   # primal state read from the linearisation record
+        macs = dim * grad + dim * valgrad + val(k) + dim * valgrad + val(k)
+        glue = 2 * dim * dim + 1 + dim + 2 + 2
+    else:
+        macs = 2 * dim * grad + dim * valgrad + 2 * val(k) + 2 * dim * valgrad + val(k)
+        glue = 2 * dim * dim + dim + 3 + 3
+    return 2 * macs + nq * (ops.value + glue)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace('.', '').isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max(float(r[3]) for r in self.rows if r[3].replace('.', '').isdigit())
+                if any(r[3].replace('.', '').isdigit() for r in self.rows) else None}
+
+
+# ------------------------------------------------------------------------------------------
+def blast_state(mesh, energy):
+    """Corner point blast on the undeformed box: e = energy / (rho0 |K0|) in element 0."""
+    import torch
+    x0 = mesh.initial_nodes()
+    u = torch.zeros(mesh.n, dtype=torch.float64, device=mesh.device)
+    nx = x0.numel()
+    u[:nx] = x0
+    vol0 = 1.0 / mesh.NE
+    nl = mesh.NEd // mesh.NE
+    u[2 * nx:2 * nx + nl] = energy / vol0
+    return u
+
+
+def setup_ours(device):
+    import torch
+    import paper_2609_16424_b300 as lh
+    W = WORKLOAD
+    mesh = lh.Mesh(W["dim"], W["n"], (0.0,) * 3, (1.0,) * 3, W["k"], gamma=W["gamma"], visc=True,
+                   device=device)
+    u = blast_state(mesh, W["energy"])
+    k = torch.zeros_like(u)
+    for _ in range(W["develop_steps"]):
+        dt = W["cfl"] * mesh.dt_estimate(u)
+        mesh.newton_step(u, k, dt, jvp_prec="fp64", **NEWTON)
+    dt = W["cfl"] * mesh.dt_estimate(u)
+    return mesh, u, k, dt
+
+
+def timed_steps(mesh, u_s, k_s, dt, steps, prec, flush, profile=False):
+    """Per-step CUDA-event times (ms) and stats; the L2 flush between steps is not timed."""
+    import torch
+    import paper_2609_16424_b300 as lh
+    u, k = u_s.clone(), k_s.clone()
+    stream = torch.cuda.current_stream()
+    times, stats = [], []
+    if profile:
+        mesh.profile(True)
+    l0 = lh.launch_count()
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u.copy_(u_s)
+        k.copy_(k_s)
+        st = mesh.newton_step(u, k, dt, jvp_prec=prec, **NEWTON)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st)
+    launches = lh.launch_count() - l0
+    prof = mesh.profile_read() if profile else None
+    if profile:
+        mesh.profile(False)
+    return times, stats, launches, prof
+
+
+def kernel_rate(mesh, fn, reps, flush):
+    """Mean CUDA-event time (ms) of fn() over reps calls, L2 flushed before each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def e2e_steps(mesh, u_s, k_s, dt, steps, prec):
+    """Same step through the public API with host buffers: pinned host -> device copy of
+    (u, k_prev), the Newton step, device -> host copy of (u, k) inside the timed region."""
+    import torch
+    hu, hk = u_s.cpu().pin_memory(), k_s.cpu().pin_memory()
+    ou, ok = torch.empty_like(hu).pin_memory(), torch.empty_like(hk).pin_memory()
+    u, k = torch.empty_like(u_s), torch.empty_like(k_s)
+    evals = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u.copy_(hu, non_blocking=True)
+        k.copy_(hk, non_blocking=True)
+        st = mesh.newton_step(u, k, dt, jvp_prec=prec, **NEWTON)
+        ou.copy_(u, non_blocking=True)
+        ok.copy_(k, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        evals += st["residual_evals"] + st["jvp_evals"]
+    t = time.perf_counter() - t0
+    nbytes = 8 * mesh.n * 2
+    return mesh.n * evals / t / 1e9, t / steps * 1e3, nbytes
+
+
+def one_thread():
+    """Limit BLAS pools to one thread when threadpoolctl is available (the oracle's
+    einsum contractions run single-threaded either way)."""
+    try:
+        from threadpoolctl import threadpool_limits
+        return threadpool_limits(limits=1)
+    except ImportError:
+        import contextlib
+        return contextlib.nullcontext()
+
+
+def oracle_residual_rate(u_np, k_np, tau, budget_s=15.0):
+    """The CPU oracle's residual on the same workload state, single-threaded."""
+    from oracle.fem import Mesh as OMesh
+    from oracle.hydro import Hydro, Params
+    W = WORKLOAD
+    with one_thread():
+        om = OMesh(W["n"], (0.0,) * 3, (1.0,) * 3, W["k"])
+        hyd = Hydro(om, Params(om, gamma=W["gamma"], visc=True))
+        t0 = time.perf_counter()
+        reps = 0
+        r = None
+        while True:
+            r = hyd.residual(u_np, k_np, tau)
+            reps += 1
+            if time.perf_counter() - t0 >= budget_s or reps >= 50:
+                break
+        t = (time.perf_counter() - t0) / reps
+    return om.n_unknowns / t / 1e9, reps, t, r
+
+
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, device):
+    import numpy as np
+    import torch
+    import paper_2609_16424_b300 as lh
+    torch.cuda.set_device(device)
+    mesh, u_s, k_s, dt = setup_ours(device)
+    n = mesh.n
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    prec = args.prec
+    # warm-up (untimed)
+    timed_steps(mesh, u_s, k_s, dt, args.warmup, prec, flush)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        wall0 = time.perf_counter()
+        torch.cuda.nvtx.range_push("timed")
+        times, stats, launches, prof = timed_steps(mesh, u_s, k_s, dt, args.steps, prec, flush, profile=True)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = sum(times) / len(times)
+    evals = sum(s["residual_evals"] + s["jvp_evals"] for s in stats)
+    total_ms = sum(times)
+    units = n * evals
+    if world > 1:
+        t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device=device)
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        total_ms, units = tmax[0].item(), tsum[1].item()
+    value = units / (total_ms * 1e-3) / 1e9
+    if rank != 0:
+        return None
+    if args.quick:
+        return {"metric": "quick", "value": round(value, 4), "ms_per_step": round(step_ms, 4),
+                "step_kernel_ms": {k2: round(v[0], 3) for k2, v in prof.items()}, "gpu_launches": launches,
+                "newton": [{k2: s[k2] for k2 in ("newton_its", "gmres_its_total", "residual_evals", "jvp_evals")}
+                           for s in stats]}
+
+    # plain FP64 form for comparison
+    t64, s64, _, _ = timed_steps(mesh, u_s, k_s, dt, max(2, min(args.steps, 5)), "fp64", flush)
+    # standalone operators on the bench state
+    kd = k_s
+    tau = 0.5 * dt
+    r = torch.empty_like(u_s)
+    dkd = torch.randn(n, dtype=torch.float64, device=device, generator=torch.Generator(device).manual_seed(0))
+    dkf = dkd.float()
+    of = torch.empty(n, dtype=torch.float32, device=device)
+    od = torch.empty_like(u_s)
+    reps = 10
+    t_res = kernel_rate(mesh, lambda: mesh.residual(u_s, kd, tau, out=r), reps, flush)
+    t_j64 = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkd, out=od), reps, flush)
+    t_j32 = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of), reps, flush)
+    mesh.linearize(u_s, kd, tau)
+    t_j32r = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of, lin=True), reps, flush)
+    # element-kernel-only times from the profiler (the roofline kernels)
+    mesh.profile(True)
+    for _ in range(reps):
+        flush.fill_(1.0)
+        mesh.residual(u_s, kd, tau, out=r)
+        flush.fill_(1.0)
+        mesh.jvp(u_s, kd, tau, dkd, out=od)
+        flush.fill_(1.0)
+        mesh.jvp(u_s, kd, tau, dkf, out=of)
+    kp = mesh.profile_read()
+    mesh.profile(True)
+    for _ in range(reps):
+        flush.fill_(1.0)
+        mesh.jvp(u_s, kd, tau, dkf, out=of, lin=True)
+    kpr = mesh.profile_read()
+    mesh.profile(False)
+
+    fp64_peak = lh.probe_fma("fp64")
+    fp32_peak = lh.probe_fma("fp32")
+    W = WORKLOAD
+    ne = mesh.NE
+    fl = {kind: flops_per_element(3, W["k"], kind) for kind in ("residual", "jvp", "jvp_rec")}
+    # dominant kernel of the timed steps
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_kind, (dom_ms, dom_cnt) = dom[0], dom[1]
+    # inside the Newton step the FP32 J.w runs from the linearisation record
+    dom_flops = ne * {"residual": fl["residual"], "jvp_fp64": fl["jvp"], "jvp_fp32": fl["jvp_rec"]}[dom_kind]
+    dom_peak = fp64_peak if dom_kind in ("residual", "jvp_fp64") else fp32_peak
+    achieved = dom_flops / (dom_ms / dom_cnt * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": {"residual": "k_residual<3,2>", "jvp_fp64": "k_jvp<3,2,double,double>",
+                                           "jvp_fp32": "k_jvp_rec<3,2,double>"}.get(dom_kind, dom_kind),
+                "pipe": "fp64" if dom_peak is fp64_peak else "fp32",
+                "achieved": round(achieved, 4), "peak": round(dom_peak, 3), "unit": "TFLOP/s",
+                "frac": round(achieved / dom_peak, 4), "peak_source": "measured FMA probe (lh_probe_fma) this run",
+                "traffic": None, "launch_ms": round(dom_ms / dom_cnt, 5), "launches": dom_cnt,
+                "share_of_step": round(dom_ms / sum(times), 4),
+                "algorithmic_flops_per_launch": dom_flops}
+
+    e2e_val, e2e_ms, e2e_bytes = e2e_steps(mesh, u_s, k_s, dt, max(2, min(args.steps, 5)), prec)
+    out = {
+        "metric": "GDoF/s of J.w & residual over the implicit step (FP64 residual, FP32 J.w)",
+        "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(step_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic (corner point blast, developed 3 steps)",
+        "config": {"workload": W["name"], "mesh": "24x24x24 hex, [0,1]^3", "order": "Q2-Q1", "n_unknowns": n,
+                   "quad_points": mesh.NQ, "dt": dt, "cfl_multiple": W["cfl"], "newton": NEWTON,
+                   "jvp_prec": prec, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "wall_s_timed_region": round(wall, 3),
+        "newton": {"its_per_step": statistics.mean(s["newton_its"] for s in stats),
+                   "gmres_its_per_step": statistics.mean(s["gmres_its_total"] for s in stats),
+                   "evals_per_step": evals / len(stats)},
+        "plain_fp64_step": {"ms_per_step": round(sum(t64) / len(t64), 4),
+                            "gmres_its_per_step": statistics.mean(s["gmres_its_total"] for s in s64),
+                            "value": round(n * sum(s["residual_evals"] + s["jvp_evals"] for s in s64) / (sum(t64) * 1e-3) / 1e9, 4)},
+        "kernels": {
+            "residual_fp64": {"gdofs": round(n / (t_res * 1e-3) / 1e9, 4), "ms": round(t_res, 5),
+                              "elem_kernel_ms": round(kp["residual"][0] / max(1, kp["residual"][1]), 5),
+                              "tflops_elem": round(fl["residual"] * ne / (kp["residual"][0] / max(1, kp["residual"][1]) * 1e-3) / 1e12, 4)},
+            "jvp_fp64": {"gdofs": round(n / (t_j64 * 1e-3) / 1e9, 4), "ms": round(t_j64, 5),
+                         "elem_kernel_ms": round(kp["jvp_fp64"][0] / max(1, kp["jvp_fp64"][1]), 5),
+                         "tflops_elem": round(fl["jvp"] * ne / (kp["jvp_fp64"][0] / max(1, kp["jvp_fp64"][1]) * 1e-3) / 1e12, 4)},
+            "jvp_fp32": {"gdofs": round(n / (t_j32 * 1e-3) / 1e9, 4), "ms": round(t_j32, 5),
+                         "elem_kernel_ms": round(kp["jvp_fp32"][0] / max(1, kp["jvp_fp32"][1]), 5),
+                         "tflops_elem": round(fl["jvp"] * ne / (kp["jvp_fp32"][0] / max(1, kp["jvp_fp32"][1]) * 1e-3) / 1e12, 4)},
+            "jvp_fp32_record": {"gdofs": round(n / (t_j32r * 1e-3) / 1e9, 4), "ms": round(t_j32r, 5),
+                                "elem_kernel_ms": round(kpr["jvp_fp32"][0] / max(1, kpr["jvp_fp32"][1]), 5),
+                                "tflops_elem": round(fl["jvp_rec"] * ne / (kpr["jvp_fp32"][0] / max(1, kpr["jvp_fp32"][1]) * 1e-3) / 1e12, 4)},
+            "flops_per_element": fl, "fp64_peak_tflops": round(fp64_peak, 3), "fp32_peak_tflops": round(fp32_peak, 2)},
+        "step_kernel_ms": {k2: round(v[0], 3) for k2, v in prof.items()},
+        "roofline": roofline,
+        "gpu_launches": launches,
+        "e2e": {"value": round(e2e_val, 4), "unit": "GDoF/s", "ms_per_step": round(e2e_ms, 4),
+                "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        import numpy as np
+        rate, reps_c, t_c, _ = oracle_residual_rate(u_s.cpu().numpy(), k_s.cpu().numpy(), tau)
+        out["cpu_baseline"] = {"value": round(rate, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                               "sample": f"oracle residual on the full bench state ({W['name']}, n={n}), "
+                                         f"{reps_c} evaluations, {t_c:.2f} s each, 1 thread"}
+    return out
+
+
+def run_reference(args, rank):
+    """The oracle (plain FP64 numpy, one thread) timed on this host: each step is one
+    residual evaluation of the bench workload state."""
+    if rank != 0:
+        return None
+    import numpy as np
+    from oracle import problems  # noqa: F401
+    from oracle.fem import Mesh as OMesh
+    from oracle.hydro import Hydro, Params
+    from oracle import solver
+    W = WORKLOAD
+    with one_thread():
+        om = OMesh(W["n"], (0.0,) * 3, (1.0,) * 3, W["k"])
+        hyd = Hydro(om, Params(om, gamma=W["gamma"], visc=True))
+        # the same state construction as the GPU arm: deposit, then no developed steps
+        # (the oracle cannot afford Newton steps at this size); dt-independent residual
+        x0 = hyd.x0
+        e = np.zeros((om.NE, om.NL))
+        e[0, :] = W["energy"] * om.NE
+        u = om.join(x0, np.zeros_like(x0), e)
+        kk = np.zeros(om.n_unknowns)
+        tau = 1e-3
+        for _ in range(args.warmup):
+            hyd.residual(u, kk, tau)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hyd.residual(u, kk, tau)
+        t = time.perf_counter() - t0
+    value = om.n_unknowns * args.steps / t / 1e9
+    return {"impl": "reference", "metric": "GDoF/s of J.w & residual over the implicit step (FP64 residual, FP32 J.w)",
+            "value": round(value, 6), "unit": "GDoF/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (corner point blast)",
+            "config": {"workload": W["name"], "n_unknowns": om.n_unknowns},
+            "cpu_baseline": {"value": round(value, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one oracle residual evaluation of the full {W['name']} state per step"},
+            "e2e": {"value": round(value, 6), "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+    else:
+        import torch
+        if world > 1:
+            torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+        out = run_ours(args, rank, world, f"cuda:{local}")
+        if world > 1:
+            torch.distributed.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -55,7 +55,9 @@ typedef enum {
 
 typedef enum {
   LH_FP64 = 0,        /* double in, double out, double arithmetic */
-  LH_FP32 = 1         /* float in, float out, float arithmetic (state gathered in double) */
+  LH_FP32 = 1,        /* float in, float out, float arithmetic (state gathered in double) */
+  LH_FP32_LIN = 2     /* float in, float out, float arithmetic from the linearisation record
+                         of the last lh_linearize (same u, k, tau pointers/value required) */
 } lh_prec;
 
 /* Mesh and model description.  Call lh_mesh_desc_init first to get the defaults. */
@@ -112,6 +114,15 @@ lh_status lh_residual(lh_mesh* mesh, const double* u, const double* k, double ta
 lh_status lh_jvp(lh_mesh* mesh, const double* u, const double* k, double tau,
                  const void* dk, void* out, lh_prec prec);
 
+/* Linearisation record (partial assembly of the tangent, paper Sec. 2.2: store the
+ * quadrature-point data once, reuse it for every action): evaluates the quadrature-point
+ * state (J, grad_hat v, e; x in 2D) at w = u + tau k in FP64 and keeps it, rounded to
+ * float, in the mesh ([NE][19 (3D) or 11 (2D)][quadrature points]).  Later lh_jvp calls
+ * with LH_FP32_LIN and the same u, k (pointers) and tau use it.  lh_newton_step with an
+ * FP32 J.w writes the record at every Newton iterate and invalidates it on return.
+ * Asynchronous; allocates the record on first use. */
+lh_status lh_linearize(lh_mesh* mesh, const double* u, const double* k, double tau);
+
 /* Transpose action out = (dR/dk)^T y (paper Sec. 3.1: transpose actions share the
  * gather-apply-scatter structure).  LH_FP64 only; y, out device [n] double. */
 lh_status lh_jtvp(lh_mesh* mesh, const double* u, const double* k, double tau,
@@ -147,6 +158,9 @@ typedef struct {
   int restart;             /* GMRES restart length (<= 64); default 30 */
   int max_halvings;        /* line-search halvings of the Newton step; default 10 */
   lh_prec jvp_prec;        /* precision of the J.w inside GMRES; default LH_FP64 */
+  int precond;             /* velocity block of the preconditioner: 0 = diagonal of M_V,
+                              1 = exact M_V inverse as a Kronecker product of 1D inverses
+                              (exact for uniform rho0; rho0-scaled otherwise); default 1 */
 } lh_newton_opts;
 
 typedef struct {
@@ -155,6 +169,7 @@ typedef struct {
   int backtracks;          /* line-search halvings */
   int residual_evals;      /* residual evaluations (incl. line-search trials) */
   int jvp_evals;           /* Jacobian actions */
+  int reorth;              /* second Gram-Schmidt passes taken */
   double r0, rfinal;       /* ||R|| at the initial guess and at exit */
   double min_detj;         /* min det J at the accepted stage state */
 } lh_step_stats;
@@ -162,8 +177,10 @@ typedef struct {
 void lh_newton_opts_init(lh_newton_opts* opts);
 
 /* One implicit midpoint step (paper Sec. 4.1, SD2): tau = dt/2, solve R(k; tau, u) = 0
- * by inexact Newton-GMRES (right preconditioner diag(I, diag(M_V)^-1, M_E^-1), a
- * stand-in for the block-diagonal AMG of Eq. (23)) with the det J line search of Sec.
+ * by inexact Newton-GMRES with the right preconditioner
+ *   P^-1 = [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1]
+ * (M_V^-1 as opts.precond selects; the upper block eliminates dR_x/dk_v = -tau I exactly;
+ * a stand-in for the block-diagonal AMG of Eq. (23)) with the det J line search of Sec.
  * 3.5, then u <- u + dt k.  u: device [n] in/out.  k_prev: device [n] initial guess on
  * entry and the converged k on exit, or NULL (zero initial guess).  Synchronises.
  * On LH_ENOCONV / LH_ETANGLED / LH_ENONFINITE u and k_prev are left unchanged. */
@@ -172,6 +189,24 @@ lh_status lh_newton_step(lh_mesh* mesh, double* u, double* k_prev, double dt,
 
 /* Message for the last failing call on mesh (or a global message if mesh is NULL). */
 const char* lh_last_error(const lh_mesh* mesh);
+
+/* Kernel timing (measurement support).  While enabled, each element-kernel launch of the
+ * kinds below is bracketed by CUDA events on the mesh's stream; lh_profile_read returns
+ * the accumulated device milliseconds and launch counts per kind (HOST arrays of
+ * LH_PROF_KINDS entries) and synchronises.  Enabling resets the accumulators. */
+enum { LH_PROF_RESIDUAL = 0, LH_PROF_JVP64 = 1, LH_PROF_JVP32 = 2, LH_PROF_JTVP = 3, LH_PROF_MASS = 4,
+       LH_PROF_KINDS = 5 };
+lh_status lh_profile_enable(lh_mesh* mesh, int enable);
+lh_status lh_profile_read(lh_mesh* mesh, double* ms, long long* count);
+
+/* Arithmetic operations (+ - * / sqrt tanh cbrt cos sin, one each) of one evaluation of
+ * the quadrature-point kernel, counted by running the kernel's code on the host with a
+ * counting scalar.  kind 0: stress (residual), 1: tangent (J.w), 2: adjoint (J^T.y).
+ * Needs no GPU.  *ops is a HOST pointer. */
+lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops);
+
+/* Number of CUDA kernels this library has launched in the process so far. */
+long long lh_launch_count(void);
 
 /* Measurement helper: throughput (TFLOP/s, HOST *tflops) of independent FMA chains on
  * every SM of the current device; prec LH_FP64 or LH_FP32.  Used as the roofline

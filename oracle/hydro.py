@@ -80,8 +80,12 @@ def stress(grad_v, detJ, rho, e, gamma, prm, d):
     grad_v: physical velocity gradient [..., d, d] ((grad v)_{cb} = dv_c/dx_b);
     detJ, rho, e, gamma: [...]; returns sigma [..., d, d].
     """
-    # Eq. (19): smooth positive part of the specific internal energy
-    e_plus = 0.5 * (e + np.sqrt(e * e + prm.eps_e ** 2))
+    # Eq. (19): smooth positive part of the specific internal energy.  For e < 0 the same
+    # quantity is evaluated as eps^2 / (2 (sqrt(e^2 + eps^2) - e)) (multiply and divide by
+    # the conjugate), which avoids the cancellation of e + sqrt(e^2 + eps^2)
+    root = np.sqrt(e * e + prm.eps_e ** 2)
+    neg = np.real(e) < 0
+    e_plus = np.where(neg, 0.5 * prm.eps_e ** 2 / np.where(neg, root - e, 1.0), 0.5 * (e + root))
     # Eq. (20): ideal-gas pressure and sound speed
     p = (gamma - 1.0) * rho * e_plus
     c_s = np.sqrt(gamma * (gamma - 1.0) * e_plus)

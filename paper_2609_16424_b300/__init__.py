@@ -11,12 +11,12 @@ from . import _lib
 
 if not os.path.exists(_lib.LIB_PATH):
     raise ImportError(
-        "liblh.so is missing: build it with `python -m paper_2609_16424_b300.build` "
+        "liblh.so is missing: build it with `python paper_2609_16424_b300/build.py` "
         "(or __graft_entry__.build()); the package has no fallback path")
 
 lib = _lib.load()
 
-from .hydro import Mesh, LHError, probe_fma, newton_opts  # noqa: E402
+from .hydro import Mesh, LHError, probe_fma, newton_opts, launch_count  # noqa: E402
 from .autograd import StageResidual  # noqa: E402
 
-__all__ = ["Mesh", "LHError", "probe_fma", "newton_opts", "StageResidual", "lib"]
+__all__ = ["Mesh", "LHError", "probe_fma", "newton_opts", "launch_count", "StageResidual", "lib"]

@@ -6,7 +6,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblh.so")
 
 LH_OK, LH_EINVAL, LH_ECUDA, LH_ENOMEM, LH_ETANGLED, LH_ENOCONV, LH_ENONFINITE = range(7)
-LH_FP64, LH_FP32 = 0, 1
+LH_FP64, LH_FP32, LH_FP32_LIN = 0, 1, 2
 STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "LH_ETANGLED",
                 5: "LH_ENOCONV", 6: "LH_ENONFINITE"}
 
@@ -14,7 +14,8 @@ STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "L
 SYMBOLS = ["lh_mesh_desc_init", "lh_mesh_create", "lh_mesh_destroy", "lh_sizes", "lh_set_stream",
            "lh_initial_nodes", "lh_residual", "lh_jvp", "lh_jtvp", "lh_mass_apply", "lh_mass_solve",
            "lh_dt_estimate", "lh_energies", "lh_newton_opts_init", "lh_newton_step", "lh_last_error",
-           "lh_probe_fma"]
+           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_linearize"]
+PROF_KINDS = ["residual", "jvp_fp64", "jvp_fp32", "jtvp", "mass_h1"]
 
 
 class MeshDesc(C.Structure):
@@ -30,12 +31,12 @@ class MeshDesc(C.Structure):
 class NewtonOpts(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("gmres_rtol", C.c_double),
                 ("newton_maxit", C.c_int), ("gmres_maxit", C.c_int), ("restart", C.c_int),
-                ("max_halvings", C.c_int), ("jvp_prec", C.c_int)]
+                ("max_halvings", C.c_int), ("jvp_prec", C.c_int), ("precond", C.c_int)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("gmres_its_total", C.c_int), ("backtracks", C.c_int),
-                ("residual_evals", C.c_int), ("jvp_evals", C.c_int), ("r0", C.c_double),
+                ("residual_evals", C.c_int), ("jvp_evals", C.c_int), ("reorth", C.c_int), ("r0", C.c_double),
                 ("rfinal", C.c_double), ("min_detj", C.c_double)]
 
 
@@ -62,6 +63,11 @@ def load(path=LIB_PATH):
         "lh_newton_step": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(StepStats)]),
         "lh_last_error": (C.c_char_p, [vp]),
         "lh_probe_fma": (i, [i, dp]),
+        "lh_profile_enable": (i, [vp, i]),
+        "lh_profile_read": (i, [vp, dp, llp]),
+        "lh_launch_count": (C.c_longlong, []),
+        "lh_qp_flops": (i, [i, i, i, llp]),
+        "lh_linearize": (i, [vp, vp, vp, d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -1,6 +1,7 @@
 """Build the in-tree shared library ``liblh.so`` from ``csrc/*.cu`` for sm_103a (B300).
 
-Usage: ``python -m paper_2609_16424_b300.build [--force] [-v]``.  Objects go to
+Usage: ``python paper_2609_16424_b300/build.py [--force] [-v]`` (run by path, so that a
+stale library is never loaded while building).  Objects go to
 ``_build/`` at the repository root; the library is written next to this file so that
 it travels with the source tree.
 """

@@ -121,6 +121,71 @@ std::vector<double> build_tables(int K) {
   return t;
 }
 
+// dense inverse by Gauss-Jordan elimination with partial pivoting (row-major, n x n)
+bool invert(std::vector<double>& a, int n) {
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)piv * n + c])) piv = r;
+    if (a[(size_t)piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int j = 0; j < n; ++j) {
+        std::swap(a[(size_t)c * n + j], a[(size_t)piv * n + j]);
+        std::swap(inv[(size_t)c * n + j], inv[(size_t)piv * n + j]);
+      }
+    const double d = 1.0 / a[(size_t)c * n + c];
+    for (int j = 0; j < n; ++j) {
+      a[(size_t)c * n + j] *= d;
+      inv[(size_t)c * n + j] *= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = a[(size_t)r * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        a[(size_t)r * n + j] -= f * a[(size_t)c * n + j];
+        inv[(size_t)r * n + j] -= f * inv[(size_t)c * n + j];
+      }
+    }
+  }
+  a.swap(inv);
+  return true;
+}
+
+// transposed inverse (float) of the assembled 1D mass matrix along one axis; with
+// drop_lo / drop_hi the end rows and columns are removed first and identity rows put back
+bool kron_factor(const std::vector<double>& tab, int K, int nel, double h, bool drop_lo, bool drop_hi,
+                 std::vector<float>& out) {
+  const int D = K + 1, Q = 2 * K, N = K * nel + 1;
+  const double* B = tab.data();
+  const double* w = tab.data() + 2 * Q * D + Q * K;
+  std::vector<double> M((size_t)N * N, 0.0);
+  for (int e = 0; e < nel; ++e)
+    for (int a = 0; a < D; ++a)
+      for (int b = 0; b < D; ++b) {
+        double s = 0.0;
+        for (int q = 0; q < Q; ++q) s += w[q] * B[q * D + a] * B[q * D + b];
+        M[(size_t)(e * K + a) * N + e * K + b] += h * s;
+      }
+  const int lo = drop_lo ? 1 : 0, hi = drop_hi ? N - 1 : N;
+  const int n = hi - lo;
+  std::vector<double> R((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) R[(size_t)i * n + j] = M[(size_t)(i + lo) * N + j + lo];
+  if (!invert(R, n)) return false;
+  out.assign((size_t)N * N, 0.f);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) {
+      double v;
+      if (i >= lo && i < hi && j >= lo && j < hi) v = R[(size_t)(i - lo) * n + (j - lo)];
+      else v = (i == j) ? 1.0 : 0.0;
+      out[(size_t)j * N + i] = (float)v;    // transposed: entry [j][i]
+    }
+  return true;
+}
+
 lh_status ensure_work(lh_mesh* m, int restart) {
   const long long n = m->n;
   const long long need = (long long)(restart + 1) * n + 8 * n;
@@ -138,31 +203,93 @@ lh_status ensure_work(lh_mesh* m, int restart) {
   return LH_OK;
 }
 
+// ---- opt-in event profiler of element kernels
+cudaError_t prof_flush(lh_mesh* m) {
+  Prof& p = m->prof;
+  if (p.n == 0) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(m->stream);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < p.n; ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]);
+    if (e != cudaSuccess) return e;
+    p.ms[p.kind[i]] += ms;
+    p.cnt[p.kind[i]] += 1;
+  }
+  p.n = 0;
+  return cudaSuccess;
+}
+
+// event pair for the next element-kernel launch of the given kind, or NULL when off
+cudaEvent_t* prof_pair(lh_mesh* m, int kind) {
+  Prof& p = m->prof;
+  if (!p.on) return nullptr;
+  if (p.n == Prof::kMax && prof_flush(m) != cudaSuccess) return nullptr;
+  p.kind[p.n] = kind;
+  return &p.ev[2 * p.n++];
+}
+
 // ||x||_2^2 into a host double (synchronises)
 lh_status dot_host(lh_mesh* m, const double* a, const double* b, long long n, double* out) {
-  LH_CK(m, launch_mdot(m->stream, a, 1, 0, b, n, m->d_part, m->d_scalar));
+  LH_CK(m, launch_mdot(m->stream, a, 1, 0, b, n, 0, m->d_part, m->d_counter, m->d_scalar));
   LH_CK(m, cudaMemcpyAsync(out, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   LH_CK(m, cudaStreamSynchronize(m->stream));
   return LH_OK;
 }
 
+// w = J z (double in, double out) in the requested arithmetic; the FP32 form reads the
+// linearisation record written by the last residual evaluation
 lh_status apply_jvp(lh_mesh* m, const double* u, const double* k, double tau, const double* z, double* w,
                     lh_prec prec) {
   if (prec == LH_FP32) {
     float* fz = m->d_fwork;
-    float* fw = m->d_fwork + m->n;
     LH_CK(m, launch_to_f32(m->stream, z, fz, m->n));
-    LH_CK(m, launch_jvp_f32(m->P, m->stream, u, k, tau, fz, reinterpret_cast<float*>(m->d_ev), fw));
-    LH_CK(m, launch_to_f64(m->stream, fw, w, m->n));
+    LH_CK(m, launch_jvp_rec_f64out(m->P, m->stream, m->d_rec, tau, fz, reinterpret_cast<float*>(m->d_ev), w,
+                                   prof_pair(m, LH_PROF_JVP32)));
   } else {
-    LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, w));
+    LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, w, prof_pair(m, LH_PROF_JVP64)));
   }
   return LH_OK;
 }
 
-// residual + min detJ (host) in one call
-lh_status residual_min(lh_mesh* m, const double* u, const double* k, double tau, double* r, double* mindet) {
-  LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r));
+// z = P^-1 r with the selected velocity block (0: Jacobi mass, 1: Kronecker mass) in the
+// block upper-triangular preconditioner [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1]
+cudaError_t apply_prec(lh_mesh* m, int kind, const double* r, double* z, double tau) {
+  if (kind == 1) return launch_kron_prec(m->stream, m->P, m->kron, m->d_invMe, r, z, tau);
+  return launch_precond(m->stream, m->P, m->d_diagMv, m->d_invMe, r, z, tau);
+}
+cudaError_t apply_prec_f32(lh_mesh* m, int kind, const double* r, float* z, double tau) {
+  if (kind == 1) return launch_kron_prec_f32(m->stream, m->P, m->kron, m->d_invMe, r, z, tau);
+  return launch_precond_f32(m->stream, m->P, m->d_diagMv, m->d_invMe, r, z, tau);
+}
+
+// w = J P^-1 v (the right-preconditioned operator of GMRES); z receives P^-1 v in FP64 mode
+lh_status apply_prec_jvp(lh_mesh* m, int pk, const double* u, const double* k, double tau, const double* v,
+                         double* z, double* w, lh_prec prec) {
+  if (prec == LH_FP32) {
+    float* fz = m->d_fwork;
+    LH_CK(m, apply_prec_f32(m, pk, v, fz, tau));
+    LH_CK(m, launch_jvp_rec_f64out(m->P, m->stream, m->d_rec, tau, fz, reinterpret_cast<float*>(m->d_ev), w,
+                                   prof_pair(m, LH_PROF_JVP32)));
+  } else {
+    LH_CK(m, apply_prec(m, pk, v, z, tau));
+    LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, w, prof_pair(m, LH_PROF_JVP64)));
+  }
+  return LH_OK;
+}
+
+lh_status ensure_rec(lh_mesh* m) {
+  if (m->d_rec) return LH_OK;
+  if (cudaMalloc(&m->d_rec, sizeof(float) * (size_t)m->NQ * rec_len(m->P.dim)) != cudaSuccess)
+    return fail(m, LH_ENOMEM, "cannot allocate the linearisation record");
+  return LH_OK;
+}
+
+// residual + min detJ (host) in one call; rec (optional) receives the linearisation record
+lh_status residual_min(lh_mesh* m, const double* u, const double* k, double tau, double* r, double* mindet,
+                       float* rec = nullptr) {
+  LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r, prof_pair(m, LH_PROF_RESIDUAL),
+                           rec));
   LH_CK(m, launch_min(m->stream, m->d_blockmin, m->nblocks_elem, m->d_scalar + 1));
   LH_CK(m, cudaMemcpyAsync(mindet, m->d_scalar + 1, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   LH_CK(m, cudaStreamSynchronize(m->stream));
@@ -200,6 +327,7 @@ void lh_newton_opts_init(lh_newton_opts* o) {
   o->restart = 30;
   o->max_halvings = 10;
   o->jvp_prec = LH_FP64;
+  o->precond = 1;
 }
 
 lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
@@ -280,6 +408,7 @@ lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
             cudaMalloc(&m->d_tab, sizeof(double) * tab.size()) == cudaSuccess &&
             cudaMalloc(&m->d_ev, sizeof(double) * evn) == cudaSuccess &&
             cudaMalloc(&m->d_part, sizeof(double) * kRedBlocks * 72) == cudaSuccess &&
+            cudaMalloc(&m->d_counter, sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&m->d_scalar, sizeof(double) * 256) == cudaSuccess &&
             cudaMalloc(&m->d_diagMv, sizeof(double) * P.NV) == cudaSuccess &&
             cudaMalloc(&m->d_invMe, sizeof(double) * P.NEd) == cudaSuccess &&
@@ -291,11 +420,80 @@ lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
   P.rho0 = m->d_rho0;
   P.gamma = m->d_gamma;
   P.tab = m->d_tab;
+  P.fh0 = (float)P.h0;
+  P.finv_hc = (float)P.inv_hc;
+  P.fq1 = (float)P.q1;
+  P.fq2 = (float)P.q2;
+  P.fscoef = (float)P.scoef;
+  P.feps2 = (float)P.eps2;
+  P.finv_detJ0 = (float)(1.0 / P.detJ0);
+  std::vector<float> fc(3 * P.NE);
+  for (long long i = 0; i < P.NE; ++i) {
+    fc[i] = (float)(rho[i] * P.detJ0);
+    fc[P.NE + i] = (float)(gam[i] - 1.0);
+    fc[2 * P.NE + i] = (float)(gam[i] * (gam[i] - 1.0));
+  }
+  if (cudaMalloc(&m->d_fconst, sizeof(float) * 3 * P.NE) != cudaSuccess) {
+    lh_mesh_destroy(m);
+    return fail(nullptr, LH_ENOMEM, "device allocation failed in lh_mesh_create");
+  }
+  P.fmq0 = m->d_fconst;
+  P.fgm1 = m->d_fconst + P.NE;
+  P.fggm1 = m->d_fconst + 2 * P.NE;
   cudaError_t e = cudaMemcpyAsync(m->d_rho0, rho.data(), sizeof(double) * P.NE, cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->d_gamma, gam.data(), sizeof(double) * P.NE, cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->d_tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_fconst, fc.data(), sizeof(float) * fc.size(), cudaMemcpyHostToDevice, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, sizeof(unsigned), m->stream);
+  // Kronecker factors of the H1 mass inverse and the nodal rho0^(-1/2) scaling
+  std::vector<std::vector<float>> kf(6);
+  const int nel[3] = {P.n0, P.n1, P.n2};
+  for (int a = 0; a < dim && e == cudaSuccess; ++a) {
+    const bool lo = (P.bc >> (2 * a)) & 1u, hi = (P.bc >> (2 * a + 1)) & 1u;
+    if (!kron_factor(tab, K, nel[a], P.h[a], false, false, kf[2 * a]) ||
+        !kron_factor(tab, K, nel[a], P.h[a], lo, hi, kf[2 * a + 1])) {
+      lh_mesh_destroy(m);
+      return fail(nullptr, LH_EINVAL, "lh_mesh_create: singular 1D mass matrix");
+    }
+    const size_t bytes = sizeof(float) * kf[2 * a].size();
+    if (cudaMalloc(&m->kron.At_free[a], bytes) != cudaSuccess || cudaMalloc(&m->kron.At_fixed[a], bytes) != cudaSuccess) {
+      lh_mesh_destroy(m);
+      return fail(nullptr, LH_ENOMEM, "device allocation failed in lh_mesh_create");
+    }
+    e = cudaMemcpy(m->kron.At_free[a], kf[2 * a].data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->kron.At_fixed[a], kf[2 * a + 1].data(), bytes, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    std::vector<double> sc(P.NV);
+    for (long long i = 0; i < P.NV; ++i) {
+      const int ic[3] = {(int)(i % P.N0), (int)((i / P.N0) % P.N1), (int)(i / ((long long)P.N0 * P.N1))};
+      int lo3[3], hi3[3];
+      for (int a = 0; a < 3; ++a) {
+        if (a >= dim) { lo3[a] = hi3[a] = 0; continue; }
+        const int q = ic[a] / K, r = ic[a] % K;
+        lo3[a] = (r == 0 && q >= 1) ? q - 1 : (q < nel[a] ? q : nel[a] - 1);
+        hi3[a] = (r == 0) ? (q < nel[a] ? q : nel[a] - 1) : q;
+      }
+      double sum = 0.0;
+      int cnt = 0;
+      for (int z = lo3[2]; z <= hi3[2]; ++z)
+        for (int y = lo3[1]; y <= hi3[1]; ++y)
+          for (int x = lo3[0]; x <= hi3[0]; ++x) {
+            sum += rho[x + (long long)P.n0 * (y + (long long)P.n1 * z)];
+            ++cnt;
+          }
+      sc[i] = 1.0 / std::sqrt(sum / cnt);
+    }
+    if (cudaMalloc(&m->kron.scale, sizeof(double) * P.NV) != cudaSuccess ||
+        cudaMalloc(&m->kron.work, sizeof(float) * 2 * dim * P.NV) != cudaSuccess) {
+      lh_mesh_destroy(m);
+      return fail(nullptr, LH_ENOMEM, "device allocation failed in lh_mesh_create");
+    }
+    e = cudaMemcpy(m->kron.scale, sc.data(), sizeof(double) * P.NV, cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = launch_setup(P, m->stream, m->d_ev, m->d_diagMv, m->d_invMe);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
   if (e != cudaSuccess) {
@@ -308,11 +506,22 @@ lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
 
 lh_status lh_mesh_destroy(lh_mesh* m) {
   if (!m) return LH_OK;
+  for (int i = 0; i < 2 * Prof::kMax; ++i)
+    if (m->prof.ev[i]) cudaEventDestroy(m->prof.ev[i]);
   double* bufs[] = {m->d_rho0, m->d_gamma, m->d_tab, m->d_ev, m->d_part, m->d_scalar,
                     m->d_diagMv, m->d_invMe, m->d_blockmin, m->d_work};
   for (double* b : bufs)
     if (b) cudaFree(b);
   if (m->d_fwork) cudaFree(m->d_fwork);
+  if (m->d_counter) cudaFree(m->d_counter);
+  if (m->d_fconst) cudaFree(m->d_fconst);
+  if (m->d_rec) cudaFree(m->d_rec);
+  for (int a = 0; a < 3; ++a) {
+    if (m->kron.At_free[a]) cudaFree(m->kron.At_free[a]);
+    if (m->kron.At_fixed[a]) cudaFree(m->kron.At_fixed[a]);
+  }
+  if (m->kron.scale) cudaFree(m->kron.scale);
+  if (m->kron.work) cudaFree(m->kron.work);
   delete m;
   return LH_OK;
 }
@@ -344,7 +553,7 @@ lh_status lh_residual(lh_mesh* m, const double* u, const double* k, double tau, 
   if (!m || !u || !k || !r) return fail(m, LH_EINVAL, "NULL argument to lh_residual");
   if (r == u || r == k) return fail(m, LH_EINVAL, "r must not alias u or k");
   if (min_detj) return residual_min(m, u, k, tau, r, min_detj);
-  LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r));
+  LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r, prof_pair(m, LH_PROF_RESIDUAL)));
   return LH_OK;
 }
 
@@ -354,13 +563,34 @@ lh_status lh_jvp(lh_mesh* m, const double* u, const double* k, double tau, const
   if (dk == out) return fail(m, LH_EINVAL, "out must not alias dk");
   if (prec == LH_FP64) {
     LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, static_cast<const double*>(dk), m->d_ev,
-                            static_cast<double*>(out)));
+                            static_cast<double*>(out), prof_pair(m, LH_PROF_JVP64)));
   } else if (prec == LH_FP32) {
     LH_CK(m, launch_jvp_f32(m->P, m->stream, u, k, tau, static_cast<const float*>(dk),
-                            reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out)));
+                            reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out),
+                            prof_pair(m, LH_PROF_JVP32)));
+  } else if (prec == LH_FP32_LIN) {
+    if (!m->rec_valid || m->rec_u != u || m->rec_k != k || m->rec_tau != tau)
+      return fail(m, LH_EINVAL, "lh_jvp(LH_FP32_LIN): call lh_linearize with the same u, k, tau first");
+    LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, static_cast<const float*>(dk),
+                                reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out),
+                                prof_pair(m, LH_PROF_JVP32)));
   } else {
     return fail(m, LH_EINVAL, "lh_jvp: unsupported precision");
   }
+  return LH_OK;
+}
+
+lh_status lh_linearize(lh_mesh* m, const double* u, const double* k, double tau) {
+  if (!m || !u || !k) return fail(m, LH_EINVAL, "NULL argument to lh_linearize");
+  lh_status st = ensure_rec(m);
+  if (st != LH_OK) return st;
+  if ((st = ensure_work(m, m->restart_alloc > 0 ? m->restart_alloc : 30)) != LH_OK) return st;
+  double* r = m->d_work;   // residual written as a by-product
+  LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r, nullptr, m->d_rec));
+  m->rec_u = u;
+  m->rec_k = k;
+  m->rec_tau = tau;
+  m->rec_valid = true;
   return LH_OK;
 }
 
@@ -370,14 +600,14 @@ lh_status lh_jtvp(lh_mesh* m, const double* u, const double* k, double tau, cons
   if (prec != LH_FP64) return fail(m, LH_EINVAL, "lh_jtvp supports LH_FP64 only");
   if (y == out) return fail(m, LH_EINVAL, "out must not alias y");
   LH_CK(m, launch_jtvp(m->P, m->stream, u, k, tau, static_cast<const double*>(y), m->d_ev,
-                       static_cast<double*>(out)));
+                       static_cast<double*>(out), prof_pair(m, LH_PROF_JTVP)));
   return LH_OK;
 }
 
 lh_status lh_mass_apply(lh_mesh* m, int which, const double* f, double* out) {
   if (!m || !f || !out) return fail(m, LH_EINVAL, "NULL argument to lh_mass_apply");
   if (which == 0) {
-    LH_CK(m, launch_mass_h1(m->P, m->stream, f, m->d_ev, out));
+    LH_CK(m, launch_mass_h1(m->P, m->stream, f, m->d_ev, out, prof_pair(m, LH_PROF_MASS)));
   } else if (which == 1) {
     LH_CK(m, launch_mass_l2(m->P, m->stream, f, out));
   } else {
@@ -414,7 +644,7 @@ lh_status lh_mass_solve(lh_mesh* m, int which, const double* rhs, double* sol, d
   int it = 0;
   bool conv = false;
   for (; it < maxit; ++it) {
-    LH_CK(m, launch_mass_h1(m->P, m->stream, p, m->d_ev, Ap));
+    LH_CK(m, launch_mass_h1(m->P, m->stream, p, m->d_ev, Ap, prof_pair(m, LH_PROF_MASS)));
     if ((st = dot_host(m, p, Ap, n, &pAp)) != LH_OK) return st;
     const double alpha = rz / pAp;
     LH_CK(m, launch_axpby(m->stream, alpha, p, 1.0, sol, n));
@@ -455,7 +685,7 @@ lh_status lh_energies(lh_mesh* m, const double* u, double* kinetic, double* inte
   if ((st = dot_host(m, u + n1, t, n1, &kv)) != LH_OK) return st;
   *kinetic = 0.5 * kv;
   LH_CK(m, launch_mass_l2(m->P, m->stream, u + 2 * n1, t));
-  LH_CK(m, launch_mdot(m->stream, t, 1, 0, nullptr, m->P.NEd, m->d_part, m->d_scalar));
+  LH_CK(m, launch_mdot(m->stream, t, 1, 0, nullptr, m->P.NEd, 0, m->d_part, m->d_counter, m->d_scalar));
   LH_CK(m, cudaMemcpyAsync(internal, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   LH_CK(m, cudaStreamSynchronize(m->stream));
   return LH_OK;
@@ -468,9 +698,16 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   if (opts_in) o = *opts_in; else lh_newton_opts_init(&o);
   if (o.restart < 1 || o.restart > 64) return fail(m, LH_EINVAL, "restart must be in 1..64");
   if (o.jvp_prec != LH_FP64 && o.jvp_prec != LH_FP32) return fail(m, LH_EINVAL, "unsupported jvp_prec");
+  if (o.precond != 0 && o.precond != 1) return fail(m, LH_EINVAL, "precond must be 0 or 1");
   if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
   lh_status st = ensure_work(m, o.restart);
   if (st != LH_OK) return st;
+  float* rec = nullptr;
+  if (o.jvp_prec == LH_FP32) {
+    if ((st = ensure_rec(m)) != LH_OK) return st;
+    rec = m->d_rec;
+  }
+  m->rec_valid = false;   // the record will describe this step's internal iterates
   lh_step_stats S;
   std::memset(&S, 0, sizeof(S));
   const long long n = m->n;
@@ -493,11 +730,11 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
     LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
   }
   double mind, nr2;
-  if ((st = residual_min(m, u, k, tau, r, &mind)) != LH_OK) return st;
+  if ((st = residual_min(m, u, k, tau, r, &mind, rec)) != LH_OK) return st;
   ++S.residual_evals;
   if (!(mind > 0.0) && k_prev) {   // a tangled initial guess: restart from k = 0
     LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
-    if ((st = residual_min(m, u, k, tau, r, &mind)) != LH_OK) return st;
+    if ((st = residual_min(m, u, k, tau, r, &mind, rec)) != LH_OK) return st;
     ++S.residual_evals;
   }
   if (!(mind > 0.0)) return fail(m, LH_ETANGLED, "lh_newton_step: det J <= 0 at the initial guess");
@@ -520,19 +757,41 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
       int j = 0;
       for (; j < mres && total < o.gmres_maxit; ++j) {
         double* vj = V + (long long)j * n;
-        LH_CK(m, launch_precond(s, m->P, m->d_diagMv, m->d_invMe, vj, z));
-        if ((st = apply_jvp(m, u, k, tau, z, w, o.jvp_prec)) != LH_OK) return st;
+        if ((st = apply_prec_jvp(m, o.precond, u, k, tau, vj, z, w, o.jvp_prec)) != LH_OK) return st;
         ++S.jvp_evals;
-        // classical Gram-Schmidt, twice
-        LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, m->d_part, dh));
+        // classical Gram-Schmidt in one fused reduction (V^T w and w.w), with the norm of
+        // the projected vector by Pythagoras; a second pass (DGKS criterion) when more
+        // than half of the norm cancelled
+        LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
         LH_CK(m, launch_gemv_sub(s, V, j + 1, n, dh, w, n));
-        LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, m->d_part, dh + 64));
-        LH_CK(m, launch_gemv_sub(s, V, j + 1, n, dh + 64, w, n));
-        LH_CK(m, launch_mdot(s, w, 1, 0, w, n, m->d_part, dh + 128));
-        LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * 129, cudaMemcpyDeviceToHost, s));
+        LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
         LH_CK(m, cudaStreamSynchronize(s));
-        const double hn = std::sqrt(hcol[128]);
-        for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = hcol[i] + hcol[64 + i];
+        double ww = hcol[j + 1], hh = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          H[(size_t)i * mres + j] = hcol[i];
+          hh += hcol[i] * hcol[i];
+        }
+        double hn2 = ww - hh;
+        if (!(hn2 > 0.5 * ww)) {
+          LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
+          LH_CK(m, launch_gemv_sub(s, V, j + 1, n, dh, w, n));
+          LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+          LH_CK(m, cudaStreamSynchronize(s));
+          ++S.reorth;
+          double hh2 = 0.0;
+          for (int i = 0; i <= j; ++i) {
+            H[(size_t)i * mres + j] += hcol[i];
+            hh2 += hcol[i] * hcol[i];
+          }
+          hn2 = hcol[j + 1] - hh2;
+          if (!(hn2 > 1e-4 * hcol[j + 1])) {   // still cancelling: take the exact norm
+            double e2;
+            if ((st = dot_host(m, w, w, n, &e2)) != LH_OK) return st;
+            hn2 = e2;
+          }
+        }
+        if (!std::isfinite(hn2)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite Krylov vector");
+        const double hn = std::sqrt(std::fmax(hn2, 0.0));
         H[(size_t)(j + 1) * mres + j] = hn;
         if (hn > 0.0) LH_CK(m, launch_axpby(s, 1.0 / hn, w, 0.0, V + (long long)(j + 1) * n, n));
         for (int i = 0; i < j; ++i) {   // previous Givens rotations
@@ -564,7 +823,7 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
       }
       LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
       LH_CK(m, launch_gemv(s, V, j, n, dh, 0.0, w, n));
-      LH_CK(m, launch_precond(s, m->P, m->d_diagMv, m->d_invMe, w, z));
+      LH_CK(m, apply_prec(m, o.precond, w, z, tau));
       LH_CK(m, launch_axpby(s, 1.0, z, 1.0, dk, n));
       if (lin_done || total >= o.gmres_maxit) break;
       // restart: r_lin = -r - J dk
@@ -584,21 +843,23 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
     for (int hlv = 0; hlv <= o.max_halvings; ++hlv) {
       LH_CK(m, cudaMemcpyAsync(kt, k, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       LH_CK(m, launch_axpby(s, lam, dk, 1.0, kt, n));
-      if ((st = residual_min(m, u, kt, tau, rt, &mind)) != LH_OK) return st;
+      if ((st = residual_min(m, u, kt, tau, rt, &mind, rec)) != LH_OK) return st;
       ++S.residual_evals;
-      if (mind > 0.0) {
-        accepted = true;
-        break;
+      if (mind > 0.0) {   // reject tangled trials (Sec. 3.5) and, as well, non-finite ones
+        if ((st = dot_host(m, rt, rt, n, &nr2)) != LH_OK) return st;
+        if (std::isfinite(nr2)) {
+          accepted = true;
+          break;
+        }
       }
       lam *= 0.5;
       ++S.backtracks;
     }
-    if (!accepted) return fail(m, LH_ETANGLED, "lh_newton_step: line search could not keep det J > 0");
+    if (!accepted) return fail(m, LH_ETANGLED, "lh_newton_step: line search found no trial with det J > 0 "
+                                               "and a finite residual");
     std::swap(k, kt);
     std::swap(r, rt);
-    if ((st = dot_host(m, r, r, n, &nr2)) != LH_OK) return st;
     nr = std::sqrt(nr2);
-    if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite residual");
     S.min_detj = mind;
     ++S.newton_its;
     conv = nr <= std::fmax(o.newton_rtol * S.r0, o.newton_atol);
@@ -614,6 +875,34 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
 }
 
 const char* lh_last_error(const lh_mesh* m) { return m ? m->err.c_str() : g_err.c_str(); }
+
+lh_status lh_profile_enable(lh_mesh* m, int enable) {
+  if (!m) return fail(nullptr, LH_EINVAL, "mesh is NULL");
+  Prof& p = m->prof;
+  if (enable && !p.ev[0]) {
+    for (int i = 0; i < 2 * Prof::kMax; ++i) LH_CK(m, cudaEventCreate(&p.ev[i]));
+  }
+  if (!enable) LH_CK(m, prof_flush(m));
+  p.n = 0;
+  for (int i = 0; i < 8; ++i) {
+    p.ms[i] = 0.0;
+    p.cnt[i] = 0;
+  }
+  p.on = enable != 0;
+  return LH_OK;
+}
+
+lh_status lh_profile_read(lh_mesh* m, double* ms, long long* count) {
+  if (!m || !ms || !count) return fail(m, LH_EINVAL, "NULL argument to lh_profile_read");
+  LH_CK(m, prof_flush(m));
+  for (int i = 0; i < LH_PROF_KINDS; ++i) {
+    ms[i] = m->prof.ms[i];
+    count[i] = m->prof.cnt[i];
+  }
+  return LH_OK;
+}
+
+long long lh_launch_count(void) { return launches(); }
 
 lh_status lh_probe_fma(int prec, double* tflops) {
   if (!tflops) return fail(nullptr, LH_EINVAL, "tflops is NULL");

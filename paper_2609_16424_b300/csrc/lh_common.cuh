@@ -27,64 +27,64 @@ struct Cfg {
 template <class T>
 struct Dual {
   T v, d;
-  __device__ __forceinline__ Dual() {}
-  __device__ __forceinline__ Dual(T a) : v(a), d(T(0)) {}
-  __device__ __forceinline__ Dual(T a, T b) : v(a), d(b) {}
+  __host__ __device__ __forceinline__ Dual() {}
+  __host__ __device__ __forceinline__ Dual(T a) : v(a), d(T(0)) {}
+  __host__ __device__ __forceinline__ Dual(T a, T b) : v(a), d(b) {}
 };
 
-template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator+(Dual<T> a, Dual<T> b) { return {a.v + b.v, a.d + b.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(Dual<T> a, Dual<T> b) { return {a.v - b.v, a.d - b.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(Dual<T> a) { return {-a.v, -a.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator*(Dual<T> a, Dual<T> b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator/(Dual<T> a, Dual<T> b) {
   T q = a.v / b.v;
   return {q, (a.d - q * b.d) / b.v};
 }
-template <class T> __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return {a.v + b, a.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator+(T a, Dual<T> b) { return {a + b.v, b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return {a.v - b, a.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return {a - b.v, -b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
-template <class T> __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
-template <class T> __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { return {a.v / b, a.d / b}; }
-template <class T> __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) {
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator+(Dual<T> a, T b) { return {a.v + b, a.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator+(T a, Dual<T> b) { return {a + b.v, b.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(Dual<T> a, T b) { return {a.v - b, a.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator-(T a, Dual<T> b) { return {a - b.v, -b.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator*(Dual<T> a, T b) { return {a.v * b, a.d * b}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator*(T a, Dual<T> b) { return {a * b.v, a * b.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator/(Dual<T> a, T b) { return {a.v / b, a.d / b}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> operator/(T a, Dual<T> b) {
   T q = a / b.v;
   return {q, -q * b.d / b.v};
 }
-template <class T> __device__ __forceinline__ Dual<T>& operator+=(Dual<T>& a, Dual<T> b) { a.v += b.v; a.d += b.d; return a; }
+template <class T> __host__ __device__ __forceinline__ Dual<T>& operator+=(Dual<T>& a, Dual<T> b) { a.v += b.v; a.d += b.d; return a; }
 
 // scalar math, overloaded for T and Dual<T>
-__device__ __forceinline__ double lsqrt(double a) { return sqrt(a); }
-__device__ __forceinline__ float lsqrt(float a) { return sqrtf(a); }
-__device__ __forceinline__ double ltanh(double a) { return tanh(a); }
-__device__ __forceinline__ float ltanh(float a) { return tanhf(a); }
-__device__ __forceinline__ double lcbrt(double a) { return cbrt(a); }
-__device__ __forceinline__ float lcbrt(float a) { return cbrtf(a); }
-__device__ __forceinline__ double lcos(double a) { return cos(a); }
-__device__ __forceinline__ float lcos(float a) { return cosf(a); }
-__device__ __forceinline__ double lsin(double a) { return sin(a); }
-__device__ __forceinline__ float lsin(float a) { return sinf(a); }
+__host__ __device__ __forceinline__ double lsqrt(double a) { return ::sqrt(a); }
+__host__ __device__ __forceinline__ float lsqrt(float a) { return ::sqrtf(a); }
+__host__ __device__ __forceinline__ double ltanh(double a) { return ::tanh(a); }
+__host__ __device__ __forceinline__ float ltanh(float a) { return ::tanhf(a); }
+__host__ __device__ __forceinline__ double lcbrt(double a) { return ::cbrt(a); }
+__host__ __device__ __forceinline__ float lcbrt(float a) { return ::cbrtf(a); }
+__host__ __device__ __forceinline__ double lcos(double a) { return ::cos(a); }
+__host__ __device__ __forceinline__ float lcos(float a) { return ::cosf(a); }
+__host__ __device__ __forceinline__ double lsin(double a) { return ::sin(a); }
+__host__ __device__ __forceinline__ float lsin(float a) { return ::sinf(a); }
 
-template <class T> __device__ __forceinline__ Dual<T> lsqrt(Dual<T> a) {
+template <class T> __host__ __device__ __forceinline__ Dual<T> lsqrt(Dual<T> a) {
   T s = lsqrt(a.v);
   return {s, a.d * (T(0.5) / s)};
 }
-template <class T> __device__ __forceinline__ Dual<T> ltanh(Dual<T> a) {
+template <class T> __host__ __device__ __forceinline__ Dual<T> ltanh(Dual<T> a) {
   T t = ltanh(a.v);
   return {t, a.d * (T(1) - t * t)};
 }
-template <class T> __device__ __forceinline__ Dual<T> lcbrt(Dual<T> a) {
+template <class T> __host__ __device__ __forceinline__ Dual<T> lcbrt(Dual<T> a) {
   T c = lcbrt(a.v);
   return {c, a.d * c / (T(3) * a.v)};
 }
-template <class T> __device__ __forceinline__ Dual<T> lcos(Dual<T> a) { return {lcos(a.v), -lsin(a.v) * a.d}; }
+template <class T> __host__ __device__ __forceinline__ Dual<T> lcos(Dual<T> a) { return {lcos(a.v), -lsin(a.v) * a.d}; }
 
 // x^(1/DIM) for the volume-scaled length of Eq. (14)
-template <int DIM, class S> __device__ __forceinline__ S root_dim(S x) {
+template <int DIM, class S> __host__ __device__ __forceinline__ S root_dim(S x) {
   if constexpr (DIM == 2) return lsqrt(x); else return lcbrt(x);
 }
 
-template <class T> __device__ __forceinline__ T value_of(T a) { return a; }
-template <class T> __device__ __forceinline__ T value_of(Dual<T> a) { return a.v; }
+template <class T> __host__ __device__ __forceinline__ T value_of(T a) { return a; }
+template <class T> __host__ __device__ __forceinline__ T value_of(Dual<T> a) { return a.v; }
 
 }  // namespace lh

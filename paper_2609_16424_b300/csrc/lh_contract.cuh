@@ -22,8 +22,9 @@ struct H1Scratch {
   static constexpr int SF = (DIM + 1) * NC * (DIM == 3 ? Q * Q * Q : Q * Q);
 };
 
-// values and reference gradients of NC H1 fields at this thread's quadrature point
-template <int DIM, int K, int NC, class T>
+// values (if VAL; 3D only skips them) and reference gradients of NC H1 fields at this
+// thread's quadrature point
+template <int DIM, int K, int NC, class T, bool VAL = true>
 __device__ __forceinline__ void h1_fwd(const T* __restrict__ in, T* t1, T* t2, const T* B, const T* G,
                                        int lt, T (&val)[NC], T (&grad)[NC][DIM]) {
   constexpr int D = K + 1, Q = 2 * K;
@@ -69,7 +70,7 @@ __device__ __forceinline__ void h1_fwd(const T* __restrict__ in, T* t1, T* t2, c
       for (int a2 = 0; a2 < D; ++a2) {
         const T b = B[q2 * D + a2], g = G[q2 * D + a2];
         const int o = base + a2 * Q * Q;
-        v += b * t2[o];
+        if constexpr (VAL) v += b * t2[o];
         dy += b * t2[S2 + o];
         dx += b * t2[2 * S2 + o];
         dz += g * t2[o];

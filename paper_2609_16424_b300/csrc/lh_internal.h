@@ -20,6 +20,33 @@ struct ElemParams {
   double h0, inv_hc, q1, q2, scoef, eps2;
   int visc, tg;
   unsigned bc;
+  // float copies for the FP32 tangent kernels (no conversions on the FP64 pipe there)
+  float fh0, finv_hc, fq1, fq2, fscoef, feps2, finv_detJ0;
+  const float* fmq0;       // device [NE]: rho0 detJ0
+  const float* fgm1;       // device [NE]: gamma - 1
+  const float* fggm1;      // device [NE]: gamma (gamma - 1)
+};
+
+// floats per quadrature point in the linearisation record: J, grad_hat v, e (and x_q in 2D)
+inline int rec_len(int dim) { return dim == 3 ? 19 : 11; }
+
+// Kronecker factors of the H1 mass inverse (lh_prec.cu); device pointers owned by the mesh
+struct KronPrec {
+  float* At_free[3] = {nullptr, nullptr, nullptr};    // transposed 1D inverses, N_d x N_d
+  float* At_fixed[3] = {nullptr, nullptr, nullptr};   // ... with the masked end rows removed
+  double* scale = nullptr;                            // nodal rho0^(-1/2) [NV]
+  float* work = nullptr;                              // 2 x dim x NV floats
+};
+
+// event-pair profiler of element-kernel launches (opt-in)
+struct Prof {
+  static constexpr int kMax = 2048;
+  bool on = false;
+  cudaEvent_t ev[2 * kMax] = {};
+  int kind[kMax] = {};
+  int n = 0;
+  double ms[8] = {};
+  long long cnt[8] = {};
 };
 
 }  // namespace lh
@@ -36,6 +63,7 @@ struct lh_mesh {
   double* d_tab = nullptr;
   double* d_ev = nullptr;          // element scratch: NE * 2*dim * ND doubles
   double* d_part = nullptr;        // reduction partials
+  unsigned* d_counter = nullptr;   // ticket counter of the fused reductions (0 between calls)
   double* d_scalar = nullptr;      // small device scalars
   double* d_diagMv = nullptr;      // diagonal of M_V [NV]
   double* d_invMe = nullptr;       // inverse of the (diagonal) L2 mass [NEd]
@@ -45,6 +73,14 @@ struct lh_mesh {
   double* d_work = nullptr;
   long long work_len = 0;
   float* d_fwork = nullptr;        // FP32 J.w in/out buffers
+  float* d_fconst = nullptr;       // [3 NE] float rho0 detJ0, gamma - 1, gamma (gamma - 1)
+  float* d_rec = nullptr;          // linearisation record [NE][rec_len][NQ] (lazily allocated)
+  const double* rec_u = nullptr;   // arguments of the last lh_linearize (for the LH_FP32_LIN check)
+  const double* rec_k = nullptr;
+  double rec_tau = 0.0;
+  bool rec_valid = false;
   int restart_alloc = 0;
+  lh::KronPrec kron;
+  lh::Prof prof;
   std::string err;
 };

@@ -138,7 +138,8 @@ __device__ __forceinline__ double block_min(double v, double* red) {
 template <int DIM, int K>
 __global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
 k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk, double tau,
-           double* __restrict__ ev, double* __restrict__ Re, double* __restrict__ blockmin) {
+           double* __restrict__ ev, double* __restrict__ Re, double* __restrict__ blockmin,
+           float* __restrict__ rec) {
   using C = Cfg<DIM, K>;
   constexpr int D = C::D, Q = C::Q, ND = C::ND, NL = C::NL, NQ = C::NQ;
   constexpr int NCH = 2 * DIM;
@@ -184,7 +185,8 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
   }
   __syncthreads();
   double hv[NCH], hg[NCH][DIM];
-  h1_fwd<DIM, K, NCH>(s_h, t1, t2, sB, sG, lt, hv, hg);
+  // positions at the quadrature points are only needed by the 2D Taylor-Green source
+  h1_fwd<DIM, K, NCH, double, DIM == 2>(s_h, t1, t2, sB, sG, lt, hv, hg);
   double kvq[DIM];
   l2_fwd<DIM, K, DIM, double, D>(s_kv, t1, t2, sB, lt, kvq);
   double lq[2];
@@ -199,6 +201,22 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
       J[i][r] = hg[i][r];
       Gv[i][r] = hg[DIM + i][r];
     }
+  if (rec && E.valid) {   // linearisation record for the FP32 tangent kernel
+    constexpr int NR = DIM == 3 ? 19 : 11;
+    float* rq = rec + E.e * NR * NQ + lt;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        rq[(i * DIM + r) * NQ] = (float)J[i][r];
+        rq[(DIM * DIM + i * DIM + r) * NQ] = (float)Gv[i][r];
+      }
+    rq[2 * DIM * DIM * NQ] = (float)lq[0];
+    if constexpr (DIM == 2) {
+      rq[(2 * DIM * DIM + 1) * NQ] = (float)hv[0];
+      rq[(2 * DIM * DIM + 2) * NQ] = (float)hv[1];
+    }
+  }
   if (!E.valid) {
 #pragma unroll
     for (int i = 0; i < DIM; ++i) J[i][i] = 1.0;   // keep the idle lanes finite
@@ -227,10 +245,10 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
 // Jacobian action (tangent of the residual along dw = tau dk, plus the mass terms).
 // State gathered in double; in float mode positions are re-centred on the element's
 // first node before rounding so that J keeps full float accuracy.
-template <int DIM, int K, class T>
+template <int DIM, int K, class T, class TO>
 __global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
 k_jvp(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk, double tau,
-      const T* __restrict__ dk, T* __restrict__ ev, T* __restrict__ oute) {
+      const T* __restrict__ dk, T* __restrict__ ev, TO* __restrict__ oute) {
   using C = Cfg<DIM, K>;
   constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ;
   constexpr int NCH = 4 * DIM;   // w_x, w_v, dk_x, dk_v
@@ -330,7 +348,117 @@ k_jvp(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk,
   T gv[1] = {g};
   l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
   if (E.valid)
-    for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = s_l[i];
+    for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = TO(s_l[i]);
+}
+
+// =====================================================================================
+// FP32 Jacobian action from the linearisation record: the primal quadrature-point state
+// (J, grad_hat v, e, rounded from the FP64 residual at the same w) is read instead of
+// being re-gathered and re-contracted; only the direction dk is gathered and contracted.
+template <int DIM, int K, class TO>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ dk,
+          float* __restrict__ ev, TO* __restrict__ oute) {
+  using C = Cfg<DIM, K>;
+  constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q;
+  constexpr int NCH = 2 * DIM;   // dk_x, dk_v
+  constexpr int NR = DIM == 3 ? 19 : 11;
+  using PL = Plan<DIM, K, NCH, 0, 1, DIM>;
+  using TB = Tab<K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  float* sB = smem + TB::B;
+  float* sG = smem + TB::G;
+  float* sBl = smem + TB::BL;
+  float* sW = smem + TB::W;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  float* s_h = smem + PL::HEAD + eb * PL::PER;
+  float* s_l = s_h + NCH * ND;
+  float* t1 = s_l + NL;
+  float* t2 = t1 + PL::T1;
+  float* sf = t2 + PL::T2;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  for (int i = lt; i < NCH * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    s_h[i] = E.valid ? dk[comp * P.NV + node_of<DIM, K>(P, E, a)] : 0.f;
+  }
+  for (int i = lt; i < NL; i += NQ) s_l[i] = E.valid ? dk[2 * DIM * P.NV + E.e * NL + i] : 0.f;
+  // primal state at this quadrature point
+  float J0[DIM][DIM], Gv0[DIM][DIM], e0 = 1.f, xq[2] = {0.f, 0.f};
+  {
+    const float* rq = rec + (E.valid ? E.e : 0) * NR * NQ + lt;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        J0[i][r] = E.valid ? rq[(i * DIM + r) * NQ] : (i == r ? 1.f : 0.f);
+        Gv0[i][r] = E.valid ? rq[(DIM * DIM + i * DIM + r) * NQ] : 0.f;
+      }
+    if (E.valid) e0 = rq[2 * DIM * DIM * NQ];
+    if constexpr (DIM == 2) {
+      if (E.valid) {
+        xq[0] = rq[(2 * DIM * DIM + 1) * NQ];
+        xq[1] = rq[(2 * DIM * DIM + 2) * NQ];
+      }
+    }
+  }
+  __syncthreads();
+  float hv[NCH], hg[NCH][DIM];
+  h1_fwd<DIM, K, NCH, float, true>(s_h, t1, t2, sB, sG, lt, hv, hg);
+  float lq[1];
+  l2_fwd<DIM, K, 1>(s_l, t1, t2, sBl, lt, lq);
+
+  QpC<float> c;
+  {
+    const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+    float a = sW[q0] * sW[q1];
+    if constexpr (DIM == 3) a *= sW[q2];
+    const long long ee = E.valid ? E.e : 0;
+    c.alpha = a;
+    c.mq = P.fmq0[ee] * a;
+    c.inv_detJ0 = P.finv_detJ0;
+    c.gm1 = P.fgm1[ee];
+    c.ggm1 = P.fggm1[ee];
+    c.h0 = P.fh0;
+    c.inv_hc = P.finv_hc;
+    c.q1 = P.fq1;
+    c.q2 = P.fq2;
+    c.scoef = P.fscoef;
+    c.eps2 = P.feps2;
+    c.visc = P.visc != 0;
+  }
+  Dual<float> J[DIM][DIM], Gv[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      J[i][r] = Dual<float>(J0[i][r], tau * hg[i][r]);
+      Gv[i][r] = Dual<float>(Gv0[i][r], tau * hg[DIM + i][r]);
+    }
+  Dual<float> So[DIM][DIM], Eo, detJ;
+  qp_forward<DIM>(J, Gv, Dual<float>(e0, tau * lq[0]), c, So, Eo, detJ);
+  float fval[DIM], fgrad[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    fval[i] = c.mq * hv[DIM + i];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) fgrad[i][r] = So[i][r].d;
+  }
+  float g = c.mq * lq[0] - Eo.d;
+  if constexpr (DIM == 2) {
+    if (P.tg) {
+      const Dual<float> x(xq[0], tau * hv[0]), y(xq[1], tau * hv[1]);
+      g -= (c.alpha * detJ * tg_source<Dual<float>, float>(x, y)).d;
+    }
+  }
+  h1_bwd<DIM, K, DIM>(fval, fgrad, sf, t1, t2, sB, sG, lt, s_h);
+  if (E.valid)
+    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
+  float gv[1] = {g};
+  l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
+  if (E.valid)
+    for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = TO(s_l[i]);
 }
 
 // =====================================================================================
@@ -589,7 +717,8 @@ k_dt_estimate(ElemParams P, const double* __restrict__ u, double* __restrict__ b
   const double det = det_adj<DIM>(J, A);
   const double rho = c.mq / (c.alpha * det);
   const double e = lq[0];
-  const double ep = 0.5 * (e + sqrt(e * e + c.eps2));
+  const double sq = sqrt(e * e + c.eps2);
+  const double ep = e >= 0.0 ? 0.5 * (e + sq) : 0.5 * c.eps2 / (sq - e);
   const double cs = sqrt(c.ggm1 * ep);
   double mu = 0.0;
   if (c.visc) {
@@ -670,16 +799,16 @@ __global__ void k_assemble_residual(ElemParams P, const double* __restrict__ u, 
   r[iv] = fixed_node<DIM>(P, nd, comp) ? kk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd);
 }
 
-template <int DIM, int K, class T>
+template <int DIM, int K, class T, class TO>
 __global__ void k_assemble_jvp(ElemParams P, const T* __restrict__ dk, double tau, const T* __restrict__ ev,
-                               T* __restrict__ out) {
+                               TO* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= DIM * P.NV) return;
   const int comp = (int)(i / P.NV);
   const long long nd = i % P.NV;
   const long long iv = DIM * P.NV + i;
-  out[i] = dk[i] - T(tau) * dk[iv];
-  out[iv] = fixed_node<DIM>(P, nd, comp) ? dk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd);
+  out[i] = TO(dk[i] - T(tau) * dk[iv]);
+  out[iv] = TO(fixed_node<DIM>(P, nd, comp) ? dk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd));
 }
 
 template <int DIM, int K>
@@ -780,48 +909,83 @@ static cudaError_t prep(size_t bytes) {
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+static long long g_launches = 0;
+void count_launches(int n) { __atomic_add_fetch(&g_launches, (long long)n, __ATOMIC_RELAXED); }
+long long launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+static inline void mark(cudaEvent_t* ev2, int i, cudaStream_t s) {
+  if (ev2) cudaEventRecord(ev2[i], s);
+}
+
 template <int DIM, int K>
 struct Launch {
   using C = Cfg<DIM, K>;
   static unsigned grid(const ElemParams& P) { return (unsigned)((P.NE + C::EPB - 1) / C::EPB); }
 
   static cudaError_t residual(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                              double* ev, double* Re, double* bmin, double* r) {
+                              double* ev, double* Re, double* bmin, double* r, cudaEvent_t* ev2, float* rec) {
     using PL = Plan<DIM, K, 2 * DIM, DIM, 2, DIM>;
     const size_t by = PL::bytes(sizeof(double));
     cudaError_t e = prep<k_residual<DIM, K>>(by);
     if (e != cudaSuccess) return e;
-    k_residual<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, ev, Re, bmin);
+    mark(ev2, 0, s);
+    k_residual<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, ev, Re, bmin, rec);
+    mark(ev2, 1, s);
+    count_launches(2);
     k_assemble_residual<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, u, k, tau, ev, r);
     return cudaGetLastError();
   }
-  template <class T>
+  template <class T, class TO>
   static cudaError_t jvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                         const T* dk, T* ev, T* out) {
+                         const T* dk, T* ev, TO* out, cudaEvent_t* ev2) {
     using PL = Plan<DIM, K, 4 * DIM, 0, 2, DIM>;
     const size_t by = PL::bytes(sizeof(T));
-    cudaError_t e = prep<k_jvp<DIM, K, T>>(by);
+    cudaError_t e = prep<k_jvp<DIM, K, T, TO>>(by);
     if (e != cudaSuccess) return e;
-    k_jvp<DIM, K, T><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, dk, ev, out + 2 * DIM * P.NV);
-    k_assemble_jvp<DIM, K, T><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    mark(ev2, 0, s);
+    k_jvp<DIM, K, T, TO><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, dk, ev, out + 2 * DIM * P.NV);
+    mark(ev2, 1, s);
+    count_launches(2);
+    k_assemble_jvp<DIM, K, T, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    return cudaGetLastError();
+  }
+  template <class TO>
+  static cudaError_t jvp_rec(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
+                             float* ev, TO* out, cudaEvent_t* ev2) {
+    using PL = Plan<DIM, K, 2 * DIM, 0, 1, DIM>;
+    const size_t by = PL::bytes(sizeof(float));
+    cudaError_t e = prep<k_jvp_rec<DIM, K, TO>>(by);
+    if (e != cudaSuccess) return e;
+    mark(ev2, 0, s);
+    k_jvp_rec<DIM, K, TO><<<grid(P), C::THREADS, by, s>>>(P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV);
+    mark(ev2, 1, s);
+    count_launches(2);
+    k_assemble_jvp<DIM, K, float, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
     return cudaGetLastError();
   }
   static cudaError_t jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                          const double* y, double* ev, double* out) {
+                          const double* y, double* ev, double* out, cudaEvent_t* ev2) {
     using PL = Plan<DIM, K, 3 * DIM, 0, 2, 2 * DIM>;
     const size_t by = PL::bytes(sizeof(double));
     cudaError_t e = prep<k_jtvp<DIM, K>>(by);
     if (e != cudaSuccess) return e;
+    mark(ev2, 0, s);
     k_jtvp<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, y, ev, out + 2 * DIM * P.NV);
+    mark(ev2, 1, s);
+    count_launches(2);
     k_assemble_jtvp<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, y, tau, ev, out);
     return cudaGetLastError();
   }
-  static cudaError_t mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out) {
+  static cudaError_t mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out,
+                             cudaEvent_t* ev2) {
     using PL = Plan<DIM, K, DIM, 0, 0, DIM>;
     const size_t by = PL::bytes(sizeof(double));
     cudaError_t e = prep<k_mass_h1<DIM, K>>(by);
     if (e != cudaSuccess) return e;
+    mark(ev2, 0, s);
     k_mass_h1<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, f, ev);
+    mark(ev2, 1, s);
+    count_launches(2);
     k_assemble_sum<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, ev, DIM, out);
     return cudaGetLastError();
   }
@@ -831,6 +995,7 @@ struct Launch {
     cudaError_t e = prep<k_mass_l2<DIM, K>>(by);
     if (e != cudaSuccess) return e;
     k_mass_l2<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, g, out);
+    count_launches(1);
     return cudaGetLastError();
   }
   static cudaError_t dt_estimate(const ElemParams& P, cudaStream_t s, const double* u, double* bmin) {
@@ -839,52 +1004,68 @@ struct Launch {
     cudaError_t e = prep<k_dt_estimate<DIM, K>>(by);
     if (e != cudaSuccess) return e;
     k_dt_estimate<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, bmin);
+    count_launches(1);
     return cudaGetLastError();
   }
   static cudaError_t setup(const ElemParams& P, cudaStream_t s, double* ev, double* diag, double* invme) {
     k_diag_mv_elem<DIM, K><<<nblk(P.NE * C::ND, 256), 256, 0, s>>>(P, ev);
     k_assemble_sum<DIM, K><<<nblk(P.NV, 256), 256, 0, s>>>(P, ev, 1, diag);
     k_inv_me<DIM, K><<<nblk(P.NE * C::NL, 256), 256, 0, s>>>(P, invme);
+    count_launches(3);
     return cudaGetLastError();
   }
   static cudaError_t initial_nodes(const ElemParams& P, cudaStream_t s, double* x0) {
     k_initial_nodes<DIM, K><<<nblk(P.NV, 256), 256, 0, s>>>(P, x0);
+    count_launches(1);
     return cudaGetLastError();
   }
 };
 
-#define LH_DISPATCH(P, CALL)                                             \
+#define LH_DISPATCH(P, ...)                                             \
   switch ((P).dim * 10 + (P).K) {                                        \
-    case 21: return Launch<2, 1>::CALL;                                  \
-    case 22: return Launch<2, 2>::CALL;                                  \
-    case 23: return Launch<2, 3>::CALL;                                  \
-    case 24: return Launch<2, 4>::CALL;                                  \
-    case 31: return Launch<3, 1>::CALL;                                  \
-    case 32: return Launch<3, 2>::CALL;                                  \
-    case 33: return Launch<3, 3>::CALL;                                  \
-    case 34: return Launch<3, 4>::CALL;                                  \
+    case 21: return Launch<2, 1>::__VA_ARGS__;                                  \
+    case 22: return Launch<2, 2>::__VA_ARGS__;                                  \
+    case 23: return Launch<2, 3>::__VA_ARGS__;                                  \
+    case 24: return Launch<2, 4>::__VA_ARGS__;                                  \
+    case 31: return Launch<3, 1>::__VA_ARGS__;                                  \
+    case 32: return Launch<3, 2>::__VA_ARGS__;                                  \
+    case 33: return Launch<3, 3>::__VA_ARGS__;                                  \
+    case 34: return Launch<3, 4>::__VA_ARGS__;                                  \
     default: return cudaErrorInvalidValue;                               \
   }
 
 cudaError_t launch_residual(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                            double* ev, double* bmin, double* r) {
+                            double* ev, double* bmin, double* r, cudaEvent_t* ev2, float* rec) {
   double* Re = r + 2 * P.dim * P.NV;
-  LH_DISPATCH(P, residual(P, s, u, k, tau, ev, Re, bmin, r))
+  LH_DISPATCH(P, residual(P, s, u, k, tau, ev, Re, bmin, r, ev2, rec))
+}
+cudaError_t launch_jvp_rec_f32(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
+                               float* ev, float* out, cudaEvent_t* ev2) {
+  LH_DISPATCH(P, template jvp_rec<float>(P, s, rec, tau, dk, ev, out, ev2))
+}
+cudaError_t launch_jvp_rec_f64out(const ElemParams& P, cudaStream_t s, const float* rec, double tau,
+                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2) {
+  LH_DISPATCH(P, template jvp_rec<double>(P, s, rec, tau, dk, ev, out, ev2))
 }
 cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                           const double* dk, double* ev, double* out) {
-  LH_DISPATCH(P, template jvp<double>(P, s, u, k, tau, dk, ev, out))
+                           const double* dk, double* ev, double* out, cudaEvent_t* ev2) {
+  LH_DISPATCH(P, template jvp<double, double>(P, s, u, k, tau, dk, ev, out, ev2))
 }
 cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                           const float* dk, float* ev, float* out) {
-  LH_DISPATCH(P, template jvp<float>(P, s, u, k, tau, dk, ev, out))
+                           const float* dk, float* ev, float* out, cudaEvent_t* ev2) {
+  LH_DISPATCH(P, template jvp<float, float>(P, s, u, k, tau, dk, ev, out, ev2))
+}
+cudaError_t launch_jvp_f32_to_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2) {
+  LH_DISPATCH(P, template jvp<float, double>(P, s, u, k, tau, dk, ev, out, ev2))
 }
 cudaError_t launch_jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                        const double* y, double* ev, double* out) {
-  LH_DISPATCH(P, jtvp(P, s, u, k, tau, y, ev, out))
+                        const double* y, double* ev, double* out, cudaEvent_t* ev2) {
+  LH_DISPATCH(P, jtvp(P, s, u, k, tau, y, ev, out, ev2))
 }
-cudaError_t launch_mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out) {
-  LH_DISPATCH(P, mass_h1(P, s, f, ev, out))
+cudaError_t launch_mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out,
+                           cudaEvent_t* ev2) {
+  LH_DISPATCH(P, mass_h1(P, s, f, ev, out, ev2))
 }
 cudaError_t launch_mass_l2(const ElemParams& P, cudaStream_t s, const double* g, double* out) {
   LH_DISPATCH(P, mass_l2(P, s, g, out))

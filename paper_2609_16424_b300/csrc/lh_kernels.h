@@ -5,16 +5,29 @@
 
 namespace lh {
 
-// element + assembly launchers (lh_kernels.cu); vectors use the layout of include/lh.h
+// kernels launched so far (all launchers add to it)
+void count_launches(int n);
+long long launches();
+
+// element + assembly launchers (lh_kernels.cu); vectors use the layout of include/lh.h.
+// ev2, if not NULL, is an event pair recorded around the element kernel only.
+// rec, if not NULL, receives the linearisation record [NE][rec_len(dim)][NQ] (float)
 cudaError_t launch_residual(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                            double* ev, double* blockmin, double* r);
+                            double* ev, double* blockmin, double* r, cudaEvent_t* ev2 = nullptr,
+                            float* rec = nullptr);
+// FP32 J.w from the linearisation record (float or double output)
+cudaError_t launch_jvp_rec_f32(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
+                               float* ev, float* out, cudaEvent_t* ev2 = nullptr);
+cudaError_t launch_jvp_rec_f64out(const ElemParams& P, cudaStream_t s, const float* rec, double tau,
+                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                           const double* dk, double* ev, double* out);
+                           const double* dk, double* ev, double* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                           const float* dk, float* ev, float* out);
+                           const float* dk, float* ev, float* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
-                        const double* y, double* ev, double* out);
-cudaError_t launch_mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out);
+                        const double* y, double* ev, double* out, cudaEvent_t* ev2 = nullptr);
+cudaError_t launch_mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out,
+                           cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_mass_l2(const ElemParams& P, cudaStream_t s, const double* g, double* out);
 cudaError_t launch_dt_estimate(const ElemParams& P, cudaStream_t s, const double* u, double* blockmin);
 cudaError_t launch_setup(const ElemParams& P, cudaStream_t s, double* ev, double* diag_mv, double* inv_me);
@@ -25,10 +38,11 @@ unsigned elem_grid(const ElemParams& P);
 // index range (a function of n only) and fixed-order sums.
 constexpr int kRedBlocks = 592;     // 4 x 148 SMs
 constexpr int kRedThreads = 256;
-// out_dev[j] = sum_i V[j*ld + i] * w[i] for j < m (w == NULL: plain sums);
-// partials: kRedBlocks * m doubles
+// out_dev[j] = sum_i V[j*ld + i] * w[i] for j < m (w == NULL: plain sums of V_j), and
+// out_dev[m] = w . w when with_self; one launch, deterministic.  partials: kRedBlocks *
+// (m + 1) doubles (m + with_self <= 72); counter: a device unsigned that is 0 between calls.
 cudaError_t launch_mdot(cudaStream_t s, const double* V, int m, long long ld, const double* w, long long n,
-                        double* partials, double* out_dev);
+                        int with_self, double* partials, unsigned* counter, double* out_dev);
 // out_dev[0] = min(v[0..n))
 cudaError_t launch_min(cudaStream_t s, const double* v, long long n, double* out_dev);
 // w -= sum_j h[j] V[j*ld + .]  (h on the device, m <= 64)
@@ -41,9 +55,21 @@ cudaError_t launch_axpby(cudaStream_t s, double a, const double* x, double b, do
 cudaError_t launch_scale_copy(cudaStream_t s, const double* x, const double* scale_dev, double* y, long long n);
 cudaError_t launch_to_f32(cudaStream_t s, const double* x, float* y, long long n);
 cudaError_t launch_to_f64(cudaStream_t s, const float* x, double* y, long long n);
-// block-diagonal preconditioner z = diag(I, diag(M_V)^-1 (identity on fixed rows), M_E^-1) r
+// block upper-triangular preconditioner: z_v = diag(M_V)^-1 r_v (identity on fixed rows),
+// z_x = r_x + tau z_v, z_e = M_E^-1 r_e
 cudaError_t launch_precond(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
-                           const double* r, double* z);
+                           const double* r, double* z, double tau);
+// the same preconditioner written to a float vector (input of the FP32 J.w)
+cudaError_t launch_precond_f32(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
+                               const double* r, float* z, double tau);
+// J.w with float arithmetic, float input and double output (inside the FP64 Krylov solver)
+cudaError_t launch_jvp_f32_to_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
+                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2 = nullptr);
+// z = P^-1 r with the Kronecker H1 mass inverse on the v rows (lh_prec.cu)
+cudaError_t launch_kron_prec(cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* inv_me,
+                             const double* r, double* z, double tau);
+cudaError_t launch_kron_prec_f32(cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* inv_me,
+                                 const double* r, float* z, double tau);
 // z = r / diag (component-wise H1 Jacobi, dim*NV entries, diag has NV entries)
 cudaError_t launch_jacobi_h1(cudaStream_t s, long long nv, int dim, const double* diag, const double* r, double* z);
 cudaError_t launch_mul(cudaStream_t s, const double* a, const double* b, double* y, long long n);

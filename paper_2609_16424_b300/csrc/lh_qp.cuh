@@ -23,7 +23,7 @@ struct QpC {
 };
 
 template <int DIM, class S>
-__device__ __forceinline__ S det_adj(const S (&J)[DIM][DIM], S (&A)[DIM][DIM]) {
+__host__ __device__ __forceinline__ S det_adj(const S (&J)[DIM][DIM], S (&A)[DIM][DIM]) {
   if constexpr (DIM == 2) {
     A[0][0] = J[1][1];
     A[0][1] = -J[0][1];
@@ -51,7 +51,7 @@ __device__ __forceinline__ S det_adj(const S (&J)[DIM][DIM], S (&A)[DIM][DIM]) {
 //   and detJ.
 // Works for S = T (residual) and S = Dual<T> (tangent of Eq. (10)).
 template <int DIM, class S, class T>
-__device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], const S (&Gv)[DIM][DIM], S e,
+__host__ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], const S (&Gv)[DIM][DIM], S e,
                                            const QpC<T>& c, S (&So)[DIM][DIM], S& Eo, S& detJ) {
   S A[DIM][DIM];
   const S det = det_adj<DIM>(J, A);
@@ -64,7 +64,10 @@ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], const S (&Gv)
     for (int j = 0; j < DIM; ++j) Jinv[i][j] = A[i][j] * inv_det;
   const S W = c.alpha * det;                       // current-domain quadrature weight
   const S rho = c.mq / W;                          // rho = rho0 detJ0 / detJ
-  const S ep = T(0.5) * (e + lsqrt(e * e + c.eps2));   // Eq. (19)
+  // Eq. (19); for e < 0 the identical expression eps^2 / (2 (sqrt(e^2 + eps^2) - e)) is
+  // used, free of the cancellation that would round e+ to 0 for strongly negative e
+  const S sq = lsqrt(e * e + c.eps2);
+  const S ep = value_of(e) >= T(0) ? T(0.5) * (e + sq) : T(0.5) * c.eps2 / (sq - e);
   const S p = c.gm1 * rho * ep;                    // Eq. (20)
   const S cs = lsqrt(c.ggm1 * ep);                 // Eq. (20)
   S Lv[DIM][DIM];                                  // physical velocity gradient
@@ -115,13 +118,13 @@ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], const S (&Gv)
 // Taylor-Green manufactured energy source per unit volume (gamma = 5/3):
 //   s = (3 pi / 8) [cos 3 pi x cos pi y - cos pi x cos 3 pi y]
 template <class S, class T>
-__device__ __forceinline__ S tg_source(S x, S y) {
+__host__ __device__ __forceinline__ S tg_source(S x, S y) {
   const T pi = T(3.14159265358979323846);
   return (T(3) * pi / T(8)) * (lcos(T(3) * pi * x) * lcos(pi * y) - lcos(pi * x) * lcos(T(3) * pi * y));
 }
 
 template <class T>
-__device__ __forceinline__ void tg_source_grad(T x, T y, T& sx, T& sy) {
+__host__ __device__ __forceinline__ void tg_source_grad(T x, T y, T& sx, T& sy) {
   const T pi = T(3.14159265358979323846);
   const T c = T(3) * pi / T(8);
   sx = c * (-T(3) * pi * lsin(T(3) * pi * x) * lcos(pi * y) + pi * lsin(pi * x) * lcos(T(3) * pi * y));
@@ -132,7 +135,7 @@ __device__ __forceinline__ void tg_source_grad(T x, T y, T& sx, T& sy) {
 // extra adjoint detb_in on detJ, return Jb, Gvb, eb.  Hand-written: the primal is
 // recomputed, then each statement of qp_forward is transposed in reverse order.
 template <int DIM, class T>
-__device__ __forceinline__ void qp_adjoint(const T (&J)[DIM][DIM], const T (&Gv)[DIM][DIM], T e,
+__host__ __device__ __forceinline__ void qp_adjoint(const T (&J)[DIM][DIM], const T (&Gv)[DIM][DIM], T e,
                                            const QpC<T>& c, const T (&Sb)[DIM][DIM], T Eb, T detb_in,
                                            T (&Jb)[DIM][DIM], T (&Gvb)[DIM][DIM], T& eb) {
   // ---- primal
@@ -145,7 +148,7 @@ __device__ __forceinline__ void qp_adjoint(const T (&J)[DIM][DIM], const T (&Gv)
   const T W = c.alpha * det;
   const T rho = c.mq / W;
   const T sq = lsqrt(e * e + c.eps2);
-  const T ep = T(0.5) * (e + sq);
+  const T ep = e >= T(0) ? T(0.5) * (e + sq) : T(0.5) * c.eps2 / (sq - e);
   const T p = c.gm1 * rho * ep;
   const T cs = lsqrt(c.ggm1 * ep);
   T Lv[DIM][DIM];
@@ -233,7 +236,8 @@ __device__ __forceinline__ void qp_adjoint(const T (&J)[DIM][DIM], const T (&Gv)
   T epb = csb * c.ggm1 / (T(2) * cs);           // cs = sqrt(g(g-1) ep)
   rhob += pb * c.gm1 * ep;                      // p = (g-1) rho ep
   epb += pb * c.gm1 * rho;
-  eb = epb * T(0.5) * (T(1) + e / sq);          // ep = (e + sqrt(e^2 + eps^2)) / 2
+  // d e+ / d e = (1 + e / sq) / 2, written as eps^2 / (2 sq (sq - e)) for e < 0
+  eb = epb * (e >= T(0) ? T(0.5) * (T(1) + e / sq) : T(0.5) * c.eps2 / (sq * (sq - e)));
   for (int i = 0; i < DIM; ++i)                 // Lv = Gv Jinv
     for (int r = 0; r < DIM; ++r) {
       T s = 0;

@@ -8,55 +8,96 @@ namespace lh {
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// block sum in fixed order (tree over shared memory); result in red[0]
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  red[threadIdx.x] = v;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-    __syncthreads();
-  }
-  const double r = red[0];
-  __syncthreads();
-  return r;
+// Fused deterministic multi-dot: out[j] = V_j . w for j < m, plus out[m] = w . w when
+// with_self.  Each block reduces a fixed contiguous chunk of the index range (one pass
+// over w for up to 8 vectors at a time, fixed-order warp and block trees) and writes its
+// partials; the last block to finish (ticket from an atomic counter) adds the partials of
+// every output in block order.  The result depends only on n and the data, not on the
+// order in which blocks finish.
+constexpr int kChunk = 8;
+
+static inline unsigned red_grid(long long n) {
+  long long g = (n + 1023) / 1024;
+  if (g < 1) g = 1;
+  if (g > kRedBlocks) g = kRedBlocks;
+  return (unsigned)g;
 }
 
-// partials[j * gridDim.x + b] = sum over this block's contiguous chunk of V_j . w
 __global__ void __launch_bounds__(kRedThreads)
-k_mdot_part(const double* __restrict__ V, int m, long long ld, const double* __restrict__ w, long long n,
-            double* __restrict__ part) {
-  __shared__ double red[kRedThreads];
+k_mdot(const double* __restrict__ V, int m, long long ld, const double* __restrict__ w, long long n, int with_self,
+       double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ out) {
+  __shared__ double red[kRedThreads / 32][kChunk];
+  __shared__ bool last;
+  const int nout = m + (with_self ? 1 : 0);
   const long long chunk = (n + gridDim.x - 1) / gridDim.x;
   const long long beg = (long long)blockIdx.x * chunk;
   const long long end = beg + chunk < n ? beg + chunk : n;
-  for (int j = 0; j < m; ++j) {
-    const double* v = V + j * ld;
-    double s = 0.0;
-    if (w) {
-      for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) s += v[i] * w[i];
-    } else {
-      for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) s += v[i];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < nout; c0 += kChunk) {
+    double acc[kChunk];
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
+    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+      const double wi = w ? w[i] : 1.0;
+#pragma unroll
+      for (int q = 0; q < kChunk; ++q) {
+        const int j = c0 + q;
+        if (j < m) acc[q] += V[j * ld + i] * wi;
+        else if (j < nout) acc[q] += wi * wi;
+      }
     }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part[(long long)j * gridDim.x + blockIdx.x] = s;
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kChunk && c0 + (int)threadIdx.x < nout) {
+      double v = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) v += red[q][threadIdx.x];
+      part[(long long)(c0 + threadIdx.x) * gridDim.x + blockIdx.x] = v;
+    }
+    __syncthreads();
   }
-}
-
-__global__ void __launch_bounds__(kRedThreads)
-k_sum_part(const double* __restrict__ part, int nb, int m, double* __restrict__ out) {
-  __shared__ double red[kRedThreads];
-  for (int j = 0; j < m; ++j) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(long long)j * nb + b];
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) out[j] = s;
+  __threadfence();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // last block: out[j] = sum over blocks of the partials, the whole block reducing up to
+  // kChunk outputs at a time (coalesced L2 loads, fixed-order trees)
+  for (int c0 = 0; c0 < nout; c0 += kChunk) {
+    double acc[kChunk];
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+      acc[q] = 0.0;
+      if (c0 + q < nout)
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+          acc[q] += __ldcg(part + (long long)(c0 + q) * gridDim.x + b);
+    }
+#pragma unroll
+    for (int q = 0; q < kChunk; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kChunk && c0 + (int)threadIdx.x < nout) {
+      double v = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) v += red[q][threadIdx.x];
+      out[c0 + threadIdx.x] = v;
+    }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 cudaError_t launch_mdot(cudaStream_t s, const double* V, int m, long long ld, const double* w, long long n,
-                        double* partials, double* out_dev) {
-  k_mdot_part<<<kRedBlocks, kRedThreads, 0, s>>>(V, m, ld, w, n, partials);
-  k_sum_part<<<1, kRedThreads, 0, s>>>(partials, kRedBlocks, m, out_dev);
+                        int with_self, double* partials, unsigned* counter, double* out_dev) {
+  if (m + (with_self ? 1 : 0) > 72) return cudaErrorInvalidValue;
+  k_mdot<<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -75,6 +116,7 @@ __global__ void __launch_bounds__(kRedThreads) k_min(const double* __restrict__ 
 
 cudaError_t launch_min(cudaStream_t s, const double* v, long long n, double* out_dev) {
   k_min<<<1, kRedThreads, 0, s>>>(v, n, out_dev);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -94,6 +136,7 @@ cudaError_t launch_gemv_sub(cudaStream_t s, const double* V, int m, long long ld
                             long long n) {
   if (m > 64) return cudaErrorInvalidValue;
   k_gemv_sub<<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, w, n);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -113,6 +156,7 @@ cudaError_t launch_gemv(cudaStream_t s, const double* V, int m, long long ld, co
                         double* y, long long n) {
   if (m > 64) return cudaErrorInvalidValue;
   k_gemv<<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, beta, y, n);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -122,7 +166,10 @@ __global__ void k_axpby(double a, const double* __restrict__ x, double b, double
 }
 
 cudaError_t launch_axpby(cudaStream_t s, double a, const double* x, double b, double* y, long long n) {
-  if (n > 0) k_axpby<<<nblk(n, 256), 256, 0, s>>>(a, x, b, y, n);
+  if (n > 0) {
+    k_axpby<<<nblk(n, 256), 256, 0, s>>>(a, x, b, y, n);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -134,7 +181,10 @@ __global__ void k_scale_copy(const double* __restrict__ x, const double* __restr
 }
 
 cudaError_t launch_scale_copy(cudaStream_t s, const double* x, const double* scale_dev, double* y, long long n) {
-  if (n > 0) k_scale_copy<<<nblk(n, 256), 256, 0, s>>>(x, scale_dev, y, n);
+  if (n > 0) {
+    k_scale_copy<<<nblk(n, 256), 256, 0, s>>>(x, scale_dev, y, n);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -147,42 +197,65 @@ __global__ void k_to_f64(const float* __restrict__ x, double* __restrict__ y, lo
   if (i < n) y[i] = (double)x[i];
 }
 cudaError_t launch_to_f32(cudaStream_t s, const double* x, float* y, long long n) {
-  if (n > 0) k_to_f32<<<nblk(n, 256), 256, 0, s>>>(x, y, n);
+  if (n > 0) {
+    k_to_f32<<<nblk(n, 256), 256, 0, s>>>(x, y, n);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 cudaError_t launch_to_f64(cudaStream_t s, const float* x, double* y, long long n) {
-  if (n > 0) k_to_f64<<<nblk(n, 256), 256, 0, s>>>(x, y, n);
+  if (n > 0) {
+    k_to_f64<<<nblk(n, 256), 256, 0, s>>>(x, y, n);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
+// velocity rows of the preconditioner: diagonal of M_V, identity on fixed rows
+__device__ __forceinline__ double jacobi_v(const ElemParams& P, const double* __restrict__ dmv,
+                                           const double* __restrict__ r, long long n1, long long j) {
+  const int comp = (int)(j / P.NV);
+  const long long nd = j % P.NV;
+  long long ic;
+  int Nc;
+  if (comp == 0) { ic = nd % P.N0; Nc = P.N0; }
+  else if (comp == 1) { ic = (nd / P.N0) % P.N1; Nc = P.N1; }
+  else { ic = nd / ((long long)P.N0 * P.N1); Nc = P.N2; }
+  const bool fixed = (((P.bc >> (2 * comp)) & 1u) && ic == 0) || (((P.bc >> (2 * comp + 1)) & 1u) && ic == Nc - 1);
+  return fixed ? r[n1 + j] : r[n1 + j] / dmv[nd];
+}
+
+// block upper-triangular preconditioner: z_v = D_V^-1 r_v, z_x = r_x + tau z_v (exact
+// elimination of the dR_x/dk_v = -tau I coupling), z_e = M_E^-1 r_e
+template <class TZ>
 __global__ void k_precond(ElemParams P, const double* __restrict__ dmv, const double* __restrict__ ime,
-                          const double* __restrict__ r, double* __restrict__ z) {
+                          const double* __restrict__ r, TZ* __restrict__ z, double tau) {
   const long long n1 = (long long)P.dim * P.NV;
   const long long n = 2 * n1 + P.NEd;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (i < n1) {
-    z[i] = r[i];
+    z[i] = TZ(r[i] + tau * jacobi_v(P, dmv, r, n1, i));
   } else if (i < 2 * n1) {
-    const long long j = i - n1;
-    const int comp = (int)(j / P.NV);
-    const long long nd = j % P.NV;
-    long long ic;
-    int Nc;
-    if (comp == 0) { ic = nd % P.N0; Nc = P.N0; }
-    else if (comp == 1) { ic = (nd / P.N0) % P.N1; Nc = P.N1; }
-    else { ic = nd / ((long long)P.N0 * P.N1); Nc = P.N2; }
-    const bool fixed = (((P.bc >> (2 * comp)) & 1u) && ic == 0) || (((P.bc >> (2 * comp + 1)) & 1u) && ic == Nc - 1);
-    z[i] = fixed ? r[i] : r[i] / dmv[nd];
+    z[i] = TZ(jacobi_v(P, dmv, r, n1, i - n1));
   } else {
-    z[i] = r[i] * ime[i - 2 * n1];
+    z[i] = TZ(r[i] * ime[i - 2 * n1]);
   }
 }
 
 cudaError_t launch_precond(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
-                           const double* r, double* z) {
+                           const double* r, double* z, double tau) {
   const long long n = 2LL * P.dim * P.NV + P.NEd;
-  k_precond<<<nblk(n, 256), 256, 0, s>>>(P, diag_mv, inv_me, r, z);
+  k_precond<double><<<nblk(n, 256), 256, 0, s>>>(P, diag_mv, inv_me, r, z, tau);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precond_f32(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
+                               const double* r, float* z, double tau) {
+  const long long n = 2LL * P.dim * P.NV + P.NEd;
+  k_precond<float><<<nblk(n, 256), 256, 0, s>>>(P, diag_mv, inv_me, r, z, tau);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -194,6 +267,7 @@ __global__ void k_jacobi_h1(long long nv, int dim, const double* __restrict__ di
 
 cudaError_t launch_jacobi_h1(cudaStream_t s, long long nv, int dim, const double* diag, const double* r, double* z) {
   k_jacobi_h1<<<nblk(nv * dim, 256), 256, 0, s>>>(nv, dim, diag, r, z);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -203,7 +277,10 @@ __global__ void k_mul(const double* __restrict__ a, const double* __restrict__ b
 }
 
 cudaError_t launch_mul(cudaStream_t s, const double* a, const double* b, double* y, long long n) {
-  if (n > 0) k_mul<<<nblk(n, 256), 256, 0, s>>>(a, b, y, n);
+  if (n > 0) {
+    k_mul<<<nblk(n, 256), 256, 0, s>>>(a, b, y, n);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 

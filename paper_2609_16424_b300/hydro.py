@@ -20,14 +20,21 @@ def _ptr(t):
 def newton_opts(**kw):
     """lh_newton_opts with the library defaults, overridden by keyword arguments
     (newton_rtol, newton_atol, gmres_rtol, newton_maxit, gmres_maxit, restart,
-    max_halvings, jvp_prec in {'fp64', 'fp32'})."""
+    max_halvings, jvp_prec in {'fp64', 'fp32'}, precond in {'jacobi', 'kron'})."""
     o = _lib.NewtonOpts()
     _L.lh_newton_opts_init(C.byref(o))
     for key, val in kw.items():
         if key == "jvp_prec":
             val = {"fp64": _lib.LH_FP64, "fp32": _lib.LH_FP32}.get(val, val)
+        if key == "precond":
+            val = {"jacobi": 0, "kron": 1}.get(val, val)
         setattr(o, key, val)
     return o
+
+
+def launch_count():
+    """CUDA kernels launched by liblh.so in this process so far."""
+    return int(_L.lh_launch_count())
 
 
 def probe_fma(prec="fp64"):
@@ -128,11 +135,23 @@ class Mesh:
                                    C.byref(md) if min_detj else None))
         return (out, md.value) if min_detj else out
 
-    def jvp(self, u, k, tau, dk, out=None):
-        """(dR/dk) dk; float64 dk -> FP64 kernel, float32 dk -> FP32 kernel."""
+    def linearize(self, u, k, tau):
+        """Store the FP64 quadrature-point state at w = u + tau k (float) for jvp(lin=True)."""
+        self._vec(u, "u")
+        self._vec(k, "k")
+        self._stream()
+        self._check(_L.lh_linearize(self._h, _ptr(u), _ptr(k), float(tau)))
+
+    def jvp(self, u, k, tau, dk, out=None, lin=False):
+        """(dR/dk) dk; float64 dk -> FP64 kernel, float32 dk -> FP32 kernel (lin=True: from
+        the record of linearize(u, k, tau))."""
         self._vec(u, "u")
         self._vec(k, "k")
         prec = _lib.LH_FP32 if dk.dtype == torch.float32 else _lib.LH_FP64
+        if lin:
+            if dk.dtype != torch.float32:
+                raise ValueError("lin=True needs a float32 direction")
+            prec = _lib.LH_FP32_LIN
         self._vec(dk, "dk", dk.dtype)
         out = self.new(dk.dtype) if out is None else self._vec(out, "out", dk.dtype)
         self._stream()
@@ -180,6 +199,18 @@ class Mesh:
         self._stream()
         self._check(_L.lh_energies(self._h, _ptr(u), C.byref(ke), C.byref(ie)))
         return ke.value, ie.value
+
+    def profile(self, enable=True):
+        """Enable (and reset) or disable the per-kind element-kernel event timers."""
+        self._stream()
+        self._check(_L.lh_profile_enable(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kind: (total device ms, launches)} since the last profile(True)."""
+        ms = (C.c_double * 5)()
+        cnt = (C.c_longlong * 5)()
+        self._check(_L.lh_profile_read(self._h, ms, cnt))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.PROF_KINDS)}
 
     def newton_step(self, u, k_prev, dt, opts=None, **kw):
         """One implicit midpoint step in place on u (and k_prev, if given).  Returns the

@@ -129,3 +129,21 @@ def test_energies(case):
     ke, ie = case.gm.energies(case.dev(case.u))
     assert abs(ke - case.hyd.kinetic_energy(case.u)) <= 1e-13 * abs(ke)
     assert abs(ie - case.hyd.internal_energy(case.u)) <= 1e-13 * abs(ie)
+
+
+def test_jvp_fp32_record_parity(case):
+    """FP32 J.w from the linearisation record (state rounded from the FP64 residual)."""
+    import paper_2609_16424_b300 as lh
+    kk = lh_synth.normal_vector(case.gm.n, 4, 0.1)
+    dk = lh_synth.normal_vector(case.gm.n, 5)
+    tau = 0.02
+    ref = case.hyd.jvp_complex_step(case.u, kk, tau, dk.astype(np.float32).astype(np.float64))
+    u, kd = case.dev(case.u), case.dev(kk)
+    with pytest.raises(lh.LHError):
+        case.gm.jvp(u, kd, tau, case.dev(dk, torch.float32), lin=True)
+    case.gm.linearize(u, kd, tau)
+    got = case.gm.jvp(u, kd, tau, case.dev(dk, torch.float32), lin=True).double().cpu().numpy()
+    rel = case.rel_blocks(got, ref)
+    assert max(rel) <= 2e-5, rel
+    with pytest.raises(lh.LHError):          # a different tau is refused
+        case.gm.jvp(u, kd, tau * 2, case.dev(dk, torch.float32), lin=True)
