@@ -187,6 +187,29 @@ void lh_newton_opts_init(lh_newton_opts* opts);
 lh_status lh_newton_step(lh_mesh* mesh, double* u, double* k_prev, double dt,
                          const lh_newton_opts* opts, lh_step_stats* stats);
 
+/* Stage residual R(k; tau, u), the same operator and kernel as lh_residual, for callers
+ * that must not allocate device memory when they call the library (for example code
+ * inside a host application that owns all device memory through its own pool, or
+ * latency-critical loops that cannot accept cudaMalloc's implicit synchronisation).
+ * The paper has no counterpart; it is a deployment variant.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  The
+ *    element scratch (16 MiB), per-block minima (512 KiB) and 1D tables (2 KiB) live in
+ *    file-scope __device__ arrays that every GPU loading the library holds until exit.
+ *  - Maximum size: NE * dim * (order+1)^dim <= 2^21 (e.g. 3D Q2: NE <= 25890; 2D Q2:
+ *    NE <= 116508); larger meshes are rejected with LH_EINVAL and a message naming the
+ *    limit.  No min det J is returned.
+ *  - desc: as for lh_mesh_create (desc->rho0 / desc->gamma host arrays are ignored; the
+ *    work runs on desc->stream).  rho0, gamma: DEVICE arrays [NE] of initial densities and
+ *    adiabatic indices.  u, k, r: DEVICE [n] double, r must not alias u or k.
+ *  - The first call on each device looks up the device addresses of those arrays
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call shares the arrays and overwrites them (the scratch keeps the last call's
+ *    contents; nothing in it must start at zero).  Calls that overlap on the GPU, e.g. on
+ *    two streams at once, race on them.
+ *  - Asynchronous on desc->stream; errors are reported by lh_last_error(NULL). */
+lh_status lh_residual_noalloc(const lh_mesh_desc* desc, const double* rho0, const double* gamma,
+                              const double* u, const double* k, double tau, double* r);
+
 /* Message for the last failing call on mesh (or a global message if mesh is NULL). */
 const char* lh_last_error(const lh_mesh* mesh);
 

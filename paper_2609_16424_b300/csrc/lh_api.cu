@@ -298,6 +298,70 @@ lh_status residual_min(lh_mesh* m, const double* u, const double* k, double tau,
 
 }  // namespace
 
+namespace lh {
+
+bool check_desc(const lh_mesh_desc* d, std::string* why) {
+  if (!d) { *why = "desc is NULL"; return false; }
+  if (d->dim != 2 && d->dim != 3) { *why = "dim must be 2 or 3"; return false; }
+  if (d->order < 1 || d->order > 4) { *why = "order must be in 1..4"; return false; }
+  if (d->quad_1d != 0 && d->quad_1d != 2 * d->order) {
+    *why = "only 2k Gauss points per direction are supported";
+    return false;
+  }
+  for (int c = 0; c < d->dim; ++c) {
+    if (d->n[c] < 1) { *why = "element counts must be >= 1"; return false; }
+    if (!(d->hi[c] > d->lo[c])) { *why = "box must have hi > lo"; return false; }
+  }
+  if (d->visc && !(d->psi0 > 0.0 && d->psi0 < 1.0)) { *why = "psi0 must be in (0, 1)"; return false; }
+  if (!(d->eps_e > 0.0)) { *why = "eps_e must be > 0"; return false; }
+  if (d->tg_source && d->dim != 2) { *why = "the Taylor-Green source is 2D"; return false; }
+  return true;
+}
+
+void fill_params(const lh_mesh_desc& d, ElemParams* out) {
+  ElemParams& P = *out;
+  P = ElemParams();
+  const int dim = d.dim, K = d.order;
+  P.dim = dim;
+  P.K = K;
+  P.n0 = d.n[0];
+  P.n1 = d.n[1];
+  P.n2 = dim == 3 ? d.n[2] : 1;
+  P.N0 = K * P.n0 + 1;
+  P.N1 = K * P.n1 + 1;
+  P.N2 = dim == 3 ? K * P.n2 + 1 : 1;
+  P.NE = (long long)P.n0 * P.n1 * P.n2;
+  P.NV = (long long)P.N0 * P.N1 * P.N2;
+  long long nl = 1;
+  for (int c = 0; c < dim; ++c) nl *= K;
+  P.NEd = P.NE * nl;
+  double vol = 1.0;
+  P.detJ0 = 1.0;
+  for (int c = 0; c < 3; ++c) {
+    P.lo[c] = c < dim ? d.lo[c] : 0.0;
+    P.h[c] = c < dim ? (d.hi[c] - d.lo[c]) / d.n[c] : 1.0;
+    if (c < dim) {
+      vol *= d.hi[c] - d.lo[c];
+      P.detJ0 *= P.h[c];
+    }
+  }
+  P.h0 = d.h0 > 0 ? d.h0 : std::pow(vol / (double)P.NE, 1.0 / dim);
+  P.inv_hc = 1.0 / (d.h_coarse > 0 ? d.h_coarse : P.h0);
+  P.q1 = d.q1;
+  P.q2 = d.q2;
+  P.scoef = 2.0 * std::atanh(1.0 - 2.0 * d.psi0);
+  P.eps2 = d.eps_e * d.eps_e;
+  P.visc = d.visc;
+  P.tg = d.tg_source;
+  P.bc = d.bc_mask;
+}
+
+std::vector<double> host_tables(int K) { return build_tables(K); }
+
+lh_status set_global_error(lh_status st, const std::string& msg) { return fail(nullptr, st, msg); }
+
+}  // namespace lh
+
 extern "C" {
 
 void lh_mesh_desc_init(lh_mesh_desc* d) {
@@ -333,61 +397,20 @@ void lh_newton_opts_init(lh_newton_opts* o) {
 lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
   if (!out) return fail(nullptr, LH_EINVAL, "out is NULL");
   *out = nullptr;
-  if (!d) return fail(nullptr, LH_EINVAL, "desc is NULL");
-  if (d->dim != 2 && d->dim != 3) return fail(nullptr, LH_EINVAL, "dim must be 2 or 3");
-  if (d->order < 1 || d->order > 4) return fail(nullptr, LH_EINVAL, "order must be in 1..4");
-  if (d->quad_1d != 0 && d->quad_1d != 2 * d->order)
-    return fail(nullptr, LH_EINVAL, "only 2k Gauss points per direction are supported");
-  for (int c = 0; c < d->dim; ++c) {
-    if (d->n[c] < 1) return fail(nullptr, LH_EINVAL, "element counts must be >= 1");
-    if (!(d->hi[c] > d->lo[c])) return fail(nullptr, LH_EINVAL, "box must have hi > lo");
-  }
-  if (d->visc && !(d->psi0 > 0.0 && d->psi0 < 1.0)) return fail(nullptr, LH_EINVAL, "psi0 must be in (0, 1)");
-  if (!(d->eps_e > 0.0)) return fail(nullptr, LH_EINVAL, "eps_e must be > 0");
-  if (d->tg_source && d->dim != 2) return fail(nullptr, LH_EINVAL, "the Taylor-Green source is 2D");
-
+  std::string why;
+  if (!lh::check_desc(d, &why)) return fail(nullptr, LH_EINVAL, why);
   lh_mesh* m = new (std::nothrow) lh_mesh();
   if (!m) return fail(nullptr, LH_ENOMEM, "host allocation failed");
   m->desc = *d;
   m->stream = reinterpret_cast<cudaStream_t>(d->stream);
   ElemParams& P = m->P;
+  lh::fill_params(*d, &P);
   const int dim = d->dim, K = d->order;
-  P.dim = dim;
-  P.K = K;
-  P.n0 = d->n[0];
-  P.n1 = d->n[1];
-  P.n2 = dim == 3 ? d->n[2] : 1;
-  P.N0 = K * P.n0 + 1;
-  P.N1 = K * P.n1 + 1;
-  P.N2 = dim == 3 ? K * P.n2 + 1 : 1;
-  P.NE = (long long)P.n0 * P.n1 * P.n2;
-  P.NV = (long long)P.N0 * P.N1 * P.N2;
-  long long nl = 1, nd = 1, nq = 1;
+  long long nd = 1, nq = 1;
   for (int c = 0; c < dim; ++c) {
-    nl *= K;
     nd *= K + 1;
     nq *= 2 * K;
   }
-  P.NEd = P.NE * nl;
-  double vol = 1.0;
-  P.detJ0 = 1.0;
-  for (int c = 0; c < 3; ++c) {
-    P.lo[c] = c < dim ? d->lo[c] : 0.0;
-    P.h[c] = c < dim ? (d->hi[c] - d->lo[c]) / d->n[c] : 1.0;
-    if (c < dim) {
-      vol *= d->hi[c] - d->lo[c];
-      P.detJ0 *= P.h[c];
-    }
-  }
-  P.h0 = d->h0 > 0 ? d->h0 : std::pow(vol / (double)P.NE, 1.0 / dim);
-  P.inv_hc = 1.0 / (d->h_coarse > 0 ? d->h_coarse : P.h0);
-  P.q1 = d->q1;
-  P.q2 = d->q2;
-  P.scoef = 2.0 * std::atanh(1.0 - 2.0 * d->psi0);
-  P.eps2 = d->eps_e * d->eps_e;
-  P.visc = d->visc;
-  P.tg = d->tg_source;
-  P.bc = d->bc_mask;
   m->n = 2LL * dim * P.NV + P.NEd;
   m->NQ = P.NE * nq;
 

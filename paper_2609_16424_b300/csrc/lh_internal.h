@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <string>
+#include <vector>
 #include "../../include/lh.h"
 
 namespace lh {
@@ -26,6 +27,12 @@ struct ElemParams {
   const float* fgm1;       // device [NE]: gamma - 1
   const float* fggm1;      // device [NE]: gamma (gamma - 1)
 };
+
+// shared set-up helpers (lh_api.cu)
+bool check_desc(const lh_mesh_desc* d, std::string* why);
+void fill_params(const lh_mesh_desc& d, ElemParams* out);
+std::vector<double> host_tables(int K);   // [B | G | Bl | w | zh | zl] for order K
+lh_status set_global_error(lh_status st, const std::string& msg);   // for lh_last_error(NULL)
 
 // floats per quadrature point in the linearisation record: J, grad_hat v, e (and x_q in 2D)
 inline int rec_len(int dim) { return dim == 3 ? 19 : 11; }
