@@ -140,6 +140,13 @@ lh_status lh_mass_apply(lh_mesh* mesh, int which, const double* f, double* out);
 lh_status lh_mass_solve(lh_mesh* mesh, int which, const double* rhs, double* sol,
                         double rtol, int maxit, int* iters);
 
+/* Apply the Newton-GMRES preconditioner of lh_newton_step (a stand-in for Eq. (23)):
+ *   z = P^-1 r,  P^-1 = [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1],
+ * with M_V^-1 the diagonal of M_V (kind 0) or its exact Kronecker-product inverse (kind 1,
+ * float arithmetic; exact for uniform rho0) on free velocity rows and identity on fixed rows.
+ * r, z: device [n] double, not aliased.  Asynchronous. */
+lh_status lh_precond(lh_mesh* mesh, int kind, double tau, const double* r, double* z);
+
 /* Explicit time step estimate used to set "CFL multiple" time steps (reading: the
  * paper's first-step CFL refers to an estimate it does not print):
  *   dt = min_q h_min,q / (c_s,q + mu_q / (rho_q h_min,q)),  h_min,q = sigma_min(J_q) / k.

@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "L
 SYMBOLS = ["lh_mesh_desc_init", "lh_mesh_create", "lh_mesh_destroy", "lh_sizes", "lh_set_stream",
            "lh_initial_nodes", "lh_residual", "lh_jvp", "lh_jtvp", "lh_mass_apply", "lh_mass_solve",
            "lh_dt_estimate", "lh_energies", "lh_newton_opts_init", "lh_newton_step", "lh_last_error",
-           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_linearize", "lh_residual_noalloc"]
+           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_linearize", "lh_residual_noalloc", "lh_precond"]
 PROF_KINDS = ["residual", "jvp_fp64", "jvp_fp32", "jtvp", "mass_h1"]
 
 
@@ -69,6 +69,7 @@ def load(path=LIB_PATH):
         "lh_qp_flops": (i, [i, i, i, llp]),
         "lh_linearize": (i, [vp, vp, vp, d]),
         "lh_residual_noalloc": (i, [C.POINTER(MeshDesc), vp, vp, vp, vp, d, vp]),
+        "lh_precond": (i, [vp, i, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)

@@ -196,7 +196,7 @@ lh_status ensure_work(lh_mesh* m, int restart) {
   m->d_fwork = nullptr;
   if (cudaMalloc(&m->d_work, sizeof(double) * need) != cudaSuccess)
     return fail(m, LH_ENOMEM, "cannot allocate Newton-GMRES workspace");
-  if (cudaMalloc(&m->d_fwork, sizeof(float) * 2 * n) != cudaSuccess)
+  if (cudaMalloc(&m->d_fwork, sizeof(float) * ((long long)(restart + 4) * n)) != cudaSuccess)
     return fail(m, LH_ENOMEM, "cannot allocate FP32 workspace");
   m->work_len = need;
   m->restart_alloc = restart;
@@ -231,50 +231,157 @@ cudaEvent_t* prof_pair(lh_mesh* m, int kind) {
 
 // ||x||_2^2 into a host double (synchronises)
 lh_status dot_host(lh_mesh* m, const double* a, const double* b, long long n, double* out) {
-  LH_CK(m, launch_mdot(m->stream, a, 1, 0, b, n, 0, m->d_part, m->d_counter, m->d_scalar));
+  LH_CK(m, launch_mdot<double>(m->stream, a, 1, 0, b, n, 0, m->d_part, m->d_counter, m->d_scalar));
   LH_CK(m, cudaMemcpyAsync(out, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   LH_CK(m, cudaStreamSynchronize(m->stream));
   return LH_OK;
 }
 
-// w = J z (double in, double out) in the requested arithmetic; the FP32 form reads the
-// linearisation record written by the last residual evaluation
-lh_status apply_jvp(lh_mesh* m, const double* u, const double* k, double tau, const double* z, double* w,
-                    lh_prec prec) {
-  if (prec == LH_FP32) {
-    float* fz = m->d_fwork;
-    LH_CK(m, launch_to_f32(m->stream, z, fz, m->n));
-    LH_CK(m, launch_jvp_rec_f64out(m->P, m->stream, m->d_rec, tau, fz, reinterpret_cast<float*>(m->d_ev), w,
-                                   prof_pair(m, LH_PROF_JVP32)));
-  } else {
-    LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, w, prof_pair(m, LH_PROF_JVP64)));
-  }
-  return LH_OK;
-}
+// Krylov operator of one Newton iteration, y = J P^-1 x, for a basis of type T:
+//   T = double: FP64 preconditioner and FP64 J.w (state re-gathered and re-contracted);
+//   T = float : FP32 preconditioner and FP32 J.w from the linearisation record written by
+//               the last residual evaluation (at the current Newton iterate).
+template <class T>
+struct KrylovOp {
+  lh_mesh* m;
+  int pk;             // preconditioner kind
+  const double* u;
+  const double* k;
+  double tau;
+  T* z;               // scratch [n]
 
-// z = P^-1 r with the selected velocity block (0: Jacobi mass, 1: Kronecker mass) in the
-// block upper-triangular preconditioner [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1]
-cudaError_t apply_prec(lh_mesh* m, int kind, const double* r, double* z, double tau) {
-  if (kind == 1) return launch_kron_prec(m->stream, m->P, m->kron, m->d_invMe, r, z, tau);
-  return launch_precond(m->stream, m->P, m->d_diagMv, m->d_invMe, r, z, tau);
-}
-cudaError_t apply_prec_f32(lh_mesh* m, int kind, const double* r, float* z, double tau) {
-  if (kind == 1) return launch_kron_prec_f32(m->stream, m->P, m->kron, m->d_invMe, r, z, tau);
-  return launch_precond_f32(m->stream, m->P, m->d_diagMv, m->d_invMe, r, z, tau);
-}
-
-// w = J P^-1 v (the right-preconditioned operator of GMRES); z receives P^-1 v in FP64 mode
-lh_status apply_prec_jvp(lh_mesh* m, int pk, const double* u, const double* k, double tau, const double* v,
-                         double* z, double* w, lh_prec prec) {
-  if (prec == LH_FP32) {
-    float* fz = m->d_fwork;
-    LH_CK(m, apply_prec_f32(m, pk, v, fz, tau));
-    LH_CK(m, launch_jvp_rec_f64out(m->P, m->stream, m->d_rec, tau, fz, reinterpret_cast<float*>(m->d_ev), w,
-                                   prof_pair(m, LH_PROF_JVP32)));
-  } else {
-    LH_CK(m, apply_prec(m, pk, v, z, tau));
-    LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, w, prof_pair(m, LH_PROF_JVP64)));
+  lh_status apply(const T* x, T* y) {
+    LH_CK(m, (launch_prec<T, T>(pk, m->stream, m->P, m->kron, m->d_diagMv, m->d_invMe, x, z, tau)));
+    if constexpr (sizeof(T) == sizeof(double)) {
+      LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, y, prof_pair(m, LH_PROF_JVP64)));
+    } else {
+      LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, z, reinterpret_cast<float*>(m->d_ev), y,
+                                  prof_pair(m, LH_PROF_JVP32)));
+    }
+    return LH_OK;
   }
+  // y = J d for a double vector d (restarts)
+  lh_status jac(const double* d, T* y) {
+    if constexpr (sizeof(T) == sizeof(double)) {
+      LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, d, m->d_ev, y, prof_pair(m, LH_PROF_JVP64)));
+    } else {
+      LH_CK(m, (launch_scale<double, float>(m->stream, 1.0, d, 0.0, nullptr, z, m->n)));
+      LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, z, reinterpret_cast<float*>(m->d_ev), y,
+                                  prof_pair(m, LH_PROF_JVP32)));
+    }
+    return LH_OK;
+  }
+};
+
+// Restarted, right-preconditioned GMRES on J dk = -r from dk = 0 (paper Sec. 3.5, Eq. (22)).
+// Classical Gram-Schmidt in one fused reduction (V^T w and w.w), the norm of the projected
+// vector by Pythagoras, a second pass when more than half of the norm cancelled (DGKS).
+// Basis V and work vectors w, ulin of type T; zd, wd double scratch; Givens on the host.
+template <class T>
+lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const double* r, double nr, double* dk,
+                T* V, T* w, T* ulin, double* zd, double* wd, lh_step_stats& S) {
+  const long long n = m->n;
+  const int mres = o.restart;
+  cudaStream_t s = m->stream;
+  double* dh = m->d_scalar + 8;   // device Hessenberg column / y (<= 72 entries)
+  lh_status st;
+  std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), g(mres + 1), hcol(72);
+  LH_CK(m, cudaMemsetAsync(dk, 0, sizeof(double) * n, s));
+  double beta = nr;
+  const double beta0 = nr;
+  LH_CK(m, (launch_scale<double, T>(s, -1.0 / beta, r, 0.0, nullptr, V, n)));
+  int total = 0;
+  bool done = false;
+  while (!done) {
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (; j < mres && total < o.gmres_maxit; ++j) {
+      T* vj = V + (long long)j * n;
+      if ((st = op.apply(vj, w)) != LH_OK) return st;
+      ++S.jvp_evals;
+      LH_CK(m, launch_mdot<T>(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
+      LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, n, dh, w, n));
+      LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+      LH_CK(m, cudaStreamSynchronize(s));
+      double ww = hcol[j + 1], hh = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        H[(size_t)i * mres + j] = hcol[i];
+        hh += hcol[i] * hcol[i];
+      }
+      double hn2 = ww - hh;
+      if (!(hn2 > 0.5 * ww)) {
+        LH_CK(m, launch_mdot<T>(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
+        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, n, dh, w, n));
+        LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+        LH_CK(m, cudaStreamSynchronize(s));
+        ++S.reorth;
+        double hh2 = 0.0;
+        for (int i = 0; i <= j; ++i) {
+          H[(size_t)i * mres + j] += hcol[i];
+          hh2 += hcol[i] * hcol[i];
+        }
+        hn2 = hcol[j + 1] - hh2;
+        if (!(hn2 > 1e-4 * hcol[j + 1])) {   // still cancelling: take the exact norm
+          LH_CK(m, launch_mdot<T>(s, w, 1, 0, w, n, 0, m->d_part, m->d_counter, dh));
+          LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double), cudaMemcpyDeviceToHost, s));
+          LH_CK(m, cudaStreamSynchronize(s));
+          hn2 = hcol[0];
+        }
+      }
+      if (!std::isfinite(hn2)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite Krylov vector");
+      const double hn = std::sqrt(std::fmax(hn2, 0.0));
+      H[(size_t)(j + 1) * mres + j] = hn;
+      if (hn > 0.0) LH_CK(m, (launch_scale<T, T>(s, 1.0 / hn, w, 0.0, nullptr, V + (long long)(j + 1) * n, n)));
+      for (int i = 0; i < j; ++i) {   // previous Givens rotations
+        const double a = H[(size_t)i * mres + j], b = H[(size_t)(i + 1) * mres + j];
+        H[(size_t)i * mres + j] = cs[i] * a + sn[i] * b;
+        H[(size_t)(i + 1) * mres + j] = -sn[i] * a + cs[i] * b;
+      }
+      const double a = H[(size_t)j * mres + j], b = H[(size_t)(j + 1) * mres + j];
+      const double rad = std::hypot(a, b);
+      cs[j] = rad > 0 ? a / rad : 1.0;
+      sn[j] = rad > 0 ? b / rad : 0.0;
+      H[(size_t)j * mres + j] = rad;
+      H[(size_t)(j + 1) * mres + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      if (std::fabs(g[j + 1]) <= o.gmres_rtol * beta0 || hn == 0.0) {
+        ++j;
+        done = true;
+        break;
+      }
+    }
+    // y = H^-1 g (upper triangular j x j), dk += P^-1 V y
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int l = i + 1; l < j; ++l) sum -= H[(size_t)i * mres + l] * y[l];
+      y[i] = sum / H[(size_t)i * mres + i];
+    }
+    LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    LH_CK(m, launch_gemv<T>(s, V, j, n, dh, 0.0, ulin, n));
+    LH_CK(m, (launch_prec<T, double>(op.pk, s, m->P, m->kron, m->d_diagMv, m->d_invMe, ulin, zd, op.tau)));
+    LH_CK(m, launch_axpby(s, 1.0, zd, 1.0, dk, n));
+    if (done || total >= o.gmres_maxit) break;
+    // restart from the true linear residual -r - J dk
+    if ((st = op.jac(dk, w)) != LH_OK) return st;
+    ++S.jvp_evals;
+    if constexpr (sizeof(T) == sizeof(double)) {
+      LH_CK(m, launch_axpby(s, -1.0, r, -1.0, w, n));
+      if (static_cast<void*>(w) != static_cast<void*>(wd))
+        LH_CK(m, cudaMemcpyAsync(wd, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      LH_CK(m, (launch_scale<double, double>(s, -1.0, r, -1.0, w, wd, n)));
+    }
+    double b2;
+    if ((st = dot_host(m, wd, wd, n, &b2)) != LH_OK) return st;
+    beta = std::sqrt(b2);
+    if (beta <= o.gmres_rtol * beta0) break;
+    LH_CK(m, (launch_scale<double, T>(s, 1.0 / beta, wd, 0.0, nullptr, V, n)));
+  }
+  S.gmres_its_total += total;
   return LH_OK;
 }
 
@@ -688,6 +795,14 @@ lh_status lh_mass_solve(lh_mesh* m, int which, const double* rhs, double* sol, d
   return conv ? LH_OK : fail(m, LH_ENOCONV, "lh_mass_solve: CG reached maxit");
 }
 
+lh_status lh_precond(lh_mesh* m, int kind, double tau, const double* r, double* z) {
+  if (!m || !r || !z) return fail(m, LH_EINVAL, "NULL argument to lh_precond");
+  if (r == z) return fail(m, LH_EINVAL, "z must not alias r");
+  if (kind != 0 && kind != 1) return fail(m, LH_EINVAL, "kind must be 0 or 1");
+  LH_CK(m, (launch_prec<double, double>(kind, m->stream, m->P, m->kron, m->d_diagMv, m->d_invMe, r, z, tau)));
+  return LH_OK;
+}
+
 lh_status lh_dt_estimate(lh_mesh* m, const double* u, double* dt) {
   if (!m || !u || !dt) return fail(m, LH_EINVAL, "NULL argument to lh_dt_estimate");
   LH_CK(m, launch_dt_estimate(m->P, m->stream, u, m->d_blockmin));
@@ -708,7 +823,7 @@ lh_status lh_energies(lh_mesh* m, const double* u, double* kinetic, double* inte
   if ((st = dot_host(m, u + n1, t, n1, &kv)) != LH_OK) return st;
   *kinetic = 0.5 * kv;
   LH_CK(m, launch_mass_l2(m->P, m->stream, u + 2 * n1, t));
-  LH_CK(m, launch_mdot(m->stream, t, 1, 0, nullptr, m->P.NEd, 0, m->d_part, m->d_counter, m->d_scalar));
+  LH_CK(m, launch_mdot<double>(m->stream, t, 1, 0, nullptr, m->P.NEd, 0, m->d_part, m->d_counter, m->d_scalar));
   LH_CK(m, cudaMemcpyAsync(internal, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   LH_CK(m, cudaStreamSynchronize(m->stream));
   return LH_OK;
@@ -725,8 +840,9 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
   lh_status st = ensure_work(m, o.restart);
   if (st != LH_OK) return st;
+  const bool f32 = o.jvp_prec == LH_FP32;
   float* rec = nullptr;
-  if (o.jvp_prec == LH_FP32) {
+  if (f32) {
     if ((st = ensure_rec(m)) != LH_OK) return st;
     rec = m->d_rec;
   }
@@ -736,15 +852,18 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   const long long n = m->n;
   const int mres = o.restart;
   cudaStream_t s = m->stream;
-  double* V = m->d_work;                      // (mres + 1) x n Krylov basis
+  double* V = m->d_work;                      // (mres + 1) x n FP64 Krylov basis
   double* k = V + (long long)(mres + 1) * n;  // Newton iterate
   double* r = k + n;                          // residual at k
   double* dk = r + n;                         // Newton correction
-  double* z = dk + n;                         // preconditioned vector
-  double* w = z + n;                          // operator output
-  double* kt = w + n;                         // trial iterate
+  double* zd = dk + n;                        // double scratch
+  double* wd = zd + n;                        // double scratch
+  double* kt = wd + n;                        // trial iterate
   double* rt = kt + n;                        // residual at the trial
-  double* dh = m->d_scalar + 8;               // device Hessenberg column (2 x 64 + 1)
+  float* Vf = m->d_fwork;                     // (mres + 1) x n FP32 Krylov basis
+  float* wf = Vf + (long long)(mres + 1) * n;
+  float* zf = wf + n;
+  float* uf = zf + n;
   const double tau = 0.5 * dt;
 
   if (k_prev) {
@@ -766,100 +885,15 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite residual");
   S.r0 = nr;
   bool conv = nr <= std::fmax(o.newton_rtol * S.r0, o.newton_atol);
-  std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), g(mres + 1), hcol(2 * 64 + 2);
   for (int it = 0; it < o.newton_maxit && !conv; ++it) {
-    // ---- GMRES(m), right preconditioned, on J dk = -r, dk0 = 0
-    LH_CK(m, cudaMemsetAsync(dk, 0, sizeof(double) * n, s));
-    double beta = nr, beta0 = nr;
-    LH_CK(m, launch_axpby(s, -1.0 / beta, r, 0.0, V, n));
-    int total = 0;
-    bool lin_done = false;
-    while (!lin_done) {
-      std::fill(g.begin(), g.end(), 0.0);
-      g[0] = beta;
-      int j = 0;
-      for (; j < mres && total < o.gmres_maxit; ++j) {
-        double* vj = V + (long long)j * n;
-        if ((st = apply_prec_jvp(m, o.precond, u, k, tau, vj, z, w, o.jvp_prec)) != LH_OK) return st;
-        ++S.jvp_evals;
-        // classical Gram-Schmidt in one fused reduction (V^T w and w.w), with the norm of
-        // the projected vector by Pythagoras; a second pass (DGKS criterion) when more
-        // than half of the norm cancelled
-        LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
-        LH_CK(m, launch_gemv_sub(s, V, j + 1, n, dh, w, n));
-        LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
-        LH_CK(m, cudaStreamSynchronize(s));
-        double ww = hcol[j + 1], hh = 0.0;
-        for (int i = 0; i <= j; ++i) {
-          H[(size_t)i * mres + j] = hcol[i];
-          hh += hcol[i] * hcol[i];
-        }
-        double hn2 = ww - hh;
-        if (!(hn2 > 0.5 * ww)) {
-          LH_CK(m, launch_mdot(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
-          LH_CK(m, launch_gemv_sub(s, V, j + 1, n, dh, w, n));
-          LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
-          LH_CK(m, cudaStreamSynchronize(s));
-          ++S.reorth;
-          double hh2 = 0.0;
-          for (int i = 0; i <= j; ++i) {
-            H[(size_t)i * mres + j] += hcol[i];
-            hh2 += hcol[i] * hcol[i];
-          }
-          hn2 = hcol[j + 1] - hh2;
-          if (!(hn2 > 1e-4 * hcol[j + 1])) {   // still cancelling: take the exact norm
-            double e2;
-            if ((st = dot_host(m, w, w, n, &e2)) != LH_OK) return st;
-            hn2 = e2;
-          }
-        }
-        if (!std::isfinite(hn2)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite Krylov vector");
-        const double hn = std::sqrt(std::fmax(hn2, 0.0));
-        H[(size_t)(j + 1) * mres + j] = hn;
-        if (hn > 0.0) LH_CK(m, launch_axpby(s, 1.0 / hn, w, 0.0, V + (long long)(j + 1) * n, n));
-        for (int i = 0; i < j; ++i) {   // previous Givens rotations
-          const double a = H[(size_t)i * mres + j], b = H[(size_t)(i + 1) * mres + j];
-          H[(size_t)i * mres + j] = cs[i] * a + sn[i] * b;
-          H[(size_t)(i + 1) * mres + j] = -sn[i] * a + cs[i] * b;
-        }
-        const double a = H[(size_t)j * mres + j], b = H[(size_t)(j + 1) * mres + j];
-        const double rad = std::hypot(a, b);
-        cs[j] = rad > 0 ? a / rad : 1.0;
-        sn[j] = rad > 0 ? b / rad : 0.0;
-        H[(size_t)j * mres + j] = rad;
-        H[(size_t)(j + 1) * mres + j] = 0.0;
-        g[j + 1] = -sn[j] * g[j];
-        g[j] = cs[j] * g[j];
-        ++total;
-        if (std::fabs(g[j + 1]) <= o.gmres_rtol * beta0 || hn == 0.0) {
-          ++j;
-          lin_done = true;
-          break;
-        }
-      }
-      // y = H^-1 g (upper triangular j x j), dk += P^-1 V y
-      std::vector<double> y(j);
-      for (int i = j - 1; i >= 0; --i) {
-        double sum = g[i];
-        for (int l = i + 1; l < j; ++l) sum -= H[(size_t)i * mres + l] * y[l];
-        y[i] = sum / H[(size_t)i * mres + i];
-      }
-      LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
-      LH_CK(m, launch_gemv(s, V, j, n, dh, 0.0, w, n));
-      LH_CK(m, apply_prec(m, o.precond, w, z, tau));
-      LH_CK(m, launch_axpby(s, 1.0, z, 1.0, dk, n));
-      if (lin_done || total >= o.gmres_maxit) break;
-      // restart: r_lin = -r - J dk
-      if ((st = apply_jvp(m, u, k, tau, dk, w, o.jvp_prec)) != LH_OK) return st;
-      ++S.jvp_evals;
-      LH_CK(m, launch_axpby(s, -1.0, r, -1.0, w, n));   // w = -r - J dk
-      double b2;
-      if ((st = dot_host(m, w, w, n, &b2)) != LH_OK) return st;
-      beta = std::sqrt(b2);
-      if (beta <= o.gmres_rtol * beta0) break;
-      LH_CK(m, launch_axpby(s, 1.0 / beta, w, 0.0, V, n));
+    // ---- linear solve J dk = -r (Eq. (22)) at the current iterate k
+    if (f32) {
+      KrylovOp<float> op{m, o.precond, u, k, tau, zf};
+      if ((st = gmres<float>(m, o, op, r, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return st;
+    } else {
+      KrylovOp<double> op{m, o.precond, u, k, tau, zd};
+      if ((st = gmres<double>(m, o, op, r, nr, dk, V, wd, wd, zd, wd, S)) != LH_OK) return st;
     }
-    S.gmres_its_total += total;
     // ---- backtracking line search on det J > 0 (Sec. 3.5)
     double lam = 1.0;
     bool accepted = false;

@@ -41,35 +41,36 @@ constexpr int kRedThreads = 256;
 // out_dev[j] = sum_i V[j*ld + i] * w[i] for j < m (w == NULL: plain sums of V_j), and
 // out_dev[m] = w . w when with_self; one launch, deterministic.  partials: kRedBlocks *
 // (m + 1) doubles (m + with_self <= 72); counter: a device unsigned that is 0 between calls.
-cudaError_t launch_mdot(cudaStream_t s, const double* V, int m, long long ld, const double* w, long long n,
-                        int with_self, double* partials, unsigned* counter, double* out_dev);
+// T = double or float (float: per-thread and warp sums in float, the rest in double).
+template <class T>
+cudaError_t launch_mdot(cudaStream_t s, const T* V, int m, long long ld, const T* w, long long n, int with_self,
+                        double* partials, unsigned* counter, double* out_dev);
 // out_dev[0] = min(v[0..n))
 cudaError_t launch_min(cudaStream_t s, const double* v, long long n, double* out_dev);
-// w -= sum_j h[j] V[j*ld + .]  (h on the device, m <= 64)
-cudaError_t launch_gemv_sub(cudaStream_t s, const double* V, int m, long long ld, const double* h, double* w,
-                            long long n);
-// y = sum_j h[j] V[j*ld + .] + beta y  (h on the device)
-cudaError_t launch_gemv(cudaStream_t s, const double* V, int m, long long ld, const double* h, double beta,
-                        double* y, long long n);
+// w -= sum_j h[j] V[j*ld + .]  (h: device doubles, m <= 64)
+template <class T>
+cudaError_t launch_gemv_sub(cudaStream_t s, const T* V, int m, long long ld, const double* h, T* w, long long n);
+// y = sum_j h[j] V[j*ld + .] + beta y  (h: device doubles, m <= 64)
+template <class T>
+cudaError_t launch_gemv(cudaStream_t s, const T* V, int m, long long ld, const double* h, double beta, T* y,
+                        long long n);
+// y = a x + b z  (z float, may be NULL)
+template <class TX, class TY>
+cudaError_t launch_scale(cudaStream_t s, double a, const TX* x, double b, const float* z, TY* y, long long n);
 cudaError_t launch_axpby(cudaStream_t s, double a, const double* x, double b, double* y, long long n);
 cudaError_t launch_scale_copy(cudaStream_t s, const double* x, const double* scale_dev, double* y, long long n);
 cudaError_t launch_to_f32(cudaStream_t s, const double* x, float* y, long long n);
 cudaError_t launch_to_f64(cudaStream_t s, const float* x, double* y, long long n);
-// block upper-triangular preconditioner: z_v = diag(M_V)^-1 r_v (identity on fixed rows),
-// z_x = r_x + tau z_v, z_e = M_E^-1 r_e
-cudaError_t launch_precond(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
-                           const double* r, double* z, double tau);
-// the same preconditioner written to a float vector (input of the FP32 J.w)
-cudaError_t launch_precond_f32(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
-                               const double* r, float* z, double tau);
+// block upper-triangular preconditioner [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1] with
+// M_V^-1 = diagonal (kind 0) or exact Kronecker inverse (kind 1, lh_prec.cu); fixed velocity
+// rows identity.  Instantiated for (double, double), (double, float), (float, float),
+// (float, double) input/output types.
+template <class TR, class TZ>
+cudaError_t launch_prec(int kind, cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* diag_mv,
+                        const double* inv_me, const TR* r, TZ* z, double tau);
 // J.w with float arithmetic, float input and double output (inside the FP64 Krylov solver)
 cudaError_t launch_jvp_f32_to_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                                   const float* dk, float* ev, double* out, cudaEvent_t* ev2 = nullptr);
-// z = P^-1 r with the Kronecker H1 mass inverse on the v rows (lh_prec.cu)
-cudaError_t launch_kron_prec(cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* inv_me,
-                             const double* r, double* z, double tau);
-cudaError_t launch_kron_prec_f32(cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* inv_me,
-                                 const double* r, float* z, double tau);
 // z = r / diag (component-wise H1 Jacobi, dim*NV entries, diag has NV entries)
 cudaError_t launch_jacobi_h1(cudaStream_t s, long long nv, int dim, const double* diag, const double* r, double* z);
 cudaError_t launch_mul(cudaStream_t s, const double* a, const double* b, double* y, long long n);

@@ -23,9 +23,12 @@ static inline unsigned red_grid(long long n) {
   return (unsigned)g;
 }
 
+template <class T>
 __global__ void __launch_bounds__(kRedThreads)
-k_mdot(const double* __restrict__ V, int m, long long ld, const double* __restrict__ w, long long n, int with_self,
+k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, long long n, int with_self,
        double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ out) {
+  // per-thread and warp sums in T (float: a few hundred terms, ~1e-7 relative), block and
+  // grid sums in double
   __shared__ double red[kRedThreads / 32][kChunk];
   __shared__ bool last;
   const int nout = m + (with_self ? 1 : 0);
@@ -34,23 +37,33 @@ k_mdot(const double* __restrict__ V, int m, long long ld, const double* __restri
   const long long end = beg + chunk < n ? beg + chunk : n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int c0 = 0; c0 < nout; c0 += kChunk) {
-    double acc[kChunk];
+    T acc[kChunk];
+    const T* vq[kChunk];   // per-vector pointers (no 64-bit index products in the loop)
 #pragma unroll
-    for (int q = 0; q < kChunk; ++q) acc[q] = 0.0;
-    for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
-      const double wi = w ? w[i] : 1.0;
+    for (int q = 0; q < kChunk; ++q) {
+      acc[q] = T(0);
+      vq[q] = c0 + q < m ? V + (long long)(c0 + q) * ld : w;
+    }
+    const int nq = nout - c0 < kChunk ? nout - c0 : kChunk;
+    if (w) {
+      for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+        const T wi = w[i];
 #pragma unroll
-      for (int q = 0; q < kChunk; ++q) {
-        const int j = c0 + q;
-        if (j < m) acc[q] += V[j * ld + i] * wi;
-        else if (j < nout) acc[q] += wi * wi;
+        for (int q = 0; q < kChunk; ++q)
+          if (q < nq) acc[q] += vq[q][i] * wi;
+      }
+    } else {
+      for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q)
+          if (q < nq) acc[q] += vq[q][i];
       }
     }
 #pragma unroll
     for (int q = 0; q < kChunk; ++q) {
-      double v = acc[q];
+      T v = acc[q];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][q] = v;
+      if (lane == 0) red[warp][q] = (double)v;
     }
     __syncthreads();
     if (threadIdx.x < kChunk && c0 + (int)threadIdx.x < nout) {
@@ -93,13 +106,18 @@ k_mdot(const double* __restrict__ V, int m, long long ld, const double* __restri
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-cudaError_t launch_mdot(cudaStream_t s, const double* V, int m, long long ld, const double* w, long long n,
-                        int with_self, double* partials, unsigned* counter, double* out_dev) {
+template <class T>
+cudaError_t launch_mdot(cudaStream_t s, const T* V, int m, long long ld, const T* w, long long n, int with_self,
+                        double* partials, unsigned* counter, double* out_dev) {
   if (m + (with_self ? 1 : 0) > 72) return cudaErrorInvalidValue;
-  k_mdot<<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
+  k_mdot<T><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
   count_launches(1);
   return cudaGetLastError();
 }
+template cudaError_t launch_mdot<double>(cudaStream_t, const double*, int, long long, const double*, long long, int,
+                                         double*, unsigned*, double*);
+template cudaError_t launch_mdot<float>(cudaStream_t, const float*, int, long long, const float*, long long, int,
+                                        double*, unsigned*, double*);
 
 __global__ void __launch_bounds__(kRedThreads) k_min(const double* __restrict__ v, long long n, double* out) {
   __shared__ double red[kRedThreads];
@@ -120,45 +138,91 @@ cudaError_t launch_min(cudaStream_t s, const double* v, long long n, double* out
   return cudaGetLastError();
 }
 
-__global__ void k_gemv_sub(const double* __restrict__ V, int m, long long ld, const double* __restrict__ h,
-                           double* __restrict__ w, long long n) {
-  __shared__ double hs[64];
-  if ((int)threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
+template <class T>
+__global__ void k_gemv_sub(const T* __restrict__ V, int m, long long ld, const double* __restrict__ h,
+                           T* __restrict__ w, long long n) {
+  __shared__ T hs[64];
+  if ((int)threadIdx.x < m) hs[threadIdx.x] = T(h[threadIdx.x]);
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double s = w[i];
-    for (int j = 0; j < m; ++j) s -= hs[j] * V[j * ld + i];
+    T s = w[i];
+    const T* v = V + i;
+    for (int j = 0; j < m; ++j, v += ld) s -= hs[j] * *v;
     w[i] = s;
   }
 }
 
-cudaError_t launch_gemv_sub(cudaStream_t s, const double* V, int m, long long ld, const double* h, double* w,
-                            long long n) {
+template <class T>
+cudaError_t launch_gemv_sub(cudaStream_t s, const T* V, int m, long long ld, const double* h, T* w, long long n) {
   if (m > 64) return cudaErrorInvalidValue;
-  k_gemv_sub<<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, w, n);
+  k_gemv_sub<T><<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, w, n);
   count_launches(1);
   return cudaGetLastError();
 }
+template cudaError_t launch_gemv_sub<double>(cudaStream_t, const double*, int, long long, const double*, double*,
+                                             long long);
+template cudaError_t launch_gemv_sub<float>(cudaStream_t, const float*, int, long long, const double*, float*,
+                                            long long);
 
-__global__ void k_gemv(const double* __restrict__ V, int m, long long ld, const double* __restrict__ h, double beta,
-                       double* __restrict__ y, long long n) {
-  __shared__ double hs[64];
-  if ((int)threadIdx.x < m) hs[threadIdx.x] = h[threadIdx.x];
+template <class T>
+__global__ void k_gemv(const T* __restrict__ V, int m, long long ld, const double* __restrict__ h, double beta,
+                       T* __restrict__ y, long long n) {
+  __shared__ T hs[64];
+  if ((int)threadIdx.x < m) hs[threadIdx.x] = T(h[threadIdx.x]);
   __syncthreads();
+  const T bt = T(beta);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double s = beta == 0.0 ? 0.0 : beta * y[i];
-    for (int j = 0; j < m; ++j) s += hs[j] * V[j * ld + i];
+    T s = beta == 0.0 ? T(0) : bt * y[i];
+    const T* v = V + i;
+    for (int j = 0; j < m; ++j, v += ld) s += hs[j] * *v;
     y[i] = s;
   }
 }
 
-cudaError_t launch_gemv(cudaStream_t s, const double* V, int m, long long ld, const double* h, double beta,
-                        double* y, long long n) {
+template <class T>
+cudaError_t launch_gemv(cudaStream_t s, const T* V, int m, long long ld, const double* h, double beta, T* y,
+                        long long n) {
   if (m > 64) return cudaErrorInvalidValue;
-  k_gemv<<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, beta, y, n);
+  k_gemv<T><<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, beta, y, n);
   count_launches(1);
   return cudaGetLastError();
 }
+template cudaError_t launch_gemv<double>(cudaStream_t, const double*, int, long long, const double*, double, double*,
+                                         long long);
+template cudaError_t launch_gemv<float>(cudaStream_t, const float*, int, long long, const double*, double, float*,
+                                        long long);
+
+// y = a x (+ b z), with x of type TX, z float (may be NULL), y of type TY
+template <class TX, class TY>
+__global__ void k_scale(double a, const TX* __restrict__ x, double b, const float* __restrict__ z, TY* __restrict__ y,
+                        long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if constexpr (sizeof(TY) == sizeof(float) && sizeof(TX) == sizeof(float)) {
+    float v = (float)a * x[i];
+    if (z) v += (float)b * z[i];
+    y[i] = v;
+  } else {
+    double v = a * (double)x[i];
+    if (z) v += b * (double)z[i];
+    y[i] = TY(v);
+  }
+}
+
+template <class TX, class TY>
+cudaError_t launch_scale(cudaStream_t s, double a, const TX* x, double b, const float* z, TY* y, long long n) {
+  if (n > 0) {
+    k_scale<TX, TY><<<nblk(n, 256), 256, 0, s>>>(a, x, b, z, y, n);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_scale<double, float>(cudaStream_t, double, const double*, double, const float*, float*,
+                                                 long long);
+template cudaError_t launch_scale<float, float>(cudaStream_t, double, const float*, double, const float*, float*,
+                                                long long);
+template cudaError_t launch_scale<double, double>(cudaStream_t, double, const double*, double, const float*,
+                                                  double*, long long);
 
 __global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -208,54 +272,6 @@ cudaError_t launch_to_f64(cudaStream_t s, const float* x, double* y, long long n
     k_to_f64<<<nblk(n, 256), 256, 0, s>>>(x, y, n);
     count_launches(1);
   }
-  return cudaGetLastError();
-}
-
-// velocity rows of the preconditioner: diagonal of M_V, identity on fixed rows
-__device__ __forceinline__ double jacobi_v(const ElemParams& P, const double* __restrict__ dmv,
-                                           const double* __restrict__ r, long long n1, long long j) {
-  const int comp = (int)(j / P.NV);
-  const long long nd = j % P.NV;
-  long long ic;
-  int Nc;
-  if (comp == 0) { ic = nd % P.N0; Nc = P.N0; }
-  else if (comp == 1) { ic = (nd / P.N0) % P.N1; Nc = P.N1; }
-  else { ic = nd / ((long long)P.N0 * P.N1); Nc = P.N2; }
-  const bool fixed = (((P.bc >> (2 * comp)) & 1u) && ic == 0) || (((P.bc >> (2 * comp + 1)) & 1u) && ic == Nc - 1);
-  return fixed ? r[n1 + j] : r[n1 + j] / dmv[nd];
-}
-
-// block upper-triangular preconditioner: z_v = D_V^-1 r_v, z_x = r_x + tau z_v (exact
-// elimination of the dR_x/dk_v = -tau I coupling), z_e = M_E^-1 r_e
-template <class TZ>
-__global__ void k_precond(ElemParams P, const double* __restrict__ dmv, const double* __restrict__ ime,
-                          const double* __restrict__ r, TZ* __restrict__ z, double tau) {
-  const long long n1 = (long long)P.dim * P.NV;
-  const long long n = 2 * n1 + P.NEd;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (i < n1) {
-    z[i] = TZ(r[i] + tau * jacobi_v(P, dmv, r, n1, i));
-  } else if (i < 2 * n1) {
-    z[i] = TZ(jacobi_v(P, dmv, r, n1, i - n1));
-  } else {
-    z[i] = TZ(r[i] * ime[i - 2 * n1]);
-  }
-}
-
-cudaError_t launch_precond(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
-                           const double* r, double* z, double tau) {
-  const long long n = 2LL * P.dim * P.NV + P.NEd;
-  k_precond<double><<<nblk(n, 256), 256, 0, s>>>(P, diag_mv, inv_me, r, z, tau);
-  count_launches(1);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_precond_f32(cudaStream_t s, const ElemParams& P, const double* diag_mv, const double* inv_me,
-                               const double* r, float* z, double tau) {
-  const long long n = 2LL * P.dim * P.NV + P.NEd;
-  k_precond<float><<<nblk(n, 256), 256, 0, s>>>(P, diag_mv, inv_me, r, z, tau);
-  count_launches(1);
   return cudaGetLastError();
 }
 

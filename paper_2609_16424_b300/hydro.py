@@ -186,6 +186,14 @@ class Mesh:
                                      C.byref(its)))
         return sol, its.value
 
+    def precond(self, r, tau, kind="kron"):
+        """z = P^-1 r with the Newton-GMRES block preconditioner (kind 'jacobi' or 'kron')."""
+        self._vec(r, "r")
+        z = self.new()
+        self._stream()
+        self._check(_L.lh_precond(self._h, {"jacobi": 0, "kron": 1}[kind], float(tau), _ptr(r), _ptr(z)))
+        return z
+
     def dt_estimate(self, u):
         self._vec(u, "u")
         dt = C.c_double()
