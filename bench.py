@@ -246,6 +246,18 @@ def oracle_residual_rate(u_np, k_np, tau, budget_s=15.0):
     return om.n_unknowns / t / 1e9, reps, t, r
 
 
+def aggregate_ranks(total_ms, units, device):
+    """Whole-job timing over ranks: the slowest rank's time and the units of all ranks
+    (weak scaling over independent replicas; no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device=device)
+    tmax, tsum = t.clone(), t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return tmax[0].item(), tsum[1].item()
+
+
 # ------------------------------------------------------------------------------------------
 def run_ours(args, rank, world, device):
     import numpy as np
@@ -275,12 +287,7 @@ def run_ours(args, rank, world, device):
     total_ms = sum(times)
     units = n * evals
     if world > 1:
-        t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device=device)
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        total_ms, units = tmax[0].item(), tsum[1].item()
+        total_ms, units = aggregate_ranks(total_ms, units, device)
     value = units / (total_ms * 1e-3) / 1e9
     if rank != 0:
         return None
@@ -391,6 +398,94 @@ def run_ours(args, rank, world, device):
     return out
 
 
+def sweep_state(mesh, n, k, seed):
+    """Synthetic perturbed state on the GPU from the seeded draws (walls on all faces)."""
+    import torch
+    import lh_synth
+    d = lh_synth.perturbed_draws(n, k, seed)
+    nv, dim = mesh.NV, len(n)
+    x0 = mesh.initial_nodes()
+    ids = torch.arange(nv, device=mesh.device)
+    interior = torch.ones(nv, dtype=torch.bool, device=mesh.device)
+    fixed = []
+    stride = 1
+    for c in range(dim):
+        ext = k * n[c] + 1
+        coord = (ids // stride) % ext
+        stride *= ext
+        on = (coord == 0) | (coord == ext - 1)
+        interior &= ~on
+        fixed.append(on)
+    u = torch.zeros(mesh.n, dtype=torch.float64, device=mesh.device)
+    h = 1.0 / n[0]
+    u[:dim * nv] = x0 + (0.1 * h / k) * (torch.tensor(d["xi"], device=mesh.device) * interior).reshape(-1)
+    v = torch.tensor(d["v"], device=mesh.device)
+    for c in range(dim):
+        v[c][fixed[c]] = 0.0
+    u[dim * nv:2 * dim * nv] = v.reshape(-1)
+    u[2 * dim * nv:] = torch.tensor(d["e"], device=mesh.device)
+    return u
+
+
+def run_sweep(args):
+    """48^3 throughput sweep over orders k = 1..4: operator GDoF/s and the roofline of each
+    element kernel (CUDA events around the element kernels, L2 flushed before each call)."""
+    import torch
+    import paper_2609_16424_b300 as lh
+    dev = "cuda:0"
+    torch.cuda.set_device(0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    fp64 = lh.probe_fma("fp64")
+    fp32 = lh.probe_fma("fp32")
+    rows = []
+    n = (48, 48, 48)
+    for k in args.orders:
+        mesh = lh.Mesh(3, n, (0, 0, 0), (1, 1, 1), k, gamma=1.4, h_coarse=1.0 / 24, device=dev)
+        u = sweep_state(mesh, n, k, 100 + k)
+        kk = torch.zeros_like(u)
+        dk = torch.randn(mesh.n, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(k))
+        dkf = dk.float()
+        tau = 1e-4
+        r = torch.empty_like(u)
+        od = torch.empty_like(u)
+        of = torch.empty(mesh.n, dtype=torch.float32, device=dev)
+        mesh.linearize(u, kk, tau)
+        for _ in range(2):   # warm-up
+            mesh.residual(u, kk, tau, out=r)
+            mesh.jvp(u, kk, tau, dk, out=od)
+            mesh.jvp(u, kk, tau, dkf, out=of, lin=True)
+        torch.cuda.synchronize()
+        reps = 5
+        res = {}
+        for name, fn in (("residual", lambda: mesh.residual(u, kk, tau, out=r)),
+                         ("jvp_fp64", lambda: mesh.jvp(u, kk, tau, dk, out=od)),
+                         ("jvp_fp32", lambda: mesh.jvp(u, kk, tau, dkf, out=of, lin=True))):
+            mesh.profile(True)
+            for _ in range(reps):
+                flush.fill_(1.0)
+                fn()
+            p = mesh.profile_read()
+            mesh.profile(False)
+            ms, cnt = p[name]
+            res[name] = ms / cnt
+        fl = {kind: flops_per_element(3, k, kind) for kind in ("residual", "jvp", "jvp_rec")}
+        ne = mesh.NE
+        row = {"order": f"Q{k}-Q{k - 1}", "n_unknowns": mesh.n, "quad_points": mesh.NQ}
+        for name, flk, peak, pipe in (("residual", "residual", fp64, "fp64"), ("jvp_fp64", "jvp", fp64, "fp64"),
+                                      ("jvp_fp32", "jvp_rec", fp32, "fp32")):
+            t = res[name]
+            tf = fl[flk] * ne / (t * 1e-3) / 1e12
+            row[name] = {"elem_kernel_ms": round(t, 4), "gdofs": round(mesh.n / (t * 1e-3) / 1e9, 3),
+                         "tflops": round(tf, 3), "frac": round(tf / peak, 4), "pipe": pipe,
+                         "flops_per_element": fl[flk]}
+        rows.append(row)
+        del mesh, u, kk, dk, dkf, r, od, of
+        torch.cuda.empty_cache()
+    return {"metric": "48^3 throughput sweep (element kernels, FP64 residual / FP64 J.w / FP32 record J.w)",
+            "fp64_peak_tflops": round(fp64, 3), "fp32_peak_tflops": round(fp32, 2), "rows": rows,
+            "data": "synthetic perturbed state (seeded), L2 flushed before each call"}
+
+
 def run_reference(args, rank):
     """The oracle (plain FP64 numpy, one thread) timed on this host: each step is one
     residual evaluation of the bench workload state."""
@@ -439,13 +534,17 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
+    ap.add_argument("--sweep", action="store_true", help="48^3 order sweep of the element kernels")
+    ap.add_argument("--orders", type=int, nargs="+", default=[1, 2, 3, 4])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.sweep:
+        out = run_sweep(args)
+    elif args.impl == "reference":
         out = run_reference(args, rank)
     else:
         import torch
