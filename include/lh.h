@@ -217,6 +217,44 @@ lh_status lh_newton_step(lh_mesh* mesh, double* u, double* k_prev, double dt,
 lh_status lh_residual_noalloc(const lh_mesh_desc* desc, const double* rho0, const double* gamma,
                               const double* u, const double* k, double tau, double* r);
 
+/* ---- Learned Newton initial guess (an addition to the paper's method) -------------------
+ * The paper starts each stage solve from the previous increment (Sec. 3.5 leaves the
+ * initial guess open).  A per-element MLP predicts the correction k^n - k^{n-1} from the
+ * element dofs of the last two increments and dt:
+ *   Linear(n_in, h) -> GELU -> [Linear(h, h) -> GELU] x (layers - 1) -> Linear(h, n_out),
+ * exact GELU z Phi(z), mean-squared-error loss, Adam (beta 0.9 / 0.999, eps 1e-8).  Matrix
+ * products on the tensor cores with BF16 operands and FP32 accumulation; FP32 master weights.
+ * Parameters are flat FP32: W_1 [h][n_in], b_1 [h], ..., W_last [n_out][h], b_last [n_out].
+ * All arrays are DEVICE float arrays, row-major [M][features], unless stated. */
+typedef struct lh_mlp lh_mlp;
+/* init_params: HOST array of lh_mlp_num_params floats, or NULL (zeros).  Synchronises. */
+lh_status lh_mlp_create(int n_in, int hidden, int layers, int n_out, const float* init_params, void* stream,
+                        lh_mlp** out);
+lh_status lh_mlp_destroy(lh_mlp* mlp);
+long long lh_mlp_num_params(const lh_mlp* mlp);
+/* copy the parameters to a HOST array (synchronises) */
+lh_status lh_mlp_params(lh_mlp* mlp, float* host_out);
+/* Y [M][n_out] = network(X [M][n_in]) */
+lh_status lh_mlp_forward(lh_mlp* mlp, const float* X, int M, float* Y);
+/* gradient of the mean squared error of network(X) against T [M][n_out]; grad_out (device,
+ * may be NULL) receives it; *loss (HOST, may be NULL) the loss (synchronises if non-NULL) */
+lh_status lh_mlp_grad(lh_mlp* mlp, const float* X, const float* T, int M, float* grad_out, double* loss);
+/* one Adam step on the batch (X, T) with learning rate lr; *loss as in lh_mlp_grad */
+lh_status lh_mlp_train_step(lh_mlp* mlp, const float* X, const float* T, int M, float lr, double* loss);
+const char* lh_mlp_last_error(const lh_mlp* mlp);
+/* Features of every element: X [NE][2 F1 + 1], F1 = 2 dim (k+1)^dim + k^dim: the element dofs
+ * [x | v | e] of k1 (device [n] double) divided by scale[0] (x rows), scale[1] (v rows),
+ * scale[2] (e rows), then the same for k2, then dt / scale[3].  scale: device float[4]. */
+lh_status lh_mlp_features(lh_mesh* mesh, const double* k1, const double* k2, double dt, const float* scale,
+                          float* X);
+/* Initial guess of the stage solve at (u, tau) from element predictions Y [NE][F2],
+ * F2 = dim (k+1)^dim + k^dim: corrections of the v rows then the e rows (scaled by scale[1],
+ * scale[2]).  k0_v = k1_v + average over the elements sharing each node (0 on fixed rows),
+ * k0_e = k1_e + the element's prediction, k0_x = u_v + tau k0_v (R_x = 0 exactly).
+ * u, k1, k0: device [n] double. */
+lh_status lh_mlp_apply_prediction(lh_mesh* mesh, const double* u, double tau, const double* k1, const float* Y,
+                                  const float* scale, double* k0);
+
 /* Message for the last failing call on mesh (or a global message if mesh is NULL). */
 const char* lh_last_error(const lh_mesh* mesh);
 
