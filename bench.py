@@ -486,6 +486,107 @@ def run_sweep(args):
             "data": "synthetic perturbed state (seeded), L2 flushed before each call"}
 
 
+def _ms(fn):
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    out = fn()
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_mlp(args):
+    """Learned initial guess vs plain extrapolation at the benchmark size: trajectories of the
+    24^3 Q2-Q1 blast with seeded gamma in [1.3, 1.7] and deposits in [0.1, 0.5] (5 for training,
+    1 held out); held-out steps timed with each guess at one absolute Newton tolerance."""
+    import numpy as np
+    import torch
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300 import mlp
+    from paper_2609_16424_b300.states import blast_state
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(0)
+    W = WORKLOAD
+    t0 = time.perf_counter()
+    runs = []
+    for gam, en in [(rng.uniform(1.3, 1.7), rng.uniform(0.1, 0.5)) for _ in range(6)]:
+        m = lh.Mesh(3, W["n"], (0,) * 3, (1,) * 3, W["k"], gamma=gam, device="cuda:0")
+        u0 = blast_state(m, en)
+        runs.append((m, u0, mlp.trajectory(m, u0, args.mlp_steps, cfl=W["cfl"], jvp_prec="fp32", **NEWTON)))
+    t_gen = time.perf_counter() - t0
+    m0 = runs[0][0]
+    train = [tr for _, _, tr in runs[:5]]
+    fscale = torch.zeros(4, dtype=torch.float32, device="cuda")
+    fscale[:3] = mlp.group_rms(m0, [k for tr in train for _, k in tr]).float()
+    fscale[3] = float(np.mean([dt for tr in train for dt, _ in tr]))
+    tscale = torch.ones(4, dtype=torch.float32, device="cuda")
+    tscale[:3] = mlp.group_rms(m0, [tr[i][1] - tr[i - 1][1] for tr in train for i in range(1, len(tr))]).float()
+    X, T = mlp.dataset(m0, train, fscale, tscale)
+    n_in, n_out = mlp.feature_sizes(3, W["k"])
+    net = mlp.MLP(n_in, 128, 3, n_out, seed=1)
+    t0 = time.perf_counter()
+    hist = mlp.train(net, X, T, epochs=args.mlp_epochs, batch=4096)
+    t_train = time.perf_counter() - t0
+    m, u0, tr = runs[5]
+    u = u0.clone()
+    rows = []
+    opts = dict(NEWTON, newton_rtol=1e-30, jvp_prec="fp32")
+    for i, (dt, kn) in enumerate(tr):
+        tau = 0.5 * dt
+        if i >= 2:
+            k1, k2 = tr[i - 1][1], tr[i - 2][1]
+            r1 = float(m.residual(u, k1, tau).norm())
+            atol = 1e-8 * r1
+            t_ex, st_ex = _ms(lambda: m.newton_step(u.clone(), k1.clone(), dt, newton_atol=atol, **opts))
+            def with_mlp():
+                k0 = mlp.apply(m, u, tau, k1, net.forward(mlp.features(m, k1, k2, dt, fscale)), tscale)
+                return k0, m.newton_step(u.clone(), k0, dt, newton_atol=atol, **opts)
+            t_ml, (k0, st_ml) = _ms(with_mlp)
+            rows.append([t_ex, st_ex["newton_its"], st_ex["gmres_its_total"], t_ml, st_ml["newton_its"],
+                         st_ml["gmres_its_total"], st_ml["r0"] / st_ex["r0"]])
+        u = u + dt * kn
+    a = np.array(rows).mean(axis=0)
+    return {"metric": "implicit step with learned initial guess vs plain extrapolation (24^3 Q2-Q1 blast, FP32 J.w)",
+            "extrapolation": {"ms_per_step": round(a[0], 3), "newton_its": round(a[1], 3), "gmres_its": round(a[2], 2)},
+            "learned": {"ms_per_step": round(a[3], 3), "newton_its": round(a[4], 3), "gmres_its": round(a[5], 2),
+                        "initial_residual_ratio": round(a[6], 4)},
+            "tolerance": "absolute 1e-8 x ||R(k^{n-1})||, same for both",
+            "training": {"samples": int(X.shape[0]), "epochs": args.mlp_epochs, "loss_first": round(hist[0], 5),
+                         "loss_last": round(hist[-1], 6), "train_s": round(t_train, 2), "datagen_s": round(t_gen, 2)},
+            "heldout_steps": len(rows), "data": "synthetic blasts, 5 training seeds, 1 held-out seed"}
+
+
+def run_blast(args):
+    """The 3D point blast (24^3 Q2-Q1, gamma 1.4, smooth viscosity, walls) from the corner
+    deposit to t = t_end with the paper's implicit time step control (first step at FS-CFL 2
+    of the explicit estimate, then driven by the Newton iteration count), Newton rtol 1e-5."""
+    import torch
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import blast_state
+    torch.cuda.set_device(0)
+    W = WORKLOAD
+    m = lh.Mesh(3, W["n"], (0,) * 3, (1,) * 3, W["k"], gamma=W["gamma"], device="cuda:0")
+    u = blast_state(m, W["energy"])
+    ke0, ie0 = m.energies(u)
+    opts = dict(NEWTON, newton_rtol=1e-5)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    steps, rejected, hist = m.advance(u, args.t_end, fs_cfl=W["cfl"], jvp_prec=args.prec, **opts)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    ke, ie = m.energies(u)
+    acc = [h for h in hist if h[3]]
+    its = [h[2] for h in acc]
+    return {"metric": "3D point blast 24^3 Q2-Q1 to t_end (implicit midpoint, FS-CFL 2 + Newton-count dt control)",
+            "t_end": args.t_end, "steps": steps, "rejected": rejected, "wall_s": round(wall, 3),
+            "ms_per_step": round(wall / max(steps, 1) * 1e3, 3), "newton_its_per_step": round(sum(its) / len(its), 3),
+            "dt_first": acc[0][1], "dt_last": acc[-1][1], "jvp_prec": args.prec, "newton_rtol": 1e-5,
+            "total_energy_start": ke0 + ie0, "total_energy_end": ke + ie,
+            "relative_energy_drift": (ke + ie - ke0 - ie0) / (ke0 + ie0), "kinetic_end": ke}
+
+
 def run_reference(args, rank):
     """The oracle (plain FP64 numpy, one thread) timed on this host: each step is one
     residual evaluation of the bench workload state."""
@@ -536,6 +637,11 @@ def main():
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
     ap.add_argument("--sweep", action="store_true", help="48^3 order sweep of the element kernels")
     ap.add_argument("--orders", type=int, nargs="+", default=[1, 2, 3, 4])
+    ap.add_argument("--mlp", action="store_true", help="learned initial guess vs extrapolation")
+    ap.add_argument("--mlp-steps", type=int, default=14)
+    ap.add_argument("--mlp-epochs", type=int, default=30)
+    ap.add_argument("--blast-run", action="store_true", help="point blast to --t-end")
+    ap.add_argument("--t-end", type=float, default=0.1)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -544,6 +650,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.sweep:
         out = run_sweep(args)
+    elif args.mlp:
+        out = run_mlp(args)
+    elif args.blast_run:
+        out = run_blast(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

@@ -220,6 +220,38 @@ class Mesh:
         self._check(_L.lh_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.PROF_KINDS)}
 
+    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, **kw):
+        """Implicit midpoint steps from t = 0 to t_end with the Newton-count time step control
+        of the paper's Sec. 4 ("Implicit time step control"): the first dt is fs_cfl times the
+        explicit estimate; after a step with <= 1 Newton iteration dt grows by 5%, with 2-3 it
+        is kept, with >= 4 the step is rejected and repeated with 0.85 dt (also after a
+        failed solve).  u is advanced in place.  Returns (steps, rejected, attempts) with
+        attempts = [(controller dt, step taken, Newton iterations or None, accepted)]."""
+        k = torch.zeros_like(u) if k is None else k
+        dt = fs_cfl * self.dt_estimate(u)
+        t, steps, rejected, hist = 0.0, 0, 0, []
+        while t < t_end - 1e-14 * max(1.0, t_end) and steps < max_steps:
+            h = min(dt, t_end - t)
+            u_try, k_try = u.clone(), k.clone()
+            try:
+                st = self.newton_step(u_try, k_try, h, **kw)
+                its = st["newton_its"]
+            except LHError:
+                its = None
+            if its is None or its >= 4:
+                hist.append((dt, h, its, False))
+                rejected += 1
+                dt = 0.85 * dt
+                continue
+            hist.append((dt, h, its, True))
+            u.copy_(u_try)
+            k.copy_(k_try)
+            t += h
+            steps += 1
+            if its <= 1:
+                dt = 1.05 * dt
+        return steps, rejected, hist
+
     def newton_step(self, u, k_prev, dt, opts=None, **kw):
         """One implicit midpoint step in place on u (and k_prev, if given).  Returns the
         step statistics as a dict; raises LHError (state unchanged) on failure."""

@@ -121,3 +121,25 @@ def test_dt_estimate_closed_form():
     mu = 1.0 * h * (1.0 * 2 * cs + 0.5 * cs * 0.5)
     hm = h / 2
     assert abs(gm.dt_estimate(u) - hm / (cs + mu / hm)) <= 1e-12
+
+
+def test_time_step_control_follows_the_rule():
+    """advance(): every attempt follows the Newton-count rule of oracle.solver.dt_control
+    (<= 1 iteration: x1.05; 2-3: keep; >= 4 or failure: reject, x0.85)."""
+    from oracle import solver as osolver
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import blast_state
+    gm = lh.Mesh(3, (6, 6, 6), (0,) * 3, (1,) * 3, 2, gamma=1.4)
+    u = blast_state(gm, 0.25)
+    dt0 = 2.0 * gm.dt_estimate(u)
+    t_end = 40 * dt0
+    steps, rejected, hist = gm.advance(u, t_end, fs_cfl=2.0, newton_rtol=1e-5, gmres_rtol=1e-4,
+                                       gmres_maxit=200, jvp_prec="fp32")
+    assert abs(hist[0][0] - dt0) <= 1e-15 * dt0
+    assert steps == sum(1 for a in hist if a[3]) and rejected == len(hist) - steps
+    dt = dt0
+    for (c_dt, h, its, accepted) in hist:
+        assert abs(c_dt - dt) <= 1e-12 * dt
+        dt, ok = osolver.dt_control(dt, 4 if its is None else its)
+        assert ok == accepted
+    assert sum(h for _, h, _, a in hist if a) == pytest.approx(t_end, rel=1e-12)
