@@ -176,6 +176,19 @@ def timed_steps(mesh, u_s, k_s, dt, steps, prec, flush, profile=False):
     return times, stats, launches, prof
 
 
+def tc_mma_flops(dim, k, ne, kind):
+    """Tensor-core flops one k_jvp_tc launch issues (dense, padded element operators:
+    per batch of 16 elements one 128 x NF x KF forward MMA and 128 x NB x 64 backward MMAs
+    over the padded quadrature points).  Not algorithmic work: reported for pipe usage."""
+    rup = lambda x, m: (x + m - 1) // m * m
+    nd, nl, nq = (k + 1) ** dim, k ** dim, (2 * k) ** dim
+    nqp = rup(nq, 16)
+    mk = 8 if kind == "tf32" else 16
+    nf, kf, nb = 4 * nqp, rup(nd + nl, mk), rup(nd + nl, 16)
+    batches = (ne + 15) // 16
+    return batches * 2 * 128 * (nf * kf + nb * 4 * nqp)
+
+
 def kernel_rate(mesh, fn, reps, flush):
     """Mean CUDA-event time (ms) of fn() over reps calls, L2 flushed before each."""
     import torch
@@ -297,8 +310,16 @@ def run_ours(args, rank, world, device):
                 "newton": [{k2: s[k2] for k2 in ("newton_its", "gmres_its_total", "residual_evals", "jvp_evals")}
                            for s in stats]}
 
-    # plain FP64 form for comparison
+    # plain FP64 form and the other reduced-precision J.w forms for comparison
     t64, s64, _, _ = timed_steps(mesh, u_s, k_s, dt, max(2, min(args.steps, 5)), "fp64", flush)
+    other = {}
+    for p2 in ("fp32", "tf32", "bf16"):
+        if p2 == prec:
+            continue
+        tp, sp, _, _ = timed_steps(mesh, u_s, k_s, dt, max(2, min(args.steps, 5)), p2, flush)
+        other[p2] = {"ms_per_step": round(sum(tp) / len(tp), 4),
+                     "newton_its_per_step": statistics.mean(s["newton_its"] for s in sp),
+                     "gmres_its_per_step": statistics.mean(s["gmres_its_total"] for s in sp)}
     # standalone operators on the bench state
     kd = k_s
     tau = 0.5 * dt
@@ -313,6 +334,16 @@ def run_ours(args, rank, world, device):
     t_j32 = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of), reps, flush)
     mesh.linearize(u_s, kd, tau)
     t_j32r = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of, lin=True), reps, flush)
+    t_tc, kp_tc = {}, {}
+    for kind in ("tf32", "bf16"):
+        t_tc[kind] = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of, tc=kind), reps, flush)
+        mesh.profile(True)
+        for _ in range(reps):
+            flush.fill_(1.0)
+            mesh.jvp(u_s, kd, tau, dkf, out=of, tc=kind)
+        kp_tc[kind] = mesh.profile_read()["jvp_tc"]
+        mesh.profile(False)
+    mesh.tc_status()
     # element-kernel-only times from the profiler (the roofline kernels)
     mesh.profile(True)
     for _ in range(reps):
@@ -339,11 +370,13 @@ def run_ours(args, rank, world, device):
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_kind, (dom_ms, dom_cnt) = dom[0], dom[1]
     # inside the Newton step the FP32 J.w runs from the linearisation record
-    dom_flops = ne * {"residual": fl["residual"], "jvp_fp64": fl["jvp"], "jvp_fp32": fl["jvp_rec"]}[dom_kind]
+    dom_flops = ne * {"residual": fl["residual"], "jvp_fp64": fl["jvp"], "jvp_fp32": fl["jvp_rec"],
+                      "jvp_tc": fl["jvp_rec"]}[dom_kind]
     dom_peak = fp64_peak if dom_kind in ("residual", "jvp_fp64") else fp32_peak
     achieved = dom_flops / (dom_ms / dom_cnt * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": {"residual": "k_residual<3,2>", "jvp_fp64": "k_jvp<3,2,double,double>",
-                                           "jvp_fp32": "k_jvp_rec<3,2,double>"}.get(dom_kind, dom_kind),
+                                           "jvp_fp32": "k_jvp_rec<3,2,double>",
+                                           "jvp_tc": f"k_jvp_tc<3,2,{prec}>"}.get(dom_kind, dom_kind),
                 "pipe": "fp64" if dom_peak is fp64_peak else "fp32",
                 "achieved": round(achieved, 4), "peak": round(dom_peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / dom_peak, 4), "peak_source": "measured FMA probe (lh_probe_fma) this run",
@@ -365,6 +398,7 @@ def run_ours(args, rank, world, device):
         "newton": {"its_per_step": statistics.mean(s["newton_its"] for s in stats),
                    "gmres_its_per_step": statistics.mean(s["gmres_its_total"] for s in stats),
                    "evals_per_step": evals / len(stats)},
+        "other_jvp_forms_step": other,
         "plain_fp64_step": {"ms_per_step": round(sum(t64) / len(t64), 4),
                             "gmres_its_per_step": statistics.mean(s["gmres_its_total"] for s in s64),
                             "value": round(n * sum(s["residual_evals"] + s["jvp_evals"] for s in s64) / (sum(t64) * 1e-3) / 1e9, 4)},
@@ -381,6 +415,12 @@ def run_ours(args, rank, world, device):
             "jvp_fp32_record": {"gdofs": round(n / (t_j32r * 1e-3) / 1e9, 4), "ms": round(t_j32r, 5),
                                 "elem_kernel_ms": round(kpr["jvp_fp32"][0] / max(1, kpr["jvp_fp32"][1]), 5),
                                 "tflops_elem": round(fl["jvp_rec"] * ne / (kpr["jvp_fp32"][0] / max(1, kpr["jvp_fp32"][1]) * 1e-3) / 1e12, 4)},
+            **{f"jvp_{kind}_tensor_core": {
+                "gdofs": round(n / (t_tc[kind] * 1e-3) / 1e9, 4), "ms": round(t_tc[kind], 5),
+                "elem_kernel_ms": round(kp_tc[kind][0] / max(1, kp_tc[kind][1]), 5),
+                "tflops_elem": round(fl["jvp_rec"] * ne / (kp_tc[kind][0] / max(1, kp_tc[kind][1]) * 1e-3) / 1e12, 4),
+                "tensor_tflops": round(tc_mma_flops(3, W["k"], ne, kind) / (kp_tc[kind][0] / max(1, kp_tc[kind][1]) * 1e-3) / 1e12, 4)}
+               for kind in ("tf32", "bf16")},
             "flops_per_element": fl, "fp64_peak_tflops": round(fp64_peak, 3), "fp32_peak_tflops": round(fp32_peak, 2)},
         "step_kernel_ms": {k2: round(v[0], 3) for k2, v in prof.items()},
         "roofline": roofline,
@@ -450,29 +490,42 @@ def run_sweep(args):
         od = torch.empty_like(u)
         of = torch.empty(mesh.n, dtype=torch.float32, device=dev)
         mesh.linearize(u, kk, tau)
+        tc_ok = k <= 2
         for _ in range(2):   # warm-up
             mesh.residual(u, kk, tau, out=r)
             mesh.jvp(u, kk, tau, dk, out=od)
             mesh.jvp(u, kk, tau, dkf, out=of, lin=True)
+            if tc_ok:
+                mesh.jvp(u, kk, tau, dkf, out=of, tc="bf16")
         torch.cuda.synchronize()
         reps = 5
         res = {}
-        for name, fn in (("residual", lambda: mesh.residual(u, kk, tau, out=r)),
-                         ("jvp_fp64", lambda: mesh.jvp(u, kk, tau, dk, out=od)),
-                         ("jvp_fp32", lambda: mesh.jvp(u, kk, tau, dkf, out=of, lin=True))):
+        ops = [("residual", "residual", lambda: mesh.residual(u, kk, tau, out=r)),
+               ("jvp_fp64", "jvp_fp64", lambda: mesh.jvp(u, kk, tau, dk, out=od)),
+               ("jvp_fp32", "jvp_fp32", lambda: mesh.jvp(u, kk, tau, dkf, out=of, lin=True))]
+        if tc_ok:
+            ops += [("jvp_tf32_tc", "jvp_tc", lambda: mesh.jvp(u, kk, tau, dkf, out=of, tc="tf32")),
+                    ("jvp_bf16_tc", "jvp_tc", lambda: mesh.jvp(u, kk, tau, dkf, out=of, tc="bf16"))]
+        for name, pk, fn in ops:
             mesh.profile(True)
             for _ in range(reps):
                 flush.fill_(1.0)
                 fn()
             p = mesh.profile_read()
             mesh.profile(False)
-            ms, cnt = p[name]
+            ms, cnt = p[pk]
             res[name] = ms / cnt
+        if tc_ok:
+            mesh.tc_status()
         fl = {kind: flops_per_element(3, k, kind) for kind in ("residual", "jvp", "jvp_rec")}
         ne = mesh.NE
         row = {"order": f"Q{k}-Q{k - 1}", "n_unknowns": mesh.n, "quad_points": mesh.NQ}
         for name, flk, peak, pipe in (("residual", "residual", fp64, "fp64"), ("jvp_fp64", "jvp", fp64, "fp64"),
-                                      ("jvp_fp32", "jvp_rec", fp32, "fp32")):
+                                      ("jvp_fp32", "jvp_rec", fp32, "fp32"), ("jvp_tf32_tc", "jvp_rec", fp32, "fp32"),
+                                      ("jvp_bf16_tc", "jvp_rec", fp32, "fp32")):
+            if name not in res:
+                row[name] = "not supported at this order (dense element operator exceeds shared memory)"
+                continue
             t = res[name]
             tf = fl[flk] * ne / (t * 1e-3) / 1e12
             row[name] = {"elem_kernel_ms": round(t, 4), "gdofs": round(mesh.n / (t * 1e-3) / 1e9, 3),
@@ -481,7 +534,8 @@ def run_sweep(args):
         rows.append(row)
         del mesh, u, kk, dk, dkf, r, od, of
         torch.cuda.empty_cache()
-    return {"metric": "48^3 throughput sweep (element kernels, FP64 residual / FP64 J.w / FP32 record J.w)",
+    return {"metric": "48^3 throughput sweep (element kernels, FP64 residual / FP64 J.w / FP32 record J.w / "
+                      "TF32 and BF16 tensor-core record J.w)",
             "fp64_peak_tflops": round(fp64, 3), "fp32_peak_tflops": round(fp32, 2), "rows": rows,
             "data": "synthetic perturbed state (seeded), L2 flushed before each call"}
 
@@ -632,7 +686,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
     ap.add_argument("--sweep", action="store_true", help="48^3 order sweep of the element kernels")

@@ -56,8 +56,12 @@ typedef enum {
 typedef enum {
   LH_FP64 = 0,        /* double in, double out, double arithmetic */
   LH_FP32 = 1,        /* float in, float out, float arithmetic (state gathered in double) */
-  LH_FP32_LIN = 2     /* float in, float out, float arithmetic from the linearisation record
+  LH_FP32_LIN = 2,    /* float in, float out, float arithmetic from the linearisation record
                          of the last lh_linearize (same u, k, tau pointers/value required) */
+  LH_TF32 = 3,        /* as LH_FP32_LIN, with the element contractions (B and B^T of Eq. (8))
+                         on the tensor cores: TF32 operands, FP32 accumulation; quadrature-
+                         point arithmetic in float.  2D orders 1-4 and 3D orders 1-2. */
+  LH_BF16 = 4         /* as LH_TF32 with BF16 operands */
 } lh_prec;
 
 /* Mesh and model description.  Call lh_mesh_desc_init first to get the defaults. */
@@ -110,7 +114,11 @@ lh_status lh_residual(lh_mesh* mesh, const double* u, const double* k, double ta
  * Eq. (10): transfers B, G unchanged, only the quadrature-point kernel differentiated).
  * dk and out are device [n] arrays of double (LH_FP64) or float (LH_FP32); u and k are
  * double.  With LH_FP32 the state is gathered and re-centred per element in double,
- * then all arithmetic runs in float. */
+ * then all arithmetic runs in float.  LH_FP32_LIN, LH_TF32 and LH_BF16 take float dk/out
+ * and need the record of a preceding lh_linearize(u, k, tau); LH_TF32/LH_BF16 return
+ * LH_EINVAL for 3D orders >= 3 (the dense element operator does not fit in shared memory).
+ * A tensor-core wait that times out writes NaN into the affected element rows and is
+ * reported by the next lh_newton_step (LH_ECUDA) and by lh_tc_status. */
 lh_status lh_jvp(lh_mesh* mesh, const double* u, const double* k, double tau,
                  const void* dk, void* out, lh_prec prec);
 
@@ -121,6 +129,10 @@ lh_status lh_jvp(lh_mesh* mesh, const double* u, const double* k, double tau,
  * with LH_FP32_LIN and the same u, k (pointers) and tau use it.  lh_newton_step with an
  * FP32 J.w writes the record at every Newton iterate and invalidates it on return.
  * Asynchronous; allocates the record on first use. */
+/* Status of the tensor-core J.w: LH_OK, or LH_ECUDA if one of its bounded waits on the
+ * tensor cores timed out since the mesh was created (synchronises; clears the flag). */
+lh_status lh_tc_status(lh_mesh* mesh);
+
 lh_status lh_linearize(lh_mesh* mesh, const double* u, const double* k, double tau);
 
 /* Transpose action out = (dR/dk)^T y (paper Sec. 3.1: transpose actions share the
@@ -164,7 +176,9 @@ typedef struct {
   int gmres_maxit;         /* total GMRES iterations per linear solve; default 60 */
   int restart;             /* GMRES restart length (<= 64); default 30 */
   int max_halvings;        /* line-search halvings of the Newton step; default 10 */
-  lh_prec jvp_prec;        /* precision of the J.w inside GMRES; default LH_FP64 */
+  lh_prec jvp_prec;        /* precision of the J.w inside GMRES; default LH_FP64.  LH_FP32,
+                              LH_TF32 and LH_BF16 use an FP32 Krylov basis and the linearisation
+                              record written at every Newton iterate */
   int precond;             /* velocity block of the preconditioner: 0 = diagonal of M_V,
                               1 = exact M_V inverse as a Kronecker product of 1D inverses
                               (exact for uniform rho0; rho0-scaled otherwise); default 1 */
@@ -263,7 +277,7 @@ const char* lh_last_error(const lh_mesh* mesh);
  * the accumulated device milliseconds and launch counts per kind (HOST arrays of
  * LH_PROF_KINDS entries) and synchronises.  Enabling resets the accumulators. */
 enum { LH_PROF_RESIDUAL = 0, LH_PROF_JVP64 = 1, LH_PROF_JVP32 = 2, LH_PROF_JTVP = 3, LH_PROF_MASS = 4,
-       LH_PROF_KINDS = 5 };
+       LH_PROF_JVPTC = 5, LH_PROF_KINDS = 6 };
 lh_status lh_profile_enable(lh_mesh* mesh, int enable);
 lh_status lh_profile_read(lh_mesh* mesh, double* ms, long long* count);
 

@@ -6,7 +6,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblh.so")
 
 LH_OK, LH_EINVAL, LH_ECUDA, LH_ENOMEM, LH_ETANGLED, LH_ENOCONV, LH_ENONFINITE = range(7)
-LH_FP64, LH_FP32, LH_FP32_LIN = 0, 1, 2
+LH_FP64, LH_FP32, LH_FP32_LIN, LH_TF32, LH_BF16 = 0, 1, 2, 3, 4
 STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "LH_ETANGLED",
                 5: "LH_ENOCONV", 6: "LH_ENONFINITE"}
 
@@ -14,10 +14,10 @@ STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "L
 SYMBOLS = ["lh_mesh_desc_init", "lh_mesh_create", "lh_mesh_destroy", "lh_sizes", "lh_set_stream",
            "lh_initial_nodes", "lh_residual", "lh_jvp", "lh_jtvp", "lh_mass_apply", "lh_mass_solve",
            "lh_dt_estimate", "lh_energies", "lh_newton_opts_init", "lh_newton_step", "lh_last_error",
-           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_linearize", "lh_residual_noalloc", "lh_precond",
+           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_linearize", "lh_tc_status", "lh_residual_noalloc", "lh_precond",
            "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_params", "lh_mlp_forward",
            "lh_mlp_grad", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_features", "lh_mlp_apply_prediction"]
-PROF_KINDS = ["residual", "jvp_fp64", "jvp_fp32", "jtvp", "mass_h1"]
+PROF_KINDS = ["residual", "jvp_fp64", "jvp_fp32", "jtvp", "mass_h1", "jvp_tc"]
 
 
 class MeshDesc(C.Structure):
@@ -70,6 +70,7 @@ def load(path=LIB_PATH):
         "lh_launch_count": (C.c_longlong, []),
         "lh_qp_flops": (i, [i, i, i, llp]),
         "lh_linearize": (i, [vp, vp, vp, d]),
+        "lh_tc_status": (i, [vp]),
         "lh_residual_noalloc": (i, [C.POINTER(MeshDesc), vp, vp, vp, vp, d, vp]),
         "lh_precond": (i, [vp, i, d, vp, vp]),
         "lh_mlp_create": (i, [i, i, i, i, vp, vp, C.POINTER(vp)]),

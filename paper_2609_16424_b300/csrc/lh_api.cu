@@ -221,6 +221,9 @@ cudaError_t prof_flush(lh_mesh* m) {
 }
 
 // event pair for the next element-kernel launch of the given kind, or NULL when off
+// device int set by the tensor-core J.w when one of its bounded waits gives up
+int* tc_err(lh_mesh* m) { return reinterpret_cast<int*>(m->d_scalar + 255); }
+
 cudaEvent_t* prof_pair(lh_mesh* m, int kind) {
   Prof& p = m->prof;
   if (!p.on) return nullptr;
@@ -245,6 +248,7 @@ template <class T>
 struct KrylovOp {
   lh_mesh* m;
   int pk;             // preconditioner kind
+  int tck;            // float J.w: -1 FP32 CUDA cores, 0 TF32 tensor cores, 1 BF16 tensor cores
   const double* u;
   const double* k;
   double tau;
@@ -255,10 +259,16 @@ struct KrylovOp {
     if constexpr (sizeof(T) == sizeof(double)) {
       LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, y, prof_pair(m, LH_PROF_JVP64)));
     } else {
-      LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, z, reinterpret_cast<float*>(m->d_ev), y,
-                                  prof_pair(m, LH_PROF_JVP32)));
+      LH_CK(m, jvp_f32(z, y));
     }
     return LH_OK;
+  }
+  cudaError_t jvp_f32(const float* x, float* y) {
+    if (tck < 0)
+      return launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, x, reinterpret_cast<float*>(m->d_ev), y,
+                                prof_pair(m, LH_PROF_JVP32));
+    return launch_jvp_tc<float>(m->P, m->stream, tck, m->d_rec, tau, x, reinterpret_cast<float*>(m->d_ev), y,
+                                tc_err(m), prof_pair(m, LH_PROF_JVPTC));
   }
   // y = J d for a double vector d (restarts)
   lh_status jac(const double* d, T* y) {
@@ -266,8 +276,7 @@ struct KrylovOp {
       LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, d, m->d_ev, y, prof_pair(m, LH_PROF_JVP64)));
     } else {
       LH_CK(m, (launch_scale<double, float>(m->stream, 1.0, d, 0.0, nullptr, z, m->n)));
-      LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, z, reinterpret_cast<float*>(m->d_ev), y,
-                                  prof_pair(m, LH_PROF_JVP32)));
+      LH_CK(m, jvp_f32(z, y));
     }
     return LH_OK;
   }
@@ -578,6 +587,7 @@ lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(m->d_fconst, fc.data(), sizeof(float) * fc.size(), cudaMemcpyHostToDevice, m->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(m->d_counter, 0, sizeof(unsigned), m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(m->d_scalar, 0, sizeof(double) * 256, m->stream);
   // Kronecker factors of the H1 mass inverse and the nodal rho0^(-1/2) scaling
   std::vector<std::vector<float>> kf(6);
   const int nel[3] = {P.n0, P.n1, P.n2};
@@ -698,12 +708,20 @@ lh_status lh_jvp(lh_mesh* m, const double* u, const double* k, double tau, const
     LH_CK(m, launch_jvp_f32(m->P, m->stream, u, k, tau, static_cast<const float*>(dk),
                             reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out),
                             prof_pair(m, LH_PROF_JVP32)));
-  } else if (prec == LH_FP32_LIN) {
+  } else if (prec == LH_FP32_LIN || prec == LH_TF32 || prec == LH_BF16) {
     if (!m->rec_valid || m->rec_u != u || m->rec_k != k || m->rec_tau != tau)
-      return fail(m, LH_EINVAL, "lh_jvp(LH_FP32_LIN): call lh_linearize with the same u, k, tau first");
-    LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, static_cast<const float*>(dk),
-                                reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out),
-                                prof_pair(m, LH_PROF_JVP32)));
+      return fail(m, LH_EINVAL, "lh_jvp(record precisions): call lh_linearize with the same u, k, tau first");
+    if (prec == LH_FP32_LIN) {
+      LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, static_cast<const float*>(dk),
+                                  reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out),
+                                  prof_pair(m, LH_PROF_JVP32)));
+    } else {
+      if (!jvp_tc_supported(m->P.dim, m->P.K))
+        return fail(m, LH_EINVAL, "lh_jvp: tensor-core J.w supports 2D orders 1-4 and 3D orders 1-2");
+      LH_CK(m, launch_jvp_tc<float>(m->P, m->stream, prec == LH_TF32 ? 0 : 1, m->d_rec, tau,
+                                    static_cast<const float*>(dk), reinterpret_cast<float*>(m->d_ev),
+                                    static_cast<float*>(out), tc_err(m), prof_pair(m, LH_PROF_JVPTC)));
+    }
   } else {
     return fail(m, LH_EINVAL, "lh_jvp: unsupported precision");
   }
@@ -835,12 +853,16 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   lh_newton_opts o;
   if (opts_in) o = *opts_in; else lh_newton_opts_init(&o);
   if (o.restart < 1 || o.restart > 64) return fail(m, LH_EINVAL, "restart must be in 1..64");
-  if (o.jvp_prec != LH_FP64 && o.jvp_prec != LH_FP32) return fail(m, LH_EINVAL, "unsupported jvp_prec");
+  if (o.jvp_prec != LH_FP64 && o.jvp_prec != LH_FP32 && o.jvp_prec != LH_TF32 && o.jvp_prec != LH_BF16)
+    return fail(m, LH_EINVAL, "unsupported jvp_prec");
+  if ((o.jvp_prec == LH_TF32 || o.jvp_prec == LH_BF16) && !jvp_tc_supported(m->P.dim, m->P.K))
+    return fail(m, LH_EINVAL, "tensor-core J.w supports 2D orders 1-4 and 3D orders 1-2");
   if (o.precond != 0 && o.precond != 1) return fail(m, LH_EINVAL, "precond must be 0 or 1");
   if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
   lh_status st = ensure_work(m, o.restart);
   if (st != LH_OK) return st;
-  const bool f32 = o.jvp_prec == LH_FP32;
+  const bool f32 = o.jvp_prec != LH_FP64;
+  const int tck = o.jvp_prec == LH_TF32 ? 0 : o.jvp_prec == LH_BF16 ? 1 : -1;
   float* rec = nullptr;
   if (f32) {
     if ((st = ensure_rec(m)) != LH_OK) return st;
@@ -888,10 +910,10 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   for (int it = 0; it < o.newton_maxit && !conv; ++it) {
     // ---- linear solve J dk = -r (Eq. (22)) at the current iterate k
     if (f32) {
-      KrylovOp<float> op{m, o.precond, u, k, tau, zf};
+      KrylovOp<float> op{m, o.precond, tck, u, k, tau, zf};
       if ((st = gmres<float>(m, o, op, r, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return st;
     } else {
-      KrylovOp<double> op{m, o.precond, u, k, tau, zd};
+      KrylovOp<double> op{m, o.precond, -1, u, k, tau, zd};
       if ((st = gmres<double>(m, o, op, r, nr, dk, V, wd, wd, zd, wd, S)) != LH_OK) return st;
     }
     // ---- backtracking line search on det J > 0 (Sec. 3.5)
@@ -924,10 +946,23 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   S.rfinal = nr;
   if (S.min_detj == 0.0) S.min_detj = mind;
   if (stats) *stats = S;
+  if (tck >= 0 && (st = lh_tc_status(m)) != LH_OK) return st;
   if (!conv) return fail(m, LH_ENOCONV, "lh_newton_step: Newton did not converge");
   LH_CK(m, launch_axpby(s, dt, k, 1.0, u, n));
   if (k_prev) LH_CK(m, cudaMemcpyAsync(k_prev, k, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   LH_CK(m, cudaStreamSynchronize(s));
+  return LH_OK;
+}
+
+lh_status lh_tc_status(lh_mesh* m) {
+  if (!m) return fail(nullptr, LH_EINVAL, "mesh is NULL");
+  int flag = 0;
+  LH_CK(m, cudaMemcpyAsync(&flag, tc_err(m), sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  if (flag) {
+    LH_CK(m, cudaMemsetAsync(tc_err(m), 0, sizeof(int), m->stream));
+    return fail(m, LH_ECUDA, "tensor-core J.w: a bounded wait on the tensor cores timed out");
+  }
   return LH_OK;
 }
 

@@ -14,6 +14,15 @@
 
 namespace lh {
 
+// 1D table layout in the device table buffer (built by the host at mesh creation):
+// [B | G | Bl | w | H1 nodes | L2 nodes]
+template <int K>
+struct Tab {
+  static constexpr int D = K + 1, L = K, Q = 2 * K;
+  static constexpr int B = 0, G = Q * D, BL = 2 * Q * D, W = 2 * Q * D + Q * L;
+  static constexpr int SMEM = 2 * Q * D + Q * L + Q;           // entries staged in shared memory
+};
+
 template <int DIM, int K, int NC>
 struct H1Scratch {
   static constexpr int D = K + 1, Q = 2 * K;

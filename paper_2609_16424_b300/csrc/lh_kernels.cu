@@ -15,14 +15,6 @@
 
 namespace lh {
 
-// ---- 1D table layout in the device table buffer (built by the host at mesh creation)
-template <int K>
-struct Tab {
-  static constexpr int D = K + 1, L = K, Q = 2 * K;
-  static constexpr int B = 0, G = Q * D, BL = 2 * Q * D, W = 2 * Q * D + Q * L;
-  static constexpr int SMEM = 2 * Q * D + Q * L + Q;           // entries staged in shared memory
-};
-
 // Per-element shared-memory plan (units of T).
 template <int DIM, int K, int NCH, int NCV, int NCL, int NCO>
 struct Plan {
@@ -963,6 +955,13 @@ struct Launch {
     k_assemble_jvp<DIM, K, float, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
     return cudaGetLastError();
   }
+  template <class TO>
+  static cudaError_t assemble_jvp(const ElemParams& P, cudaStream_t s, const float* dk, double tau, const float* ev,
+                                  TO* out) {
+    count_launches(1);
+    k_assemble_jvp<DIM, K, float, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    return cudaGetLastError();
+  }
   static cudaError_t jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                           const double* y, double* ev, double* out, cudaEvent_t* ev2) {
     using PL = Plan<DIM, K, 3 * DIM, 0, 2, 2 * DIM>;
@@ -1047,6 +1046,15 @@ cudaError_t launch_jvp_rec_f64out(const ElemParams& P, cudaStream_t s, const flo
                                   const float* dk, float* ev, double* out, cudaEvent_t* ev2) {
   LH_DISPATCH(P, template jvp_rec<double>(P, s, rec, tau, dk, ev, out, ev2))
 }
+template <class TO>
+cudaError_t launch_assemble_jvp(const ElemParams& P, cudaStream_t s, const float* dk, double tau, const float* ev,
+                                TO* out) {
+  LH_DISPATCH(P, template assemble_jvp<TO>(P, s, dk, tau, ev, out))
+}
+template cudaError_t launch_assemble_jvp<float>(const ElemParams&, cudaStream_t, const float*, double, const float*,
+                                                float*);
+template cudaError_t launch_assemble_jvp<double>(const ElemParams&, cudaStream_t, const float*, double,
+                                                 const float*, double*);
 cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                            const double* dk, double* ev, double* out, cudaEvent_t* ev2) {
   LH_DISPATCH(P, template jvp<double, double>(P, s, u, k, tau, dk, ev, out, ev2))

@@ -20,6 +20,19 @@ cudaError_t launch_jvp_rec_f32(const ElemParams& P, cudaStream_t s, const float*
                                float* ev, float* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jvp_rec_f64out(const ElemParams& P, cudaStream_t s, const float* rec, double tau,
                                   const float* dk, float* ev, double* out, cudaEvent_t* ev2 = nullptr);
+// node-centric assembly of a float J.w from its element scratch (x rows from dk)
+template <class TO>
+cudaError_t launch_assemble_jvp(const ElemParams& P, cudaStream_t s, const float* dk, double tau, const float* ev,
+                                TO* out);
+// Tensor-core J.w from the linearisation record (lh_tc_jvp.cu): element contractions as
+// tcgen05 MMAs, kind 0 = TF32, 1 = BF16 operands, FP32 accumulation; quadrature-point
+// arithmetic in FP32.  err (device int) is set non-zero if a tensor-core wait timed out.
+// Returns cudaErrorNotSupported for orders whose dense element operator does not fit in
+// shared memory (3D k >= 3).
+template <class TO>
+cudaError_t launch_jvp_tc(const ElemParams& P, cudaStream_t s, int kind, const float* rec, double tau,
+                          const float* dk, float* ev, TO* out, int* err, cudaEvent_t* ev2 = nullptr);
+bool jvp_tc_supported(int dim, int k);
 cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                            const double* dk, double* ev, double* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,

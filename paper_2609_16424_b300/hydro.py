@@ -20,12 +20,14 @@ def _ptr(t):
 def newton_opts(**kw):
     """lh_newton_opts with the library defaults, overridden by keyword arguments
     (newton_rtol, newton_atol, gmres_rtol, newton_maxit, gmres_maxit, restart,
-    max_halvings, jvp_prec in {'fp64', 'fp32'}, precond in {'jacobi', 'kron'})."""
+    max_halvings, jvp_prec in {'fp64', 'fp32', 'tf32', 'bf16'}, precond in {'jacobi', 'kron'});
+    'tf32' and 'bf16' run the element contractions of J.w on the tensor cores."""
     o = _lib.NewtonOpts()
     _L.lh_newton_opts_init(C.byref(o))
     for key, val in kw.items():
         if key == "jvp_prec":
-            val = {"fp64": _lib.LH_FP64, "fp32": _lib.LH_FP32}.get(val, val)
+            val = {"fp64": _lib.LH_FP64, "fp32": _lib.LH_FP32, "tf32": _lib.LH_TF32,
+                   "bf16": _lib.LH_BF16}.get(val, val)
         if key == "precond":
             val = {"jacobi": 0, "kron": 1}.get(val, val)
         setattr(o, key, val)
@@ -142,16 +144,21 @@ class Mesh:
         self._stream()
         self._check(_L.lh_linearize(self._h, _ptr(u), _ptr(k), float(tau)))
 
-    def jvp(self, u, k, tau, dk, out=None, lin=False):
+    def tc_status(self):
+        """Raise LHError if a bounded tensor-core wait of the TF32/BF16 J.w timed out."""
+        self._check(_L.lh_tc_status(self._h))
+
+    def jvp(self, u, k, tau, dk, out=None, lin=False, tc=None):
         """(dR/dk) dk; float64 dk -> FP64 kernel, float32 dk -> FP32 kernel (lin=True: from
-        the record of linearize(u, k, tau))."""
+        the record of linearize(u, k, tau)); tc='tf32' or 'bf16': from the record, element
+        contractions on the tensor cores."""
         self._vec(u, "u")
         self._vec(k, "k")
         prec = _lib.LH_FP32 if dk.dtype == torch.float32 else _lib.LH_FP64
-        if lin:
+        if lin or tc:
             if dk.dtype != torch.float32:
-                raise ValueError("lin=True needs a float32 direction")
-            prec = _lib.LH_FP32_LIN
+                raise ValueError("record-based J.w needs a float32 direction")
+            prec = {None: _lib.LH_FP32_LIN, "tf32": _lib.LH_TF32, "bf16": _lib.LH_BF16}[tc]
         self._vec(dk, "dk", dk.dtype)
         out = self.new(dk.dtype) if out is None else self._vec(out, "out", dk.dtype)
         self._stream()
@@ -215,8 +222,8 @@ class Mesh:
 
     def profile_read(self):
         """{kind: (total device ms, launches)} since the last profile(True)."""
-        ms = (C.c_double * 5)()
-        cnt = (C.c_longlong * 5)()
+        ms = (C.c_double * len(_lib.PROF_KINDS))()
+        cnt = (C.c_longlong * len(_lib.PROF_KINDS))()
         self._check(_L.lh_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.PROF_KINDS)}
 

@@ -33,6 +33,12 @@ def test_blast24_residual_and_jvp_full_vector():
     jf = c.gm.jvp(u, kd, tau, c.dev(dk, torch.float32), lin=True).double().cpu().numpy()
     jref32 = c.hyd.jvp_complex_step(c.u, kk, tau, dk.astype(np.float32).astype(np.float64))
     assert max(c.rel_blocks(jf, jref32)) <= 2e-5
+    # tensor-core J.w (bounds: five unit roundoffs of TF32 / BF16; x rows stay FP32)
+    for kind, tol in (("tf32", 5 * 2.0 ** -11), ("bf16", 5 * 2.0 ** -9)):
+        jt = c.gm.jvp(u, kd, tau, c.dev(dk, torch.float32), tc=kind).double().cpu().numpy()
+        rel = c.rel_blocks(jt, jref32)
+        assert rel[0] <= 2e-5 and max(rel[1:]) <= tol, (kind, rel)
+    c.gm.tc_status()
 
 
 def test_interface_problem_full_size():
@@ -55,6 +61,16 @@ def test_interface_problem_full_size():
     jref = hyd.jvp_complex_step(u, kk, tau, dk)
     jgot = gm.jvp(ud, kd, tau, torch.tensor(dk, device="cuda")).cpu().numpy()
     assert np.linalg.norm(jgot - jref) <= 1e-11 * np.linalg.norm(jref)
+    # TF32 tensor-core J.w from the record (the interface workload's reduced-precision form)
+    dk32 = dk.astype(np.float32).astype(np.float64)
+    jref32 = hyd.jvp_complex_step(u, kk, tau, dk32)
+    gm.linearize(ud, kd, tau)
+    jt = gm.jvp(ud, kd, tau, torch.tensor(dk32, device="cuda", dtype=torch.float32), tc="tf32")
+    jt = jt.double().cpu().numpy()
+    assert np.linalg.norm(jt[:nx] - jref32[:nx]) <= 2e-5 * np.linalg.norm(jref32[:nx])
+    for g, r in ((jt[nx:2 * nx], jref32[nx:2 * nx]), (jt[2 * nx:], jref32[2 * nx:])):
+        assert np.linalg.norm(g - r) <= 5 * 2.0 ** -11 * np.linalg.norm(r)
+    gm.tc_status()
 
 
 @pytest.mark.parametrize("k", [1, 2, 3])
