@@ -129,6 +129,21 @@ lh_status lh_jvp(lh_mesh* mesh, const double* u, const double* k, double tau,
  * with LH_FP32_LIN and the same u, k (pointers) and tau use it.  lh_newton_step with an
  * FP32 J.w writes the record at every Newton iterate and invalidates it on return.
  * Asynchronous; allocates the record on first use. */
+/* Box decomposition (paper Sec. 2.2, Eq. (8) with P != I).  A partition is a mesh of a
+ * sub-box of the global box: same element size, the global h0 and h_coarse, walls only on
+ * the global boundary (the shared face unmasked).  On a shared face the velocity rows of
+ * the residual and of J.w hold each side's partial sums (mass and force terms of its own
+ * elements); summing the two sides' values gives the global operator there.  x rows,
+ * fixed velocity rows and L2 rows are complete on each side.
+ * face = 2 axis + side (side 0 low, 1 high, numbered as bc_mask).  buf holds
+ * dim * (nodes of the face) entries, component-major, the face nodes lexicographic over the
+ * remaining axes.  prec LH_FP64: r, buf double; any other precision: float.
+ * lh_halo_pack copies the velocity rows of the face nodes of r into buf; lh_halo_add adds
+ * buf (the other side's packed rows) into the free velocity rows of r.  Asynchronous. */
+lh_status lh_halo_len(const lh_mesh* mesh, int face, long long* len);
+lh_status lh_halo_pack(lh_mesh* mesh, int face, const void* r, void* buf, lh_prec prec);
+lh_status lh_halo_add(lh_mesh* mesh, int face, const void* buf, void* r, lh_prec prec);
+
 /* Status of the tensor-core J.w: LH_OK, or LH_ECUDA if one of its bounded waits on the
  * tensor cores timed out since the mesh was created (synchronises; clears the flag). */
 lh_status lh_tc_status(lh_mesh* mesh);

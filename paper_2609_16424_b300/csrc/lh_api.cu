@@ -954,6 +954,35 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   return LH_OK;
 }
 
+lh_status lh_halo_len(const lh_mesh* m, int face, long long* len) {
+  if (!m || !len) return set_global_error(LH_EINVAL, "NULL argument to lh_halo_len");
+  if (face < 0 || face >= 2 * m->P.dim) return set_global_error(LH_EINVAL, "lh_halo_len: face out of range");
+  *len = halo_len(m->P, face / 2);
+  return LH_OK;
+}
+
+static lh_status halo_call(lh_mesh* m, int face, int mode, const void* src, void* dst, lh_prec prec) {
+  if (!m || !src || !dst) return fail(m, LH_EINVAL, "NULL argument to lh_halo_pack/lh_halo_add");
+  if (face < 0 || face >= 2 * m->P.dim) return fail(m, LH_EINVAL, "halo: face out of range");
+  if ((m->P.bc >> face) & 1u) return fail(m, LH_EINVAL, "halo: the face is a wall of this mesh");
+  if (prec == LH_FP64) {
+    LH_CK(m, launch_halo<double>(m->P, m->stream, face, mode, static_cast<const double*>(src),
+                                 static_cast<double*>(dst)));
+  } else {
+    LH_CK(m, launch_halo<float>(m->P, m->stream, face, mode, static_cast<const float*>(src),
+                                static_cast<float*>(dst)));
+  }
+  return LH_OK;
+}
+
+lh_status lh_halo_pack(lh_mesh* m, int face, const void* r, void* buf, lh_prec prec) {
+  return halo_call(m, face, 0, r, buf, prec);
+}
+
+lh_status lh_halo_add(lh_mesh* m, int face, const void* buf, void* r, lh_prec prec) {
+  return halo_call(m, face, 1, buf, r, prec);
+}
+
 lh_status lh_tc_status(lh_mesh* m) {
   if (!m) return fail(nullptr, LH_EINVAL, "mesh is NULL");
   int flag = 0;

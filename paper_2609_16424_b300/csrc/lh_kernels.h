@@ -33,6 +33,11 @@ template <class TO>
 cudaError_t launch_jvp_tc(const ElemParams& P, cudaStream_t s, int kind, const float* rec, double tau,
                           const float* dk, float* ev, TO* out, int* err, cudaEvent_t* ev2 = nullptr);
 bool jvp_tc_supported(int dim, int k);
+// halo of a box face (lh_halo.cu): mode 0 packs the dim velocity rows of the face nodes
+// into dst[dim][face nodes]; mode 1 adds src into the free velocity rows of dst
+long long halo_len(const ElemParams& P, int axis);
+template <class T>
+cudaError_t launch_halo(const ElemParams& P, cudaStream_t s, int face, int mode, const T* src, T* dst);
 cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                            const double* dk, double* ev, double* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,

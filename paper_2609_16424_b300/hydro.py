@@ -144,6 +144,33 @@ class Mesh:
         self._stream()
         self._check(_L.lh_linearize(self._h, _ptr(u), _ptr(k), float(tau)))
 
+    # -- box decomposition (halo of a shared face) -----------------------------------------
+    def halo_len(self, face):
+        n = C.c_longlong()
+        st = _L.lh_halo_len(self._h, int(face), C.byref(n))
+        if st != _lib.LH_OK:
+            raise LHError(st, _L.lh_last_error(None).decode())
+        return int(n.value)
+
+    def halo_pack(self, face, r, buf=None):
+        """Velocity rows of the nodes of a face of r (partial sums of this side)."""
+        self._vec(r, "r", r.dtype)
+        buf = torch.empty(self.halo_len(face), dtype=r.dtype, device=self.device) if buf is None else buf
+        self._vec(buf, "buf", r.dtype, self.halo_len(face))
+        self._stream()
+        prec = _lib.LH_FP64 if r.dtype == torch.float64 else _lib.LH_FP32
+        self._check(_L.lh_halo_pack(self._h, int(face), _ptr(r), _ptr(buf), prec))
+        return buf
+
+    def halo_add(self, face, buf, r):
+        """r[free velocity rows of the face] += buf (the other side's packed rows)."""
+        self._vec(r, "r", r.dtype)
+        self._vec(buf, "buf", r.dtype, self.halo_len(face))
+        self._stream()
+        prec = _lib.LH_FP64 if r.dtype == torch.float64 else _lib.LH_FP32
+        self._check(_L.lh_halo_add(self._h, int(face), _ptr(buf), _ptr(r), prec))
+        return r
+
     def tc_status(self):
         """Raise LHError if a bounded tensor-core wait of the TF32/BF16 J.w timed out."""
         self._check(_L.lh_tc_status(self._h))
