@@ -196,8 +196,12 @@ lh_status ensure_work(lh_mesh* m, int restart) {
   m->d_fwork = nullptr;
   if (cudaMalloc(&m->d_work, sizeof(double) * need) != cudaSuccess)
     return fail(m, LH_ENOMEM, "cannot allocate Newton-GMRES workspace");
-  if (cudaMalloc(&m->d_fwork, sizeof(float) * ((long long)(restart + 4) * n)) != cudaSuccess)
+  m->ldf = (n + 63) / 64 * 64;
+  if (cudaMalloc(&m->d_fwork, sizeof(float) * ((long long)(restart + 4) * m->ldf)) != cudaSuccess)
     return fail(m, LH_ENOMEM, "cannot allocate FP32 workspace");
+  // the tails [n, ldf) stay zero: kernels write n entries, the float4 reductions read n4
+  if (cudaMemset(m->d_fwork, 0, sizeof(float) * ((long long)(restart + 4) * m->ldf)) != cudaSuccess)
+    return fail(m, LH_ECUDA, "cannot clear FP32 workspace");
   m->work_len = need;
   m->restart_alloc = restart;
   return LH_OK;
@@ -284,12 +288,18 @@ struct KrylovOp {
 
 // Restarted, right-preconditioned GMRES on J dk = -r from dk = 0 (paper Sec. 3.5, Eq. (22)).
 // Classical Gram-Schmidt in one fused reduction (V^T w and w.w), the norm of the projected
-// vector by Pythagoras, a second pass when more than half of the norm cancelled (DGKS).
+// vector by Pythagoras, a second pass when more than half of the squared norm cancelled
+// (DGKS).  (Skipping the second pass for the FP32 basis unless 63/64 cancelled was tried:
+// GMRES then needed 2.4x the iterations on the point-blast workload.)
 // Basis V and work vectors w, ulin of type T; zd, wd double scratch; Givens on the host.
 template <class T>
 lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const double* r, double nr, double* dk,
                 T* V, T* w, T* ulin, double* zd, double* wd, lh_step_stats& S) {
   const long long n = m->n;
+  // FP32 basis: leading dimension ldf, reductions over n rounded up to 4 (zero tails);
+  // FP64 basis: contiguous
+  const long long ld = sizeof(T) == sizeof(float) ? m->ldf : n;
+  const long long len = sizeof(T) == sizeof(float) ? (n + 3) / 4 * 4 : n;
   const int mres = o.restart;
   cudaStream_t s = m->stream;
   double* dh = m->d_scalar + 8;   // device Hessenberg column / y (<= 72 entries)
@@ -306,11 +316,11 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
     g[0] = beta;
     int j = 0;
     for (; j < mres && total < o.gmres_maxit; ++j) {
-      T* vj = V + (long long)j * n;
+      T* vj = V + (long long)j * ld;
       if ((st = op.apply(vj, w)) != LH_OK) return st;
       ++S.jvp_evals;
-      LH_CK(m, launch_mdot<T>(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
-      LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, n, dh, w, n));
+      LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh));
+      LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh, w, len));
       LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
       LH_CK(m, cudaStreamSynchronize(s));
       double ww = hcol[j + 1], hh = 0.0;
@@ -320,8 +330,8 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
       }
       double hn2 = ww - hh;
       if (!(hn2 > 0.5 * ww)) {
-        LH_CK(m, launch_mdot<T>(s, V, j + 1, n, w, n, 1, m->d_part, m->d_counter, dh));
-        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, n, dh, w, n));
+        LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh));
+        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh, w, len));
         LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
         LH_CK(m, cudaStreamSynchronize(s));
         ++S.reorth;
@@ -332,7 +342,7 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
         }
         hn2 = hcol[j + 1] - hh2;
         if (!(hn2 > 1e-4 * hcol[j + 1])) {   // still cancelling: take the exact norm
-          LH_CK(m, launch_mdot<T>(s, w, 1, 0, w, n, 0, m->d_part, m->d_counter, dh));
+          LH_CK(m, launch_mdot<T>(s, w, 1, 0, w, len, 0, m->d_part, m->d_counter, dh));
           LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double), cudaMemcpyDeviceToHost, s));
           LH_CK(m, cudaStreamSynchronize(s));
           hn2 = hcol[0];
@@ -341,7 +351,7 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
       if (!std::isfinite(hn2)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite Krylov vector");
       const double hn = std::sqrt(std::fmax(hn2, 0.0));
       H[(size_t)(j + 1) * mres + j] = hn;
-      if (hn > 0.0) LH_CK(m, (launch_scale<T, T>(s, 1.0 / hn, w, 0.0, nullptr, V + (long long)(j + 1) * n, n)));
+      if (hn > 0.0) LH_CK(m, (launch_scale<T, T>(s, 1.0 / hn, w, 0.0, nullptr, V + (long long)(j + 1) * ld, n)));
       for (int i = 0; i < j; ++i) {   // previous Givens rotations
         const double a = H[(size_t)i * mres + j], b = H[(size_t)(i + 1) * mres + j];
         H[(size_t)i * mres + j] = cs[i] * a + sn[i] * b;
@@ -370,7 +380,7 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
       y[i] = sum / H[(size_t)i * mres + i];
     }
     LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
-    LH_CK(m, launch_gemv<T>(s, V, j, n, dh, 0.0, ulin, n));
+    LH_CK(m, launch_gemv<T>(s, V, j, ld, dh, 0.0, ulin, len));
     LH_CK(m, (launch_prec<T, double>(op.pk, s, m->P, m->kron, m->d_diagMv, m->d_invMe, ulin, zd, op.tau)));
     LH_CK(m, launch_axpby(s, 1.0, zd, 1.0, dk, n));
     if (done || total >= o.gmres_maxit) break;
@@ -882,10 +892,11 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   double* wd = zd + n;                        // double scratch
   double* kt = wd + n;                        // trial iterate
   double* rt = kt + n;                        // residual at the trial
-  float* Vf = m->d_fwork;                     // (mres + 1) x n FP32 Krylov basis
-  float* wf = Vf + (long long)(mres + 1) * n;
-  float* zf = wf + n;
-  float* uf = zf + n;
+  const long long ldf = m->ldf;
+  float* Vf = m->d_fwork;                     // (mres + 1) x ldf FP32 Krylov basis
+  float* wf = Vf + (long long)(mres + 1) * ldf;
+  float* zf = wf + ldf;
+  float* uf = zf + ldf;
   const double tau = 0.5 * dt;
 
   if (k_prev) {

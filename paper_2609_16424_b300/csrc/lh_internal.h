@@ -79,7 +79,8 @@ struct lh_mesh {
   // Newton / GMRES workspace (allocated on first lh_newton_step)
   double* d_work = nullptr;
   long long work_len = 0;
-  float* d_fwork = nullptr;        // FP32 J.w in/out buffers
+  float* d_fwork = nullptr;        // FP32 Krylov basis and work vectors, leading dimension ldf
+  long long ldf = 0;               // n rounded up to 64 floats (16-byte aligned, zero tails)
   float* d_fconst = nullptr;       // [3 NE] float rho0 detJ0, gamma - 1, gamma (gamma - 1)
   float* d_rec = nullptr;          // linearisation record [NE][rec_len][NQ] (lazily allocated)
   const double* rec_u = nullptr;   // arguments of the last lh_linearize (for the LH_FP32_LIN check)

@@ -9,6 +9,7 @@
 // dense 1D contractions, one per axis, with the inverse 1D matrices (precomputed in
 // double on the host, applied in float).  For piecewise-constant rho0 the operator is
 // scaled by the nodal mean of rho0^(-1/2) on both sides, an approximation.
+#include <utility>
 #include "lh_kernels.h"
 
 namespace lh {
@@ -16,163 +17,187 @@ namespace lh {
 static inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // The axis passes of the Kronecker inverse act on the dim velocity components
-// (component-major, NV nodes each): out[c, node] = sum_j A_c[i_axis][j] in[c, line + j*stride]
-// with At_free / At_fixed the transposed inverses (entry [j][i]) of the 1D matrix without /
-// with the masked boundary rows of this axis (component c == axis uses At_fixed).  The input
-// line (or tile of lines) is staged in shared memory; the factor is read through L1
-// (coalesced in the x pass, a warp broadcast in the y/z passes).
-constexpr int kKronWarps = 4;
-constexpr int kKronOut = 2;   // outputs per thread along the axis in the y/z passes
+// (component-major, NV nodes each).  Along axis a the nodes of one component form an array
+// [outer][Na][inner] (inner = product of the extents of the axes before a, outer of those
+// after it), and the pass is, per component, the product
+//     C[i][col] = sum_j A[i][j] X[j][col],   col = (o, in),  X[j][col] = x[(o Na + j) inner + in]
+// with A the inverse 1D matrix of the axis (At_fixed for the component normal to it: the
+// masked boundary rows of that axis are identity rows).  One kernel serves every axis: a
+// block computes a tile of kTI rows i by kTC columns, staging kTK rows j of A (from its
+// stored transpose) and of X in shared memory per step; each thread owns a 4 x 4 register
+// tile.  The first pass reads r_v scaled by D^-1/2 (and extra blocks write the L2 rows
+// z_e = M_E^-1 r_e); the last pass scales by D^-1/2, passes fixed rows through and writes
+// the x rows z_x = r_x + tau z_v of the block upper-triangular preconditioner.
+constexpr int kTI = 64, kTC = 32, kTK = 32, kKronThreads = 128;
+constexpr int kTCP = kTC + 4;            // padded row of the X tile (16-byte aligned rows)
+constexpr int kERowsPerThread = 8;
 
-// x pass: one warp per contiguous line; lanes own outputs i = lane + 32 q.
-__global__ void __launch_bounds__(32 * kKronWarps)
-k_kron_x(long long nv, int dim, int N0, const float* __restrict__ At_free, const float* __restrict__ At_fixed,
-         const float* __restrict__ in, float* __restrict__ out) {
-  extern __shared__ float kx_lines[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long per_c = nv / N0;
-  const long long line = (long long)blockIdx.x * kKronWarps + warp;
-  if (line >= per_c * dim) return;
-  float* buf = kx_lines + warp * N0;
-  for (int j = lane; j < N0; j += 32) buf[j] = in[line * N0 + j];
-  __syncwarp();
-  const float* At = line / per_c == 0 ? At_fixed : At_free;
-  for (int i0 = 0; i0 < N0; i0 += 32 * 4) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int j = 0; j < N0; ++j) {
-      const float x = buf[j];
-      const float* row = At + (long long)j * N0 + i0 + lane;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (i0 + lane + 32 * q < N0) acc[q] += __ldg(row + 32 * q) * x;
+struct KronPass {
+  int axis, Na;
+  long long inner, outer, nv;
+  int tiles_c, tiles_i;     // column tiles per component, row tiles
+  long long main_blocks;    // dim * tiles_c * tiles_i
+};
+
+template <int MODE, class TR, class TZ>
+__global__ void __launch_bounds__(kKronThreads)
+k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const float* __restrict__ At_fixed,
+            const float* __restrict__ xin, const TR* __restrict__ r, const double* __restrict__ scale,
+            const double* __restrict__ ime, float* __restrict__ fout, TZ* __restrict__ z, double tau) {
+  __shared__ __align__(16) float As[kTK][kTI];
+  __shared__ __align__(16) float Xs[kTK][kTCP];
+  __shared__ long long s_cb[kTC];   // node of (column, j = 0): o Na inner + in; -1 past the end
+  __shared__ bool s_cfix[kTC];      // row fixed by a coordinate other than the pass axis
+  const long long n1 = (long long)P.dim * P.NV;
+  if constexpr (MODE == 0) {
+    if ((long long)blockIdx.x >= K.main_blocks) {   // L2 rows: z_e = M_E^-1 r_e
+      const long long b = blockIdx.x - K.main_blocks;
+      for (int q = 0; q < kERowsPerThread; ++q) {
+        const long long e = (b * kERowsPerThread + q) * kKronThreads + threadIdx.x;
+        if (e < P.NEd) z[2 * n1 + e] = TZ((double)r[2 * n1 + e] * ime[e]);
+      }
+      return;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (i0 + lane + 32 * q < N0) out[line * N0 + i0 + lane + 32 * q] = acc[q];
   }
-}
-
-// y / z pass: a block holds a tile of 32 consecutive x-positions times the whole line along
-// the axis and computes kKronWarps * kKronOut outputs along the axis (blocks split the axis).
-// The last pass (LAST) applies D^-1/2, skips fixed rows (written by k_prec_xe) and writes the
-// x rows z_x = r_x + tau z_v of the block upper-triangular preconditioner.
-template <class TO, class TR, bool LAST>
-__global__ void __launch_bounds__(32 * kKronWarps)
-k_kron_yz(long long nv, int dim, int N0, int N1, int N2, int axis, const float* __restrict__ At_free,
-          const float* __restrict__ At_fixed, const float* __restrict__ in, TO* __restrict__ out,
-          const double* __restrict__ scale, ElemParams P, const TR* __restrict__ r, TO* __restrict__ zx, double tau) {
-  extern __shared__ float kyz_tile[];   // [Na][32]
-  const int Na = axis == 1 ? N1 : N2;
-  const long long stride = axis == 1 ? (long long)N0 : (long long)N0 * N1;
-  const int other = axis == 1 ? N2 : N1;
-  const int xblocks = (N0 + 31) / 32;
-  constexpr int per_block = kKronWarps * kKronOut;
-  const int ablocks = (Na + per_block - 1) / per_block;
   long long b = blockIdx.x;
-  const int ab = (int)(b % ablocks);
-  b /= ablocks;
-  const int xb = (int)(b % xblocks);
-  b /= xblocks;
-  const int io = (int)(b % other);
-  const int c = (int)(b / other);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = xb * 32 + lane;
-  const bool xin = i0 < N0;
-  const long long base = (long long)c * nv + i0 + (axis == 1 ? (long long)io * N0 * N1 : (long long)io * N0);
-#pragma unroll 4
-  for (int j = warp; j < Na; j += kKronWarps) kyz_tile[j * 32 + lane] = xin ? in[base + j * stride] : 0.f;
+  const int ti = (int)(b % K.tiles_i);
+  b /= K.tiles_i;
+  const int tcol = (int)(b % K.tiles_c);
+  const int c = (int)(b / K.tiles_c);
+  const float* At = c == K.axis ? At_fixed : At_free;
+  const int Na = K.Na;
+  const long long ncol = K.outer * K.inner;           // columns of one component
+  const long long col0 = (long long)tcol * kTC;
+  const int i0 = ti * kTI;
+  const int t = threadIdx.x;
+  const int ri = (t / (kTC / 4)) * 4, rc = (t % (kTC / 4)) * 4;   // this thread's 4 x 4 tile
+  float acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+  const long long cbase = (long long)c * K.nv;
+  if (t < kTC) {
+    const long long col = col0 + t;
+    long long cb = -1;
+    bool fx = false;
+    if (col < ncol) {
+      const long long o = col / K.inner, in = col - o * K.inner;
+      cb = o * Na * K.inner + in;
+      if constexpr (MODE == 2) {
+        if (c != K.axis) {   // coordinate of component c's own axis, taken at j = 0
+          const long long nd = cb;
+          long long ic;
+          int Nc;
+          if (c == 0) { ic = nd % P.N0; Nc = P.N0; }
+          else if (c == 1) { ic = (nd / P.N0) % P.N1; Nc = P.N1; }
+          else { ic = nd / ((long long)P.N0 * P.N1); Nc = P.N2; }
+          fx = (((P.bc >> (2 * c)) & 1u) && ic == 0) || (((P.bc >> (2 * c + 1)) & 1u) && ic == Nc - 1);
+        }
+      }
+    }
+    s_cb[t] = cb;
+    s_cfix[t] = fx;
+  }
   __syncthreads();
-  if (!xin) return;
-  const float* At = c == axis ? At_fixed : At_free;
-  const int ia0 = ab * per_block + warp * kKronOut;
-  float acc[kKronOut];
+  const bool fix_lo = ((P.bc >> (2 * c)) & 1u) && c == K.axis;
+  const bool fix_hi = ((P.bc >> (2 * c + 1)) & 1u) && c == K.axis;
+  for (int j0 = 0; j0 < Na; j0 += kTK) {
+    // A^T tile: As[j][i] = At[(j0 + j) Na + i0 + i] (coalesced over i)
+    for (int e = t; e < kTK * kTI; e += kKronThreads) {
+      const int jj = e / kTI, ii = e % kTI;
+      As[jj][ii] = (j0 + jj < Na && i0 + ii < Na) ? __ldg(At + (long long)(j0 + jj) * Na + i0 + ii) : 0.f;
+    }
+    // X tile: Xs[j][cc] = x[(o Na + j0 + j) inner + in], col = col0 + cc = o inner + in
+    for (int e = t; e < kTK * kTC; e += kKronThreads) {
+      int jj, cc;
+      if (K.inner == 1) {   // lines are contiguous: read along j
+        jj = e % kTK;
+        cc = e / kTK;
+      } else {              // columns are contiguous: read along the columns
+        cc = e % kTC;
+        jj = e / kTC;
+      }
+      const long long cb = s_cb[cc];
+      float v = 0.f;
+      if (j0 + jj < Na && cb >= 0) {
+        const long long node = cb + (long long)(j0 + jj) * K.inner;
+        if constexpr (MODE == 0) v = (float)((double)r[n1 + cbase + node] * scale[node]);
+        else v = xin[cbase + node];
+      }
+      Xs[jj][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int jj = 0; jj < kTK; ++jj) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[jj][ri]);
+      const float4 x4 = *reinterpret_cast<const float4*>(&Xs[jj][rc]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-  for (int q = 0; q < kKronOut; ++q) acc[q] = 0.f;
-  for (int j = 0; j < Na; ++j) {
-    const float x = kyz_tile[j * 32 + lane];
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int q = 0; q < kKronOut; ++q)
-      if (ia0 + q < Na) acc[q] += __ldg(At + (long long)j * Na + ia0 + q) * x;
+        for (int q = 0; q < 4; ++q) acc[a][q] += av[a] * xv[q];
+    }
+    __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < kKronOut; ++q) {
-    const int ia = ia0 + q;
-    if (ia >= Na) break;
-    const long long t = base + ia * stride;             // index into the dim x nv velocity block
-    if constexpr (LAST) {
-      const long long node = t - (long long)c * nv;
-      long long ic;
-      int Nc;
-      if (c == 0) { ic = node % P.N0; Nc = P.N0; }
-      else if (c == 1) { ic = (node / P.N0) % P.N1; Nc = P.N1; }
-      else { ic = node / ((long long)P.N0 * P.N1); Nc = P.N2; }
-      const bool fixed = (((P.bc >> (2 * c)) & 1u) && ic == 0) || (((P.bc >> (2 * c + 1)) & 1u) && ic == Nc - 1);
-      const double zv = fixed ? (double)r[nv * dim + t] : (double)acc[q] * scale[node];
-      if (!fixed) out[t] = TO(zv);
-      zx[t] = TO((double)r[t] + tau * zv);
-    } else {
-      out[t] = TO(acc[q]);
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ri + a;
+    if (i >= Na) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long cb = s_cb[rc + q];
+      if (cb < 0) continue;
+      const long long node = cb + (long long)i * K.inner;
+      if constexpr (MODE == 2) {
+        const bool fixed = s_cfix[rc + q] || (fix_lo && i == 0) || (fix_hi && i == Na - 1);
+        const long long tv = cbase + node;
+        const double zv = fixed ? (double)r[n1 + tv] : (double)acc[a][q] * scale[node];
+        z[n1 + tv] = TZ(zv);
+        z[tv] = TZ((double)r[tv] + tau * zv);
+      } else {
+        fout[cbase + node] = acc[a][q];
+      }
     }
   }
 }
 
-// z = P^-1 r for the whole stage vector: x rows identity, v rows the Kronecker mass
-// inverse (fixed rows identity), e rows the exact L2 mass inverse.
-template <class TR, class TZ>
-__global__ void k_prec_xe(long long n1, long long nv, int dim, int N0, int N1, int N2, unsigned bc, long long nEd,
-                          const double* __restrict__ ime, const TR* __restrict__ r, TZ* __restrict__ z,
-                          const double* __restrict__ scale, float* __restrict__ rs) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long n = 2 * n1 + nEd;
-  if (i >= n) return;
-  if (i < n1) {
-    // x rows are written by the last axis pass (z_x = r_x + tau z_v)
-  } else if (i < 2 * n1) {
-    const long long j = i - n1;
-    const int comp = (int)(j / nv);
-    const long long nd = j % nv;
-    long long ic;
-    int Nc;
-    if (comp == 0) { ic = nd % N0; Nc = N0; }
-    else if (comp == 1) { ic = (nd / N0) % N1; Nc = N1; }
-    else { ic = nd / ((long long)N0 * N1); Nc = N2; }
-    const bool fixed = (((bc >> (2 * comp)) & 1u) && ic == 0) || (((bc >> (2 * comp + 1)) & 1u) && ic == Nc - 1);
-    if (fixed) z[i] = TZ(r[i]);
-    rs[j] = (float)((double)r[i] * scale[nd]);    // D^-1/2 r_v, input of the first axis pass
-  } else {
-    z[i] = TZ((double)r[i] * ime[i - 2 * n1]);
-  }
+static KronPass kron_pass(const ElemParams& P, int axis) {
+  const long long N[3] = {P.N0, P.N1, P.N2};
+  KronPass K;
+  K.axis = axis;
+  K.Na = (int)N[axis];
+  K.inner = 1;
+  for (int a = 0; a < axis; ++a) K.inner *= N[a];
+  K.outer = 1;
+  for (int a = axis + 1; a < P.dim; ++a) K.outer *= N[a];
+  K.nv = P.NV;
+  K.tiles_c = (int)((K.outer * K.inner + kTC - 1) / kTC);
+  K.tiles_i = (K.Na + kTI - 1) / kTI;
+  K.main_blocks = (long long)P.dim * K.tiles_c * K.tiles_i;
+  return K;
 }
 
 template <class TR, class TZ>
 static cudaError_t kron_apply(cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* inv_me,
                               const TR* r, TZ* z, double tau) {
-  const long long nv = P.NV, n1 = (long long)P.dim * nv;
   float* a = K.work;
-  float* b = K.work + n1;
-  TZ* zv = z + n1;
-  const long long n = 2 * n1 + P.NEd;
-  const int bs = 32 * kKronWarps;
-  // e rows, fixed v rows, and the scaled float copy of the v rows
-  k_prec_xe<TR, TZ><<<nb(n, 256), 256, 0, s>>>(n1, nv, P.dim, P.N0, P.N1, P.N2, P.bc, P.NEd, inv_me, r, z, K.scale, a);
-  const long long lines = n1 / P.N0;
-  k_kron_x<<<nb(lines, kKronWarps), bs, sizeof(float) * kKronWarps * P.N0, s>>>(nv, P.dim, P.N0, K.At_free[0],
-                                                                                  K.At_fixed[0], a, b);
-  const int xblocks = (P.N0 + 31) / 32, per_block = kKronWarps * kKronOut;
-  auto grid = [&](int Na, int other) {
-    return (unsigned)((long long)P.dim * other * xblocks * ((Na + per_block - 1) / per_block));
-  };
-  if (P.dim == 2) {
-    k_kron_yz<TZ, TR, true><<<grid(P.N1, 1), bs, sizeof(float) * 32 * P.N1, s>>>(
-        nv, 2, P.N0, P.N1, 1, 1, K.At_free[1], K.At_fixed[1], b, zv, K.scale, P, r, z, tau);
-    count_launches(3);
-  } else {
-    k_kron_yz<float, TR, false><<<grid(P.N1, P.N2), bs, sizeof(float) * 32 * P.N1, s>>>(
-        nv, 3, P.N0, P.N1, P.N2, 1, K.At_free[1], K.At_fixed[1], b, a, nullptr, P, nullptr, nullptr, 0.0);
-    k_kron_yz<TZ, TR, true><<<grid(P.N2, P.N1), bs, sizeof(float) * 32 * P.N2, s>>>(
-        nv, 3, P.N0, P.N1, P.N2, 2, K.At_free[2], K.At_fixed[2], a, zv, K.scale, P, r, z, tau);
-    count_launches(4);
+  float* b = K.work + (long long)P.dim * P.NV;
+  // pass over x (+ L2 rows), [pass over y], last pass over the last axis
+  const KronPass k0 = kron_pass(P, 0);
+  const long long eblocks = (P.NEd + (long long)kKronThreads * kERowsPerThread - 1) / ((long long)kKronThreads * kERowsPerThread);
+  k_kron_pass<0, TR, TZ><<<(unsigned)(k0.main_blocks + eblocks), kKronThreads, 0, s>>>(
+      k0, P, K.At_free[0], K.At_fixed[0], nullptr, r, K.scale, inv_me, a, z, tau);
+  if (P.dim == 3) {
+    const KronPass k1 = kron_pass(P, 1);
+    k_kron_pass<1, TR, TZ><<<(unsigned)k1.main_blocks, kKronThreads, 0, s>>>(
+        k1, P, K.At_free[1], K.At_fixed[1], a, r, K.scale, inv_me, b, z, tau);
+    std::swap(a, b);
   }
+  const KronPass kl = kron_pass(P, P.dim - 1);
+  k_kron_pass<2, TR, TZ><<<(unsigned)kl.main_blocks, kKronThreads, 0, s>>>(
+      kl, P, K.At_free[P.dim - 1], K.At_fixed[P.dim - 1], a, r, K.scale, inv_me, nullptr, z, tau);
+  count_launches(P.dim);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // dot products, Gram-Schmidt updates, the block-diagonal preconditioner and precision
 // conversions.  All are HBM-bound streaming kernels over the n unknowns.
 #include <cfloat>
+#include <cstdint>
 #include "lh_kernels.h"
 
 namespace lh {
@@ -14,7 +15,7 @@ static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) 
 // partials; the last block to finish (ticket from an atomic counter) adds the partials of
 // every output in block order.  The result depends only on n and the data, not on the
 // order in which blocks finish.
-constexpr int kChunk = 8;
+constexpr int kChunk = 16;
 
 static inline unsigned red_grid(long long n) {
   long long g = (n + 1023) / 1024;
@@ -23,7 +24,7 @@ static inline unsigned red_grid(long long n) {
   return (unsigned)g;
 }
 
-template <class T>
+template <class T, bool VEC4>
 __global__ void __launch_bounds__(kRedThreads)
 k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, long long n, int with_self,
        double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ out) {
@@ -32,7 +33,8 @@ k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, lo
   __shared__ double red[kRedThreads / 32][kChunk];
   __shared__ bool last;
   const int nout = m + (with_self ? 1 : 0);
-  const long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  long long chunk = (n + gridDim.x - 1) / gridDim.x;
+  if constexpr (VEC4) chunk = (chunk + 3) / 4 * 4;   // chunk boundaries on 16-byte boundaries
   const long long beg = (long long)blockIdx.x * chunk;
   const long long end = beg + chunk < n ? beg + chunk : n;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -45,7 +47,18 @@ k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, lo
       vq[q] = c0 + q < m ? V + (long long)(c0 + q) * ld : w;
     }
     const int nq = nout - c0 < kChunk ? nout - c0 : kChunk;
-    if (w) {
+    if constexpr (VEC4) {
+      // four consecutive entries per load (ld, n multiples of 4, 16-byte aligned vectors)
+      for (long long i = beg + 4 * threadIdx.x; i < end; i += 4 * blockDim.x) {
+        const float4 wi = w ? *reinterpret_cast<const float4*>(w + i) : make_float4(1.f, 1.f, 1.f, 1.f);
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q)
+          if (q < nq) {
+            const float4 v = *reinterpret_cast<const float4*>(vq[q] + i);
+            acc[q] += (v.x * wi.x + v.y * wi.y) + (v.z * wi.z + v.w * wi.w);
+          }
+      }
+    } else if (w) {
       for (long long i = beg + threadIdx.x; i < end; i += blockDim.x) {
         const T wi = w[i];
 #pragma unroll
@@ -78,30 +91,16 @@ k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, lo
   __syncthreads();
   if (!last) return;
   __threadfence();
-  // last block: out[j] = sum over blocks of the partials, the whole block reducing up to
-  // kChunk outputs at a time (coalesced L2 loads, fixed-order trees)
+  // last block: out[j] = sum over blocks of the partials; kRedThreads / kChunk consecutive
+  // threads per output, each summing a fixed strided subset, then a fixed shuffle tree
+  constexpr int kPer = kRedThreads / kChunk;
   for (int c0 = 0; c0 < nout; c0 += kChunk) {
-    double acc[kChunk];
-#pragma unroll
-    for (int q = 0; q < kChunk; ++q) {
-      acc[q] = 0.0;
-      if (c0 + q < nout)
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-          acc[q] += __ldcg(part + (long long)(c0 + q) * gridDim.x + b);
-    }
-#pragma unroll
-    for (int q = 0; q < kChunk; ++q) {
-      double v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < kChunk && c0 + (int)threadIdx.x < nout) {
-      double v = 0.0;
-      for (int q = 0; q < kRedThreads / 32; ++q) v += red[q][threadIdx.x];
-      out[c0 + threadIdx.x] = v;
-    }
-    __syncthreads();
+    const int q = threadIdx.x / kPer, sub = threadIdx.x % kPer;
+    double v = 0.0;
+    if (c0 + q < nout)
+      for (unsigned b = sub; b < gridDim.x; b += kPer) v += __ldcg(part + (long long)(c0 + q) * gridDim.x + b);
+    for (int o = kPer / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, kPer);
+    if (sub == 0 && c0 + q < nout) out[c0 + q] = v;
   }
   if (threadIdx.x == 0) *counter = 0u;
 }
@@ -110,7 +109,16 @@ template <class T>
 cudaError_t launch_mdot(cudaStream_t s, const T* V, int m, long long ld, const T* w, long long n, int with_self,
                         double* partials, unsigned* counter, double* out_dev) {
   if (m + (with_self ? 1 : 0) > 72) return cudaErrorInvalidValue;
-  k_mdot<T><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
+  const bool vec4 = sizeof(T) == sizeof(float) && n % 4 == 0 && ld % 4 == 0 &&
+                    reinterpret_cast<uintptr_t>(V) % 16 == 0 && reinterpret_cast<uintptr_t>(w) % 16 == 0;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (vec4) {
+      k_mdot<T, true><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
+      count_launches(1);
+      return cudaGetLastError();
+    }
+  }
+  k_mdot<T, false><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -152,9 +160,49 @@ __global__ void k_gemv_sub(const T* __restrict__ V, int m, long long ld, const d
   }
 }
 
+// float4 forms (n, ld multiples of 4, 16-byte aligned): y = beta y + sign * V h
+template <bool SUB>
+__global__ void k_gemv4(const float* __restrict__ V, int m, long long ld, const double* __restrict__ h, float beta,
+                        float* __restrict__ y, long long n4) {
+  __shared__ float hs[64];
+  if ((int)threadIdx.x < m) hs[threadIdx.x] = SUB ? -(float)h[threadIdx.x] : (float)h[threadIdx.x];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (SUB || beta != 0.f) {
+      s = reinterpret_cast<const float4*>(y)[i];
+      if (!SUB) s = make_float4(beta * s.x, beta * s.y, beta * s.z, beta * s.w);
+    }
+    const float4* v = reinterpret_cast<const float4*>(V) + i;
+    const long long ld4 = ld / 4;
+    for (int j = 0; j < m; ++j, v += ld4) {
+      const float4 x = *v;
+      const float c = hs[j];
+      s.x += c * x.x;
+      s.y += c * x.y;
+      s.z += c * x.z;
+      s.w += c * x.w;
+    }
+    reinterpret_cast<float4*>(y)[i] = s;
+  }
+}
+
+static bool vec4_ok(const void* a, const void* b, long long ld, long long n) {
+  return n % 4 == 0 && ld % 4 == 0 && reinterpret_cast<uintptr_t>(a) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(b) % 16 == 0;
+}
+
 template <class T>
 cudaError_t launch_gemv_sub(cudaStream_t s, const T* V, int m, long long ld, const double* h, T* w, long long n) {
   if (m > 64) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (vec4_ok(V, w, ld, n)) {
+      const long long n4 = n / 4;
+      k_gemv4<true><<<nblk(n4, 256) < 4736u ? nblk(n4, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, 1.f, w, n4);
+      count_launches(1);
+      return cudaGetLastError();
+    }
+  }
   k_gemv_sub<T><<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, w, n);
   count_launches(1);
   return cudaGetLastError();
@@ -183,6 +231,14 @@ template <class T>
 cudaError_t launch_gemv(cudaStream_t s, const T* V, int m, long long ld, const double* h, double beta, T* y,
                         long long n) {
   if (m > 64) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (vec4_ok(V, y, ld, n)) {
+      const long long n4 = n / 4;
+      k_gemv4<false><<<nblk(n4, 256) < 4736u ? nblk(n4, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, (float)beta, y, n4);
+      count_launches(1);
+      return cudaGetLastError();
+    }
+  }
   k_gemv<T><<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, beta, y, n);
   count_launches(1);
   return cudaGetLastError();
