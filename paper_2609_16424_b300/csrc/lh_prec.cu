@@ -103,21 +103,23 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
   const bool fix_lo = ((P.bc >> (2 * c)) & 1u) && c == K.axis;
   const bool fix_hi = ((P.bc >> (2 * c + 1)) & 1u) && c == K.axis;
   for (int j0 = 0; j0 < Na; j0 += kTK) {
-    // A^T tile: As[j][i] = At[(j0 + j) Na + i0 + i] (coalesced over i)
-    for (int e = t; e < kTK * kTI; e += kKronThreads) {
-      const int jj = e / kTI, ii = e % kTI;
-      As[jj][ii] = (j0 + jj < Na && i0 + ii < Na) ? __ldg(At + (long long)(j0 + jj) * Na + i0 + ii) : 0.f;
+    // A^T tile As[j][i] = At[(j0 + j) Na + i0 + i] (coalesced over i) and X tile
+    // Xs[j][cc] = x[node(col0 + cc, j0 + j)]: every load of the stage is issued into
+    // registers before the first shared-memory store (fixed trip counts, unrolled), so the
+    // L2 latency is paid once per stage rather than once per element
+    constexpr int LA = kTK * kTI / kKronThreads, LX = kTK * kTC / kKronThreads;
+    float ra[LA], rx[LX];
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int e = t + u * kKronThreads, jj = e / kTI, ii = e % kTI;
+      ra[u] = (j0 + jj < Na && i0 + ii < Na) ? __ldg(At + (long long)(j0 + jj) * Na + i0 + ii) : 0.f;
     }
-    // X tile: Xs[j][cc] = x[(o Na + j0 + j) inner + in], col = col0 + cc = o inner + in
-    for (int e = t; e < kTK * kTC; e += kKronThreads) {
-      int jj, cc;
-      if (K.inner == 1) {   // lines are contiguous: read along j
-        jj = e % kTK;
-        cc = e / kTK;
-      } else {              // columns are contiguous: read along the columns
-        cc = e % kTC;
-        jj = e / kTC;
-      }
+#pragma unroll
+    for (int u = 0; u < LX; ++u) {
+      const int e = t + u * kKronThreads;
+      // lines contiguous (x pass): read along j; otherwise along the columns
+      const int jj = K.inner == 1 ? e % kTK : e / kTC;
+      const int cc = K.inner == 1 ? e / kTK : e % kTC;
       const long long cb = s_cb[cc];
       float v = 0.f;
       if (j0 + jj < Na && cb >= 0) {
@@ -125,7 +127,19 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
         if constexpr (MODE == 0) v = (float)((double)r[n1 + cbase + node] * scale[node]);
         else v = xin[cbase + node];
       }
-      Xs[jj][cc] = v;
+      rx[u] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      const int e = t + u * kKronThreads;
+      As[e / kTI][e % kTI] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < LX; ++u) {
+      const int e = t + u * kKronThreads;
+      const int jj = K.inner == 1 ? e % kTK : e / kTC;
+      const int cc = K.inner == 1 ? e / kTK : e % kTC;
+      Xs[jj][cc] = rx[u];
     }
     __syncthreads();
 #pragma unroll 8
