@@ -287,10 +287,12 @@ struct KrylovOp {
 };
 
 // Restarted, right-preconditioned GMRES on J dk = -r from dk = 0 (paper Sec. 3.5, Eq. (22)).
-// Classical Gram-Schmidt in one fused reduction (V^T w and w.w), the norm of the projected
-// vector by Pythagoras, a second pass when more than half of the squared norm cancelled
-// (DGKS).  (Skipping the second pass for the FP32 basis unless 63/64 cancelled was tried:
-// GMRES then needed 2.4x the iterations on the point-blast workload.)
+// Classical Gram-Schmidt applied twice (CGS2), each pass one fused reduction (V^T w and
+// w.w); the norm of the projected vector by Pythagoras from the second pass, computed on
+// the device by the update that writes v_{j+1}, so an iteration reads back one column of
+// coefficients; an exact norm only if the second pass still cancelled.  (Skipping the
+// second pass for the FP32 basis unless 63/64 of the norm cancelled was tried: GMRES then
+// needed 2.4x the iterations on the point-blast workload.)
 // Basis V and work vectors w, ulin of type T; zd, wd double scratch; Givens on the host.
 template <class T>
 lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const double* r, double nr, double* dk,
@@ -302,9 +304,9 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
   const long long len = sizeof(T) == sizeof(float) ? (n + 3) / 4 * 4 : n;
   const int mres = o.restart;
   cudaStream_t s = m->stream;
-  double* dh = m->d_scalar + 8;   // device Hessenberg column / y (<= 72 entries)
+  double* dh = m->d_scalar + 8;   // device coefficients: first pass [0, 72), second [72, 144); y
   lh_status st;
-  std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), g(mres + 1), hcol(72);
+  std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), g(mres + 1), hcol(144);
   LH_CK(m, cudaMemsetAsync(dk, 0, sizeof(double) * n, s));
   double beta = nr;
   const double beta0 = nr;
@@ -319,39 +321,34 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
       T* vj = V + (long long)j * ld;
       if ((st = op.apply(vj, w)) != LH_OK) return st;
       ++S.jvp_evals;
+      // CGS2: both passes and the normalisation on the device, one read-back per iteration
+      double* dh2 = dh + 72;   // the first pass writes up to 66 values at dh
+      T* vn = V + (long long)(j + 1) * ld;
       LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh));
       LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh, w, len));
-      LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+      LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh2));
+      LH_CK(m, launch_gemv_norm<T>(s, V, j + 1, ld, dh2, w, vn, len));
+      LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (72 + j + 2), cudaMemcpyDeviceToHost, s));
       LH_CK(m, cudaStreamSynchronize(s));
-      double ww = hcol[j + 1], hh = 0.0;
+      ++S.reorth;
+      double hh2 = 0.0;
       for (int i = 0; i <= j; ++i) {
-        H[(size_t)i * mres + j] = hcol[i];
-        hh += hcol[i] * hcol[i];
+        H[(size_t)i * mres + j] = hcol[i] + hcol[72 + i];
+        hh2 += hcol[72 + i] * hcol[72 + i];
       }
-      double hn2 = ww - hh;
-      if (!(hn2 > 0.5 * ww)) {
-        LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh));
-        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh, w, len));
-        LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+      const double ww2 = hcol[72 + j + 1];
+      double hn2 = ww2 - hh2;
+      if (!(hn2 > 1e-4 * ww2)) {   // the second pass still cancelled: take the exact norm
+        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh2, w, len));
+        LH_CK(m, launch_mdot<T>(s, w, 1, 0, w, len, 0, m->d_part, m->d_counter, dh));
+        LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double), cudaMemcpyDeviceToHost, s));
         LH_CK(m, cudaStreamSynchronize(s));
-        ++S.reorth;
-        double hh2 = 0.0;
-        for (int i = 0; i <= j; ++i) {
-          H[(size_t)i * mres + j] += hcol[i];
-          hh2 += hcol[i] * hcol[i];
-        }
-        hn2 = hcol[j + 1] - hh2;
-        if (!(hn2 > 1e-4 * hcol[j + 1])) {   // still cancelling: take the exact norm
-          LH_CK(m, launch_mdot<T>(s, w, 1, 0, w, len, 0, m->d_part, m->d_counter, dh));
-          LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double), cudaMemcpyDeviceToHost, s));
-          LH_CK(m, cudaStreamSynchronize(s));
-          hn2 = hcol[0];
-        }
+        hn2 = hcol[0];
+        if (hn2 > 0.0) LH_CK(m, (launch_scale<T, T>(s, 1.0 / std::sqrt(hn2), w, 0.0, nullptr, vn, n)));
       }
       if (!std::isfinite(hn2)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite Krylov vector");
       const double hn = std::sqrt(std::fmax(hn2, 0.0));
       H[(size_t)(j + 1) * mres + j] = hn;
-      if (hn > 0.0) LH_CK(m, (launch_scale<T, T>(s, 1.0 / hn, w, 0.0, nullptr, V + (long long)(j + 1) * ld, n)));
       for (int i = 0; i < j; ++i) {   // previous Givens rotations
         const double a = H[(size_t)i * mres + j], b = H[(size_t)(i + 1) * mres + j];
         H[(size_t)i * mres + j] = cs[i] * a + sn[i] * b;
@@ -437,6 +434,14 @@ bool check_desc(const lh_mesh_desc* d, std::string* why) {
   for (int c = 0; c < d->dim; ++c) {
     if (d->n[c] < 1) { *why = "element counts must be >= 1"; return false; }
     if (!(d->hi[c] > d->lo[c])) { *why = "box must have hi > lo"; return false; }
+  }
+  {
+    long long nv = 1;
+    for (int c = 0; c < d->dim; ++c) nv *= (long long)d->order * d->n[c] + 1;
+    if (d->dim * nv >= (1LL << 31)) {   // node-centric kernels index the lattice in 32 bits
+      *why = "mesh too large: dim * H1 nodes must stay below 2^31";
+      return false;
+    }
   }
   if (d->visc && !(d->psi0 > 0.0 && d->psi0 < 1.0)) { *why = "psi0 must be in (0, 1)"; return false; }
   if (!(d->eps_e > 0.0)) { *why = "eps_e must be > 0"; return false; }

@@ -86,9 +86,9 @@ __device__ __forceinline__ QpC<T> qp_consts(const ElemParams& P, const ElemIdx& 
 
 // true if velocity component comp of lattice node nd is fixed (v.n = 0 on a masked face)
 template <int DIM>
-__device__ __forceinline__ bool fixed_node(const ElemParams& P, long long nd, int comp) {
-  long long ic;
-  int Nc;
+__device__ __forceinline__ bool fixed_node(const ElemParams& P, long long nd_, int comp) {
+  const int nd = (int)nd_;
+  int ic, Nc;
   if (comp == 0) {
     ic = nd % P.N0;
     Nc = P.N0;
@@ -96,7 +96,7 @@ __device__ __forceinline__ bool fixed_node(const ElemParams& P, long long nd, in
     ic = (nd / P.N0) % P.N1;
     Nc = P.N1;
   } else {
-    ic = nd / ((long long)P.N0 * P.N1);
+    ic = nd / (P.N0 * P.N1);
     Nc = P.N2;
   }
   const bool lo = ((P.bc >> (2 * comp)) & 1u) && ic == 0;
@@ -741,38 +741,43 @@ k_dt_estimate(ElemParams P, const double* __restrict__ u, double* __restrict__ b
 // from an element scratch laid out [e][ncomp][ND], in a fixed order.
 template <int DIM, int K, class T>
 __device__ __forceinline__ T gather_node(const ElemParams& P, const T* __restrict__ ev, int ncomp, int comp,
-                                         long long nd) {
+                                         long long nd_) {
+  // 32-bit lattice arithmetic (node counts stay far below 2^31); per axis at most two
+  // elements share the node: option 0 (the lower element, or the only one) and option 1
+  // (the upper element), summed in the fixed order lower-then-upper per axis
   constexpr int D = K + 1, ND = Cfg<DIM, K>::ND;
-  int ic[3];
-  ic[0] = (int)(nd % P.N0);
-  ic[1] = (int)((nd / P.N0) % P.N1);
-  ic[2] = DIM == 3 ? (int)(nd / ((long long)P.N0 * P.N1)) : 0;
+  const int nd = (int)nd_;
+  const int ic[3] = {nd % P.N0, (nd / P.N0) % P.N1, DIM == 3 ? nd / (P.N0 * P.N1) : 0};
   const int nel[3] = {P.n0, P.n1, P.n2};
-  int el[3][2], loc[3][2], cnt[3];
+  int e0[3], l0[3], e1[3], l1[3];
+  bool v0[3], v1[3];
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
-    cnt[d] = 0;
     if (d >= DIM) {
-      el[d][0] = 0;
-      loc[d][0] = 0;
-      cnt[d] = 1;
+      e0[d] = 0; l0[d] = 0; v0[d] = true; e1[d] = 0; l1[d] = 0; v1[d] = false;
       continue;
     }
     const int q = ic[d] / K, r = ic[d] % K;
-    if (r == 0) {
-      if (q >= 1) { el[d][cnt[d]] = q - 1; loc[d][cnt[d]] = K; ++cnt[d]; }
-      if (q < nel[d]) { el[d][cnt[d]] = q; loc[d][cnt[d]] = 0; ++cnt[d]; }
+    if (r != 0) {
+      e0[d] = q; l0[d] = r; v0[d] = true;
+      e1[d] = 0; l1[d] = 0; v1[d] = false;
     } else {
-      el[d][0] = q;
-      loc[d][0] = r;
-      cnt[d] = 1;
+      e0[d] = q - 1; l0[d] = K; v0[d] = q >= 1;
+      e1[d] = q; l1[d] = 0; v1[d] = q < nel[d];
     }
   }
   T s = T(0);
-  for (int k2 = 0; k2 < cnt[2]; ++k2)
-    for (int k1 = 0; k1 < cnt[1]; ++k1)
-      for (int k0 = 0; k0 < cnt[0]; ++k0) {
-        const long long e = el[0][k0] + (long long)P.n0 * (el[1][k1] + (long long)P.n1 * el[2][k2]);
-        const int a = loc[0][k0] + D * (loc[1][k1] + D * loc[2][k2]);
+#pragma unroll
+  for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+    for (int b1 = 0; b1 < 2; ++b1)
+#pragma unroll
+      for (int b0 = 0; b0 < 2; ++b0) {
+        const bool ok = (b0 ? v1[0] : v0[0]) && (b1 ? v1[1] : v0[1]) && (b2 ? v1[2] : v0[2]);
+        if (!ok) continue;
+        const int ex = b0 ? e1[0] : e0[0], ey = b1 ? e1[1] : e0[1], ez = b2 ? e1[2] : e0[2];
+        const int a = (b0 ? l1[0] : l0[0]) + D * ((b1 ? l1[1] : l0[1]) + D * (b2 ? l1[2] : l0[2]));
+        const long long e = ex + (long long)P.n0 * (ey + (long long)P.n1 * ez);
         s += ev[(e * ncomp + comp) * ND + a];
       }
   return s;
@@ -796,8 +801,9 @@ __global__ void k_assemble_jvp(ElemParams P, const T* __restrict__ dk, double ta
                                TO* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= DIM * P.NV) return;
-  const int comp = (int)(i / P.NV);
-  const long long nd = i % P.NV;
+  const int nv = (int)P.NV, i32 = (int)i;
+  const int comp = i32 / nv;
+  const long long nd = i32 - comp * nv;
   const long long iv = DIM * P.NV + i;
   out[i] = TO(dk[i] - T(tau) * dk[iv]);
   out[iv] = TO(fixed_node<DIM>(P, nd, comp) ? dk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd));

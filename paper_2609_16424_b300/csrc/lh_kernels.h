@@ -68,6 +68,11 @@ cudaError_t launch_min(cudaStream_t s, const double* v, long long n, double* out
 // w -= sum_j h[j] V[j*ld + .]  (h: device doubles, m <= 64)
 template <class T>
 cudaError_t launch_gemv_sub(cudaStream_t s, const T* V, int m, long long ld, const double* h, T* w, long long n);
+// second Gram-Schmidt pass fused with the normalisation: y = (w - V h) / hn, with
+// hn^2 = h[m] - sum_{q<m} h[q]^2 (h[m] = w.w of the same multi-dot); y = 0 if hn^2 <= 0
+template <class T>
+cudaError_t launch_gemv_norm(cudaStream_t s, const T* V, int m, long long ld, const double* h, const T* w, T* y,
+                             long long n);
 // y = sum_j h[j] V[j*ld + .] + beta y  (h: device doubles, m <= 64)
 template <class T>
 cudaError_t launch_gemv(cudaStream_t s, const T* V, int m, long long ld, const double* h, double beta, T* y,

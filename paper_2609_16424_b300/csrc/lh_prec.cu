@@ -102,13 +102,13 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
   __syncthreads();
   const bool fix_lo = ((P.bc >> (2 * c)) & 1u) && c == K.axis;
   const bool fix_hi = ((P.bc >> (2 * c + 1)) & 1u) && c == K.axis;
-  for (int j0 = 0; j0 < Na; j0 += kTK) {
-    // A^T tile As[j][i] = At[(j0 + j) Na + i0 + i] (coalesced over i) and X tile
-    // Xs[j][cc] = x[node(col0 + cc, j0 + j)]: every load of the stage is issued into
-    // registers before the first shared-memory store (fixed trip counts, unrolled), so the
-    // L2 latency is paid once per stage rather than once per element
-    constexpr int LA = kTK * kTI / kKronThreads, LX = kTK * kTC / kKronThreads;
-    float ra[LA], rx[LX];
+  // A^T tile As[j][i] = At[(j0 + j) Na + i0 + i] (coalesced over i) and X tile
+  // Xs[j][cc] = x[node(col0 + cc, j0 + j)].  All loads of a stage go to registers first
+  // (fixed trip counts, unrolled) and the next stage's loads are issued before the current
+  // stage's FMAs, so the L2 latency overlaps the compute.
+  constexpr int LA = kTK * kTI / kKronThreads, LX = kTK * kTC / kKronThreads;
+  float ra[LA], rx[LX];
+  auto load_stage = [&](int j0) {
 #pragma unroll
     for (int u = 0; u < LA; ++u) {
       const int e = t + u * kKronThreads, jj = e / kTI, ii = e % kTI;
@@ -129,6 +129,9 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
       }
       rx[u] = v;
     }
+  };
+  load_stage(0);
+  for (int j0 = 0; j0 < Na; j0 += kTK) {
 #pragma unroll
     for (int u = 0; u < LA; ++u) {
       const int e = t + u * kKronThreads;
@@ -142,6 +145,7 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
       Xs[jj][cc] = rx[u];
     }
     __syncthreads();
+    if (j0 + kTK < Na) load_stage(j0 + kTK);
 #pragma unroll 8
     for (int jj = 0; jj < kTK; ++jj) {
       const float4 a4 = *reinterpret_cast<const float4*>(&As[jj][ri]);

@@ -15,7 +15,9 @@ static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) 
 // partials; the last block to finish (ticket from an atomic counter) adds the partials of
 // every output in block order.  The result depends only on n and the data, not on the
 // order in which blocks finish.
-constexpr int kChunk = 16;
+// outputs per pass over the chunk: 16 in float, 8 in double (register budget)
+template <class T> struct MdotChunk { static constexpr int value = sizeof(T) == sizeof(float) ? 16 : 8; };
+constexpr int kChunkMax = 16;
 
 static inline unsigned red_grid(long long n) {
   long long g = (n + 1023) / 1024;
@@ -30,7 +32,8 @@ k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, lo
        double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ out) {
   // per-thread and warp sums in T (float: a few hundred terms, ~1e-7 relative), block and
   // grid sums in double
-  __shared__ double red[kRedThreads / 32][kChunk];
+  constexpr int kChunk = MdotChunk<T>::value;
+  __shared__ double red[kRedThreads / 32][kChunkMax];
   __shared__ bool last;
   const int nout = m + (with_self ? 1 : 0);
   long long chunk = (n + gridDim.x - 1) / gridDim.x;
@@ -187,6 +190,59 @@ __global__ void k_gemv4(const float* __restrict__ V, int m, long long ld, const 
   }
 }
 
+// second Gram-Schmidt pass fused with the normalisation: y = (w - V h) / hn with
+// hn^2 = h[m] - sum_q h[q]^2 (h[m] = w.w from the same multi-dot); y = 0 if hn^2 <= 0
+__global__ void k_gemv4_norm(const float* __restrict__ V, int m, long long ld, const double* __restrict__ h,
+                             const float* __restrict__ w, float* __restrict__ y, long long n4) {
+  __shared__ float hs[64];
+  __shared__ float s_inv;
+  if (threadIdx.x == 0) {
+    double hh = 0.0;
+    for (int q = 0; q < m; ++q) hh += h[q] * h[q];
+    const double hn2 = h[m] - hh;
+    s_inv = hn2 > 0.0 ? (float)(1.0 / sqrt(hn2)) : 0.f;
+  }
+  if ((int)threadIdx.x < m) hs[threadIdx.x] = -(float)h[threadIdx.x];
+  __syncthreads();
+  const float inv = s_inv;
+  const long long ld4 = ld / 4;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    float4 s = reinterpret_cast<const float4*>(w)[i];
+    const float4* v = reinterpret_cast<const float4*>(V) + i;
+    for (int j = 0; j < m; ++j, v += ld4) {
+      const float4 x = *v;
+      const float c = hs[j];
+      s.x += c * x.x;
+      s.y += c * x.y;
+      s.z += c * x.z;
+      s.w += c * x.w;
+    }
+    reinterpret_cast<float4*>(y)[i] = make_float4(s.x * inv, s.y * inv, s.z * inv, s.w * inv);
+  }
+}
+
+template <class T>
+__global__ void k_gemv_norm(const T* __restrict__ V, int m, long long ld, const double* __restrict__ h,
+                            const T* __restrict__ w, T* __restrict__ y, long long n) {
+  __shared__ T hs[64];
+  __shared__ double s_inv;
+  if (threadIdx.x == 0) {
+    double hh = 0.0;
+    for (int q = 0; q < m; ++q) hh += h[q] * h[q];
+    const double hn2 = h[m] - hh;
+    s_inv = hn2 > 0.0 ? 1.0 / sqrt(hn2) : 0.0;
+  }
+  if ((int)threadIdx.x < m) hs[threadIdx.x] = T(h[threadIdx.x]);
+  __syncthreads();
+  const T inv = T(s_inv);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T s = w[i];
+    const T* v = V + i;
+    for (int j = 0; j < m; ++j, v += ld) s -= hs[j] * *v;
+    y[i] = s * inv;
+  }
+}
+
 static bool vec4_ok(const void* a, const void* b, long long ld, long long n) {
   return n % 4 == 0 && ld % 4 == 0 && reinterpret_cast<uintptr_t>(a) % 16 == 0 &&
          reinterpret_cast<uintptr_t>(b) % 16 == 0;
@@ -207,6 +263,27 @@ cudaError_t launch_gemv_sub(cudaStream_t s, const T* V, int m, long long ld, con
   count_launches(1);
   return cudaGetLastError();
 }
+template <class T>
+cudaError_t launch_gemv_norm(cudaStream_t s, const T* V, int m, long long ld, const double* h, const T* w, T* y,
+                             long long n) {
+  if (m > 64) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (vec4_ok(V, w, ld, n) && reinterpret_cast<uintptr_t>(y) % 16 == 0) {
+      const long long n4 = n / 4;
+      k_gemv4_norm<<<nblk(n4, 256) < 4736u ? nblk(n4, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, w, y, n4);
+      count_launches(1);
+      return cudaGetLastError();
+    }
+  }
+  k_gemv_norm<T><<<nblk(n, 256) < 4736u ? nblk(n, 256) : 4736u, 256, 0, s>>>(V, m, ld, h, w, y, n);
+  count_launches(1);
+  return cudaGetLastError();
+}
+template cudaError_t launch_gemv_norm<double>(cudaStream_t, const double*, int, long long, const double*,
+                                              const double*, double*, long long);
+template cudaError_t launch_gemv_norm<float>(cudaStream_t, const float*, int, long long, const double*,
+                                             const float*, float*, long long);
+
 template cudaError_t launch_gemv_sub<double>(cudaStream_t, const double*, int, long long, const double*, double*,
                                              long long);
 template cudaError_t launch_gemv_sub<float>(cudaStream_t, const float*, int, long long, const double*, float*,
