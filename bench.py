@@ -176,6 +176,11 @@ def timed_steps(mesh, u_s, k_s, dt, steps, prec, flush, profile=False):
     return times, stats, launches, prof
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the unchanged kernel, bench
+# workload (profiles/k_residual_blast3d_24_q2q1.md); None for kernels without a capture
+NCU_TRAFFIC_BYTES = {"k_residual<3,2>": 13348096}
+
+
 def tc_mma_flops(dim, k, ne, kind):
     """Tensor-core flops one k_jvp_tc launch issues (dense, padded element operators:
     per batch of 16 elements one 128 x NF x KF forward MMA and 128 x NB x 64 backward MMAs
@@ -384,6 +389,9 @@ def run_ours(args, rank, world, device):
                 "share_of_step": round(dom_ms / sum(times), 4),
                 "algorithmic_flops_per_launch": dom_flops}
 
+    roofline["traffic"] = NCU_TRAFFIC_BYTES.get(roofline["kernel"])
+    if roofline["traffic"] is not None:
+        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
     e2e_val, e2e_ms, e2e_bytes = e2e_steps(mesh, u_s, k_s, dt, max(2, min(args.steps, 5)), prec)
     out = {
         "metric": "GDoF/s of J.w & residual over the implicit step (FP64 residual, FP32 J.w)",
