@@ -24,12 +24,13 @@ static inline unsigned nb(long long n, int t) { return (unsigned)((n + t - 1) / 
 // with A the inverse 1D matrix of the axis (At_fixed for the component normal to it: the
 // masked boundary rows of that axis are identity rows).  One kernel serves every axis: a
 // block computes a tile of kTI rows i by kTC columns, staging kTK rows j of A (from its
-// stored transpose) and of X in shared memory per step; each thread owns a 4 x 4 register
-// tile.  The first pass reads r_v scaled by D^-1/2 (and extra blocks write the L2 rows
+// stored transpose) and of X in shared memory per step; each thread owns a 4 x kCQ register
+// tile (narrow column tiles: more blocks in flight, since the passes are latency bound).  The first pass reads r_v scaled by D^-1/2 (and extra blocks write the L2 rows
 // z_e = M_E^-1 r_e); the last pass scales by D^-1/2, passes fixed rows through and writes
 // the x rows z_x = r_x + tau z_v of the block upper-triangular preconditioner.
-constexpr int kTI = 64, kTC = 32, kTK = 32, kKronThreads = 128;
-constexpr int kTCP = kTC + 4;            // padded row of the X tile (16-byte aligned rows)
+constexpr int kTI = 64, kTC = 16, kTK = 32, kKronThreads = 128;
+constexpr int kCQ = 2;                   // columns per thread (thread tile 4 x kCQ)
+constexpr int kTCP = kTC + 4;            // padded row of the X tile
 constexpr int kERowsPerThread = 8;
 
 struct KronPass {
@@ -46,6 +47,7 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
             const double* __restrict__ ime, float* __restrict__ fout, TZ* __restrict__ z, double tau) {
   __shared__ __align__(16) float As[kTK][kTI];
   __shared__ __align__(16) float Xs[kTK][kTCP];
+  static_assert(kTI / 4 * (kTC / kCQ) == kKronThreads && kCQ == 2, "thread tiling");
   __shared__ long long s_cb[kTC];   // node of (column, j = 0): o Na inner + in; -1 past the end
   __shared__ bool s_cfix[kTC];      // row fixed by a coordinate other than the pass axis
   const long long n1 = (long long)P.dim * P.NV;
@@ -70,12 +72,12 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
   const long long col0 = (long long)tcol * kTC;
   const int i0 = ti * kTI;
   const int t = threadIdx.x;
-  const int ri = (t / (kTC / 4)) * 4, rc = (t % (kTC / 4)) * 4;   // this thread's 4 x 4 tile
-  float acc[4][4];
+  const int ri = (t / (kTC / kCQ)) * 4, rc = (t % (kTC / kCQ)) * kCQ;   // this thread's 4 x kCQ tile
+  float acc[4][kCQ];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[a][q] = 0.f;
+    for (int q = 0; q < kCQ; ++q) acc[a][q] = 0.f;
   const long long cbase = (long long)c * K.nv;
   if (t < kTC) {
     const long long col = col0 + t;
@@ -149,12 +151,12 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
 #pragma unroll 8
     for (int jj = 0; jj < kTK; ++jj) {
       const float4 a4 = *reinterpret_cast<const float4*>(&As[jj][ri]);
-      const float4 x4 = *reinterpret_cast<const float4*>(&Xs[jj][rc]);
-      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, xv[4] = {x4.x, x4.y, x4.z, x4.w};
+      const float2 x2 = *reinterpret_cast<const float2*>(&Xs[jj][rc]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, xv[2] = {x2.x, x2.y};
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[a][q] += av[a] * xv[q];
+        for (int q = 0; q < kCQ; ++q) acc[a][q] += av[a] * xv[q];
     }
     __syncthreads();
   }
@@ -163,7 +165,7 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
     const int i = i0 + ri + a;
     if (i >= Na) continue;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kCQ; ++q) {
       const long long cb = s_cb[rc + q];
       if (cb < 0) continue;
       const long long node = cb + (long long)i * K.inner;

@@ -75,11 +75,32 @@ k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, lo
           if (q < nq) acc[q] += vq[q][i];
       }
     }
+    // warp reduce-scatter (fixed butterfly): at each step the lanes with bit o set keep the
+    // upper half of their outputs and receive the partner's upper half; after log2(kChunk)
+    // halvings every lane holds one output, the remaining steps add the lane pairs.
+    // kChunk - 1 + 5 - log2(kChunk) shuffles instead of 5 kChunk.
 #pragma unroll
-    for (int q = 0; q < kChunk; ++q) {
-      T v = acc[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) red[warp][q] = (double)v;
+    for (int st = 0; st < 5; ++st) {
+      const int o = 16 >> st;
+      const int cnt = kChunk >> st;   // outputs held per lane before this step
+      if (cnt >= 2) {
+        const int half = cnt / 2;
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < kChunk / 2; ++q)
+          if (q < half) {
+            const T send = up ? acc[q] : acc[q + half];
+            const T keep = up ? acc[q + half] : acc[q];
+            acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+          }
+      } else {
+        acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+      }
+    }
+    {
+      constexpr int shift = kChunk == 16 ? 1 : kChunk == 8 ? 2 : 0;
+      static_assert(kChunk == 16 || kChunk == 8, "butterfly layout");
+      if ((lane & ((1 << shift) - 1)) == 0) red[warp][lane >> shift] = (double)acc[0];
     }
     __syncthreads();
     if (threadIdx.x < kChunk && c0 + (int)threadIdx.x < nout) {
