@@ -122,13 +122,6 @@ lh_status lh_residual(lh_mesh* mesh, const double* u, const double* k, double ta
 lh_status lh_jvp(lh_mesh* mesh, const double* u, const double* k, double tau,
                  const void* dk, void* out, lh_prec prec);
 
-/* Linearisation record (partial assembly of the tangent, paper Sec. 2.2: store the
- * quadrature-point data once, reuse it for every action): evaluates the quadrature-point
- * state (J, grad_hat v, e; x in 2D) at w = u + tau k in FP64 and keeps it, rounded to
- * float, in the mesh ([NE][19 (3D) or 11 (2D)][quadrature points]).  Later lh_jvp calls
- * with LH_FP32_LIN and the same u, k (pointers) and tau use it.  lh_newton_step with an
- * FP32 J.w writes the record at every Newton iterate and invalidates it on return.
- * Asynchronous; allocates the record on first use. */
 /* Box decomposition (paper Sec. 2.2, Eq. (8) with P != I).  A partition is a mesh of a
  * sub-box of the global box: same element size, the global h0 and h_coarse, walls only on
  * the global boundary (the shared face unmasked).  On a shared face the velocity rows of
@@ -148,6 +141,15 @@ lh_status lh_halo_add(lh_mesh* mesh, int face, const void* buf, void* r, lh_prec
  * tensor cores timed out since the mesh was created (synchronises; clears the flag). */
 lh_status lh_tc_status(lh_mesh* mesh);
 
+/* Linearisation record (partial assembly of the tangent, paper Sec. 2.2: store the
+ * quadrature-point data once, reuse it for every action): evaluates the residual at
+ * w = u + tau k in FP64 and keeps, rounded to float, the linearisation of the
+ * quadrature-point map at every point ([NE][31 (3D) or 24 (2D)][quadrature points]:
+ * J^-1, grad v, and the scalars of the pressure and viscosity chain of Eqs. (11)-(20)).
+ * Later lh_jvp calls with LH_FP32_LIN, LH_TF32 or LH_BF16 and the same u, k (pointers)
+ * and tau apply the linearised map instead of re-evaluating the point kernel.
+ * lh_newton_step with a reduced-precision J.w writes the record at every Newton iterate
+ * and invalidates it on return.  Asynchronous; allocates the record on first use. */
 lh_status lh_linearize(lh_mesh* mesh, const double* u, const double* k, double tau);
 
 /* Transpose action out = (dR/dk)^T y (paper Sec. 3.1: transpose actions share the

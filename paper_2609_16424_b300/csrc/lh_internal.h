@@ -34,8 +34,9 @@ void fill_params(const lh_mesh_desc& d, ElemParams* out);
 std::vector<double> host_tables(int K);   // [B | G | Bl | w | zh | zl] for order K
 lh_status set_global_error(lh_status st, const std::string& msg);   // for lh_last_error(NULL)
 
-// floats per quadrature point in the linearisation record: J, grad_hat v, e (and x_q in 2D)
-inline int rec_len(int dim) { return dim == 3 ? 19 : 11; }
+// floats per quadrature point in the linearisation record (lh_qp.cuh, lin_record): J^-1,
+// grad v, 13 scalars of the stress and viscosity chain (and the Taylor-Green source in 2D)
+inline int rec_len(int dim) { return dim == 3 ? 31 : 24; }
 
 // Kronecker factors of the H1 mass inverse (lh_prec.cu); device pointers owned by the mesh
 struct KronPrec {

@@ -193,28 +193,27 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
       J[i][r] = hg[i][r];
       Gv[i][r] = hg[DIM + i][r];
     }
-  if (rec && E.valid) {   // linearisation record for the FP32 tangent kernel
-    constexpr int NR = DIM == 3 ? 19 : 11;
-    float* rq = rec + E.e * NR * NQ + lt;
-#pragma unroll
-    for (int i = 0; i < DIM; ++i)
-#pragma unroll
-      for (int r = 0; r < DIM; ++r) {
-        rq[(i * DIM + r) * NQ] = (float)J[i][r];
-        rq[(DIM * DIM + i * DIM + r) * NQ] = (float)Gv[i][r];
-      }
-    rq[2 * DIM * DIM * NQ] = (float)lq[0];
-    if constexpr (DIM == 2) {
-      rq[(2 * DIM * DIM + 1) * NQ] = (float)hv[0];
-      rq[(2 * DIM * DIM + 2) * NQ] = (float)hv[1];
-    }
-  }
   if (!E.valid) {
 #pragma unroll
     for (int i = 0; i < DIM; ++i) J[i][i] = 1.0;   // keep the idle lanes finite
   }
   double So[DIM][DIM], Eo, detJ;
-  qp_forward<DIM>(J, Gv, lq[0], c, So, Eo, detJ);
+  QpPrimal<DIM, double> pr;
+  qp_forward<DIM>(J, Gv, lq[0], c, So, Eo, detJ, rec ? &pr : nullptr);
+  if (rec && E.valid) {   // linearisation record of the tangent (float, [NE][fields][NQ])
+    double tgs = 0.0, tgx = 0.0, tgy = 0.0;
+    if constexpr (DIM == 2) {
+      if (P.tg) {
+        tgs = tg_source<double, double>(hv[0], hv[1]);
+        tg_source_grad<double>(hv[0], hv[1], tgx, tgy);
+      }
+    }
+    float L[lin_len<DIM>()];
+    lin_record<DIM>(pr, c.gm1, c.visc, tgs, tgx, tgy, L);
+    float* rq = rec + E.e * lin_len<DIM>() * NQ + lt;
+#pragma unroll
+    for (int f = 0; f < lin_len<DIM>(); ++f) rq[f * NQ] = L[f];
+  }
   double fval[DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i) fval[i] = c.mq * kvq[i];
@@ -354,7 +353,7 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
   using C = Cfg<DIM, K>;
   constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q;
   constexpr int NCH = 2 * DIM;   // dk_x, dk_v
-  constexpr int NR = DIM == 3 ? 19 : 11;
+  constexpr int NR = lin_len<DIM>();
   using PL = Plan<DIM, K, NCH, 0, 1, DIM>;
   using TB = Tab<K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -376,72 +375,44 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
     s_h[i] = E.valid ? dk[comp * P.NV + node_of<DIM, K>(P, E, a)] : 0.f;
   }
   for (int i = lt; i < NL; i += NQ) s_l[i] = E.valid ? dk[2 * DIM * P.NV + E.e * NL + i] : 0.f;
-  // primal state at this quadrature point
-  float J0[DIM][DIM], Gv0[DIM][DIM], e0 = 1.f, xq[2] = {0.f, 0.f};
+  // linearisation record of this quadrature point (zeros on idle lanes: the linear
+  // tangent divides by nothing)
+  float Lr[NR];
   {
     const float* rq = rec + (E.valid ? E.e : 0) * NR * NQ + lt;
 #pragma unroll
-    for (int i = 0; i < DIM; ++i)
-#pragma unroll
-      for (int r = 0; r < DIM; ++r) {
-        J0[i][r] = E.valid ? rq[(i * DIM + r) * NQ] : (i == r ? 1.f : 0.f);
-        Gv0[i][r] = E.valid ? rq[(DIM * DIM + i * DIM + r) * NQ] : 0.f;
-      }
-    if (E.valid) e0 = rq[2 * DIM * DIM * NQ];
-    if constexpr (DIM == 2) {
-      if (E.valid) {
-        xq[0] = rq[(2 * DIM * DIM + 1) * NQ];
-        xq[1] = rq[(2 * DIM * DIM + 2) * NQ];
-      }
-    }
+    for (int f = 0; f < NR; ++f) Lr[f] = E.valid ? rq[f * NQ] : 0.f;
   }
   __syncthreads();
   float hv[NCH], hg[NCH][DIM];
   h1_fwd<DIM, K, NCH, float, true>(s_h, t1, t2, sB, sG, lt, hv, hg);
   float lq[1];
   l2_fwd<DIM, K, 1>(s_l, t1, t2, sBl, lt, lq);
-
-  QpC<float> c;
+  float mq;
   {
     const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
     float a = sW[q0] * sW[q1];
     if constexpr (DIM == 3) a *= sW[q2];
-    const long long ee = E.valid ? E.e : 0;
-    c.alpha = a;
-    c.mq = P.fmq0[ee] * a;
-    c.inv_detJ0 = P.finv_detJ0;
-    c.gm1 = P.fgm1[ee];
-    c.ggm1 = P.fggm1[ee];
-    c.h0 = P.fh0;
-    c.inv_hc = P.finv_hc;
-    c.q1 = P.fq1;
-    c.q2 = P.fq2;
-    c.scoef = P.fscoef;
-    c.eps2 = P.feps2;
-    c.visc = P.visc != 0;
+    mq = P.fmq0[E.valid ? E.e : 0] * a;
   }
-  Dual<float> J[DIM][DIM], Gv[DIM][DIM];
+  float dJ[DIM][DIM], dGv[DIM][DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
 #pragma unroll
     for (int r = 0; r < DIM; ++r) {
-      J[i][r] = Dual<float>(J0[i][r], tau * hg[i][r]);
-      Gv[i][r] = Dual<float>(Gv0[i][r], tau * hg[DIM + i][r]);
+      dJ[i][r] = tau * hg[i][r];
+      dGv[i][r] = tau * hg[DIM + i][r];
     }
-  Dual<float> So[DIM][DIM], Eo, detJ;
-  qp_forward<DIM>(J, Gv, Dual<float>(e0, tau * lq[0]), c, So, Eo, detJ);
-  float fval[DIM], fgrad[DIM][DIM];
+  float fgrad[DIM][DIM], dEo, dW;
+  qp_tangent_lin<DIM>(Lr, dJ, dGv, tau * lq[0], P.fq1, P.fq2, P.visc != 0, fgrad, dEo, dW);
+  float fval[DIM];
 #pragma unroll
-  for (int i = 0; i < DIM; ++i) {
-    fval[i] = c.mq * hv[DIM + i];
-#pragma unroll
-    for (int r = 0; r < DIM; ++r) fgrad[i][r] = So[i][r].d;
-  }
-  float g = c.mq * lq[0] - Eo.d;
+  for (int i = 0; i < DIM; ++i) fval[i] = mq * hv[DIM + i];
+  float g = mq * lq[0] - dEo;
   if constexpr (DIM == 2) {
-    if (P.tg) {
-      const Dual<float> x(xq[0], tau * hv[0]), y(xq[1], tau * hv[1]);
-      g -= (c.alpha * detJ * tg_source<Dual<float>, float>(x, y)).d;
+    if (P.tg) {   // d(W s(x_q)) = dW s + W grad s . dx
+      constexpr int O = 2 * DIM * DIM;
+      g -= dW * Lr[O + LF_TGS] + Lr[O + LF_W] * (Lr[O + LF_TGX] * tau * hv[0] + Lr[O + LF_TGY] * tau * hv[1]);
     }
   }
   h1_bwd<DIM, K, DIM>(fval, fgrad, sf, t1, t2, sB, sG, lt, s_h);

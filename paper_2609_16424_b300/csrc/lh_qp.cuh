@@ -22,6 +22,15 @@ struct QpC {
   bool visc;
 };
 
+// Primal intermediates of qp_forward at one point (filled on request by the residual
+// kernel, from which the linearisation record of the tangent is formed).
+template <int DIM, class T>
+struct QpPrimal {
+  T Jinv[DIM][DIM], Lv[DIM][DIM];
+  T W, rho, sq, ep, p, cs;
+  T h, ds, ab, t, mu;
+};
+
 template <int DIM, class S>
 __host__ __device__ __forceinline__ S det_adj(const S (&J)[DIM][DIM], S (&A)[DIM][DIM]) {
   if constexpr (DIM == 2) {
@@ -52,7 +61,8 @@ __host__ __device__ __forceinline__ S det_adj(const S (&J)[DIM][DIM], S (&A)[DIM
 // Works for S = T (residual) and S = Dual<T> (tangent of Eq. (10)).
 template <int DIM, class S, class T>
 __host__ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], const S (&Gv)[DIM][DIM], S e,
-                                           const QpC<T>& c, S (&So)[DIM][DIM], S& Eo, S& detJ) {
+                                           const QpC<T>& c, S (&So)[DIM][DIM], S& Eo, S& detJ,
+                                           QpPrimal<DIM, T>* prim = nullptr) {
   S A[DIM][DIM];
   const S det = det_adj<DIM>(J, A);
   detJ = det;
@@ -80,6 +90,22 @@ __host__ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], cons
       for (int r = 1; r < DIM; ++r) s = s + Gv[i][r] * Jinv[r][j];
       Lv[i][j] = s;
     }
+  if (prim) {
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        prim->Jinv[i][j] = value_of(Jinv[i][j]);
+        prim->Lv[i][j] = value_of(Lv[i][j]);
+      }
+    prim->W = value_of(W);
+    prim->rho = value_of(rho);
+    prim->sq = value_of(sq);
+    prim->ep = value_of(ep);
+    prim->p = value_of(p);
+    prim->cs = value_of(cs);
+    prim->h = prim->ds = prim->ab = prim->t = prim->mu = T(0);
+  }
   S sig[DIM][DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
@@ -94,8 +120,16 @@ __host__ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], cons
     const S ds = (T(2) * c.inv_hc) * (h * cs);               // Eq. (18)
     const S ab = lsqrt(dv * dv + ds * ds);                   // Eq. (16)
     const S arg = (-dv - c.scoef * ds) / (T(2) * ds);
-    const S psi = T(0.5) + T(0.5) * ltanh(arg);              // Eq. (17)
+    const S th = ltanh(arg);
+    const S psi = T(0.5) + T(0.5) * th;                      // Eq. (17)
     const S mu = rho * h * (c.q2 * ab + c.q1 * cs * psi);    // Eq. (13)
+    if (prim) {
+      prim->h = value_of(h);
+      prim->ds = value_of(ds);
+      prim->ab = value_of(ab);
+      prim->t = value_of(th);
+      prim->mu = value_of(mu);
+    }
 #pragma unroll
     for (int i = 0; i < DIM; ++i)
 #pragma unroll
@@ -113,6 +147,169 @@ __host__ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], cons
       So[i][j] = W * s;
     }
   Eo = W * E;
+}
+
+// ---- Linearisation record of the quadrature-point map (partial assembly of the tangent,
+// paper Sec. 2.2: the point data are stored once per Newton iterate and reused by every
+// Jacobian action).  Fields per point, float:
+//   [0, D^2) J^-1, [D^2, 2 D^2) grad v, then W = alpha detJ, p, pe = (gamma-1) rho e+',
+//   cs, ke = e+' / (2 e+) (so dcs = cs ke de), h, ds, 1/ds, 1/|.|_ds, psi, g = (1 - t^2)/2
+//   (t the tanh of Eq. (17)), mu, rho h; in 2D also the Taylor-Green source s and its
+//   gradient at x_q.  e+' = e+ / sqrt(e^2 + eps^2) in both branches of Eq. (19).
+template <int DIM>
+__host__ __device__ constexpr int lin_len() { return DIM == 3 ? 31 : 24; }
+
+enum LinField : int { LF_W = 0, LF_P, LF_PE, LF_CS, LF_KE, LF_H, LF_DS, LF_IDS, LF_IAB, LF_PSI, LF_G, LF_MU, LF_RH,
+                      LF_TGS, LF_TGX, LF_TGY };
+
+template <int DIM, class R = float>
+__host__ __device__ __forceinline__ void lin_record(const QpPrimal<DIM, double>& pr, double gm1, bool visc,
+                                                    double tgs, double tgx, double tgy,
+                                                    R (&L)[lin_len<DIM>()]) {
+  constexpr int O = 2 * DIM * DIM;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      L[i * DIM + j] = R(pr.Jinv[i][j]);
+      L[DIM * DIM + i * DIM + j] = R(pr.Lv[i][j]);
+    }
+  const R ep = R(pr.ep), epd = ep / R(pr.sq);      // e+ and d e+ / d e
+  L[O + LF_W] = R(pr.W);
+  L[O + LF_P] = R(pr.p);
+  L[O + LF_PE] = R(gm1) * R(pr.rho) * epd;
+  L[O + LF_CS] = R(pr.cs);
+  L[O + LF_KE] = epd / (R(2) * ep);
+  if (visc) {
+    L[O + LF_H] = R(pr.h);
+    L[O + LF_DS] = R(pr.ds);
+    L[O + LF_IDS] = R(1) / R(pr.ds);
+    L[O + LF_IAB] = R(1) / R(pr.ab);
+    L[O + LF_PSI] = R(0.5 + 0.5 * pr.t);
+    L[O + LF_G] = R(0.5 * (1.0 - pr.t * pr.t));   // in double: 1 - t^2 cancels as |t| -> 1
+    L[O + LF_MU] = R(pr.mu);
+    L[O + LF_RH] = R(pr.rho * pr.h);
+  } else {
+    for (int f = LF_H; f <= LF_RH; ++f) L[O + f] = R(0);
+  }
+  if constexpr (DIM == 2) {
+    L[O + LF_TGS] = R(tgs);
+    L[O + LF_TGX] = R(tgx);
+    L[O + LF_TGY] = R(tgy);
+  }
+}
+
+// Tangent of qp_forward from the record: given dJ = d(grad_hat x), dGv = d(grad_hat v), de,
+// returns dS, dE and dW = d(alpha detJ).  With theta = tr(J^-1 dJ) (= d detJ / detJ):
+//   d grad v = (dGv - grad v dJ) J^-1,  drho = -rho theta,  dp = -p theta + pe de,
+//   dcs = cs ke de,  dh = h theta / dim,  and the chain of Eqs. (13)-(18) for dmu;
+//   dsigma = -dp I + dmu eps(grad v) + mu eps(d grad v),
+//   dS = W [theta sigma + dsigma - sigma J^-T dJ^T] J^-T,
+//   dE = W [theta sigma : grad v + dsigma : grad v + sigma : d grad v].
+template <int DIM, class T = float>
+__host__ __device__ __forceinline__ void qp_tangent_lin(const T (&L)[lin_len<DIM>()], const T (&dJ)[DIM][DIM],
+                                                        const T (&dGv)[DIM][DIM], T de, T q1, T q2,
+                                                        bool visc, T (&dSo)[DIM][DIM], T& dEo, T& dW) {
+  constexpr int O = 2 * DIM * DIM;
+  T Ji[DIM][DIM], Lv[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      Ji[i][j] = L[i * DIM + j];
+      Lv[i][j] = L[DIM * DIM + i * DIM + j];
+    }
+  const T W = L[O + LF_W], p = L[O + LF_P];
+  T th = T(0.);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) th += Ji[i][r] * dJ[r][i];
+  T dL[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    T Y[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      T y = dGv[i][r];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) y -= Lv[i][b] * dJ[b][r];
+      Y[r] = y;
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      T v = T(0.);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) v += Y[r] * Ji[r][j];
+      dL[i][j] = v;
+    }
+  }
+  const T dp = -p * th + L[O + LF_PE] * de;
+  T mu = T(0.), dmu = T(0.);
+  if (visc) {
+    const T cs = L[O + LF_CS], dcs = cs * L[O + LF_KE] * de;
+    const T h = L[O + LF_H], ds = L[O + LF_DS], ids = L[O + LF_IDS];
+    T div = T(0.), ddiv = T(0.);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      div += Lv[i][i];
+      ddiv += dL[i][i];
+    }
+    const T dv = h * div;
+    const T tq = th * (T(1.) / DIM);
+    const T ddv = h * (tq * div + ddiv);
+    const T dds = ds * (tq + L[O + LF_KE] * de);
+    const T dab = (dv * ddv + ds * dds) * L[O + LF_IAB];
+    const T darg = -T(0.5) * ids * (ddv - dv * dds * ids);
+    const T dpsi = L[O + LF_G] * darg;
+    const T dX = q2 * dab + q1 * (dcs * L[O + LF_PSI] + cs * dpsi);
+    mu = L[O + LF_MU];
+    dmu = mu * th * (T(1.) / DIM - T(1.)) + L[O + LF_RH] * dX;
+  }
+  T sg[DIM][DIM], dsg[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      const T ep = T(0.5) * (Lv[i][j] + Lv[j][i]), dep = T(0.5) * (dL[i][j] + dL[j][i]);
+      sg[i][j] = (i == j ? -p : T(0.)) + mu * ep;
+      dsg[i][j] = (i == j ? -dp : T(0.)) + dmu * ep + mu * dep;
+    }
+  T E = T(0.), dE = T(0.);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      E += sg[i][j] * Lv[i][j];
+      dE += dsg[i][j] * Lv[i][j] + sg[i][j] * dL[i][j];
+    }
+  dEo = W * (th * E + dE);
+  dW = W * th;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    T M[DIM], N[DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {   // M = sigma J^-T (row i)
+      T v = T(0.);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) v += sg[i][k] * Ji[b][k];
+      M[b] = v;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {   // N = theta sigma + dsigma - M dJ^T (row i)
+      T v = th * sg[i][a] + dsg[i][a];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) v -= M[b] * dJ[a][b];
+      N[a] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      T v = T(0.);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) v += N[a] * Ji[j][a];
+      dSo[i][j] = W * v;
+    }
+  }
 }
 
 // Taylor-Green manufactured energy source per unit volume (gamma = 5/3):

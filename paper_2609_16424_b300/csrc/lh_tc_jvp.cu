@@ -150,7 +150,7 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
   using PL = TcPlan<DIM, K, KIND>;
   using C = Cfg<DIM, K>;
   constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q;
-  constexpr int NR = DIM == 3 ? 19 : 11;
+  constexpr int NR = lin_len<DIM>();
   constexpr int ESZ = PL::ESZ, MK = PL::MK;
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte aligned base (the launch adds 1024 bytes of slack)
@@ -195,16 +195,6 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
   uint32_t ph_f = 0, ph_b = 0;
   bool ok = true;
 
-  // per-thread quadrature constants that do not depend on the element
-  QpC<float> c;
-  c.inv_detJ0 = P.finv_detJ0;
-  c.h0 = P.fh0;
-  c.inv_hc = P.finv_hc;
-  c.q1 = P.fq1;
-  c.q2 = P.fq2;
-  c.scoef = P.fscoef;
-  c.eps2 = P.feps2;
-  c.visc = P.visc != 0;
 
   const long long nbatch = (P.NE + EB - 1) / EB;
   for (long long b = blockIdx.x; b < nbatch; b += gridDim.x) {
@@ -295,36 +285,31 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
           }
         }
         const float* rq = rec + eg * NR * NQ + q;
+        float Lr[NR];
+#pragma unroll
+        for (int f = 0; f < NR; ++f) Lr[f] = rq[f * NQ];
         const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
         float a = sW[q0] * sW[q1];
         if constexpr (DIM == 3) a *= sW[q2];
-        c.alpha = a;
-        c.mq = P.fmq0[eg] * a;
-        c.gm1 = P.fgm1[eg];
-        c.ggm1 = P.fggm1[eg];
-        Dual<float> J[DIM][DIM], Gv[DIM][DIM];
+        const float mq = P.fmq0[eg] * a;
+        float dJ[DIM][DIM], dGv[DIM][DIM];
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
           for (int r = 0; r < DIM; ++r) {
-            J[i][r] = Dual<float>(rq[(i * DIM + r) * NQ], tau * hg[i][r]);
-            Gv[i][r] = Dual<float>(rq[(DIM * DIM + i * DIM + r) * NQ], tau * hg[DIM + i][r]);
+            dJ[i][r] = tau * hg[i][r];
+            dGv[i][r] = tau * hg[DIM + i][r];
           }
         const float lq = hv[2 * DIM];
-        Dual<float> So[DIM][DIM], Eo, detJ;
-        qp_forward<DIM>(J, Gv, Dual<float>(rq[2 * DIM * DIM * NQ], tau * lq), c, So, Eo, detJ);
+        float dEo, dW;
+        qp_tangent_lin<DIM>(Lr, dJ, dGv, tau * lq, P.fq1, P.fq2, P.visc != 0, fgrad, dEo, dW);
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          fval[i] = c.mq * hv[DIM + i];
-#pragma unroll
-          for (int r = 0; r < DIM; ++r) fgrad[i][r] = So[i][r].d;
-        }
-        g = c.mq * lq - Eo.d;
+        for (int i = 0; i < DIM; ++i) fval[i] = mq * hv[DIM + i];
+        g = mq * lq - dEo;
         if constexpr (DIM == 2) {
-          if (P.tg) {
-            const Dual<float> x(rq[(2 * DIM * DIM + 1) * NQ], tau * hv[0]);
-            const Dual<float> y(rq[(2 * DIM * DIM + 2) * NQ], tau * hv[1]);
-            g -= (c.alpha * detJ * tg_source<Dual<float>, float>(x, y)).d;
+          if (P.tg) {   // d(W s(x_q)) = dW s + W grad s . dx
+            constexpr int O = 2 * DIM * DIM;
+            g -= dW * Lr[O + LF_TGS] + Lr[O + LF_W] * (Lr[O + LF_TGX] * tau * hv[0] + Lr[O + LF_TGY] * tau * hv[1]);
           }
         }
       }
