@@ -27,7 +27,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = {"name": "blast3d_24_q2q1", "dim": 3, "n": (24, 24, 24), "k": 2, "gamma": 1.4, "energy": 0.25,
             "develop_steps": 3, "cfl": 2.0}
-NEWTON = {"newton_rtol": 1e-8, "gmres_rtol": 1e-4, "gmres_maxit": 200, "restart": 30, "newton_maxit": 20}
+# Newton relative tolerance of the paper's defaults (Sec. 3.5); inexact Newton with GMRES to
+# 1e-4 per linear solve.  (At 1e-8 the third Newton iterate of the workload sits at the
+# threshold, 0.9-1.6e-8 depending on rounding, and the iteration count flips between forms.)
+NEWTON = {"newton_rtol": 1e-5, "gmres_rtol": 1e-4, "gmres_maxit": 200, "restart": 30, "newton_maxit": 20}
 L2_FLUSH_BYTES = 512 << 20
 
 
