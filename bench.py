@@ -59,7 +59,7 @@ def flops_per_element(dim, k, kind, visc=True):
     import paper_2609_16424_b300 as lh
     grad, valgrad, val = sf_macs(dim, k)
     nq = (2 * k) ** dim
-    qk = {"residual": 0, "jvp": 1, "jvp_rec": 1, "jtvp": 2}[kind]
+    qk = {"residual": 0, "jvp": 1, "jvp_rec": 3, "jtvp": 2}[kind]
     ops = C.c_longlong()
     lh.lib.lh_qp_flops(dim, qk, int(visc), C.byref(ops))
     if kind == "residual":
@@ -68,7 +68,7 @@ def flops_per_element(dim, k, kind, visc=True):
     elif kind == "jvp":
         macs = 3 * dim * grad + dim * valgrad + 2 * val(k) + dim * valgrad + val(k)
         glue = 2 * dim * dim + 1 + dim + 2 + 3
-    elif kind == "jvp_rec":   # primal state read from the linearisation record
+    elif kind == "jvp_rec":   # linearised point map read from the record
         macs = dim * grad + dim * valgrad + val(k) + dim * valgrad + val(k)
         glue = 2 * dim * dim + 1 + dim + 2 + 2
     else:

@@ -300,7 +300,8 @@ lh_status lh_profile_read(lh_mesh* mesh, double* ms, long long* count);
 
 /* Arithmetic operations (+ - * / sqrt tanh cbrt cos sin, one each) of one evaluation of
  * the quadrature-point kernel, counted by running the kernel's code on the host with a
- * counting scalar.  kind 0: stress (residual), 1: tangent (J.w), 2: adjoint (J^T.y).
+ * counting scalar.  kind 0: stress (residual), 1: tangent (J.w), 2: adjoint (J^T.y),
+ * 3: tangent from the linearisation record (reduced-precision J.w).
  * Needs no GPU.  *ops is a HOST pointer. */
 lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops);
 

@@ -75,6 +75,16 @@ long long count(int kind, bool visc) {
       }
     g_ops = 0;
     lh::qp_forward<DIM>(J, Gv, Dual<Cnt>(Cnt(2.0), Cnt(0.1)), c, S, E, det);
+  } else if (kind == 3) {   // tangent from the linearisation record (reduced-precision J.w)
+    Cnt L[lh::lin_len<DIM>()], dJ[DIM][DIM], dGv[DIM][DIM], dS[DIM][DIM], dE, dW;
+    for (int f = 0; f < lh::lin_len<DIM>(); ++f) L[f] = 0.1 + 0.01 * f;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        dJ[i][j] = 0.001 * (i + j + 1);
+        dGv[i][j] = 0.01 * (i - j);
+      }
+    g_ops = 0;
+    lh::qp_tangent_lin<DIM, Cnt>(L, dJ, dGv, Cnt(0.1), Cnt(0.5), Cnt(1.0), visc, dS, dE, dW);
   } else {
     Cnt J[DIM][DIM], Gv[DIM][DIM], Sb[DIM][DIM], Jb[DIM][DIM], Gvb[DIM][DIM], eb;
     for (int i = 0; i < DIM; ++i)
@@ -92,7 +102,7 @@ long long count(int kind, bool visc) {
 }  // namespace
 
 extern "C" lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops) {
-  if (!ops || (dim != 2 && dim != 3) || kind < 0 || kind > 2) return LH_EINVAL;
+  if (!ops || (dim != 2 && dim != 3) || kind < 0 || kind > 3) return LH_EINVAL;
   *ops = dim == 2 ? count<2>(kind, visc != 0) : count<3>(kind, visc != 0);
   return LH_OK;
 }
