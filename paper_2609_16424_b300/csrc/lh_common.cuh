@@ -87,4 +87,57 @@ template <int DIM, class S> __host__ __device__ __forceinline__ S root_dim(S x) 
 template <class T> __host__ __device__ __forceinline__ T value_of(T a) { return a; }
 template <class T> __host__ __device__ __forceinline__ T value_of(Dual<T> a) { return a.v; }
 
+// ---------------------------------------------------------------------------------------
+// Double-float arithmetic for the FP64 residual's element contractions: a value is an
+// unevaluated sum hi + lo of two floats (about 48 significant bits), built from the
+// error-free transformations TwoSum (Knuth, TAOCP vol. 2, 4.2.2), FastTwoSum (Dekker 1971)
+// and TwoProduct through a fused multiply-add.  Each multiply-add costs about fifteen FP32
+// instructions, which on this GPU's FP32 pipe is several times cheaper than one FP64 FMA on
+// its FP64 pipe; relative error per operation about 2^-46.
+struct DFProd {   // a product hi * hi' with its rounding error and the cross terms, not normalised
+  float p, e;
+};
+struct DF {
+  float hi, lo;
+  __device__ __forceinline__ DF() {}
+  __device__ __forceinline__ DF(int a) : hi((float)a), lo(0.f) {}
+  __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ explicit DF(double a) {
+    hi = (float)a;
+    lo = (float)(a - (double)hi);
+  }
+};
+__device__ __forceinline__ double to_double(DF a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return DF(s, b - (s - a));
+}
+__device__ __forceinline__ DFProd operator*(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);           // exact error of the leading product
+  return DFProd{p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e))};
+}
+__device__ __forceinline__ DF operator+(DFProd a, DFProd b) {
+  float s, t;
+  two_sum(a.p, b.p, s, t);
+  return fast_two_sum(s, t + (a.e + b.e));
+}
+__device__ __forceinline__ DF& operator+=(DF& acc, DFProd a) {
+  float s, t;
+  two_sum(acc.hi, a.p, s, t);
+  acc = fast_two_sum(s, t + (acc.lo + a.e));
+  return acc;
+}
+__device__ __forceinline__ DF& operator+=(DF& acc, DF a) {
+  float s, t;
+  two_sum(acc.hi, a.hi, s, t);
+  acc = fast_two_sum(s, t + (acc.lo + a.lo));
+  return acc;
+}
+
 }  // namespace lh

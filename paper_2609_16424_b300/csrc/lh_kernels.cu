@@ -132,38 +132,57 @@ __global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
 k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk, double tau,
            double* __restrict__ ev, double* __restrict__ Re, double* __restrict__ blockmin,
            float* __restrict__ rec) {
+  // Element contractions in double-float (DF, FP32 pipe), the quadrature-point kernel and
+  // everything written out in FP64.  Positions enter the contractions relative to the
+  // element's first node (the reference gradients of the basis sum to zero, so J is
+  // unchanged), which keeps J accurate to ~2^-46 relative on fine meshes.
   using C = Cfg<DIM, K>;
   constexpr int D = C::D, Q = C::Q, ND = C::ND, NL = C::NL, NQ = C::NQ;
   constexpr int NCH = 2 * DIM;
   using PL = Plan<DIM, K, NCH, DIM, 2, DIM>;
   using TB = Tab<K>;
+  static_assert(sizeof(DF) == sizeof(double), "the shared-memory plan counts 8-byte entries");
   extern __shared__ double smem[];
-  double* sB = smem + TB::B;
-  double* sG = smem + TB::G;
-  double* sBl = smem + TB::BL;
-  double* sW = smem + TB::W;
+  DF* sdf = reinterpret_cast<DF*>(smem);
+  const DF* sB = sdf + TB::B;
+  const DF* sG = sdf + TB::G;
+  const DF* sBl = sdf + TB::BL;
+  const double* sW = smem + TB::W;
   double* red = smem + TB::SMEM;
-  load_tables(P, smem, TB::SMEM);
+  for (int i = threadIdx.x; i < TB::SMEM; i += blockDim.x) {
+    if (i < TB::W) sdf[i] = DF(P.tab[i]);
+    else smem[i] = P.tab[i];
+  }
   const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
-  double* s_h = smem + PL::HEAD + eb * PL::PER;   // [2 DIM][ND]: w_x, w_v
-  double* s_kv = s_h + NCH * ND;                  // [DIM][ND]: k_v
-  double* s_l = s_kv + DIM * ND;                  // [2][NL]: w_e, k_e
-  double* t1 = s_l + 2 * NL;
-  double* t2 = t1 + PL::T1;
-  double* sf = t2 + PL::T2;
+  DF* s_h = sdf + PL::HEAD + eb * PL::PER;   // [2 DIM][ND]: w_x - w_x(node 0), w_v
+  DF* s_kv = s_h + NCH * ND;                 // [DIM][ND]: k_v
+  DF* s_l = s_kv + DIM * ND;                 // [2][NL]: w_e, k_e
+  DF* t1 = s_l + 2 * NL;
+  DF* t2 = t1 + PL::T1;
+  DF* sf = t2 + PL::T2;
   const ElemIdx E = elem_index<DIM, K>(P);
+  double x0[DIM];   // position of the element's first node at w = u + tau k
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    x0[c] = 0.0;
+    if (E.valid) {
+      const long long g = c * P.NV + node_of<DIM, K>(P, E, 0);
+      x0[c] = u[g] + tau * kk[g];
+    }
+  }
   for (int i = lt; i < NCH * ND; i += NQ) {
     const int comp = i / ND, a = i % ND;
     double v = 0.0;
     if (E.valid) {
       const long long g = comp * P.NV + node_of<DIM, K>(P, E, a);
       v = u[g] + tau * kk[g];
+      if (comp < DIM) v -= x0[comp];
     }
-    s_h[i] = v;
+    s_h[i] = DF(v);
   }
   for (int i = lt; i < DIM * ND; i += NQ) {
     const int comp = i / ND, a = i % ND;
-    s_kv[i] = E.valid ? kk[(DIM + comp) * P.NV + node_of<DIM, K>(P, E, a)] : 0.0;
+    s_kv[i] = DF(E.valid ? kk[(DIM + comp) * P.NV + node_of<DIM, K>(P, E, a)] : 0.0);
   }
   for (int i = lt; i < NL; i += NQ) {
     double we = 0.0, ke = 0.0;
@@ -172,17 +191,23 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
       ke = kk[g];
       we = u[g] + tau * ke;
     }
-    s_l[i] = we;
-    s_l[NL + i] = ke;
+    s_l[i] = DF(we);
+    s_l[NL + i] = DF(ke);
   }
   __syncthreads();
-  double hv[NCH], hg[NCH][DIM];
+  DF hvd[NCH], hgd[NCH][DIM];
   // positions at the quadrature points are only needed by the 2D Taylor-Green source
-  h1_fwd<DIM, K, NCH, double, DIM == 2>(s_h, t1, t2, sB, sG, lt, hv, hg);
-  double kvq[DIM];
-  l2_fwd<DIM, K, DIM, double, D>(s_kv, t1, t2, sB, lt, kvq);
-  double lq[2];
-  l2_fwd<DIM, K, 2>(s_l, t1, t2, sBl, lt, lq);
+  h1_fwd<DIM, K, NCH, DF, DIM == 2>(s_h, t1, t2, sB, sG, lt, hvd, hgd);
+  DF kvd[DIM];
+  l2_fwd<DIM, K, DIM, DF, D>(s_kv, t1, t2, sB, lt, kvd);
+  DF lqd[2];
+  l2_fwd<DIM, K, 2, DF>(s_l, t1, t2, sBl, lt, lqd);
+  double hv[DIM], kvq[DIM], lq[2] = {to_double(lqd[0]), to_double(lqd[1])};
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) {
+    hv[c] = DIM == 2 ? to_double(hvd[c]) + x0[c] : 0.0;
+    kvq[c] = to_double(kvd[c]);
+  }
 
   const QpC<double> c = qp_consts<DIM, K, double>(P, E, sW, lt);
   double J[DIM][DIM], Gv[DIM][DIM];
@@ -190,8 +215,8 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
   for (int i = 0; i < DIM; ++i)
 #pragma unroll
     for (int r = 0; r < DIM; ++r) {
-      J[i][r] = hg[i][r];
-      Gv[i][r] = hg[DIM + i][r];
+      J[i][r] = to_double(hgd[i][r]);
+      Gv[i][r] = to_double(hgd[DIM + i][r]);
     }
   if (!E.valid) {
 #pragma unroll
@@ -214,20 +239,24 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
 #pragma unroll
     for (int f = 0; f < lin_len<DIM>(); ++f) rq[f * NQ] = L[f];
   }
-  double fval[DIM];
+  DF fval[DIM], Sd[DIM][DIM];
 #pragma unroll
-  for (int i = 0; i < DIM; ++i) fval[i] = c.mq * kvq[i];
+  for (int i = 0; i < DIM; ++i) {
+    fval[i] = DF(c.mq * kvq[i]);
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) Sd[i][r] = DF(So[i][r]);
+  }
   double g = c.mq * lq[1] - Eo;
   if constexpr (DIM == 2) {
     if (P.tg) g -= c.alpha * detJ * tg_source<double, double>(hv[0], hv[1]);
   }
-  h1_bwd<DIM, K, DIM>(fval, So, sf, t1, t2, sB, sG, lt, s_h);
+  h1_bwd<DIM, K, DIM>(fval, Sd, sf, t1, t2, sB, sG, lt, s_h);
   if (E.valid)
-    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
-  double gv[1] = {g};
+    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = to_double(s_h[i]);
+  DF gv[1] = {DF(g)};
   l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
   if (E.valid)
-    for (int i = lt; i < NL; i += NQ) Re[E.e * NL + i] = s_l[i];
+    for (int i = lt; i < NL; i += NQ) Re[E.e * NL + i] = to_double(s_l[i]);
   const double m = block_min(E.valid ? detJ : DBL_MAX, red);
   if (threadIdx.x == 0) blockmin[blockIdx.x] = m;
 }
