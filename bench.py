@@ -182,7 +182,7 @@ def timed_steps(mesh, u_s, k_s, dt, steps, prec, flush, profile=False):
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged kernel inside
 # the timed Newton steps of this workload (profiles/k_residual_blast3d_24_q2q1.md); None for
 # kernels without a capture
-NCU_TRAFFIC_BYTES = {"k_residual<3,2>": 13355776 + 59123200}
+NCU_TRAFFIC_BYTES = {"k_residual<3,2>": 13393920 + 61006336}
 
 
 def tc_mma_flops(dim, k, ne, kind):
