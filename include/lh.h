@@ -199,6 +199,13 @@ typedef struct {
   int precond;             /* velocity block of the preconditioner: 0 = diagonal of M_V,
                               1 = exact M_V inverse as a Kronecker product of 1D inverses
                               (exact for uniform rho0; rho0-scaled otherwise); default 1 */
+  int forcing;             /* 0: every linear solve to gmres_rtol (default); 1: adaptive
+                              forcing terms (Eisenstat and Walker 1996, choice 2 with gamma 0.9,
+                              alpha 2, and the safeguard against oversolving the last step):
+                              eta_0 = eta_max, eta_k = 0.9 (|R_k| / |R_{k-1}|)^2, kept >= 0.9
+                              eta_{k-1}^2 when that exceeds 0.1 and >= 0.5 target / |R_k|,
+                              clamped to [gmres_rtol, eta_max] */
+  double eta_max;          /* largest forcing term; default 0.1 */
 } lh_newton_opts;
 
 typedef struct {

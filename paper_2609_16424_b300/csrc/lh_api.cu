@@ -523,6 +523,8 @@ void lh_newton_opts_init(lh_newton_opts* o) {
   o->max_halvings = 10;
   o->jvp_prec = LH_FP64;
   o->precond = 1;
+  o->forcing = 0;
+  o->eta_max = 0.1;
 }
 
 lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
@@ -873,6 +875,9 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   if ((o.jvp_prec == LH_TF32 || o.jvp_prec == LH_BF16) && !jvp_tc_supported(m->P.dim, m->P.K))
     return fail(m, LH_EINVAL, "tensor-core J.w supports 2D orders 1-4 and 3D orders 1-2");
   if (o.precond != 0 && o.precond != 1) return fail(m, LH_EINVAL, "precond must be 0 or 1");
+  if (o.forcing != 0 && o.forcing != 1) return fail(m, LH_EINVAL, "forcing must be 0 or 1");
+  if (o.forcing && !(o.eta_max >= o.gmres_rtol && o.eta_max < 1.0))
+    return fail(m, LH_EINVAL, "eta_max must be in [gmres_rtol, 1)");
   if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
   lh_status st = ensure_work(m, o.restart);
   if (st != LH_OK) return st;
@@ -923,15 +928,20 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite residual");
   S.r0 = nr;
   bool conv = nr <= std::fmax(o.newton_rtol * S.r0, o.newton_atol);
+  double eta = o.forcing ? o.eta_max : o.gmres_rtol;   // relative tolerance of the next solve
+  const double target = std::fmax(o.newton_rtol * S.r0, o.newton_atol);
   for (int it = 0; it < o.newton_maxit && !conv; ++it) {
     // ---- linear solve J dk = -r (Eq. (22)) at the current iterate k
+    lh_newton_opts oi = o;
+    oi.gmres_rtol = eta;
     if (f32) {
       KrylovOp<float> op{m, o.precond, tck, u, k, tau, zf};
-      if ((st = gmres<float>(m, o, op, r, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return st;
+      if ((st = gmres<float>(m, oi, op, r, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return st;
     } else {
       KrylovOp<double> op{m, o.precond, -1, u, k, tau, zd};
-      if ((st = gmres<double>(m, o, op, r, nr, dk, V, wd, wd, zd, wd, S)) != LH_OK) return st;
+      if ((st = gmres<double>(m, oi, op, r, nr, dk, V, wd, wd, zd, wd, S)) != LH_OK) return st;
     }
+    const double nr_prev = nr;
     // ---- backtracking line search on det J > 0 (Sec. 3.5)
     double lam = 1.0;
     bool accepted = false;
@@ -957,7 +967,14 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
     nr = std::sqrt(nr2);
     S.min_detj = mind;
     ++S.newton_its;
-    conv = nr <= std::fmax(o.newton_rtol * S.r0, o.newton_atol);
+    conv = nr <= target;
+    if (o.forcing && !conv) {   // Eisenstat-Walker choice 2 with safeguards
+      double e = 0.9 * (nr / nr_prev) * (nr / nr_prev);
+      const double prev = 0.9 * eta * eta;
+      if (prev > 0.1) e = std::fmax(e, prev);
+      e = std::fmax(e, 0.5 * target / nr);
+      eta = std::fmax(std::fmin(e, o.eta_max), o.gmres_rtol);
+    }
   }
   S.rfinal = nr;
   if (S.min_detj == 0.0) S.min_detj = mind;

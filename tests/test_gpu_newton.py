@@ -143,3 +143,21 @@ def test_time_step_control_follows_the_rule():
         dt, ok = osolver.dt_control(dt, 4 if its is None else its)
         assert ok == accepted
     assert sum(h for _, h, _, a in hist if a) == pytest.approx(t_end, rel=1e-12)
+
+
+def test_adaptive_forcing_reaches_the_same_root():
+    """Eisenstat-Walker forcing terms change the linear tolerances, not the Newton root."""
+    c = Case(3, (4, 4, 4), 2, seed=3, vscale=1.0)
+    u = c.dev(c.u)
+    outs = []
+    for forcing in (0, 1):
+        ug, kg = u.clone(), torch.zeros_like(u)
+        st = c.gm.newton_step(ug, kg, 0.01, newton_rtol=1e-10, gmres_rtol=1e-8, gmres_maxit=300, restart=40,
+                              jvp_prec="fp32", forcing=forcing, eta_max=0.1)
+        assert st["rfinal"] <= 1e-10 * st["r0"]
+        outs.append((ug.cpu().numpy(), st))
+    (a, sa), (b, sb) = outs
+    assert np.linalg.norm(a - b) <= 1e-8 * np.linalg.norm(a), (sa, sb)
+    import paper_2609_16424_b300 as lh
+    with pytest.raises(lh.LHError):
+        c.gm.newton_step(u.clone(), None, 0.01, forcing=1, eta_max=1.5)
