@@ -238,11 +238,23 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
 
     bool pending_b = false;
     for (int s = 0; s < PL::NSUB; ++s) {
+      // the record of this thread's (element, point) does not depend on the MMA: issue its
+      // loads first so their latency overlaps the transposition below
+      const int e = tid / QS, ql = tid % QS;
+      const int q = QS * s + ql;
+      const long long eg = e0 + e;
+      const bool valid = eg < P.NE && q < NQ;
+      float Lr[NR];
+      {
+        const float* rq = rec + (valid ? eg * NR * NQ + q : 0);
+#pragma unroll
+        for (int f = 0; f < NR; ++f) Lr[f] = valid ? rq[f * NQ] : 0.f;
+      }
       // ---- 3. D_f columns of this sub-chunk -> sX[e][q][slot][r] (slot = c ^ e ^ q, 16 B)
       {
         const int quarter = warp & 3, half = warp >> 2;
         const int row = 32 * quarter + lane;
-        const int cc = row / EB, e = row % EB;
+        const int cc = row / EB, er = row % EB;
         float v[16];
 #pragma unroll
         for (int part = 0; part < 2; ++part) {
@@ -251,19 +263,15 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
           tc::tmem_wait_ld();
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            const int ql = 8 * half + 4 * part + t;
-            const int slot = cc ^ (e & 7) ^ (ql & 7);
-            *reinterpret_cast<float4*>(sX + ((e * QS + ql) * 8 + slot) * 4) =
+            const int qw = 8 * half + 4 * part + t;
+            const int slot = cc ^ (er & 7) ^ (qw & 7);
+            *reinterpret_cast<float4*>(sX + ((er * QS + qw) * 8 + slot) * 4) =
                 make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
           }
         }
       }
       cta_sync();
       // ---- 4. quadrature-point tangent, thread = (e, ql)
-      const int e = tid / QS, ql = tid % QS;
-      const int q = QS * s + ql;
-      const long long eg = e0 + e;
-      const bool valid = eg < P.NE && q < NQ;
       float fval[DIM], fgrad[DIM][DIM], g = 0.f;
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
@@ -284,10 +292,6 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
             if constexpr (DIM == 3) hg[cc][2] = x.w;
           }
         }
-        const float* rq = rec + eg * NR * NQ + q;
-        float Lr[NR];
-#pragma unroll
-        for (int f = 0; f < NR; ++f) Lr[f] = rq[f * NQ];
         const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
         float a = sW[q0] * sW[q1];
         if constexpr (DIM == 3) a *= sW[q2];
