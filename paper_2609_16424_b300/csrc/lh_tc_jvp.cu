@@ -2,7 +2,8 @@
 // GMRES; the tangent of paper Sec. 3.1, Eq. (10), with the element operator B of Sec. 2.2,
 // Eq. (8), applied on the 5th-generation tensor cores).
 //
-// The element interpolation of a batch of EB = 16 elements is one dense MMA per batch:
+// The element interpolation of a batch of EB = 16 elements is a dense MMA per sub-chunk of
+// QS = 16 quadrature points (the next sub-chunk's MMA runs while this one is processed):
 //   D_f[(c, e)][(q, r)] = sum_k U[(c, e)][k] Bf[(q, r)][k]
 // rows (c, e) = component c of the direction (dk_x, dk_v, dk_e) of element e (M = 128:
 // 8 component slots x 16 elements), K = element dofs (H1 then L2), columns (q, r) = value
@@ -16,8 +17,8 @@
 // the CUDA cores between the two MMAs, one thread per (element, quadrature point).
 //
 // Dense element operators are (Q^d x 4) x (D^d + L^d) entries; they fit in shared memory
-// for 2D k <= 4 and 3D k <= 2.  One CTA per SM (persistent over batches) owns its tensor
-// memory for the whole launch.
+// for 2D k <= 4 and 3D k <= 2.  Persistent CTAs (two per SM with BF16 operands, one with
+// TF32 by shared memory) each own 256 tensor-memory columns for the whole launch.
 #include <cfloat>
 #include "lh_internal.h"
 #include "lh_kernels.h"
@@ -55,7 +56,7 @@ struct TcPlan {
   static constexpr int KBC = 4 * QS;               // backward K per sub-chunk
   static constexpr int NCF = 2 * DIM + 1;          // forward component slots used
   static constexpr int NCB = DIM + 1;              // backward component slots used
-  static constexpr int NCOLS = pow2_cols(NF + NB); // TMEM allocation
+  static constexpr int NCOLS = pow2_cols(2 * 4 * QS + NB);   // TMEM: two forward buffers + D_b
   // shared memory (bytes): A_b first (128-byte swizzle wants 1024-byte alignment)
   static constexpr uint32_t AB_ASTRIDE = 16u * 1024u;                 // 128 rows / 8 x 1024
   static constexpr uint32_t SZ_AB = 128u * KBC * ESZ;
@@ -72,7 +73,7 @@ struct TcPlan {
   static constexpr uint32_t BYTES = O_BAR + 32 + 1024;                 // + alignment slack
   static_assert(NF <= 256 && NF % 16 == 0, "forward N out of range");
   static_assert(NB <= 256 && NB % 16 == 0, "backward N out of range");
-  static_assert(NF + NB <= 512, "tensor memory");
+  static_assert(2 * 4 * QS + NB <= 256, "tensor memory: two CTAs per SM");
   static_assert(KBC * ESZ % 128 == 0, "sub-chunk K must fill 128-byte atoms");
   static_assert((uint32_t)EB * (DIM * ND + NL) * 4 <= SZ_X, "output staging");
   static_assert(NCF <= 8 && NCB <= 4, "component slots");
@@ -144,7 +145,7 @@ __device__ __forceinline__ long long node_lattice(const ElemParams& P, long long
 }  // namespace
 
 template <int DIM, int K, tc::Kind KIND, class TO>
-__global__ void __launch_bounds__(NTH, 1)
+__global__ void __launch_bounds__(NTH, 2)
 k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ dk,
          float* __restrict__ ev, TO* __restrict__ oute, int* __restrict__ err) {
   using PL = TcPlan<DIM, K, KIND>;
@@ -190,8 +191,21 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
   tc::fence_proxy_async();
   cta_sync();
   const uint32_t tm = *s_taddr;
-  const uint32_t tmf = tm, tmb = tm + PL::NF;
-  const uint32_t id_f = tc::instr_desc(KIND, 128, PL::NF), id_b = tc::instr_desc(KIND, 128, PL::NB);
+  // forward accumulators: two buffers of one sub-chunk (4 QS columns) each; then D_b
+  const uint32_t tmf = tm, tmb = tm + 2 * PL::KBC;
+  const uint32_t id_f = tc::instr_desc(KIND, 128, PL::KBC), id_b = tc::instr_desc(KIND, 128, PL::NB);
+  // forward MMA of sub-chunk s: rows [KBC s, KBC (s + 1)) of Bf into buffer s & 1
+  auto issue_fwd = [&](int s) {
+    const uint32_t rowoff = (uint32_t)(PL::KBC * s / 8) * PL::SBO_F;
+#pragma unroll
+    for (int j = 0; j < PL::KF / MK; ++j) {
+      const uint32_t ko = (uint32_t)(j * MK / PL::T) * 128u;
+      tc::mma<KIND>(tmf + (uint32_t)((s & 1) * PL::KBC),
+                    tc::smem_desc(tc::smem_u32(sAf) + ko, 128u, PL::SBO_F, tc::SW_NONE),
+                    tc::smem_desc(tc::smem_u32(sBf) + rowoff + ko, 128u, PL::SBO_F, tc::SW_NONE), id_f, j > 0);
+    }
+    tc::commit(mbf);
+  };
   uint32_t ph_f = 0, ph_b = 0;
   bool ok = true;
 
@@ -222,19 +236,8 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
     }
     tc::fence_proxy_async();
     cta_sync();
-    // ---- 2. forward MMA: D_f = U Bf^T
-    if (tid == 0) {
-#pragma unroll
-      for (int j = 0; j < PL::KF / MK; ++j) {
-        const uint32_t ko = (uint32_t)(j * MK / PL::T) * 128u;
-        tc::mma<KIND>(tmf, tc::smem_desc(tc::smem_u32(sAf) + ko, 128u, PL::SBO_F, tc::SW_NONE),
-                      tc::smem_desc(tc::smem_u32(sBf) + ko, 128u, PL::SBO_F, tc::SW_NONE), id_f, j > 0);
-      }
-      tc::commit(mbf);
-    }
-    ok = tc::mbar_wait(mbf, ph_f, kWaitPolls) && ok;
-    ph_f ^= 1u;
-    tc::fence_after_sync();
+    // ---- 2. forward MMA of the first sub-chunk: D_f = U Bf^T (its 4 QS columns)
+    if (tid == 0) issue_fwd(0);
 
     bool pending_b = false;
     for (int s = 0; s < PL::NSUB; ++s) {
@@ -250,6 +253,11 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
 #pragma unroll
         for (int f = 0; f < NR; ++f) Lr[f] = valid ? rq[f * NQ] : 0.f;
       }
+      ok = tc::mbar_wait(mbf, ph_f, kWaitPolls) && ok;   // forward MMA of this sub-chunk
+      ph_f ^= 1u;
+      tc::fence_after_sync();
+      // the other buffer was read in the previous sub-chunk (completed before its barrier)
+      if (tid == 0 && s + 1 < PL::NSUB) issue_fwd(s + 1);
       // ---- 3. D_f columns of this sub-chunk -> sX[e][q][slot][r] (slot = c ^ e ^ q, 16 B)
       {
         const int quarter = warp & 3, half = warp >> 2;
@@ -258,7 +266,7 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
         float v[16];
 #pragma unroll
         for (int part = 0; part < 2; ++part) {
-          const int col = 4 * QS * s + 32 * half + 16 * part;
+          const int col = (s & 1) * PL::KBC + 32 * half + 16 * part;
           tc::tmem_ld16(tmf + ((uint32_t)(32 * quarter) << 16) + (uint32_t)col, v);
           tc::tmem_wait_ld();
 #pragma unroll
