@@ -256,8 +256,6 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
       ok = tc::mbar_wait(mbf, ph_f, kWaitPolls) && ok;   // forward MMA of this sub-chunk
       ph_f ^= 1u;
       tc::fence_after_sync();
-      // the other buffer was read in the previous sub-chunk (completed before its barrier)
-      if (tid == 0 && s + 1 < PL::NSUB) issue_fwd(s + 1);
       // ---- 3. D_f columns of this sub-chunk -> sX[e][q][slot][r] (slot = c ^ e ^ q, 16 B)
       {
         const int quarter = warp & 3, half = warp >> 2;
@@ -279,6 +277,10 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
         }
       }
       cta_sync();
+      // next sub-chunk's forward MMA, into the other buffer (read in the previous sub-chunk).
+      // Issued only after this barrier: every thread has then finished its wait on the
+      // current phase of mbf, so that barrier cannot run a phase ahead of a waiting thread.
+      if (tid == 0 && s + 1 < PL::NSUB) issue_fwd(s + 1);
       // ---- 4. quadrature-point tangent, thread = (e, ql)
       float fval[DIM], fgrad[DIM][DIM], g = 0.f;
 #pragma unroll
