@@ -94,3 +94,29 @@ def test_tc_newton_gives_the_fp64_solution(kind):
     (a, sa), (b, sb) = outs
     assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(a), (sa, sb)
     c.gm.tc_status()
+
+
+@pytest.mark.parametrize("dim,n,k", [(3, (24, 24, 24), 2), (2, (80, 70), 3), (2, (60, 60), 4)])
+def test_tc_many_batches_per_cta(dim, n, k):
+    """Persistent CTAs that process several batches, each with several sub-chunks of
+    quadrature points (the pipelined forward MMAs): the tensor-core J.w agrees with the
+    FP32 record J.w (itself checked against the oracle) and no bounded wait expires."""
+    import paper_2609_16424_b300 as lh
+    import lh_synth
+    gm = lh.Mesh(dim, n, (0.0,) * dim, (1.0,) * dim, k, gamma=1.4)
+    x0 = gm.initial_nodes()
+    u = torch.zeros(gm.n, dtype=torch.float64, device="cuda")
+    u[:x0.numel()] = x0
+    u[dim * gm.NV:2 * dim * gm.NV] = torch.tensor(lh_synth.normal_vector(dim * gm.NV, 11, 0.1), device="cuda")
+    u[2 * dim * gm.NV:] = 1.0
+    kk = torch.zeros_like(u)
+    tau = 1e-3
+    gm.linearize(u, kk, tau)
+    dk = torch.tensor(lh_synth.normal_vector(gm.n, 12), dtype=torch.float32, device="cuda")
+    ref = gm.jvp(u, kk, tau, dk, lin=True).double()
+    nx = dim * gm.NV
+    for kind in ("tf32", "bf16"):
+        got = gm.jvp(u, kk, tau, dk, tc=kind).double()
+        gm.tc_status()
+        for sl in (slice(nx, 2 * nx), slice(2 * nx, gm.n)):
+            assert float((got[sl] - ref[sl]).norm() / ref[sl].norm()) <= TOL[kind]
