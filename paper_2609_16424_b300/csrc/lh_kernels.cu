@@ -372,9 +372,10 @@ k_jvp(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk,
 }
 
 // =====================================================================================
-// FP32 Jacobian action from the linearisation record: the primal quadrature-point state
-// (J, grad_hat v, e, rounded from the FP64 residual at the same w) is read instead of
-// being re-gathered and re-contracted; only the direction dk is gathered and contracted.
+// FP32 Jacobian action from the linearisation record: the direction dk is gathered and
+// contracted, and the linearised point map stored by the FP64 residual at the same w
+// (lh_qp.cuh, lin_record / qp_tangent_lin) turns its reference gradients and values into
+// the stress and energy tangents; no point-kernel re-evaluation.
 template <int DIM, int K, class TO>
 __global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
 k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ dk,

@@ -138,7 +138,8 @@ class Mesh:
         return (out, md.value) if min_detj else out
 
     def linearize(self, u, k, tau):
-        """Store the FP64 quadrature-point state at w = u + tau k (float) for jvp(lin=True)."""
+        """Evaluate the residual at w = u + tau k and keep the linearisation of the point map
+        (float) for jvp(lin=True) and jvp(tc=...)."""
         self._vec(u, "u")
         self._vec(k, "k")
         self._stream()

@@ -132,7 +132,7 @@ def test_energies(case):
 
 
 def test_jvp_fp32_record_parity(case):
-    """FP32 J.w from the linearisation record (state rounded from the FP64 residual)."""
+    """FP32 J.w from the linearisation record (the point map linearised by the FP64 residual)."""
     import paper_2609_16424_b300 as lh
     kk = lh_synth.normal_vector(case.gm.n, 4, 0.1)
     dk = lh_synth.normal_vector(case.gm.n, 5)
