@@ -653,6 +653,41 @@ def run_blast(args):
             "relative_energy_drift": (ke + ie - ke0 - ie0) / (ke0 + ie0), "kinetic_end": ke}
 
 
+def run_interface(args):
+    """Three-state interface problem 56x24 Q3-Q2: 50 implicit midpoint steps at 10x the
+    explicit time-step estimate, FP32 and TF32 J.w (the paper's Newton rtol 1e-5)."""
+    import torch
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import interface_problem
+    torch.cuda.set_device(0)
+    out = {"metric": "three-state interface 56x24 Q3-Q2, 50 implicit steps at 10x explicit dt", "runs": {}}
+    for prec in ("fp32", "tf32"):
+        mesh, u = interface_problem(56, 24, 3, device="cuda:0")
+        k = torch.zeros_like(u)
+        ke0, ie0 = mesh.energies(u)
+        times, its, gm, t = [], 0, 0, 0.0
+        status = "ok"
+        for step in range(50):
+            dt = 10.0 * mesh.dt_estimate(u)
+            try:
+                ms, st = _ms(lambda: mesh.newton_step(u, k, dt, jvp_prec=prec, **NEWTON))
+            except lh.LHError as err:
+                status = f"step {step} failed: {err}"
+                break
+            times.append(ms)
+            its += st["newton_its"]
+            gm += st["gmres_its_total"]
+            t += dt
+        nsteps = max(1, len(times))
+        ke1, ie1 = mesh.energies(u)
+        out["runs"][prec] = {"status": status, "steps": len(times), "t_end": t,
+                             "ms_per_step": round(statistics.mean(times), 3) if times else None,
+                             "newton_its_per_step": its / nsteps, "gmres_its_per_step": gm / nsteps,
+                             "relative_energy_drift": (ke1 + ie1 - ke0 - ie0) / (ke0 + ie0),
+                             "n_unknowns": mesh.n}
+    return out
+
+
 def run_reference(args, rank):
     """The oracle (plain FP64 numpy, one thread) timed on this host: each step is one
     residual evaluation of the bench workload state."""
@@ -707,6 +742,8 @@ def main():
     ap.add_argument("--mlp-steps", type=int, default=14)
     ap.add_argument("--mlp-epochs", type=int, default=30)
     ap.add_argument("--blast-run", action="store_true", help="point blast to --t-end")
+    ap.add_argument("--interface-run", action="store_true",
+                    help="three-state interface problem, 50 steps at 10x explicit dt")
     ap.add_argument("--t-end", type=float, default=0.1)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -718,6 +755,8 @@ def main():
         out = run_sweep(args)
     elif args.mlp:
         out = run_mlp(args)
+    elif args.interface_run:
+        out = run_interface(args)
     elif args.blast_run:
         out = run_blast(args)
     elif args.impl == "reference":
