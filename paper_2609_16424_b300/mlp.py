@@ -5,7 +5,7 @@ Workflow of one implicit step with the proposal:
     Y  = net.forward(X)                    # per-element correction        (lh_mlp_forward)
     k0 = apply(mesh, k1, Y)                # nodal average, k0 = k1 + dk   (lh_mlp_apply_prediction)
     mesh.newton_step(u, k0, dt)            # k0 is the initial guess; k0 <- converged k
-Plain extrapolation is k0 = k1; the converged k judges both.
+Plain extrapolation is k0 = k1; both are measured against the converged k.
 """
 import ctypes as C
 
