@@ -182,6 +182,93 @@ k_kron_pass(KronPass K, ElemParams P, const float* __restrict__ At_free, const f
   }
 }
 
+// Fused x and y passes for 3D meshes whose lattice planes fit in shared memory (N0, N1 <=
+// kNP): one block per (component, z plane) reads the plane of D^-1/2 r_v (stored transposed),
+// applies A_x along x and then A_y along y in shared memory (4 x 4 register tiles, float4
+// loads, zero padding to kNP) and writes the plane for the z pass; extra blocks write the L2
+// rows z_e = M_E^-1 r_e.  Same operator as k_kron_pass<0> followed by k_kron_pass<1>,
+// without the global round trip between them.
+constexpr int kNP = 52;   // padded plane extent, a multiple of 4
+constexpr int kXYThreads = 256;
+
+template <class TR, class TZ>
+__global__ void __launch_bounds__(kXYThreads)
+k_kron_xy(ElemParams P, const float* __restrict__ Ax_free, const float* __restrict__ Ax_fixed,
+          const float* __restrict__ Ay_free, const float* __restrict__ Ay_fixed, const TR* __restrict__ r,
+          const double* __restrict__ scale, const double* __restrict__ ime, float* __restrict__ fout,
+          TZ* __restrict__ z, long long main_blocks) {
+  __shared__ __align__(16) float sAx[kNP][kNP];   // [j][i] = A_x[i][j] (the stored transpose)
+  __shared__ __align__(16) float sAy[kNP][kNP];   // [j][i] = A_y[i][j]
+  __shared__ __align__(16) float sPT[kNP][kNP];   // input plane, transposed: [x][y]
+  __shared__ __align__(16) float sQ[kNP][kNP];    // after the x pass: [y][x]
+  const long long nv = P.NV, n1 = 3 * nv;
+  const int t = threadIdx.x;
+  if ((long long)blockIdx.x >= main_blocks) {
+    const long long b = blockIdx.x - main_blocks;
+    for (int q = 0; q < kERowsPerThread; ++q) {
+      const long long e = (b * kERowsPerThread + q) * kXYThreads + t;
+      if (e < P.NEd) z[2 * n1 + e] = TZ((double)r[2 * n1 + e] * ime[e]);
+    }
+    return;
+  }
+  const int N0 = P.N0, N1 = P.N1;
+  const int c = (int)(blockIdx.x / P.N2), zp = (int)(blockIdx.x % P.N2);
+  const float* Ax = c == 0 ? Ax_fixed : Ax_free;
+  const float* Ay = c == 1 ? Ay_fixed : Ay_free;
+  const long long plane = (long long)c * nv + (long long)N0 * N1 * zp;
+  for (int i = t; i < kNP * kNP; i += kXYThreads) {
+    const int a = i / kNP, b = i % kNP;
+    sAx[a][b] = (a < N0 && b < N0) ? __ldg(Ax + a * N0 + b) : 0.f;
+    sAy[a][b] = (a < N1 && b < N1) ? __ldg(Ay + a * N1 + b) : 0.f;
+    const int y = a, x = b;   // plane read coalesced along x, stored transposed
+    float v = 0.f;
+    if (x < N0 && y < N1) {
+      const long long node = (long long)x + (long long)N0 * y + (plane - (long long)c * nv);
+      v = (float)((double)r[n1 + (long long)c * nv + node] * scale[node]);
+    }
+    sPT[x][y] = v;
+  }
+  __syncthreads();
+  constexpr int NT = kNP / 4;
+  for (int tile = t; tile < NT * NT; tile += kXYThreads) {   // x pass: Q[y][i] = sum_j A_x[i][j] X[y][j]
+    const int i0 = (tile % NT) * 4, y0 = (tile / NT) * 4;
+    float acc[4][4] = {};
+    for (int j = 0; j < N0; ++j) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&sAx[j][i0]);
+      const float4 p4 = *reinterpret_cast<const float4*>(&sPT[j][y0]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, pv[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int yy = 0; yy < 4; ++yy) acc[ii][yy] += av[ii] * pv[yy];
+    }
+#pragma unroll
+    for (int yy = 0; yy < 4; ++yy)
+      *reinterpret_cast<float4*>(&sQ[y0 + yy][i0]) = make_float4(acc[0][yy], acc[1][yy], acc[2][yy], acc[3][yy]);
+  }
+  __syncthreads();
+  for (int tile = t; tile < NT * NT; tile += kXYThreads) {   // y pass: R[i][x] = sum_j A_y[i][j] Q[j][x]
+    const int x0 = (tile % NT) * 4, i0 = (tile / NT) * 4;
+    float acc[4][4] = {};
+    for (int j = 0; j < N1; ++j) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&sAy[j][i0]);
+      const float4 q4 = *reinterpret_cast<const float4*>(&sQ[j][x0]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int xx = 0; xx < 4; ++xx) acc[ii][xx] += av[ii] * qv[xx];
+    }
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii) {
+      if (i0 + ii >= N1) break;
+#pragma unroll
+      for (int xx = 0; xx < 4; ++xx)
+        if (x0 + xx < N0) fout[plane + (long long)N0 * (i0 + ii) + x0 + xx] = acc[ii][xx];
+    }
+  }
+}
+
 static KronPass kron_pass(const ElemParams& P, int axis) {
   const long long N[3] = {P.N0, P.N1, P.N2};
   KronPass K;
@@ -204,6 +291,17 @@ static cudaError_t kron_apply(cudaStream_t s, const ElemParams& P, const KronPre
   float* a = K.work;
   float* b = K.work + (long long)P.dim * P.NV;
   // pass over x (+ L2 rows), [pass over y], last pass over the last axis
+  if (P.dim == 3 && P.N0 <= kNP && P.N1 <= kNP) {   // x and y passes fused per z plane
+    const long long main_blocks = 3LL * P.N2;
+    const long long eblk = (P.NEd + (long long)kXYThreads * kERowsPerThread - 1) / ((long long)kXYThreads * kERowsPerThread);
+    k_kron_xy<TR, TZ><<<(unsigned)(main_blocks + eblk), kXYThreads, 0, s>>>(
+        P, K.At_free[0], K.At_fixed[0], K.At_free[1], K.At_fixed[1], r, K.scale, inv_me, a, z, main_blocks);
+    const KronPass kl = kron_pass(P, 2);
+    k_kron_pass<2, TR, TZ><<<(unsigned)kl.main_blocks, kKronThreads, 0, s>>>(
+        kl, P, K.At_free[2], K.At_fixed[2], a, r, K.scale, inv_me, nullptr, z, tau);
+    count_launches(2);
+    return cudaGetLastError();
+  }
   const KronPass k0 = kron_pass(P, 0);
   const long long eblocks = (P.NEd + (long long)kKronThreads * kERowsPerThread - 1) / ((long long)kKronThreads * kERowsPerThread);
   k_kron_pass<0, TR, TZ><<<(unsigned)(k0.main_blocks + eblocks), kKronThreads, 0, s>>>(
