@@ -312,6 +312,15 @@ lh_status lh_profile_read(lh_mesh* mesh, double* ms, long long* count);
  * Needs no GPU.  *ops is a HOST pointer. */
 lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops);
 
+/* Host check of the linearisation record: on `trials` random points near the undeformed
+ * element (seeded), compares the tangent formed from the record (lin_record + the linear
+ * map of the J.w kernels) with the dual-number tangent of the point kernel.  Writes the
+ * largest relative error of the record path evaluated in double (formula check) and the
+ * median relative error of dS when the record and the tangent are float (as on the GPU).
+ * Needs no GPU.  Output pointers are HOST pointers. */
+lh_status lh_qp_tangent_check(int dim, int visc, int trials, unsigned seed, double* max_err_double,
+                              double* median_err_float);
+
 /* Number of CUDA kernels this library has launched in the process so far. */
 long long lh_launch_count(void);
 

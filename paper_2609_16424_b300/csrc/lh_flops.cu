@@ -4,7 +4,9 @@
 // scalar: every +, -, *, / and every sqrt, tanh, cbrt, cos, sin counts one operation
 // (negation counts none).  The counts feed the algorithmic FLOP totals that the
 // benchmark divides by measured kernel time.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 #include "../../include/lh.h"
 
 // the counting scalar is host-only; the templated kernel code it runs is host+device
@@ -104,5 +106,81 @@ long long count(int kind, bool visc) {
 extern "C" lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops) {
   if (!ops || (dim != 2 && dim != 3) || kind < 0 || kind > 3) return LH_EINVAL;
   *ops = dim == 2 ? count<2>(kind, visc != 0) : count<3>(kind, visc != 0);
+  return LH_OK;
+}
+
+// ---- host check of the linearised tangent (lin_record + qp_tangent_lin) against the
+// dual-number tangent of qp_forward on random states near the undeformed element
+namespace {
+struct Lcg {
+  unsigned long long s;
+  double next() {   // uniform in [-1, 1)
+    s = s * 6364136223846793005ULL + 1442695040888963407ULL;
+    return (double)(s >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+};
+template <int DIM>
+void tangent_check(bool visc, int trials, unsigned seed, double* max_double, double* median_float) {
+  lh::QpC<double> c;
+  c.alpha = 0.3; c.mq = 1.3 * 0.3 * 0.002; c.inv_detJ0 = 500.0; c.gm1 = 0.4; c.ggm1 = 0.56;
+  c.h0 = 0.05; c.inv_hc = 20.0; c.q1 = 0.5; c.q2 = 1.0; c.scoef = 0.3; c.eps2 = 1e-12; c.visc = visc;
+  Lcg g{0x9E3779B97F4A7C15ULL ^ seed};
+  std::vector<double> ef;
+  double md = 0.0;
+  const double s = DIM == 3 ? 0.126 : 0.045;
+  for (int tr = 0; tr < trials; ++tr) {
+    double J[DIM][DIM], Gv[DIM][DIM], dJ[DIM][DIM], dGv[DIM][DIM];
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        J[i][j] = s * ((i == j) + 0.2 * g.next());
+        Gv[i][j] = g.next();
+        dJ[i][j] = 0.01 * s * g.next();
+        dGv[i][j] = g.next();
+      }
+    const double e = g.next(), de = g.next();
+    lh::Dual<double> Jd[DIM][DIM], Gd[DIM][DIM], Sd[DIM][DIM], Ed, dd;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        Jd[i][j] = lh::Dual<double>(J[i][j], dJ[i][j]);
+        Gd[i][j] = lh::Dual<double>(Gv[i][j], dGv[i][j]);
+      }
+    lh::qp_forward<DIM>(Jd, Gd, lh::Dual<double>(e, de), c, Sd, Ed, dd);
+    double So[DIM][DIM], Eo, det;
+    lh::QpPrimal<DIM, double> pr;
+    lh::qp_forward<DIM>(J, Gv, e, c, So, Eo, det, &pr);
+    double Ld[lh::lin_len<DIM>()], dSd[DIM][DIM], dEd, dWd;
+    lh::lin_record<DIM, double>(pr, c.gm1, visc, 0, 0, 0, Ld);
+    lh::qp_tangent_lin<DIM, double>(Ld, dJ, dGv, de, c.q1, c.q2, visc, dSd, dEd, dWd);
+    float Lf[lh::lin_len<DIM>()], dJf[DIM][DIM], dGf[DIM][DIM], dSf[DIM][DIM], dEf, dWf;
+    lh::lin_record<DIM, float>(pr, c.gm1, visc, 0, 0, 0, Lf);
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        dJf[i][j] = (float)dJ[i][j];
+        dGf[i][j] = (float)dGv[i][j];
+      }
+    lh::qp_tangent_lin<DIM, float>(Lf, dJf, dGf, (float)de, (float)c.q1, (float)c.q2, visc, dSf, dEf, dWf);
+    double n = 0.0, nd = 0.0, nf = 0.0;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        n += Sd[i][j].d * Sd[i][j].d;
+        nd += (dSd[i][j] - Sd[i][j].d) * (dSd[i][j] - Sd[i][j].d);
+        nf += (dSf[i][j] - Sd[i][j].d) * (dSf[i][j] - Sd[i][j].d);
+      }
+    const double rd = std::max({std::sqrt(nd / n), std::fabs(dEd - Ed.d) / std::fabs(Ed.d),
+                                std::fabs(dWd - c.alpha * dd.d) / std::fabs(c.alpha * dd.d)});
+    md = std::max(md, rd);
+    ef.push_back(std::sqrt(nf / n));
+  }
+  std::sort(ef.begin(), ef.end());
+  *max_double = md;
+  *median_float = ef[ef.size() / 2];
+}
+}  // namespace
+
+extern "C" lh_status lh_qp_tangent_check(int dim, int visc, int trials, unsigned seed, double* max_err_double,
+                                         double* median_err_float) {
+  if (!max_err_double || !median_err_float || (dim != 2 && dim != 3) || trials < 1) return LH_EINVAL;
+  if (dim == 2) tangent_check<2>(visc != 0, trials, seed, max_err_double, median_err_float);
+  else tangent_check<3>(visc != 0, trials, seed, max_err_double, median_err_float);
   return LH_OK;
 }
