@@ -153,7 +153,9 @@ lh_status lh_tc_status(lh_mesh* mesh);
 lh_status lh_linearize(lh_mesh* mesh, const double* u, const double* k, double tau);
 
 /* Transpose action out = (dR/dk)^T y (paper Sec. 3.1: transpose actions share the
- * gather-apply-scatter structure).  LH_FP64 only; y, out device [n] double. */
+ * gather-apply-scatter structure).  LH_FP64: y, out device [n] double, the point kernel's
+ * hand-written reverse mode.  LH_FP32_LIN: y, out float, the transpose of the linearised
+ * point map of the record of a preceding lh_linearize(u, k, tau). */
 lh_status lh_jtvp(lh_mesh* mesh, const double* u, const double* k, double tau,
                   const void* y, void* out, lh_prec prec);
 
@@ -320,6 +322,11 @@ lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops);
  * Needs no GPU.  Output pointers are HOST pointers. */
 lh_status lh_qp_tangent_check(int dim, int visc, int trials, unsigned seed, double* max_err_double,
                               double* median_err_float);
+
+/* Host check of the transposed linearised map used by the reduced-precision J^T y: the
+ * dot-product identity <L x, y> = <x, L^T y> on `trials` random records, directions and
+ * adjoints (double).  Writes the largest relative defect.  Needs no GPU. */
+lh_status lh_qp_adjoint_check(int dim, int visc, int trials, unsigned seed, double* max_rel);
 
 /* Number of CUDA kernels this library has launched in the process so far. */
 long long lh_launch_count(void);

@@ -762,8 +762,16 @@ lh_status lh_linearize(lh_mesh* m, const double* u, const double* k, double tau)
 lh_status lh_jtvp(lh_mesh* m, const double* u, const double* k, double tau, const void* y, void* out,
                   lh_prec prec) {
   if (!m || !u || !k || !y || !out) return fail(m, LH_EINVAL, "NULL argument to lh_jtvp");
-  if (prec != LH_FP64) return fail(m, LH_EINVAL, "lh_jtvp supports LH_FP64 only");
   if (y == out) return fail(m, LH_EINVAL, "out must not alias y");
+  if (prec == LH_FP32_LIN) {
+    if (!m->rec_valid || m->rec_u != u || m->rec_k != k || m->rec_tau != tau)
+      return fail(m, LH_EINVAL, "lh_jtvp(LH_FP32_LIN): call lh_linearize with the same u, k, tau first");
+    LH_CK(m, launch_jtvp_rec_f32(m->P, m->stream, m->d_rec, tau, static_cast<const float*>(y),
+                                 reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out),
+                                 prof_pair(m, LH_PROF_JTVP)));
+    return LH_OK;
+  }
+  if (prec != LH_FP64) return fail(m, LH_EINVAL, "lh_jtvp supports LH_FP64 and LH_FP32_LIN");
   LH_CK(m, launch_jtvp(m->P, m->stream, u, k, tau, static_cast<const double*>(y), m->d_ev,
                        static_cast<double*>(out), prof_pair(m, LH_PROF_JTVP)));
   return LH_OK;

@@ -184,3 +184,42 @@ extern "C" lh_status lh_qp_tangent_check(int dim, int visc, int trials, unsigned
   else tangent_check<3>(visc != 0, trials, seed, max_err_double, median_err_float);
   return LH_OK;
 }
+
+// ---- host check of the transposed linearised map: <L x, yb> = <x, L^T yb> on random data
+namespace {
+template <int DIM>
+double adjoint_check(bool visc, int trials, unsigned seed) {
+  Lcg g{0x51ED270B27A8D5A1ULL ^ seed};
+  double worst = 0.0;
+  for (int tr = 0; tr < trials; ++tr) {
+    double L[lh::lin_len<DIM>()];
+    for (int f = 0; f < lh::lin_len<DIM>(); ++f) L[f] = g.next();
+    double dJ[DIM][DIM], dGv[DIM][DIM], Sb[DIM][DIM], dS[DIM][DIM], Jb[DIM][DIM], Gvb[DIM][DIM];
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        dJ[i][j] = g.next();
+        dGv[i][j] = g.next();
+        Sb[i][j] = g.next();
+      }
+    const double de = g.next(), Eb = g.next(), Wb = g.next();
+    double dE, dW, eb;
+    lh::qp_tangent_lin<DIM, double>(L, dJ, dGv, de, 0.5, 1.0, visc, dS, dE, dW);
+    lh::qp_tangent_lin_adj<DIM, double>(L, Sb, Eb, Wb, 0.5, 1.0, visc, Jb, Gvb, eb);
+    double lhs = dE * Eb + dW * Wb, rhs = de * eb, scale = std::fabs(dE * Eb) + std::fabs(dW * Wb) + std::fabs(de * eb);
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        lhs += dS[i][j] * Sb[i][j];
+        rhs += dJ[i][j] * Jb[i][j] + dGv[i][j] * Gvb[i][j];
+        scale += std::fabs(dS[i][j] * Sb[i][j]) + std::fabs(dJ[i][j] * Jb[i][j]) + std::fabs(dGv[i][j] * Gvb[i][j]);
+      }
+    worst = std::max(worst, std::fabs(lhs - rhs) / scale);
+  }
+  return worst;
+}
+}  // namespace
+
+extern "C" lh_status lh_qp_adjoint_check(int dim, int visc, int trials, unsigned seed, double* max_rel) {
+  if (!max_rel || (dim != 2 && dim != 3) || trials < 1) return LH_EINVAL;
+  *max_rel = dim == 2 ? adjoint_check<2>(visc != 0, trials, seed) : adjoint_check<3>(visc != 0, trials, seed);
+  return LH_OK;
+}

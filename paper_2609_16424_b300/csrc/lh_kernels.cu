@@ -455,6 +455,98 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
 }
 
 // =====================================================================================
+// FP32 transpose action from the linearisation record: y_v (fixed rows masked) and y_e are
+// gathered and contracted; the transpose of the linearised point map (qp_tangent_lin_adj)
+// gives the adjoints of the reference gradients and values; contributions to the x and v
+// rows go to the element scratch ([e][2 DIM][ND]), e rows directly.
+template <int DIM, int K>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_jtvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ y,
+           float* __restrict__ ev, float* __restrict__ oute) {
+  using C = Cfg<DIM, K>;
+  constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q;
+  constexpr int NR = lin_len<DIM>();
+  using PL = Plan<DIM, K, 2 * DIM, 0, 1, 2 * DIM>;
+  using TB = Tab<K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  float* sB = smem + TB::B;
+  float* sG = smem + TB::G;
+  float* sBl = smem + TB::BL;
+  float* sW = smem + TB::W;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  float* s_h = smem + PL::HEAD + eb * PL::PER;   // [DIM][ND] y_v in, [2 DIM][ND] out
+  float* s_l = s_h + 2 * DIM * ND;
+  float* t1 = s_l + NL;
+  float* t2 = t1 + PL::T1;
+  float* sf = t2 + PL::T2;
+  const ElemIdx E = elem_index<DIM, K>(P);
+  for (int i = lt; i < DIM * ND; i += NQ) {
+    const int comp = i / ND, a = i % ND;
+    float v = 0.f;
+    if (E.valid) {
+      const long long nd = node_of<DIM, K>(P, E, a);
+      v = fixed_node<DIM>(P, nd, comp) ? 0.f : y[(DIM + comp) * P.NV + nd];
+    }
+    s_h[i] = v;
+  }
+  for (int i = lt; i < NL; i += NQ) s_l[i] = E.valid ? y[2 * DIM * P.NV + E.e * NL + i] : 0.f;
+  float Lr[NR];
+  {
+    const float* rq = rec + (E.valid ? E.e : 0) * NR * NQ + lt;
+#pragma unroll
+    for (int f = 0; f < NR; ++f) Lr[f] = E.valid ? rq[f * NQ] : 0.f;
+  }
+  __syncthreads();
+  float hv[DIM], hg[DIM][DIM];
+  h1_fwd<DIM, K, DIM, float, true>(s_h, t1, t2, sB, sG, lt, hv, hg);
+  float lq[1];
+  l2_fwd<DIM, K, 1>(s_l, t1, t2, sBl, lt, lq);
+  float mq;
+  {
+    const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+    float a = sW[q0] * sW[q1];
+    if constexpr (DIM == 3) a *= sW[q2];
+    mq = P.fmq0[E.valid ? E.e : 0] * a;
+  }
+  // adjoints of the point outputs: dS against grad y_v, dE against -y_e (g = mq e - dE)
+  const float Eb = -lq[0];
+  float Wb = 0.f, xb[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) xb[i] = 0.f;
+  if constexpr (DIM == 2) {
+    if (P.tg) {   // g -= dW s + W grad s . dx
+      constexpr int O = 2 * DIM * DIM;
+      Wb = -lq[0] * Lr[O + LF_TGS];
+      xb[0] = -lq[0] * Lr[O + LF_W] * Lr[O + LF_TGX];
+      xb[1] = -lq[0] * Lr[O + LF_W] * Lr[O + LF_TGY];
+    }
+  }
+  float Jb[DIM][DIM], Gvb[DIM][DIM], ebv;
+  qp_tangent_lin_adj<DIM>(Lr, hg, Eb, Wb, P.fq1, P.fq2, P.visc != 0, Jb, Gvb, ebv);
+  float fval[2 * DIM], fgrad[2 * DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    fval[i] = tau * xb[i];
+    fval[DIM + i] = mq * hv[i];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      fgrad[i][r] = tau * Jb[i][r];
+      fgrad[DIM + i][r] = tau * Gvb[i][r];
+    }
+  }
+  const float g = mq * lq[0] + tau * ebv;
+  h1_bwd<DIM, K, 2 * DIM>(fval, fgrad, sf, t1, t2, sB, sG, lt, s_h);
+  if (E.valid)
+    for (int i = lt; i < 2 * DIM * ND; i += NQ) ev[E.e * (2 * DIM * ND) + i] = s_h[i];
+  float gv[1] = {g};
+  l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
+  if (E.valid)
+    for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = s_l[i];
+}
+
+// =====================================================================================
 // Transpose action: adjoint of the element residual map, contributions to the x and v
 // rows in the element scratch ([e][2 DIM][ND]), e rows directly.
 template <int DIM, int K>
@@ -810,16 +902,16 @@ __global__ void k_assemble_jvp(ElemParams P, const T* __restrict__ dk, double ta
   out[iv] = TO(fixed_node<DIM>(P, nd, comp) ? dk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd));
 }
 
-template <int DIM, int K>
-__global__ void k_assemble_jtvp(ElemParams P, const double* __restrict__ y, double tau,
-                                const double* __restrict__ ev, double* __restrict__ out) {
+template <int DIM, int K, class T>
+__global__ void k_assemble_jtvp(ElemParams P, const T* __restrict__ y, double tau,
+                                  const T* __restrict__ ev, T* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= DIM * P.NV) return;
   const int comp = (int)(i / P.NV);
   const long long nd = i % P.NV;
   const long long iv = DIM * P.NV + i;
   out[i] = y[i] + gather_node<DIM, K>(P, ev, 2 * DIM, comp, nd);
-  double s = -tau * y[i] + gather_node<DIM, K>(P, ev, 2 * DIM, DIM + comp, nd);
+  T s = T(-tau) * y[i] + gather_node<DIM, K>(P, ev, 2 * DIM, DIM + comp, nd);
   if (fixed_node<DIM>(P, nd, comp)) s += y[iv];
   out[iv] = s;
 }
@@ -969,6 +1061,19 @@ struct Launch {
     k_assemble_jvp<DIM, K, float, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
     return cudaGetLastError();
   }
+  static cudaError_t jtvp_rec(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* y,
+                              float* ev, float* out, cudaEvent_t* ev2) {
+    using PL = Plan<DIM, K, 2 * DIM, 0, 1, 2 * DIM>;
+    const size_t by = PL::bytes(sizeof(float));
+    cudaError_t e = prep<k_jtvp_rec<DIM, K>>(by);
+    if (e != cudaSuccess) return e;
+    mark(ev2, 0, s);
+    k_jtvp_rec<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, rec, (float)tau, y, ev, out + 2 * DIM * P.NV);
+    mark(ev2, 1, s);
+    count_launches(2);
+    k_assemble_jtvp<DIM, K, float><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, y, tau, ev, out);
+    return cudaGetLastError();
+  }
   static cudaError_t jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                           const double* y, double* ev, double* out, cudaEvent_t* ev2) {
     using PL = Plan<DIM, K, 3 * DIM, 0, 2, 2 * DIM>;
@@ -979,7 +1084,7 @@ struct Launch {
     k_jtvp<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, y, ev, out + 2 * DIM * P.NV);
     mark(ev2, 1, s);
     count_launches(2);
-    k_assemble_jtvp<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, y, tau, ev, out);
+    k_assemble_jtvp<DIM, K, double><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, y, tau, ev, out);
     return cudaGetLastError();
   }
   static cudaError_t mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out,
@@ -1073,6 +1178,10 @@ cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u,
 cudaError_t launch_jvp_f32_to_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                                   const float* dk, float* ev, double* out, cudaEvent_t* ev2) {
   LH_DISPATCH(P, template jvp<float, double>(P, s, u, k, tau, dk, ev, out, ev2))
+}
+cudaError_t launch_jtvp_rec_f32(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* y,
+                               float* ev, float* out, cudaEvent_t* ev2) {
+  LH_DISPATCH(P, jtvp_rec(P, s, rec, tau, y, ev, out, ev2))
 }
 cudaError_t launch_jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                         const double* y, double* ev, double* out, cudaEvent_t* ev2) {

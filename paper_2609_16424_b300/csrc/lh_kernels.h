@@ -42,6 +42,9 @@ cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u,
                            const double* dk, double* ev, double* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                            const float* dk, float* ev, float* out, cudaEvent_t* ev2 = nullptr);
+// FP32 transpose action from the linearisation record (float y and out)
+cudaError_t launch_jtvp_rec_f32(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* y,
+                               float* ev, float* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                         const double* y, double* ev, double* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out,

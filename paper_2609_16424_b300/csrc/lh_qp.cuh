@@ -312,6 +312,140 @@ __host__ __device__ __forceinline__ void qp_tangent_lin(const T (&L)[lin_len<DIM
   }
 }
 
+// Transpose of qp_tangent_lin (the adjoint of the linearised point map, for the
+// reduced-precision J^T y): given the adjoints Sb of dS, Eb of dE and Wb of dW, returns the
+// adjoints Jb of dJ, Gvb of dGv and eb of de.  Each statement of qp_tangent_lin is
+// transposed in reverse order; the map is linear, so only record values enter.
+template <int DIM, class T = float>
+__host__ __device__ __forceinline__ void qp_tangent_lin_adj(const T (&L)[lin_len<DIM>()], const T (&Sb)[DIM][DIM],
+                                                            T Eb, T Wb, T q1, T q2, bool visc,
+                                                            T (&Jb)[DIM][DIM], T (&Gvb)[DIM][DIM], T& eb) {
+  constexpr int O = 2 * DIM * DIM;
+  T Ji[DIM][DIM], Lv[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      Ji[i][j] = L[i * DIM + j];
+      Lv[i][j] = L[DIM * DIM + i * DIM + j];
+      Jb[i][j] = T(0);
+    }
+  const T W = L[O + LF_W], p = L[O + LF_P];
+  const T mu = visc ? L[O + LF_MU] : T(0);
+  // primal stress, strain rate and their products
+  T sg[DIM][DIM], ep[DIM][DIM], E = T(0);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      ep[i][j] = T(0.5) * (Lv[i][j] + Lv[j][i]);
+      sg[i][j] = (i == j ? -p : T(0)) + mu * ep[i][j];
+    }
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) E += sg[i][j] * Lv[i][j];
+  // dS = W N J^-T  ->  Nb = W Sb J^-1
+  T Nb[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      T v = T(0);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) v += Sb[i][j] * Ji[j][a];
+      Nb[i][a] = W * v;
+    }
+  // dE = W (theta E + dE_in), dW = W theta
+  T thb = W * E * Eb + W * Wb;
+  const T dEinb = W * Eb;
+  // N = theta sg + dsg - M dJ^T,  M = sg J^-T
+  T dsgb[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    T M[DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      T v = T(0);
+#pragma unroll
+      for (int k = 0; k < DIM; ++k) v += sg[i][k] * Ji[b][k];
+      M[b] = v;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      thb += Nb[i][a] * sg[i][a];
+      dsgb[i][a] = Nb[i][a] + dEinb * Lv[i][a];          // also from dE_in = dsg : grad v
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) Jb[a][b] -= Nb[i][a] * M[b];
+    }
+  }
+  // dE_in also = sg : dL;  dsg = -dp I + dmu eps + mu eps(dL)
+  T dLb[DIM][DIM];
+  T dpb = T(0), dmub = T(0);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    dpb -= dsgb[i][i];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      dmub += dsgb[i][j] * ep[i][j];
+      dLb[i][j] = dEinb * sg[i][j] + mu * T(0.5) * (dsgb[i][j] + dsgb[j][i]);
+    }
+  }
+  T ebv = T(0);
+  if (visc) {
+    const T cs = L[O + LF_CS], ke = L[O + LF_KE], h = L[O + LF_H], ds = L[O + LF_DS], ids = L[O + LF_IDS];
+    const T iab = L[O + LF_IAB], psi = L[O + LF_PSI], G = L[O + LF_G], rh = L[O + LF_RH];
+    T div = T(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) div += Lv[i][i];
+    const T dv = h * div;
+    // dmu = mu theta (1/dim - 1) + rh dX
+    thb += mu * (T(1) / DIM - T(1)) * dmub;
+    const T dXb = rh * dmub;
+    // dX = q2 dab + q1 (psi dcs + cs dpsi)
+    const T dabb = q2 * dXb, dcsb = q1 * psi * dXb, dpsib = q1 * cs * dXb;
+    const T dargb = G * dpsib;
+    // darg = -1/2 ids (ddv - dv dds ids);  dab = iab (dv ddv + ds dds)
+    const T ddvb = -T(0.5) * ids * dargb + iab * dv * dabb;
+    const T ddsb = T(0.5) * ids * ids * dv * dargb + iab * ds * dabb;
+    // dds = ds (tq + ke de);  ddv = h (tq div + ddiv);  tq = theta / dim
+    const T tqb = ds * ddsb + h * div * ddvb;
+    ebv += ds * ke * ddsb + cs * ke * dcsb;   // dcs = cs ke de
+    const T ddivb = h * ddvb;
+    thb += tqb * (T(1) / DIM);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) dLb[i][i] += ddivb;
+  }
+  // dp = -p theta + pe de
+  thb += -p * dpb;
+  ebv += L[O + LF_PE] * dpb;
+  // dL = Y J^-1 -> Yb = dLb J^-T;  Y = dGv - grad v dJ
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      T v = T(0);
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) v += dLb[i][j] * Ji[r][j];
+      Gvb[i][r] = v;
+    }
+#pragma unroll
+  for (int b = 0; b < DIM; ++b)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      T v = T(0);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) v += Gvb[i][r] * Lv[i][b];
+      Jb[b][r] -= v;
+    }
+  // theta = sum_{i,r} J^-1[i][r] dJ[r][i]
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) Jb[r][i] += thb * Ji[i][r];
+  eb = ebv;
+}
+
 // Taylor-Green manufactured energy source per unit volume (gamma = 5/3):
 //   s = (3 pi / 8) [cos 3 pi x cos pi y - cos pi x cos 3 pi y]
 template <class S, class T>

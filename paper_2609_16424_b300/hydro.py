@@ -193,14 +193,17 @@ class Mesh:
         self._check(_L.lh_jvp(self._h, _ptr(u), _ptr(k), float(tau), _ptr(dk), _ptr(out), prec))
         return out
 
-    def jtvp(self, u, k, tau, y, out=None):
-        """(dR/dk)^T y (FP64)."""
+    def jtvp(self, u, k, tau, y, out=None, lin=False):
+        """(dR/dk)^T y: FP64 (float64 y), or FP32 from the record of linearize(u, k, tau)
+        (lin=True, float32 y)."""
         self._vec(u, "u")
         self._vec(k, "k")
-        self._vec(y, "y")
-        out = self.new() if out is None else self._vec(out, "out")
+        dt = torch.float32 if lin else torch.float64
+        self._vec(y, "y", dt)
+        out = self.new(dt) if out is None else self._vec(out, "out", dt)
         self._stream()
-        self._check(_L.lh_jtvp(self._h, _ptr(u), _ptr(k), float(tau), _ptr(y), _ptr(out), _lib.LH_FP64))
+        prec = _lib.LH_FP32_LIN if lin else _lib.LH_FP64
+        self._check(_L.lh_jtvp(self._h, _ptr(u), _ptr(k), float(tau), _ptr(y), _ptr(out), prec))
         return out
 
     def mass_apply(self, which, f):

@@ -170,3 +170,25 @@ def test_kronecker_preconditioner_is_the_exact_block_inverse(dim, n, k):
     ref = np.concatenate([rx + tau * zv, zv, ze])
     rel = c.rel_blocks(z, ref)
     assert max(rel) <= 2e-6, rel
+
+
+def test_jtvp_fp32_record(case):
+    """FP32 transpose action from the record: against the FP64 adjoint (per block), and the
+    dot-product identity with the FP32 record J.w."""
+    kk = lh_synth.normal_vector(case.gm.n, 14, 0.1)
+    y = lh_synth.normal_vector(case.gm.n, 15)
+    dk = lh_synth.normal_vector(case.gm.n, 16)
+    tau = 0.02
+    u, kd = case.dev(case.u), case.dev(kk)
+    ref = case.gm.jtvp(u, kd, tau, case.dev(y)).cpu().numpy()
+    case.gm.linearize(u, kd, tau)
+    yf = case.dev(y, torch.float32)
+    got = case.gm.jtvp(u, kd, tau, yf, lin=True).double().cpu().numpy()
+    rel = case.rel_blocks(got, ref)
+    assert max(rel) <= 2e-5, rel
+    dkf = case.dev(dk, torch.float32)
+    jv = case.gm.jvp(u, kd, tau, dkf, lin=True).double()
+    lhs = float((jv * yf.double()).sum())
+    rhs = float((dkf.double() * case.gm.jtvp(u, kd, tau, yf, lin=True).double()).sum())
+    scale = float((jv.abs() * yf.double().abs()).sum())
+    assert abs(lhs - rhs) <= 1e-6 * scale
