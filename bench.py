@@ -348,6 +348,10 @@ def run_ours(args, rank, world, device):
     t_j32 = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of), reps, flush)
     mesh.linearize(u_s, kd, tau)
     t_j32r = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of, lin=True), reps, flush)
+    yv = torch.randn(n, dtype=torch.float64, device=device, generator=torch.Generator(device).manual_seed(5))
+    yf = yv.float()
+    t_jt64 = kernel_rate(mesh, lambda: mesh.jtvp(u_s, kd, tau, yv), reps, flush)
+    t_jt32 = kernel_rate(mesh, lambda: mesh.jtvp(u_s, kd, tau, yf, lin=True), reps, flush)
     t_tc, kp_tc = {}, {}
     for kind in ("tf32", "bf16"):
         t_tc[kind] = kernel_rate(mesh, lambda: mesh.jvp(u_s, kd, tau, dkf, out=of, tc=kind), reps, flush)
@@ -432,6 +436,8 @@ def run_ours(args, rank, world, device):
             "jvp_fp32_record": {"gdofs": round(n / (t_j32r * 1e-3) / 1e9, 4), "ms": round(t_j32r, 5),
                                 "elem_kernel_ms": round(kpr["jvp_fp32"][0] / max(1, kpr["jvp_fp32"][1]), 5),
                                 "tflops_elem": round(fl["jvp_rec"] * ne / (kpr["jvp_fp32"][0] / max(1, kpr["jvp_fp32"][1]) * 1e-3) / 1e12, 4)},
+            "jtvp_fp64": {"gdofs": round(n / (t_jt64 * 1e-3) / 1e9, 4), "ms": round(t_jt64, 5)},
+            "jtvp_fp32_record": {"gdofs": round(n / (t_jt32 * 1e-3) / 1e9, 4), "ms": round(t_jt32, 5)},
             **{f"jvp_{kind}_tensor_core": {
                 "gdofs": round(n / (t_tc[kind] * 1e-3) / 1e9, 4), "ms": round(t_tc[kind], 5),
                 "elem_kernel_ms": round(kp_tc[kind][0] / max(1, kp_tc[kind][1]), 5),
