@@ -11,7 +11,15 @@ the first step).  The linear solve is exact (dense LU of the complex-step Jacobi
 small systems and preconditioned GMRES with complex-step Jacobian actions otherwise;
 the converged Newton solution does not depend on that choice.
 
-Also the Newton-count time step control of Sec. 4 ("Implicit time step control").
+Also the Newton-count time step control of Sec. 4 ("Implicit time step control") and the
+three SDIRK schemes of Sec. 4 (SD2/SD3/SD4: implicit midpoint, and the 3-stage methods of
+orders 3 and 4).  Each stage i solves the stage system of Eq. (21),
+R(k_i; a_ii dt, u^n + dt sum_{j<i} a_ij k_j) = 0, and u^{n+1} = u^n + dt sum_i b_i k_i.
+The paper names the schemes only by order and stage count; the tableaux are the classical
+ones with those properties (reading): Alexander's L-stable stiffly accurate method (gamma the
+root in (1/6, 1/2) of gamma^3 - 3 gamma^2 + 3/2 gamma - 1/6) and Crouzeix's A-stable method
+(gamma = 1/2 + cos(pi/18)/sqrt(3)).  Stage initial guesses: the previous stage's k (the
+caller's k_prev, or zero, for the first stage).
 """
 import numpy as np
 
@@ -125,3 +133,57 @@ def dt_control(dt, newton_iters):
     if newton_iters <= 3:
         return dt, True
     return 0.85 * dt, False
+
+
+def sdirk_tableau(scheme):
+    """Butcher tableau (A [s x s] lower triangular with equal diagonal, b [s]) of SD2/SD3/SD4."""
+    if scheme == 2:
+        return np.array([[0.5]]), np.array([1.0])
+    if scheme == 3:
+        r = np.roots([1.0, -3.0, 1.5, -1.0 / 6.0])
+        g = float(min(r.real[(abs(r.imag) < 1e-12) & (r.real > 1.0 / 6.0) & (r.real < 0.5)]))
+        b1 = -(6.0 * g * g - 16.0 * g + 1.0) / 4.0
+        b2 = (6.0 * g * g - 20.0 * g + 5.0) / 4.0
+        A = np.array([[g, 0.0, 0.0], [(1.0 - g) / 2.0, g, 0.0], [b1, b2, g]])
+        return A, A[2].copy()
+    if scheme == 4:
+        g = 0.5 + np.cos(np.pi / 18.0) / np.sqrt(3.0)
+        d = 1.0 / (6.0 * (2.0 * g - 1.0) ** 2)
+        A = np.array([[g, 0.0, 0.0], [0.5 - g, g, 0.0], [2.0 * g, 1.0 - 4.0 * g, g]])
+        return A, np.array([d, 1.0 - 2.0 * d, d])
+    raise ValueError("scheme must be 2, 3 or 4")
+
+
+def sdirk_stages(stage_solve, u, dt, A, b, k0=None):
+    """The SDIRK stage loop for any stage solver stage_solve(base, tau, k_guess) -> k.
+
+    Returns (u^{n+1}, [k_1 .. k_s])."""
+    ks = []
+    guess = k0
+    for i in range(len(b)):
+        base = u.copy()
+        for j in range(i):
+            base = base + dt * A[i, j] * ks[j]
+        k = stage_solve(base, dt * A[i, i], guess)
+        ks.append(k)
+        guess = k
+    unew = u.copy()
+    for i in range(len(b)):
+        unew = unew + dt * b[i] * ks[i]
+    return unew, ks
+
+
+def sdirk_step(hyd, u, dt, scheme, k_prev=None, **kw):
+    """One SDn step (n = scheme): Newton on each stage system.  Returns (u^{n+1}, k_s,
+    [NewtonResult per stage]); raises RuntimeError if a stage does not converge."""
+    A, b = sdirk_tableau(scheme)
+    results = []
+
+    def solve(base, tau, guess):
+        k, res = newton(hyd, base, tau, k0=guess, **kw)
+        if not res.converged:
+            raise RuntimeError("SDIRK stage did not converge")
+        results.append(res)
+        return k
+    unew, ks = sdirk_stages(solve, u, dt, A, b, k_prev)
+    return unew, ks[-1], results
