@@ -15,6 +15,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -699,6 +700,64 @@ def run_interface(args):
     return out
 
 
+# The paper's Taylor-Green table (Sec. 4.1, implicit columns; one MPI task on a laptop with
+# an assembled Jacobian and a sparse direct solver): (k, FS-CFL, 1/h) -> (L1 error, steps, s)
+PAPER_TG = {
+    (2, 0.5, 16): (5.11e-02, 13, 0.2), (2, 2.0, 16): (5.75e-02, 4, 0.1), (2, 8.0, 16): (1.54e-01, 1, 0.1),
+    (2, 0.5, 32): (9.42e-03, 26, 0.3), (2, 2.0, 32): (1.20e-02, 7, 0.2), (2, 8.0, 32): (1.05e-01, 2, 0.1),
+    (2, 0.5, 64): (2.57e-03, 51, 1.4), (2, 2.0, 64): (3.55e-03, 12, 0.6), (2, 8.0, 64): (4.30e-02, 4, 0.4),
+    (2, 0.5, 128): (6.66e-04, 102, 12), (2, 2.0, 128): (9.35e-04, 26, 3.6), (2, 8.0, 128): (9.46e-03, 7, 2.1),
+    (2, 0.5, 256): (1.64e-04, 203, 126), (2, 2.0, 256): (2.35e-04, 51, 34), (2, 8.0, 256): (2.45e-03, 13, 16),
+    (3, 0.5, 16): (1.24e-02, 20, 0.3), (3, 2.0, 16): (1.20e-02, 5, 0.2), (3, 8.0, 16): (2.09e-01, 2, 0.1),
+    (3, 0.5, 32): (1.57e-03, 38, 1.3), (3, 2.0, 32): (1.64e-03, 10, 0.5), (3, 8.0, 32): (1.94e-02, 3, 0.3),
+    (3, 0.5, 64): (1.80e-04, 76, 11), (3, 2.0, 64): (2.08e-04, 19, 3), (3, 8.0, 64): (3.39e-03, 5, 1.6),
+    (3, 0.5, 128): (2.02e-05, 152, 106), (3, 2.0, 128): (2.42e-05, 38, 26), (3, 8.0, 128): (5.52e-04, 10, 7.7),
+    (3, 0.5, 256): (2.32e-06, 304, 1150), (3, 2.0, 256): (3.66e-06, 76, 288), (3, 8.0, 256): (7.54e-05, 19, 71),
+    (4, 0.5, 16): (5.25e-03, 26, 0.7), (4, 2.0, 16): (7.77e-03, 7, 0.4), (4, 8.0, 16): (7.62e+01, 2, 0.2),
+    (4, 0.5, 32): (4.50e-04, 51, 4.3), (4, 2.0, 32): (9.63e-04, 13, 1.4), (4, 8.0, 32): (2.29e+02, 4, 1),
+    (4, 0.5, 64): (1.49e-05, 102, 37), (4, 2.0, 64): (6.08e-05, 26, 9.5), (4, 8.0, 64): (5.45e-03, 7, 5.1),
+    (4, 0.5, 128): (1.44e-06, 203, 360), (4, 2.0, 128): (4.34e-06, 51, 87), (4, 8.0, 128): (6.86e-04, 13, 28),
+    (4, 0.5, 256): (8.36e-08, 405, 3613), (4, 2.0, 256): (2.66e-07, 102, 906), (4, 8.0, 256): (5.50e-05, 26, 242),
+}
+
+
+def run_tg_table(args):
+    """2D Taylor-Green to t = 0.5 (Sec. 4.1): Q2-Q1 + SD2, Q3-Q2 + SD3, Q4-Q3 + SD4 on
+    h = 1/16 .. 1/256 at the given FS-CFL values, with the Newton-count time step control;
+    L1 velocity error, its rate, accepted steps and wall time of each run."""
+    import torch
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import taylor_green_problem
+    torch.cuda.set_device(0)
+    rows, t_start = [], time.perf_counter()
+    for k in args.tg_orders:
+        for cfl in args.tg_cfl:
+            prev = None
+            for inv_h in args.tg_h:
+                if time.perf_counter() - t_start > args.tg_budget:
+                    rows.append({"k": k, "fs_cfl": cfl, "inv_h": inv_h, "status": "skipped (time budget)"})
+                    continue
+                mesh, u = taylor_green_problem(inv_h, k, device="cuda:0")
+                torch.cuda.synchronize()
+                w0 = time.perf_counter()
+                steps, rejected, hist = mesh.advance(u, 0.5, fs_cfl=cfl, scheme=k, jvp_prec=args.prec, **NEWTON)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - w0
+                err = mesh.tg_velocity_error(u)
+                its = [h[2] for h in hist if h[3]]
+                paper = PAPER_TG.get((k, cfl, inv_h))
+                rows.append({"k": k, "scheme": f"SD{k}", "fs_cfl": cfl, "inv_h": inv_h, "n_unknowns": mesh.n,
+                             "l1_error": err, "rate": (math.log2(prev / err) if prev else None), "steps": steps,
+                             "rejected": rejected, "newton_its_max_mean": round(sum(its) / max(len(its), 1), 3),
+                             "wall_s": round(wall, 3),
+                             "paper": ({"l1_error": paper[0], "steps": paper[1], "time_s": paper[2]}
+                                       if paper else None)})
+                prev = err
+                del mesh, u
+    return {"metric": "2D Taylor-Green to t = 0.5, implicit SDIRK + Newton-count dt control",
+            "jvp_prec": args.prec, "newton": NEWTON, "runs": rows}
+
+
 def run_reference(args, rank):
     """The oracle (plain FP64 numpy, one thread) timed on this host: each step is one
     residual evaluation of the bench workload state."""
@@ -756,6 +815,11 @@ def main():
     ap.add_argument("--interface-run", action="store_true",
                     help="three-state interface problem, 50 steps at 10x explicit dt")
     ap.add_argument("--t-end", type=float, default=0.1)
+    ap.add_argument("--tg-table", action="store_true", help="Taylor-Green convergence table, SD2/SD3/SD4")
+    ap.add_argument("--tg-orders", type=int, nargs="+", default=[2, 3, 4])
+    ap.add_argument("--tg-cfl", type=float, nargs="+", default=[8.0, 2.0])
+    ap.add_argument("--tg-h", type=int, nargs="+", default=[16, 32, 64, 128, 256])
+    ap.add_argument("--tg-budget", type=float, default=240.0, help="seconds; later runs are skipped")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -770,6 +834,8 @@ def main():
         out = run_interface(args)
     elif args.blast_run:
         out = run_blast(args)
+    elif args.tg_table:
+        out = run_tg_table(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

@@ -184,6 +184,12 @@ lh_status lh_precond(lh_mesh* mesh, int kind, double tau, const double* r, doubl
  * u device [n]; *dt (HOST).  Synchronises. */
 lh_status lh_dt_estimate(lh_mesh* mesh, const double* u, double* dt);
 
+/* L1 velocity error of the 2D Taylor-Green vortex (Sec. 4.1): sum over elements and the
+ * 2k-point Gauss rule of alpha_q detJ_q |v_h(x_q) - v*(x_q)|_2 with the steady exact
+ * velocity v* = (sin pi x cos pi y, -cos pi x sin pi y) at the moved points x_q.  u: device
+ * state [n]; l1: HOST output.  LH_EINVAL on a 3D mesh.  Synchronises. */
+lh_status lh_tg_velocity_error(lh_mesh* mesh, const double* u, double* l1);
+
 /* Kinetic 1/2 v^T M_V v and internal 1^T M_E e energies of state u (HOST outputs). */
 lh_status lh_energies(lh_mesh* mesh, const double* u, double* kinetic, double* internal);
 
@@ -219,6 +225,8 @@ typedef struct {
   int reorth;              /* second Gram-Schmidt passes taken */
   double r0, rfinal;       /* ||R|| at the initial guess and at exit */
   double min_detj;         /* min det J at the accepted stage state */
+  int newton_its_max;      /* most Newton iterations of one stage solve (the count the
+                              Newton-count time-step control of Sec. 4 reads) */
 } lh_step_stats;
 
 void lh_newton_opts_init(lh_newton_opts* opts);
@@ -233,6 +241,29 @@ void lh_newton_opts_init(lh_newton_opts* opts);
  * On LH_ENOCONV / LH_ETANGLED / LH_ENONFINITE u and k_prev are left unchanged. */
 lh_status lh_newton_step(lh_mesh* mesh, double* u, double* k_prev, double dt,
                          const lh_newton_opts* opts, lh_step_stats* stats);
+
+/* Solve one SDIRK stage system R(k; tau, u_base) = 0 (Eq. (21)) by the Newton-GMRES of
+ * lh_newton_step, without changing any state.  u_base: device [n] stage base state (read
+ * only).  k: device [n], the initial guess on entry and the converged stage increment on
+ * exit (unchanged on failure); must not alias u_base.  tau > 0: the stage scaling (the
+ * diagonal entry of the tableau times dt).  stats as for lh_newton_step (also written on
+ * LH_ENOCONV).  Synchronises. */
+lh_status lh_stage_solve(lh_mesh* mesh, const double* u_base, double* k, double tau,
+                         const lh_newton_opts* opts, lh_step_stats* stats);
+
+/* One step of the SDIRK scheme SD<scheme> of Sec. 4: 2 = implicit midpoint (one stage,
+ * tau = dt/2; the same arithmetic as lh_newton_step), 3 = the 3-stage L-stable method of
+ * order 3 (Alexander; diagonal gamma = 0.43586652150845899...), 4 = the 3-stage A-stable
+ * method of order 4 (Crouzeix; gamma = 1/2 + cos(pi/18)/sqrt(3)).  Stage i solves
+ * R(k_i; a_ii dt, u + dt sum_{j<i} a_ij k_j) = 0 from the initial guess k_{i-1} (k_prev, or
+ * zero, for the first stage); then u <- u + dt sum_i b_i k_i.
+ *  u: device [n] in/out.  k_prev: device [n] first-stage initial guess on entry and the last
+ *  stage's k on exit, or NULL.  stats: sums over the stages of the counts, newton_its_max
+ *  the largest stage count, r0 / rfinal the largest and min_detj the smallest over the
+ *  stages.  Allocates 4 n doubles of stage storage on the first call.  Synchronises.
+ *  On any error u and k_prev are left unchanged; LH_EINVAL for a scheme other than 2-4. */
+lh_status lh_sdirk_step(lh_mesh* mesh, int scheme, double* u, double* k_prev, double dt,
+                        const lh_newton_opts* opts, lh_step_stats* stats);
 
 /* Stage residual R(k; tau, u), the same operator and kernel as lh_residual, for callers
  * that must not allocate device memory when they call the library (for example code

@@ -1,5 +1,6 @@
 // C ABI of the library (include/lh.h): mesh set-up, operator calls, mass solves and the
 // Newton-GMRES implicit midpoint step (paper Sec. 3.5 and Sec. 4.1).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -673,6 +674,7 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_counter) cudaFree(m->d_counter);
   if (m->d_fconst) cudaFree(m->d_fconst);
   if (m->d_rec) cudaFree(m->d_rec);
+  if (m->d_stage) cudaFree(m->d_stage);
   for (int a = 0; a < 3; ++a) {
     if (m->kron.At_free[a]) cudaFree(m->kron.At_free[a]);
     if (m->kron.At_fixed[a]) cudaFree(m->kron.At_fixed[a]);
@@ -872,11 +874,21 @@ lh_status lh_energies(lh_mesh* m, const double* u, double* kinetic, double* inte
   return LH_OK;
 }
 
-lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const lh_newton_opts* opts_in,
-                         lh_step_stats* stats) {
-  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_newton_step");
-  lh_newton_opts o;
-  if (opts_in) o = *opts_in; else lh_newton_opts_init(&o);
+lh_status lh_tg_velocity_error(lh_mesh* m, const double* u, double* l1) {
+  if (!m || !u || !l1) return fail(m, LH_EINVAL, "NULL argument to lh_tg_velocity_error");
+  if (m->P.dim != 2) return fail(m, LH_EINVAL, "lh_tg_velocity_error: the Taylor-Green velocity is 2D");
+  lh_status st = ensure_work(m, m->restart_alloc > 0 ? m->restart_alloc : 30);
+  if (st != LH_OK) return st;
+  double* t = m->d_work;   // NE (2k)^2 terms, fewer than the n = 4 NV + k^2 NE of the work buffer
+  LH_CK(m, launch_tg_error(m->P, m->stream, u, t));
+  LH_CK(m, launch_mdot<double>(m->stream, t, 1, 0, nullptr, tg_error_terms(m->P), 0, m->d_part, m->d_counter,
+                               m->d_scalar));
+  LH_CK(m, cudaMemcpyAsync(l1, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  return LH_OK;
+}
+
+static lh_status check_newton_opts(lh_mesh* m, const lh_newton_opts& o) {
   if (o.restart < 1 || o.restart > 64) return fail(m, LH_EINVAL, "restart must be in 1..64");
   if (o.jvp_prec != LH_FP64 && o.jvp_prec != LH_FP32 && o.jvp_prec != LH_TF32 && o.jvp_prec != LH_BF16)
     return fail(m, LH_EINVAL, "unsupported jvp_prec");
@@ -886,9 +898,16 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   if (o.forcing != 0 && o.forcing != 1) return fail(m, LH_EINVAL, "forcing must be 0 or 1");
   if (o.forcing && !(o.eta_max >= o.gmres_rtol && o.eta_max < 1.0))
     return fail(m, LH_EINVAL, "eta_max must be in [gmres_rtol, 1)");
-  if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
-  lh_status st = ensure_work(m, o.restart);
-  if (st != LH_OK) return st;
+  return ensure_work(m, o.restart);
+}
+
+// Inexact Newton-GMRES on the stage system R(k; tau, u) = 0 (Eqs. (21)-(22), Sec. 3.5) from
+// the initial guess k_init (device [n], or NULL for zero).  Fills S.  On LH_OK *k_out points
+// at the converged k inside the mesh's work buffer (overwritten by the next solve); a solve
+// that ends without convergence returns LH_ENOCONV with S filled.
+static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init, double tau,
+                              const lh_newton_opts& o, lh_step_stats& S, const double** k_out) {
+  lh_status st;
   const bool f32 = o.jvp_prec != LH_FP64;
   const int tck = o.jvp_prec == LH_TF32 ? 0 : o.jvp_prec == LH_BF16 ? 1 : -1;
   float* rec = nullptr;
@@ -896,8 +915,7 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
     if ((st = ensure_rec(m)) != LH_OK) return st;
     rec = m->d_rec;
   }
-  m->rec_valid = false;   // the record will describe this step's internal iterates
-  lh_step_stats S;
+  m->rec_valid = false;   // the record will describe this solve's internal iterates
   std::memset(&S, 0, sizeof(S));
   const long long n = m->n;
   const int mres = o.restart;
@@ -915,25 +933,24 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
   float* wf = Vf + (long long)(mres + 1) * ldf;
   float* zf = wf + ldf;
   float* uf = zf + ldf;
-  const double tau = 0.5 * dt;
 
-  if (k_prev) {
-    LH_CK(m, cudaMemcpyAsync(k, k_prev, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  if (k_init) {
+    LH_CK(m, cudaMemcpyAsync(k, k_init, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else {
     LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
   }
   double mind, nr2;
   if ((st = residual_min(m, u, k, tau, r, &mind, rec)) != LH_OK) return st;
   ++S.residual_evals;
-  if (!(mind > 0.0) && k_prev) {   // a tangled initial guess: restart from k = 0
+  if (!(mind > 0.0) && k_init) {   // a tangled initial guess: restart from k = 0
     LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
     if ((st = residual_min(m, u, k, tau, r, &mind, rec)) != LH_OK) return st;
     ++S.residual_evals;
   }
-  if (!(mind > 0.0)) return fail(m, LH_ETANGLED, "lh_newton_step: det J <= 0 at the initial guess");
+  if (!(mind > 0.0)) return fail(m, LH_ETANGLED, "Newton: det J <= 0 at the initial guess");
   if ((st = dot_host(m, r, r, n, &nr2)) != LH_OK) return st;
   double nr = std::sqrt(nr2);
-  if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite residual");
+  if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "Newton: non-finite residual");
   S.r0 = nr;
   bool conv = nr <= std::fmax(o.newton_rtol * S.r0, o.newton_atol);
   double eta = o.forcing ? o.eta_max : o.gmres_rtol;   // relative tolerance of the next solve
@@ -968,7 +985,7 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
       lam *= 0.5;
       ++S.backtracks;
     }
-    if (!accepted) return fail(m, LH_ETANGLED, "lh_newton_step: line search found no trial with det J > 0 "
+    if (!accepted) return fail(m, LH_ETANGLED, "Newton: line search found no trial with det J > 0 "
                                                "and a finite residual");
     std::swap(k, kt);
     std::swap(r, rt);
@@ -985,13 +1002,166 @@ lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const
     }
   }
   S.rfinal = nr;
+  S.newton_its_max = S.newton_its;
   if (S.min_detj == 0.0) S.min_detj = mind;
-  if (stats) *stats = S;
   if (tck >= 0 && (st = lh_tc_status(m)) != LH_OK) return st;
-  if (!conv) return fail(m, LH_ENOCONV, "lh_newton_step: Newton did not converge");
-  LH_CK(m, launch_axpby(s, dt, k, 1.0, u, n));
-  if (k_prev) LH_CK(m, cudaMemcpyAsync(k_prev, k, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  *k_out = k;
+  if (!conv) return fail(m, LH_ENOCONV, "Newton did not converge");
+  return LH_OK;
+}
+
+lh_status lh_newton_step(lh_mesh* m, double* u, double* k_prev, double dt, const lh_newton_opts* opts_in,
+                         lh_step_stats* stats) {
+  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_newton_step");
+  lh_newton_opts o;
+  if (opts_in) o = *opts_in; else lh_newton_opts_init(&o);
+  if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
+  lh_status st = check_newton_opts(m, o);
+  if (st != LH_OK) return st;
+  lh_step_stats S;
+  const double* k = nullptr;
+  st = newton_solve(m, u, k_prev, 0.5 * dt, o, S, &k);
+  if (st == LH_OK || st == LH_ENOCONV) {
+    if (stats) *stats = S;
+  }
+  if (st != LH_OK) return st;
+  cudaStream_t s = m->stream;
+  LH_CK(m, launch_axpby(s, dt, k, 1.0, u, m->n));
+  if (k_prev) LH_CK(m, cudaMemcpyAsync(k_prev, k, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, s));
   LH_CK(m, cudaStreamSynchronize(s));
+  return LH_OK;
+}
+
+lh_status lh_stage_solve(lh_mesh* m, const double* u_base, double* k, double tau, const lh_newton_opts* opts_in,
+                         lh_step_stats* stats) {
+  if (!m || !u_base || !k) return fail(m, LH_EINVAL, "NULL argument to lh_stage_solve");
+  if (k == u_base) return fail(m, LH_EINVAL, "lh_stage_solve: k must not alias u_base");
+  if (!(tau > 0.0)) return fail(m, LH_EINVAL, "tau must be > 0");
+  lh_newton_opts o;
+  if (opts_in) o = *opts_in; else lh_newton_opts_init(&o);
+  lh_status st = check_newton_opts(m, o);
+  if (st != LH_OK) return st;
+  lh_step_stats S;
+  const double* kc = nullptr;
+  st = newton_solve(m, u_base, k, tau, o, S, &kc);
+  if (st == LH_OK || st == LH_ENOCONV) {
+    if (stats) *stats = S;
+  }
+  if (st != LH_OK) return st;
+  LH_CK(m, cudaMemcpyAsync(k, kc, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  return LH_OK;
+}
+
+namespace {
+
+// Butcher tableaux of the SDIRK schemes of Sec. 4 (SD2/SD3/SD4): A lower triangular with
+// the common diagonal gamma, weights b.  SD3: Alexander's 3-stage L-stable, stiffly accurate
+// method of order 3, gamma the root in (1/6, 1/2) of g^3 - 3 g^2 + 3/2 g - 1/6 = 0.  SD4:
+// Crouzeix's 3-stage A-stable method of order 4, gamma = 1/2 + cos(pi/18)/sqrt(3).
+struct Tableau {
+  int s = 0;
+  double a[3][3] = {};
+  double b[3] = {};
+};
+
+bool sdirk_tableau(int scheme, Tableau* t) {
+  *t = Tableau();
+  if (scheme == 2) {
+    t->s = 1;
+    t->a[0][0] = 0.5;
+    t->b[0] = 1.0;
+    return true;
+  }
+  if (scheme == 3) {
+    double g = 0.45;   // Newton on the cubic; the root is simple and 0.45 lies in its basin
+    for (int it = 0; it < 50; ++it) {
+      const double f = ((g - 3.0) * g + 1.5) * g - 1.0 / 6.0;
+      const double df = (3.0 * g - 6.0) * g + 1.5;
+      const double d = f / df;
+      g -= d;
+      if (std::fabs(d) < 1e-17) break;
+    }
+    t->s = 3;
+    t->a[0][0] = t->a[1][1] = t->a[2][2] = g;
+    t->a[1][0] = 0.5 * (1.0 - g);
+    t->a[2][0] = t->b[0] = -0.25 * ((6.0 * g - 16.0) * g + 1.0);
+    t->a[2][1] = t->b[1] = 0.25 * ((6.0 * g - 20.0) * g + 5.0);
+    t->b[2] = g;
+    return true;
+  }
+  if (scheme == 4) {
+    const double pi = 3.14159265358979323846;
+    const double g = 0.5 + std::cos(pi / 18.0) / std::sqrt(3.0);
+    const double d = 1.0 / (6.0 * (2.0 * g - 1.0) * (2.0 * g - 1.0));
+    t->s = 3;
+    t->a[0][0] = t->a[1][1] = t->a[2][2] = g;
+    t->a[1][0] = 0.5 - g;
+    t->a[2][0] = 2.0 * g;
+    t->a[2][1] = 1.0 - 4.0 * g;
+    t->b[0] = t->b[2] = d;
+    t->b[1] = 1.0 - 2.0 * d;
+    return true;
+  }
+  return false;
+}
+
+void merge_stats(lh_step_stats& acc, const lh_step_stats& st, bool first) {
+  acc.newton_its += st.newton_its;
+  acc.gmres_its_total += st.gmres_its_total;
+  acc.backtracks += st.backtracks;
+  acc.residual_evals += st.residual_evals;
+  acc.jvp_evals += st.jvp_evals;
+  acc.reorth += st.reorth;
+  acc.newton_its_max = std::max(acc.newton_its_max, st.newton_its);
+  acc.r0 = first ? st.r0 : std::fmax(acc.r0, st.r0);
+  acc.rfinal = first ? st.rfinal : std::fmax(acc.rfinal, st.rfinal);
+  acc.min_detj = first ? st.min_detj : std::fmin(acc.min_detj, st.min_detj);
+}
+
+}  // namespace
+
+lh_status lh_sdirk_step(lh_mesh* m, int scheme, double* u, double* k_prev, double dt,
+                        const lh_newton_opts* opts_in, lh_step_stats* stats) {
+  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_sdirk_step");
+  Tableau T;
+  if (!sdirk_tableau(scheme, &T)) return fail(m, LH_EINVAL, "scheme must be 2, 3 or 4");
+  if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
+  lh_newton_opts o;
+  if (opts_in) o = *opts_in; else lh_newton_opts_init(&o);
+  lh_status st = check_newton_opts(m, o);
+  if (st != LH_OK) return st;
+  const long long n = m->n;
+  if (!m->d_stage && cudaMalloc(&m->d_stage, sizeof(double) * 4 * (size_t)n) != cudaSuccess)
+    return fail(m, LH_ENOMEM, "cannot allocate the SDIRK stage vectors");
+  cudaStream_t s = m->stream;
+  double* K[3] = {m->d_stage, m->d_stage + n, m->d_stage + 2 * n};
+  double* base = m->d_stage + 3 * n;
+  lh_step_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  for (int i = 0; i < T.s; ++i) {
+    // stage base state u + dt sum_{j<i} a_ij k_j; the first stage starts from u itself
+    const double* ub = u;
+    if (i > 0) {
+      LH_CK(m, cudaMemcpyAsync(base, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      for (int j = 0; j < i; ++j) LH_CK(m, launch_axpby(s, dt * T.a[i][j], K[j], 1.0, base, n));
+      ub = base;
+    }
+    const double* guess = i == 0 ? k_prev : K[i - 1];
+    lh_step_stats Si;
+    const double* kc = nullptr;
+    st = newton_solve(m, ub, guess, dt * T.a[i][i], o, Si, &kc);
+    if (st == LH_OK || st == LH_ENOCONV) merge_stats(acc, Si, i == 0);
+    if (st != LH_OK) {
+      if (st == LH_ENOCONV && stats) *stats = acc;
+      return st;
+    }
+    LH_CK(m, cudaMemcpyAsync(K[i], kc, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  for (int i = 0; i < T.s; ++i) LH_CK(m, launch_axpby(s, dt * T.b[i], K[i], 1.0, u, n));
+  if (k_prev) LH_CK(m, cudaMemcpyAsync(k_prev, K[T.s - 1], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  LH_CK(m, cudaStreamSynchronize(s));
+  if (stats) *stats = acc;
   return LH_OK;
 }
 

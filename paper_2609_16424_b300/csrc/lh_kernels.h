@@ -38,6 +38,9 @@ bool jvp_tc_supported(int dim, int k);
 long long halo_len(const ElemParams& P, int axis);
 template <class T>
 cudaError_t launch_halo(const ElemParams& P, cudaStream_t s, int face, int mode, const T* src, T* dst);
+// Taylor-Green L1 velocity error terms (2D), one per (element, quadrature point) (lh_diag.cu)
+long long tg_error_terms(const ElemParams& P);
+cudaError_t launch_tg_error(const ElemParams& P, cudaStream_t s, const double* u, double* out);
 cudaError_t launch_jvp_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                            const double* dk, double* ev, double* out, cudaEvent_t* ev2 = nullptr);
 cudaError_t launch_jvp_f32(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,

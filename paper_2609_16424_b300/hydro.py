@@ -239,6 +239,14 @@ class Mesh:
         self._check(_L.lh_dt_estimate(self._h, _ptr(u), C.byref(dt)))
         return dt.value
 
+    def tg_velocity_error(self, u):
+        """L1 velocity error of the 2D Taylor-Green vortex at state u (Sec. 4.1)."""
+        self._vec(u, "u")
+        out = C.c_double()
+        self._stream()
+        self._check(_L.lh_tg_velocity_error(self._h, _ptr(u), C.byref(out)))
+        return out.value
+
     def energies(self, u):
         self._vec(u, "u")
         ke, ie = C.c_double(), C.c_double()
@@ -258,13 +266,15 @@ class Mesh:
         self._check(_L.lh_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.PROF_KINDS)}
 
-    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, **kw):
-        """Implicit midpoint steps from t = 0 to t_end with the Newton-count time step control
-        of the paper's Sec. 4 ("Implicit time step control"): the first dt is fs_cfl times the
-        explicit estimate; after a step with <= 1 Newton iteration dt grows by 5%, with 2-3 it
-        is kept, with >= 4 the step is rejected and repeated with 0.85 dt (also after a
-        failed solve).  u is advanced in place.  Returns (steps, rejected, attempts) with
-        attempts = [(controller dt, step taken, Newton iterations or None, accepted)]."""
+    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, scheme=2, **kw):
+        """SDIRK steps (scheme 2: implicit midpoint, 3: SD3, 4: SD4) from t = 0 to t_end with
+        the Newton-count time step control of the paper's Sec. 4 ("Implicit time step
+        control"): the first dt is fs_cfl times the explicit estimate; after a step with <= 1
+        Newton iteration dt grows by 5%, with 2-3 it is kept, with >= 4 the step is rejected
+        and repeated with 0.85 dt (also after a failed solve).  A multi-stage step counts the
+        most iterations any of its stages took.  u is advanced in place.  Returns (steps,
+        rejected, attempts) with attempts = [(controller dt, step taken, Newton iterations or
+        None, accepted)]."""
         k = torch.zeros_like(u) if k is None else k
         dt = fs_cfl * self.dt_estimate(u)
         t, steps, rejected, hist = 0.0, 0, 0, []
@@ -272,8 +282,11 @@ class Mesh:
             h = min(dt, t_end - t)
             u_try, k_try = u.clone(), k.clone()
             try:
-                st = self.newton_step(u_try, k_try, h, **kw)
-                its = st["newton_its"]
+                if scheme == 2:
+                    st = self.newton_step(u_try, k_try, h, **kw)
+                else:
+                    st = self.sdirk_step(u_try, k_try, h, scheme=scheme, **kw)
+                its = st["newton_its_max"]
             except LHError:
                 its = None
             if its is None or its >= 4:
@@ -307,3 +320,36 @@ class Mesh:
             err.stats = out
             raise err
         return out
+
+    def _stats_call(self, fn, *args):
+        stats = _lib.StepStats()
+        self._stream()
+        st = fn(*args, C.byref(stats))
+        out = {f: getattr(stats, f) for f, _ in _lib.StepStats._fields_}
+        if st != _lib.LH_OK:
+            err = LHError(st, _L.lh_last_error(self._h).decode())
+            err.stats = out
+            raise err
+        return out
+
+    def stage_solve(self, u_base, k, tau, opts=None, **kw):
+        """Solve the stage system R(k; tau, u_base) = 0 (Eq. (21)) in place on k (the initial
+        guess on entry); u_base is not changed.  Returns the solve statistics as a dict;
+        raises LHError (k unchanged) on failure."""
+        self._vec(u_base, "u_base")
+        self._vec(k, "k")
+        o = opts if opts is not None else newton_opts(**kw)
+        return self._stats_call(_L.lh_stage_solve, self._h, _ptr(u_base), _ptr(k), float(tau), C.byref(o))
+
+    def sdirk_step(self, u, k_prev, dt, scheme=3, opts=None, **kw):
+        """One SDIRK step in place on u: scheme 2 (implicit midpoint), 3 (SD3, order 3,
+        L-stable) or 4 (SD4, order 4, A-stable), each stage solved by Newton-GMRES.  k_prev
+        (or None) is the first stage's initial guess and receives the last stage's k.
+        Returns the statistics summed over the stages (newton_its_max: the largest stage
+        count); raises LHError (state unchanged) on failure."""
+        self._vec(u, "u")
+        if k_prev is not None:
+            self._vec(k_prev, "k_prev")
+        o = opts if opts is not None else newton_opts(**kw)
+        return self._stats_call(_L.lh_sdirk_step, self._h, int(scheme), _ptr(u),
+                                _ptr(k_prev) if k_prev is not None else None, float(dt), C.byref(o))

@@ -1,6 +1,10 @@
 """Initial states of the test problems built on the GPU (problem set-up, not the hot path):
-the point blast (corner deposit of a given total internal energy) and the three-state
-interface problem (three regions of density, pressure and gamma), v = 0, undeformed mesh."""
+the point blast (corner deposit of a given total internal energy), the three-state
+interface problem (three regions of density, pressure and gamma), v = 0, and the 2D
+Taylor-Green vortex; undeformed mesh."""
+import math
+
+import numpy as np
 import torch
 
 
@@ -41,4 +45,32 @@ def interface_problem(nx=56, ny=24, k=3, device=None):
     u[:x0.numel()] = x0
     nl = mesh.NEd // mesh.NE
     u[2 * x0.numel():] = torch.tensor(e_el, dtype=torch.float64, device=mesh.device).repeat_interleave(nl)
+    return mesh, u
+
+
+def taylor_green_problem(n, k, device=None):
+    """2D Taylor-Green vortex (Sec. 4.1) on [0,1]^2 with n x n Q_k-Q_{k-1} elements: rho 1,
+    gamma 5/3, no artificial viscosity, the energy source on, walls on all sides;
+    v = (sin pi x cos pi y, -cos pi x sin pi y) at the H1 nodes and e = p / ((gamma - 1) rho)
+    with p = 100 + (cos 2 pi x + cos 2 pi y) / 4 at the L2 nodes (the Gauss-Legendre points of
+    each element).  Returns (mesh, u)."""
+    from .hydro import Mesh
+    gamma = 5.0 / 3.0
+    mesh = Mesh(2, (n, n), (0.0, 0.0), (1.0, 1.0), k, rho0=1.0, gamma=gamma, visc=False, tg_source=True,
+                device=device)
+    x0 = mesh.initial_nodes()
+    nv = mesh.NV
+    u = torch.zeros(mesh.n, dtype=torch.float64, device=mesh.device)
+    u[:2 * nv] = x0
+    x, y = x0[:nv], x0[nv:]
+    u[2 * nv:3 * nv] = torch.sin(math.pi * x) * torch.cos(math.pi * y)
+    u[3 * nv:4 * nv] = -torch.cos(math.pi * x) * torch.sin(math.pi * y)
+    z = (np.polynomial.legendre.leggauss(k)[0] + 1.0) / 2.0        # L2 nodes on [0, 1]
+    h = 1.0 / n
+    e_idx = np.arange(n * n)
+    ex, ey = e_idx % n, e_idx // n
+    px = (ex[:, None, None] + z[None, None, :]) * h                 # [e][j1][j0]
+    py = (ey[:, None, None] + z[None, :, None]) * h
+    p = 100.0 + (np.cos(2 * math.pi * px) + np.cos(2 * math.pi * py)) / 4.0
+    u[4 * nv:] = torch.tensor((p / (gamma - 1.0)).reshape(-1), dtype=torch.float64, device=mesh.device)
     return mesh, u

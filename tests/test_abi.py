@@ -38,7 +38,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(lh_mesh_desc), offsetof(lh_mesh_desc, rho0),
          offsetof(lh_mesh_desc, bc_mask), offsetof(lh_mesh_desc, tg_source), offsetof(lh_mesh_desc, stream));
   printf("%zu %zu\n", sizeof(lh_newton_opts), offsetof(lh_newton_opts, jvp_prec));
-  printf("%zu %zu\n", sizeof(lh_step_stats), offsetof(lh_step_stats, min_detj));
+  printf("%zu %zu %zu\n", sizeof(lh_step_stats), offsetof(lh_step_stats, min_detj),
+         offsetof(lh_step_stats, newton_its_max));
   return 0;
 }
 ''')
@@ -51,7 +52,7 @@ int main(void) {
     N = _lib.NewtonOpts
     assert [int(x) for x in out[1].split()] == [C.sizeof(N), N.jvp_prec.offset]
     S = _lib.StepStats
-    assert [int(x) for x in out[2].split()] == [C.sizeof(S), S.min_detj.offset]
+    assert [int(x) for x in out[2].split()] == [C.sizeof(S), S.min_detj.offset, S.newton_its_max.offset]
 
 
 def test_defaults_and_argument_checks_without_gpu():
