@@ -266,19 +266,21 @@ class Mesh:
         self._check(_L.lh_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.PROF_KINDS)}
 
-    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, scheme=2, **kw):
+    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, scheme=2, max_attempts=None, **kw):
         """SDIRK steps (scheme 2: implicit midpoint, 3: SD3, 4: SD4) from t = 0 to t_end with
         the Newton-count time step control of the paper's Sec. 4 ("Implicit time step
         control"): the first dt is fs_cfl times the explicit estimate; after a step with <= 1
         Newton iteration dt grows by 5%, with 2-3 it is kept, with >= 4 the step is rejected
         and repeated with 0.85 dt (also after a failed solve).  A multi-stage step counts the
-        most iterations any of its stages took.  u is advanced in place.  Returns (steps,
-        rejected, attempts) with attempts = [(controller dt, step taken, Newton iterations or
-        None, accepted)]."""
+        most iterations any of its stages took.  u is advanced in place; the loop also ends
+        after max_attempts attempts (accepted or not), if given.  Returns (steps, rejected,
+        attempts) with attempts = [(controller dt, step taken, Newton iterations or None,
+        accepted)]."""
         k = torch.zeros_like(u) if k is None else k
         dt = fs_cfl * self.dt_estimate(u)
         t, steps, rejected, hist = 0.0, 0, 0, []
-        while t < t_end - 1e-14 * max(1.0, t_end) and steps < max_steps:
+        while t < t_end - 1e-14 * max(1.0, t_end) and steps < max_steps and (
+                max_attempts is None or len(hist) < max_attempts):
             h = min(dt, t_end - t)
             u_try, k_try = u.clone(), k.clone()
             try:

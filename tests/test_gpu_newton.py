@@ -17,7 +17,7 @@ def _gpu_tg(n):
 
 def test_taylor_green_ten_steps_match_oracle():
     """Taylor-Green Q2-Q1 on 8x8, dt = 0.01, 10 implicit midpoint steps, Newton rtol 1e-10."""
-    hyd, u0 = problems.taylor_green(8, 2)
+    hyd, u0 = problems.taylor_green(8, 2, p0=100.0)
     u, kp = u0.copy(), None
     for _ in range(10):
         u, kp, res = solver.implicit_midpoint_step(hyd, u, 0.01, kp, rtol=1e-11, atol=1e-12)

@@ -35,7 +35,7 @@ def test_stage_solve_matches_oracle_newton():
 @pytest.mark.parametrize("scheme", [3, 4])
 def test_sdirk_steps_match_oracle(scheme):
     """Two SD3 / SD4 steps of Taylor-Green Q2-Q1 on 3 x 3 elements, dt = 0.004."""
-    hyd, u0 = problems.taylor_green(3, 2)
+    hyd, u0 = problems.taylor_green(3, 2, p0=100.0)
     u, kp = u0.copy(), None
     for _ in range(2):
         u, kp, res = solver.sdirk_step(hyd, u, 0.004, scheme, kp, rtol=1e-12, atol=1e-11)
@@ -67,7 +67,7 @@ def test_sdirk_temporal_order(scheme, lo, hi):
     """Q1-Q0 Taylor-Green on 2 x 2 elements to t = 0.004: halving dt divides the difference
     to a 32-step solution by about 2^p."""
     gm = _gpu_tg(2, 1)
-    hyd, u0 = problems.taylor_green(2, 1)
+    hyd, u0 = problems.taylor_green(2, 1, p0=100.0)
 
     def run(nsteps):
         ug = torch.tensor(u0, device="cuda")
@@ -128,8 +128,8 @@ def test_taylor_green_state_and_l1_error(k):
     """The GPU Taylor-Green initial state equals the oracle's, and the L1 velocity error of
     Sec. 4.1 agrees with the oracle's on the initial and on a moved mesh."""
     from paper_2609_16424_b300.states import taylor_green_problem
-    hyd, u0 = problems.taylor_green(3, k)
-    gm, ug = taylor_green_problem(3, k)
+    hyd, u0 = problems.taylor_green(3, k, p0=1.0)
+    gm, ug = taylor_green_problem(3, k, p0=1.0)
     assert np.allclose(ug.cpu().numpy(), u0, rtol=1e-14, atol=1e-12)
     e_ref = problems.l1_velocity_error(hyd, u0)
     assert abs(gm.tg_velocity_error(ug) - e_ref) <= 1e-12 * max(e_ref, 1e-3)

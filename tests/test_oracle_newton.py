@@ -13,7 +13,7 @@ def _energy(hyd, u):
 
 
 def test_sparse_jacobian_equals_dense():
-    hyd, u = problems.taylor_green(3, 2)
+    hyd, u = problems.taylor_green(3, 2, p0=100.0)
     k = lh_synth.normal_vector(u.size, 0, 0.1)
     Jd = hyd.jacobian(u, k, 0.01)
     Js = jacobian_sparse(hyd, u, k, 0.01).toarray()
@@ -57,7 +57,7 @@ def test_midpoint_is_second_order_in_time():
     """Implicit midpoint (SD2, Sec. 4.1) is second order: halving dt divides the
     difference to a fine-step solution by about 4."""
     def run(nsteps):
-        hyd, u = problems.taylor_green(2, 2)
+        hyd, u = problems.taylor_green(2, 2, p0=100.0)
         kp = None
         for _ in range(nsteps):
             u, kp, _ = solver.implicit_midpoint_step(hyd, u, 0.01 / nsteps, kp, rtol=1e-13)
@@ -92,7 +92,7 @@ def test_taylor_green_spatial_rate():
     under refinement (Table 1 reports rates 1.9-2.5 for Q2Q1 + SD2)."""
     errs = []
     for n in (4, 8):
-        hyd, u = problems.taylor_green(n, 2)
+        hyd, u = problems.taylor_green(n, 2, p0=100.0)
         kp = None
         for _ in range(8):
             u, kp, _ = solver.implicit_midpoint_step(hyd, u, 0.025, kp)

@@ -91,7 +91,7 @@ def test_stage_loop_matches_coupled_system(scheme):
 
 
 def test_sd2_step_is_the_implicit_midpoint_step():
-    hyd, u = problems.taylor_green(2, 2)
+    hyd, u = problems.taylor_green(2, 2, p0=100.0)
     ua, ka, _ = solver.implicit_midpoint_step(hyd, u, 0.003)
     ub, kb, res = solver.sdirk_step(hyd, u, 0.003, 2)
     assert len(res) == 1
@@ -103,7 +103,7 @@ def test_sdirk_temporal_order_on_taylor_green(scheme, lo, hi):
     """Q1-Q0 Taylor-Green on 2 x 2 elements to t = 0.004: halving dt divides the difference
     to a 32-step solution by about 2^p (p = 2, 3, 4)."""
     def run(nsteps):
-        hyd, u = problems.taylor_green(2, 1)
+        hyd, u = problems.taylor_green(2, 1, p0=100.0)
         kp = None
         for _ in range(nsteps):
             u, kp, _ = solver.sdirk_step(hyd, u, 0.004 / nsteps, scheme, kp, rtol=1e-13, atol=1e-13)
