@@ -748,7 +748,8 @@ def run_tg_table(args):
                 torch.cuda.synchronize()
                 w0 = time.perf_counter()
                 steps, rejected, hist = mesh.advance(u, 0.5, fs_cfl=cfl, scheme=k, max_attempts=args.tg_attempts,
-                                                     jvp_prec=args.prec, **TG_NEWTON)
+                                                     grow=not args.tg_fixed_dt, jvp_prec=args.prec,
+                                                     **dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol))
                 done = sum(h[1] for h in hist if h[3]) >= 0.5 - 1e-12
                 torch.cuda.synchronize()
                 wall = time.perf_counter() - w0
@@ -756,6 +757,7 @@ def run_tg_table(args):
                 its = [h[2] for h in hist if h[3]]
                 paper = PAPER_TG.get((k, cfl, inv_h))
                 rows.append({"k": k, "scheme": f"SD{k}", "fs_cfl": cfl, "inv_h": inv_h, "n_unknowns": mesh.n,
+                             "dt_first": hist[0][1] if hist else None,
                              "status": "ok" if done else f"stopped after {len(hist)} attempts",
                              "l1_error": err, "rate": (math.log2(prev / err) if prev else None), "steps": steps,
                              "rejected": rejected, "newton_its_max_mean": round(sum(its) / max(len(its), 1), 3),
@@ -766,7 +768,8 @@ def run_tg_table(args):
                 prev = err if done else None
                 del mesh, u
     return {"metric": "2D Taylor-Green (p0 = 1) to t = 0.5, implicit SDIRK + Newton-count dt control",
-            "jvp_prec": args.prec, "newton": TG_NEWTON, "runs": rows}
+            "dt_growth": not args.tg_fixed_dt, "jvp_prec": args.prec,
+            "newton": dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol), "runs": rows}
 
 
 def run_reference(args, rank):
@@ -832,6 +835,8 @@ def main():
     ap.add_argument("--tg-h", type=int, nargs="+", default=[16, 32, 64, 128, 256])
     ap.add_argument("--tg-budget", type=float, default=240.0, help="seconds; later runs are skipped")
     ap.add_argument("--tg-attempts", type=int, default=600, help="step attempts per run at most")
+    ap.add_argument("--tg-fixed-dt", action="store_true", help="never enlarge dt (rejections still shrink it)")
+    ap.add_argument("--tg-newton-rtol", type=float, default=NEWTON["newton_rtol"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

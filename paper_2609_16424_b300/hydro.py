@@ -266,14 +266,16 @@ class Mesh:
         self._check(_L.lh_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.PROF_KINDS)}
 
-    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, scheme=2, max_attempts=None, **kw):
+    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, scheme=2, max_attempts=None, grow=True,
+                **kw):
         """SDIRK steps (scheme 2: implicit midpoint, 3: SD3, 4: SD4) from t = 0 to t_end with
         the Newton-count time step control of the paper's Sec. 4 ("Implicit time step
         control"): the first dt is fs_cfl times the explicit estimate; after a step with <= 1
         Newton iteration dt grows by 5%, with 2-3 it is kept, with >= 4 the step is rejected
         and repeated with 0.85 dt (also after a failed solve).  A multi-stage step counts the
-        most iterations any of its stages took.  u is advanced in place; the loop also ends
-        after max_attempts attempts (accepted or not), if given.  Returns (steps, rejected,
+        most iterations any of its stages took.  grow=False never enlarges dt (steps of
+        FS-CFL times the first estimate, reduced only by rejections).  u is advanced in place;
+        the loop also ends after max_attempts attempts (accepted or not), if given.  Returns (steps, rejected,
         attempts) with attempts = [(controller dt, step taken, Newton iterations or None,
         accepted)]."""
         k = torch.zeros_like(u) if k is None else k
@@ -301,7 +303,7 @@ class Mesh:
             k.copy_(k_try)
             t += h
             steps += 1
-            if its <= 1:
+            if its <= 1 and grow:
                 dt = 1.05 * dt
         return steps, rejected, hist
 
