@@ -749,7 +749,8 @@ def run_tg_table(args):
                 w0 = time.perf_counter()
                 steps, rejected, hist = mesh.advance(u, 0.5, fs_cfl=cfl, scheme=k, max_attempts=args.tg_attempts,
                                                      grow=not args.tg_fixed_dt, jvp_prec=args.prec,
-                                                     **dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol))
+                                                     **dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol,
+                                                            scaled_norm=int(args.tg_scaled_norm)))
                 done = sum(h[1] for h in hist if h[3]) >= 0.5 - 1e-12
                 torch.cuda.synchronize()
                 wall = time.perf_counter() - w0
@@ -769,7 +770,8 @@ def run_tg_table(args):
                 del mesh, u
     return {"metric": "2D Taylor-Green (p0 = 1) to t = 0.5, implicit SDIRK + Newton-count dt control",
             "dt_growth": not args.tg_fixed_dt, "jvp_prec": args.prec,
-            "newton": dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol), "runs": rows}
+            "newton": dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol, scaled_norm=int(args.tg_scaled_norm)),
+            "runs": rows}
 
 
 def run_reference(args, rank):
@@ -837,6 +839,7 @@ def main():
     ap.add_argument("--tg-attempts", type=int, default=600, help="step attempts per run at most")
     ap.add_argument("--tg-fixed-dt", action="store_true", help="never enlarge dt (rejections still shrink it)")
     ap.add_argument("--tg-newton-rtol", type=float, default=NEWTON["newton_rtol"])
+    ap.add_argument("--tg-scaled-norm", action="store_true", help="row-weighted Newton/GMRES norm")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -214,6 +214,12 @@ typedef struct {
                               eta_{k-1}^2 when that exceeds 0.1 and >= 0.5 target / |R_k|,
                               clamped to [gmres_rtol, eta_max] */
   double eta_max;          /* largest forcing term; default 0.1 */
+  int scaled_norm;         /* 0: the Newton test and GMRES use ||R||_2 (default); 1: both use
+                              ||W R||_2 with W = 1 on x rows and fixed v rows, 1/(M_V)_ii on
+                              free v rows and (M_E^-1)_ii on e rows (GMRES then solves the
+                              row-scaled system W J dk = -W R), so the v and e rows are not
+                              weighted by mass factors that shrink with the mesh size; stats
+                              r0 / rfinal are then in that norm */
 } lh_newton_opts;
 
 typedef struct {

@@ -258,6 +258,7 @@ struct KrylovOp {
   const double* k;
   double tau;
   T* z;               // scratch [n]
+  const double* wsc = nullptr;   // row weights W of the scaled norm: the operator is W J P^-1
 
   lh_status apply(const T* x, T* y) {
     LH_CK(m, (launch_prec<T, T>(pk, m->stream, m->P, m->kron, m->d_diagMv, m->d_invMe, x, z, tau)));
@@ -266,6 +267,7 @@ struct KrylovOp {
     } else {
       LH_CK(m, jvp_f32(z, y));
     }
+    if (wsc) LH_CK(m, launch_row_mul<T>(m->stream, wsc, y, y, m->n));
     return LH_OK;
   }
   cudaError_t jvp_f32(const float* x, float* y) {
@@ -283,6 +285,7 @@ struct KrylovOp {
       LH_CK(m, (launch_scale<double, float>(m->stream, 1.0, d, 0.0, nullptr, z, m->n)));
       LH_CK(m, jvp_f32(z, y));
     }
+    if (wsc) LH_CK(m, launch_row_mul<T>(m->stream, wsc, y, y, m->n));
     return LH_OK;
   }
 };
@@ -526,6 +529,7 @@ void lh_newton_opts_init(lh_newton_opts* o) {
   o->precond = 1;
   o->forcing = 0;
   o->eta_max = 0.1;
+  o->scaled_norm = 0;
 }
 
 lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
@@ -675,6 +679,7 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_fconst) cudaFree(m->d_fconst);
   if (m->d_rec) cudaFree(m->d_rec);
   if (m->d_stage) cudaFree(m->d_stage);
+  if (m->d_wscale) cudaFree(m->d_wscale);
   for (int a = 0; a < 3; ++a) {
     if (m->kron.At_free[a]) cudaFree(m->kron.At_free[a]);
     if (m->kron.At_fixed[a]) cudaFree(m->kron.At_fixed[a]);
@@ -898,6 +903,7 @@ static lh_status check_newton_opts(lh_mesh* m, const lh_newton_opts& o) {
   if (o.forcing != 0 && o.forcing != 1) return fail(m, LH_EINVAL, "forcing must be 0 or 1");
   if (o.forcing && !(o.eta_max >= o.gmres_rtol && o.eta_max < 1.0))
     return fail(m, LH_EINVAL, "eta_max must be in [gmres_rtol, 1)");
+  if (o.scaled_norm != 0 && o.scaled_norm != 1) return fail(m, LH_EINVAL, "scaled_norm must be 0 or 1");
   return ensure_work(m, o.restart);
 }
 
@@ -928,11 +934,28 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
   double* wd = zd + n;                        // double scratch
   double* kt = wd + n;                        // trial iterate
   double* rt = kt + n;                        // residual at the trial
+  double* rs = rt + n;                        // row-weighted residual (scaled_norm)
   const long long ldf = m->ldf;
   float* Vf = m->d_fwork;                     // (mres + 1) x ldf FP32 Krylov basis
   float* wf = Vf + (long long)(mres + 1) * ldf;
   float* zf = wf + ldf;
   float* uf = zf + ldf;
+
+  const double* wsc = nullptr;
+  if (o.scaled_norm) {
+    if (!m->d_wscale) {
+      if (cudaMalloc(&m->d_wscale, sizeof(double) * n) != cudaSuccess)
+        return fail(m, LH_ENOMEM, "cannot allocate the residual row weights");
+      LH_CK(m, launch_row_weights(m->P, s, m->d_diagMv, m->d_invMe, m->d_wscale));
+    }
+    wsc = m->d_wscale;
+  }
+  // squared norm of the stopping test: ||x||_2^2, or ||W x||_2^2 with scaled_norm (W x left in rs)
+  auto norm2 = [&](const double* x, double* out) -> lh_status {
+    if (!wsc) return dot_host(m, x, x, n, out);
+    LH_CK(m, launch_row_mul<double>(s, wsc, x, rs, n));
+    return dot_host(m, rs, rs, n, out);
+  };
 
   if (k_init) {
     LH_CK(m, cudaMemcpyAsync(k, k_init, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -948,7 +971,7 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     ++S.residual_evals;
   }
   if (!(mind > 0.0)) return fail(m, LH_ETANGLED, "Newton: det J <= 0 at the initial guess");
-  if ((st = dot_host(m, r, r, n, &nr2)) != LH_OK) return st;
+  if ((st = norm2(r, &nr2)) != LH_OK) return st;
   double nr = std::sqrt(nr2);
   if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "Newton: non-finite residual");
   S.r0 = nr;
@@ -959,12 +982,19 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     // ---- linear solve J dk = -r (Eq. (22)) at the current iterate k
     lh_newton_opts oi = o;
     oi.gmres_rtol = eta;
+    const double* rhs = r;   // with scaled_norm GMRES solves W J dk = -W r
+    if (wsc) {
+      LH_CK(m, launch_row_mul<double>(s, wsc, r, rs, n));
+      rhs = rs;
+    }
     if (f32) {
       KrylovOp<float> op{m, o.precond, tck, u, k, tau, zf};
-      if ((st = gmres<float>(m, oi, op, r, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return st;
+      op.wsc = wsc;
+      if ((st = gmres<float>(m, oi, op, rhs, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return st;
     } else {
       KrylovOp<double> op{m, o.precond, -1, u, k, tau, zd};
-      if ((st = gmres<double>(m, oi, op, r, nr, dk, V, wd, wd, zd, wd, S)) != LH_OK) return st;
+      op.wsc = wsc;
+      if ((st = gmres<double>(m, oi, op, rhs, nr, dk, V, wd, wd, zd, wd, S)) != LH_OK) return st;
     }
     const double nr_prev = nr;
     // ---- backtracking line search on det J > 0 (Sec. 3.5)
@@ -976,7 +1006,7 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
       if ((st = residual_min(m, u, kt, tau, rt, &mind, rec)) != LH_OK) return st;
       ++S.residual_evals;
       if (mind > 0.0) {   // reject tangled trials (Sec. 3.5) and, as well, non-finite ones
-        if ((st = dot_host(m, rt, rt, n, &nr2)) != LH_OK) return st;
+        if ((st = norm2(rt, &nr2)) != LH_OK) return st;
         if (std::isfinite(nr2)) {
           accepted = true;
           break;

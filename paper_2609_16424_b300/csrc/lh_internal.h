@@ -85,6 +85,7 @@ struct lh_mesh {
   float* d_fconst = nullptr;       // [3 NE] float rho0 detJ0, gamma - 1, gamma (gamma - 1)
   float* d_rec = nullptr;          // linearisation record [NE][rec_len][NQ] (lazily allocated)
   double* d_stage = nullptr;       // SDIRK stage increments k_1..k_3 and stage base state [4 n] (lazily)
+  double* d_wscale = nullptr;      // row weights of the scaled Newton norm [n] (lazily)
   const double* rec_u = nullptr;   // arguments of the last lh_linearize (for the LH_FP32_LIN check)
   const double* rec_k = nullptr;
   double rec_tau = 0.0;

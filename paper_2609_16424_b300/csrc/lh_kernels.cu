@@ -1194,6 +1194,34 @@ cudaError_t launch_mass_h1(const ElemParams& P, cudaStream_t s, const double* f,
 cudaError_t launch_mass_l2(const ElemParams& P, cudaStream_t s, const double* g, double* out) {
   LH_DISPATCH(P, mass_l2(P, s, g, out))
 }
+template <int DIM>
+__global__ void k_row_weights(ElemParams P, const double* __restrict__ diagMv, const double* __restrict__ invMe,
+                              double* __restrict__ w, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long nx = (long long)DIM * P.NV;
+  double v = 1.0;
+  if (i >= 2 * nx) {
+    v = invMe[i - 2 * nx];
+  } else if (i >= nx) {
+    const long long j = i - nx;
+    const int comp = (int)(j / P.NV);
+    const long long nd = j % P.NV;
+    if (!fixed_node<DIM>(P, nd, comp)) v = 1.0 / diagMv[nd];
+  }
+  w[i] = v;
+}
+
+cudaError_t launch_row_weights(const ElemParams& P, cudaStream_t s, const double* diagMv, const double* invMe,
+                               double* w) {
+  const long long n = 2LL * P.dim * P.NV + P.NEd;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  count_launches(1);
+  if (P.dim == 2) k_row_weights<2><<<g, 256, 0, s>>>(P, diagMv, invMe, w, n);
+  else k_row_weights<3><<<g, 256, 0, s>>>(P, diagMv, invMe, w, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dt_estimate(const ElemParams& P, cudaStream_t s, const double* u, double* bmin) {
   LH_DISPATCH(P, dt_estimate(P, s, u, bmin))
 }

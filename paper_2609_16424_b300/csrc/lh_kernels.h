@@ -88,6 +88,13 @@ template <class TX, class TY>
 cudaError_t launch_scale(cudaStream_t s, double a, const TX* x, double b, const float* z, TY* y, long long n);
 cudaError_t launch_axpby(cudaStream_t s, double a, const double* x, double b, double* y, long long n);
 cudaError_t launch_scale_copy(cudaStream_t s, const double* x, const double* scale_dev, double* y, long long n);
+// y = w * x elementwise (x may alias y)
+template <class T>
+cudaError_t launch_row_mul(cudaStream_t s, const double* w, const T* x, T* y, long long n);
+// row weights of the scaled residual norm: 1 on x rows and fixed v rows, 1 / (M_V)_ii on
+// free v rows, (M_E^-1)_ii on e rows
+cudaError_t launch_row_weights(const ElemParams& P, cudaStream_t s, const double* diagMv, const double* invMe,
+                               double* w);
 cudaError_t launch_to_f32(cudaStream_t s, const double* x, float* y, long long n);
 cudaError_t launch_to_f64(cudaStream_t s, const float* x, double* y, long long n);
 // block upper-triangular preconditioner [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1] with

@@ -392,6 +392,24 @@ cudaError_t launch_axpby(cudaStream_t s, double a, const double* x, double b, do
 }
 
 // y = x * (1 / scale_dev[0])
+// y = w * x elementwise (x may alias y)
+template <class T>
+__global__ void k_row_mul(const double* __restrict__ w, const T* x, T* y, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = T((double)x[i] * w[i]);
+}
+
+template <class T>
+cudaError_t launch_row_mul(cudaStream_t s, const double* w, const T* x, T* y, long long n) {
+  if (n > 0) {
+    k_row_mul<T><<<nblk(n, 256), 256, 0, s>>>(w, x, y, n);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_row_mul<double>(cudaStream_t, const double*, const double*, double*, long long);
+template cudaError_t launch_row_mul<float>(cudaStream_t, const double*, const float*, float*, long long);
+
 __global__ void k_scale_copy(const double* __restrict__ x, const double* __restrict__ sc, double* __restrict__ y,
                              long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;

@@ -20,11 +20,15 @@ def _ptr(t):
 def newton_opts(**kw):
     """lh_newton_opts with the library defaults, overridden by keyword arguments
     (newton_rtol, newton_atol, gmres_rtol, newton_maxit, gmres_maxit, restart,
-    max_halvings, jvp_prec in {'fp64', 'fp32', 'tf32', 'bf16'}, precond in {'jacobi', 'kron'});
+    max_halvings, jvp_prec in {'fp64', 'fp32', 'tf32', 'bf16'}, precond in {'jacobi', 'kron'},
+    forcing, eta_max, scaled_norm);
     'tf32' and 'bf16' run the element contractions of J.w on the tensor cores."""
     o = _lib.NewtonOpts()
     _L.lh_newton_opts_init(C.byref(o))
+    fields = {f for f, _ in _lib.NewtonOpts._fields_}
     for key, val in kw.items():
+        if key not in fields:
+            raise TypeError(f"unknown Newton option {key!r}")
         if key == "jvp_prec":
             val = {"fp64": _lib.LH_FP64, "fp32": _lib.LH_FP32, "tf32": _lib.LH_TF32,
                    "bf16": _lib.LH_BF16}.get(val, val)

@@ -136,3 +136,31 @@ def test_taylor_green_state_and_l1_error(k):
     u1, _, _ = solver.implicit_midpoint_step(hyd, u0, 0.01, None, rtol=1e-12, atol=1e-11)
     e1 = problems.l1_velocity_error(hyd, u1)
     assert abs(gm.tg_velocity_error(torch.tensor(u1, device="cuda")) - e1) <= 1e-12 * max(e1, 1e-3)
+
+
+def test_scaled_norm_reaches_the_root_and_tightens_the_v_rows():
+    """scaled_norm = 1 (Newton test and GMRES on the row-weighted residual): the stage solve
+    reaches the same FP64 root, and at the loose relative tolerance 1e-5 its v and e rows are
+    closer to the root than with the plain l2 norm, whose x rows carry no mass factor."""
+    from paper_2609_16424_b300.states import taylor_green_problem
+    gm, u = taylor_green_problem(16, 3, p0=1.0)
+    nx = 2 * gm.NV
+    tau = 0.004
+    ref = torch.zeros_like(u)
+    gm.stage_solve(u, ref, tau, newton_rtol=1e-11, gmres_rtol=1e-12, gmres_maxit=600, restart=60, jvp_prec="fp64")
+    tight = torch.zeros_like(u)
+    st = gm.stage_solve(u, tight, tau, newton_rtol=1e-11, gmres_rtol=1e-12, gmres_maxit=600, restart=60,
+                        jvp_prec="fp64", scaled_norm=1)
+    assert st["rfinal"] <= 1e-11 * st["r0"]
+
+    def rel(a, sl):
+        return float((a[sl] - ref[sl]).norm() / ref[sl].norm())
+    sv, se = slice(nx, 2 * nx), slice(2 * nx, None)
+    assert rel(tight, sv) <= 1e-8 and rel(tight, se) <= 1e-8
+    errs = {}
+    for scaled in (0, 1):
+        kk = torch.zeros_like(u)
+        gm.stage_solve(u, kk, tau, newton_rtol=1e-5, gmres_rtol=1e-6, gmres_maxit=200, restart=30,
+                       jvp_prec="fp32", scaled_norm=scaled)
+        errs[scaled] = (rel(kk, sv), rel(kk, se))
+    assert errs[1][0] < errs[0][0] and errs[1][0] <= 1e-4, errs
