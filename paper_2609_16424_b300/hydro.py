@@ -278,10 +278,10 @@ class Mesh:
         Newton iteration dt grows by 5%, with 2-3 it is kept, with >= 4 the step is rejected
         and repeated with 0.85 dt (also after a failed solve).  A multi-stage step counts the
         most iterations any of its stages took.  grow=False never enlarges dt (steps of
-        FS-CFL times the first estimate, reduced only by rejections).  u is advanced in place;
-        the loop also ends after max_attempts attempts (accepted or not), if given.  Returns (steps, rejected,
-        attempts) with attempts = [(controller dt, step taken, Newton iterations or None,
-        accepted)]."""
+        FS-CFL times the first estimate, reduced only by rejections).  u is advanced in
+        place; the loop also ends after max_attempts attempts (accepted or not), if given.
+        Returns (steps, rejected, attempts) with attempts = [(controller dt, step taken,
+        Newton iterations or None, accepted)]."""
         k = torch.zeros_like(u) if k is None else k
         dt = fs_cfl * self.dt_estimate(u)
         t, steps, rejected, hist = 0.0, 0, 0, []
