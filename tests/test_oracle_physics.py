@@ -188,3 +188,13 @@ def test_jacobian_structure_and_fd():
     a = J @ dk
     b = hyd.jvp_fd(u, k, tau, dk, 1e-6)
     assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(a)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_taylor_green_l1_error_of_the_interpolant(k):
+    """The L1 velocity error (Sec. 4.1 table) of the nodal Q_k interpolant of the exact
+    Taylor-Green velocity falls as h^(k+1); the pressure level p0 does not enter it."""
+    errs = [problems.l1_velocity_error(*problems.taylor_green(n, k)) for n in (4, 8)]
+    assert abs(np.log2(errs[0] / errs[1]) - (k + 1)) < 0.1, errs
+    hyd, u = problems.taylor_green(4, k, p0=100.0)
+    assert problems.l1_velocity_error(hyd, u) == errs[0]
