@@ -187,3 +187,12 @@ def sdirk_step(hyd, u, dt, scheme, k_prev=None, **kw):
         return k
     unew, ks = sdirk_stages(solve, u, dt, A, b, k_prev)
     return unew, ks[-1], results
+
+
+def velocity_block_diagonal(hyd, u, k, tau):
+    """Diagonal of the velocity block dR_v/dk_v = M_V + tau dF.1/dv of the stage Jacobian
+    (the block the paper's Eq. (23) preconditions; identity on fixed rows), [d * NV], read
+    off the complex-step sparse Jacobian."""
+    from .hydro import jacobian_sparse
+    n1 = hyd.m.d * hyd.m.NV
+    return jacobian_sparse(hyd, u, k, tau).diagonal()[n1:2 * n1].copy()

@@ -99,3 +99,29 @@ def test_taylor_green_spatial_rate():
         errs.append(problems.l1_velocity_error(hyd, u))
     rate = np.log2(errs[0] / errs[1])
     assert rate > 1.9, errs
+
+
+def test_velocity_block_diagonal():
+    """diag(dR_v/dk_v) equals central differences of the residual, one velocity unknown at
+    a time; at tau = 0 it is the diagonal of M_V (1 on the fixed rows)."""
+    m = Mesh((2, 2), (0.0, 0.0), (1.0, 1.0), 2)
+    hyd = Hydro(m, Params(m, gamma=1.4, visc=True))
+    u = problems.perturbed_state(hyd, lh_synth.perturbed_draws((2, 2), 2, 4), vscale=3.0)
+    k = lh_synth.normal_vector(u.size, 1, 0.5)
+    tau = 0.01
+    d = solver.velocity_block_diagonal(hyd, u, k, tau)
+    n1 = m.d * m.NV
+    h = 1e-6
+    fd = np.empty(n1)
+    for i in range(n1):
+        e = np.zeros(u.size)
+        e[n1 + i] = h
+        fd[i] = (hyd.residual(u, k + e, tau)[n1 + i] - hyd.residual(u, k - e, tau)[n1 + i]) / (2 * h)
+    assert np.allclose(d, fd, rtol=1e-6, atol=1e-9 * np.abs(d).max())
+    d0 = solver.velocity_block_diagonal(hyd, u, k, 0.0)
+    mv = np.tile(hyd.mass_v_sparse().diagonal(), m.d)
+    free = ~hyd.fixed.ravel()
+    assert np.allclose(d0[free], mv[free], rtol=1e-13)
+    assert np.all(d0[~free] == 1.0) and np.all(d[~free] == 1.0)
+    # the viscous term changes the free rows at tau > 0
+    assert np.abs(d - d0)[free].max() > 1e-6 * np.abs(d0).max()
