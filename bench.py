@@ -774,6 +774,48 @@ def run_tg_table(args):
             "runs": rows}
 
 
+def run_precond_compare(args):
+    """Velocity-block preconditioners of the Newton-GMRES step (FP32 J.w, Newton rtol 1e-5,
+    GMRES 1e-4): the exact mass inverse (kron, the benchmark's), the Jacobi of M_V alone
+    (jacobi) and the Jacobi of the paper's block M_V + tau dF/dv (jvv_diag, Eq. (23)); median
+    of 5 steps from the same state, on the point blast at the benchmark dt and at 4x it and
+    on a Taylor-Green Q3 state at FS-CFL 8."""
+    import torch
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import blast_state, taylor_green_problem
+    torch.cuda.set_device(0)
+    rows = []
+
+    def probe(name, m, u, dt, kk, reps=5):
+        for pc in ("kron", "jvv_diag", "jacobi"):
+            ts, st = [], None
+            for _ in range(reps):
+                ug, kg = u.clone(), kk.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st = m.newton_step(ug, kg, dt, jvp_prec="fp32", precond=pc, **NEWTON)
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e3)
+            rows.append({"case": name, "precond": pc, "ms": round(statistics.median(ts), 3),
+                         "newton": st["newton_its"], "gmres": st["gmres_its_total"]})
+
+    W = WORKLOAD
+    m = lh.Mesh(3, W["n"], (0,) * 3, (1,) * 3, W["k"], gamma=W["gamma"], device="cuda:0")
+    u = blast_state(m, W["energy"])
+    kk = torch.zeros_like(u)
+    dt = W["cfl"] * m.dt_estimate(u)
+    for _ in range(W["develop_steps"]):
+        m.newton_step(u, kk, dt, jvp_prec="fp32", **NEWTON)
+    probe("blast3d 24^3 Q2-Q1, benchmark dt", m, u, dt, kk)
+    probe("blast3d 24^3 Q2-Q1, 4x the benchmark dt", m, u, 4 * dt, kk)
+    m2, u2 = taylor_green_problem(64, 3, device="cuda:0")
+    k2 = torch.zeros_like(u2)
+    dt2 = 8.0 * m2.dt_estimate(u2)
+    m2.sdirk_step(u2, k2, dt2, scheme=3, jvp_prec="fp32", **NEWTON)
+    probe("Taylor-Green 64^2 Q3-Q2, FS-CFL 8 (implicit midpoint step)", m2, u2, dt2, k2)
+    return {"metric": "implicit step time by velocity-block preconditioner", "newton": NEWTON, "runs": rows}
+
+
 def run_reference(args, rank):
     """The oracle (plain FP64 numpy, one thread) timed on this host: each step is one
     residual evaluation of the bench workload state."""
@@ -831,6 +873,7 @@ def main():
     ap.add_argument("--interface-run", action="store_true",
                     help="three-state interface problem, 50 steps at 10x explicit dt")
     ap.add_argument("--t-end", type=float, default=0.1)
+    ap.add_argument("--precond-compare", action="store_true", help="velocity-block preconditioners")
     ap.add_argument("--tg-table", action="store_true", help="Taylor-Green convergence table, SD2/SD3/SD4")
     ap.add_argument("--tg-orders", type=int, nargs="+", default=[2, 3, 4])
     ap.add_argument("--tg-cfl", type=float, nargs="+", default=[8.0, 2.0])
@@ -856,6 +899,8 @@ def main():
         out = run_blast(args)
     elif args.tg_table:
         out = run_tg_table(args)
+    elif args.precond_compare:
+        out = run_precond_compare(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

@@ -152,6 +152,13 @@ lh_status lh_tc_status(lh_mesh* mesh);
  * and invalidates it on return.  Asynchronous; allocates the record on first use. */
 lh_status lh_linearize(lh_mesh* mesh, const double* u, const double* k, double tau);
 
+/* Diagonal of the velocity block dR_v/dk_v = M_V + tau dF.1/dv of the stage Jacobian at
+ * (u, k, tau) (the block the paper's Eq. (23) preconditions): 1 on fixed rows, diag(M_V) plus
+ * tau times the viscous part (from the FP32 linearisation record, which this call writes as
+ * lh_linearize does) on free rows.  u, k: device [n]; out: device double [dim * NV], the
+ * velocity rows in the layout of the state.  Asynchronous. */
+lh_status lh_jvv_diagonal(lh_mesh* mesh, const double* u, const double* k, double tau, double* out);
+
 /* Transpose action out = (dR/dk)^T y (paper Sec. 3.1: transpose actions share the
  * gather-apply-scatter structure).  LH_FP64: y, out device [n] double, the point kernel's
  * hand-written reverse mode.  LH_FP32_LIN: y, out float, the transpose of the linearised
@@ -206,7 +213,10 @@ typedef struct {
                               record written at every Newton iterate */
   int precond;             /* velocity block of the preconditioner: 0 = diagonal of M_V,
                               1 = exact M_V inverse as a Kronecker product of 1D inverses
-                              (exact for uniform rho0; rho0-scaled otherwise); default 1 */
+                              (exact for uniform rho0; rho0-scaled otherwise); 2 = inverse of
+                              the diagonal of the paper's velocity block M_V + tau dF/dv
+                              (Eq. (23)), recomputed from the linearisation record at every
+                              Newton iterate (needs jvp_prec other than LH_FP64); default 1 */
   int forcing;             /* 0: every linear solve to gmres_rtol (default); 1: adaptive
                               forcing terms (Eisenstat and Walker 1996, choice 2 with gamma 0.9,
                               alpha 2, and the safeguard against oversolving the last step):

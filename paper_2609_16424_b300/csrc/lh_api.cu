@@ -249,6 +249,10 @@ lh_status dot_host(lh_mesh* m, const double* a, const double* b, long long n, do
 //   T = double: FP64 preconditioner and FP64 J.w (state re-gathered and re-contracted);
 //   T = float : FP32 preconditioner and FP32 J.w from the linearisation record written by
 //               the last residual evaluation (at the current Newton iterate).
+// velocity diagonal of the preconditioner kind: diag(M_V) per node, or (kind 2) the per-dof
+// diagonal of dR_v/dk_v at the current Newton iterate
+const double* prec_diag(const lh_mesh* m, int pk) { return pk == 2 ? m->d_jdiag : m->d_diagMv; }
+
 template <class T>
 struct KrylovOp {
   lh_mesh* m;
@@ -261,7 +265,7 @@ struct KrylovOp {
   const double* wsc = nullptr;   // row weights W of the scaled norm: the operator is W J P^-1
 
   lh_status apply(const T* x, T* y) {
-    LH_CK(m, (launch_prec<T, T>(pk, m->stream, m->P, m->kron, m->d_diagMv, m->d_invMe, x, z, tau)));
+    LH_CK(m, (launch_prec<T, T>(pk, m->stream, m->P, m->kron, prec_diag(m, pk), m->d_invMe, x, z, tau)));
     if constexpr (sizeof(T) == sizeof(double)) {
       LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, y, prof_pair(m, LH_PROF_JVP64)));
     } else {
@@ -382,7 +386,7 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
     }
     LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
     LH_CK(m, launch_gemv<T>(s, V, j, ld, dh, 0.0, ulin, len));
-    LH_CK(m, (launch_prec<T, double>(op.pk, s, m->P, m->kron, m->d_diagMv, m->d_invMe, ulin, zd, op.tau)));
+    LH_CK(m, (launch_prec<T, double>(op.pk, s, m->P, m->kron, prec_diag(m, op.pk), m->d_invMe, ulin, zd, op.tau)));
     LH_CK(m, launch_axpby(s, 1.0, zd, 1.0, dk, n));
     if (done || total >= o.gmres_maxit) break;
     // restart from the true linear residual -r - J dk
@@ -680,6 +684,7 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_rec) cudaFree(m->d_rec);
   if (m->d_stage) cudaFree(m->d_stage);
   if (m->d_wscale) cudaFree(m->d_wscale);
+  if (m->d_jdiag) cudaFree(m->d_jdiag);
   for (int a = 0; a < 3; ++a) {
     if (m->kron.At_free[a]) cudaFree(m->kron.At_free[a]);
     if (m->kron.At_fixed[a]) cudaFree(m->kron.At_fixed[a]);
@@ -763,6 +768,14 @@ lh_status lh_linearize(lh_mesh* m, const double* u, const double* k, double tau)
   m->rec_k = k;
   m->rec_tau = tau;
   m->rec_valid = true;
+  return LH_OK;
+}
+
+lh_status lh_jvv_diagonal(lh_mesh* m, const double* u, const double* k, double tau, double* out) {
+  if (!m || !u || !k || !out) return fail(m, LH_EINVAL, "NULL argument to lh_jvv_diagonal");
+  lh_status st = lh_linearize(m, u, k, tau);
+  if (st != LH_OK) return st;
+  LH_CK(m, launch_jvv_diag(m->P, m->stream, m->d_rec, tau, reinterpret_cast<float*>(m->d_ev), m->d_diagMv, out));
   return LH_OK;
 }
 
@@ -899,7 +912,9 @@ static lh_status check_newton_opts(lh_mesh* m, const lh_newton_opts& o) {
     return fail(m, LH_EINVAL, "unsupported jvp_prec");
   if ((o.jvp_prec == LH_TF32 || o.jvp_prec == LH_BF16) && !jvp_tc_supported(m->P.dim, m->P.K))
     return fail(m, LH_EINVAL, "tensor-core J.w supports 2D orders 1-4 and 3D orders 1-2");
-  if (o.precond != 0 && o.precond != 1) return fail(m, LH_EINVAL, "precond must be 0 or 1");
+  if (o.precond != 0 && o.precond != 1 && o.precond != 2) return fail(m, LH_EINVAL, "precond must be 0, 1 or 2");
+  if (o.precond == 2 && o.jvp_prec == LH_FP64)
+    return fail(m, LH_EINVAL, "precond 2 (diagonal of the velocity block) needs a reduced-precision J.w");
   if (o.forcing != 0 && o.forcing != 1) return fail(m, LH_EINVAL, "forcing must be 0 or 1");
   if (o.forcing && !(o.eta_max >= o.gmres_rtol && o.eta_max < 1.0))
     return fail(m, LH_EINVAL, "eta_max must be in [gmres_rtol, 1)");
@@ -941,6 +956,9 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
   float* zf = wf + ldf;
   float* uf = zf + ldf;
 
+  if (o.precond == 2 && !m->d_jdiag &&
+      cudaMalloc(&m->d_jdiag, sizeof(double) * (size_t)m->P.dim * m->P.NV) != cudaSuccess)
+    return fail(m, LH_ENOMEM, "cannot allocate the velocity-block diagonal");
   const double* wsc = nullptr;
   if (o.scaled_norm) {
     if (!m->d_wscale) {
@@ -982,6 +1000,8 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     // ---- linear solve J dk = -r (Eq. (22)) at the current iterate k
     lh_newton_opts oi = o;
     oi.gmres_rtol = eta;
+    if (o.precond == 2)   // the record describes the current iterate k (its last residual)
+      LH_CK(m, launch_jvv_diag(m->P, s, rec, tau, reinterpret_cast<float*>(m->d_ev), m->d_diagMv, m->d_jdiag));
     const double* rhs = r;   // with scaled_norm GMRES solves W J dk = -W r
     if (wsc) {
       LH_CK(m, launch_row_mul<double>(s, wsc, r, rs, n));

@@ -86,6 +86,7 @@ struct lh_mesh {
   float* d_rec = nullptr;          // linearisation record [NE][rec_len][NQ] (lazily allocated)
   double* d_stage = nullptr;       // SDIRK stage increments k_1..k_3 and stage base state [4 n] (lazily)
   double* d_wscale = nullptr;      // row weights of the scaled Newton norm [n] (lazily)
+  double* d_jdiag = nullptr;       // diagonal of dR_v/dk_v for preconditioner kind 2 [dim NV] (lazily)
   const double* rec_u = nullptr;   // arguments of the last lh_linearize (for the LH_FP32_LIN check)
   const double* rec_k = nullptr;
   double rec_tau = 0.0;

@@ -916,6 +916,98 @@ __global__ void k_assemble_jtvp(ElemParams P, const T* __restrict__ y, double ta
   out[iv] = s;
 }
 
+// =====================================================================================
+// Diagonal of the velocity block dR_v/dk_v = M_V + tau dF.1/dw_v of the stage Jacobian
+// (the block of the paper's Eq. (23) preconditioner), element part, from the linearisation
+// record.  The point map is linear in the reference velocity gradient, so per point the
+// responses dS to the d^2 unit directions E_{c,l} give K_c[r][l] = dS(E_{c,l})[c][r], and
+// dof (c, a) of the element collects sum_q g_a(q)^T K_c(q) g_a(q), g_a(q) the reference
+// gradient of basis function a at point q (one tangent per direction, not per dof).
+template <int DIM, int K>
+__global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
+k_jvv_diag(ElemParams P, const float* __restrict__ rec, float* __restrict__ ev) {
+  using C = Cfg<DIM, K>;
+  constexpr int D = K + 1, ND = C::ND, NQ = C::NQ, Q = C::Q;
+  constexpr int NR = lin_len<DIM>();
+  constexpr int KK = DIM * DIM * DIM;
+  using TB = Tab<K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  const float* sB = smem + TB::B;
+  const float* sG = smem + TB::G;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
+  float* sK = smem + TB::SMEM + eb * NQ * KK;   // [q][c][r][l]
+  const ElemIdx E = elem_index<DIM, K>(P);
+  float Lr[NR];
+  {
+    const float* rq = rec + (E.valid ? E.e : 0) * NR * NQ + lt;
+#pragma unroll
+    for (int f = 0; f < NR; ++f) Lr[f] = E.valid ? rq[f * NQ] : 0.f;
+  }
+  float dJ[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) dJ[i][j] = 0.f;
+#pragma unroll 1
+  for (int c = 0; c < DIM; ++c) {
+#pragma unroll 1
+    for (int l = 0; l < DIM; ++l) {
+      float dGv[DIM][DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) dGv[i][j] = (i == c && j == l) ? 1.f : 0.f;
+      float dS[DIM][DIM], dE, dW;
+      qp_tangent_lin<DIM>(Lr, dJ, dGv, 0.f, P.fq1, P.fq2, P.visc != 0, dS, dE, dW);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) sK[lt * KK + (c * DIM + r) * DIM + l] = dS[c][r];
+    }
+  }
+  __syncthreads();
+  if (!E.valid) return;   // no barrier follows
+  for (int o = lt; o < DIM * ND; o += NQ) {
+    const int c = o / ND, a = o % ND;
+    const int a0 = a % D, a1 = (a / D) % D, a2 = a / (D * D);
+    float acc = 0.f;
+    for (int q = 0; q < NQ; ++q) {
+      const int q0 = q % Q, q1 = (q / Q) % Q, q2 = q / (Q * Q);
+      float g[DIM];
+      if constexpr (DIM == 2) {
+        g[0] = sG[q0 * D + a0] * sB[q1 * D + a1];
+        g[1] = sB[q0 * D + a0] * sG[q1 * D + a1];
+      } else {
+        const float b0 = sB[q0 * D + a0], b1 = sB[q1 * D + a1], b2 = sB[q2 * D + a2];
+        g[0] = sG[q0 * D + a0] * b1 * b2;
+        g[1] = b0 * sG[q1 * D + a1] * b2;
+        g[2] = b0 * b1 * sG[q2 * D + a2];
+      }
+      const float* Kc = sK + q * KK + c * DIM * DIM;
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        float t = 0.f;
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) t += Kc[r * DIM + l] * g[l];
+        acc += g[r] * t;
+      }
+    }
+    ev[E.e * (DIM * ND) + o] = acc;
+  }
+}
+
+// node-centric sum of the element parts: out = diag(M_V) + tau * sum (free rows), 1 (fixed)
+template <int DIM, int K>
+__global__ void k_assemble_jvv_diag(ElemParams P, const float* __restrict__ ev, const double* __restrict__ dmv,
+                                    double tau, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= DIM * P.NV) return;
+  const int comp = (int)(i / P.NV);
+  const long long nd = i % P.NV;
+  out[i] = fixed_node<DIM>(P, nd, comp) ? 1.0
+                                         : dmv[nd] + tau * (double)gather_node<DIM, K>(P, ev, DIM, comp, nd);
+}
+
 template <int DIM, int K>
 __global__ void k_assemble_sum(ElemParams P, const double* __restrict__ ev, int ncomp, double* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1059,6 +1151,16 @@ struct Launch {
                                   TO* out) {
     count_launches(1);
     k_assemble_jvp<DIM, K, float, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    return cudaGetLastError();
+  }
+  static cudaError_t jvv_diag(const ElemParams& P, cudaStream_t s, const float* rec, double tau, float* ev,
+                              const double* dmv, double* out) {
+    const size_t by = sizeof(float) * ((size_t)Tab<K>::SMEM + (size_t)C::THREADS * DIM * DIM * DIM);
+    cudaError_t e = prep<k_jvv_diag<DIM, K>>(by);
+    if (e != cudaSuccess) return e;
+    count_launches(2);
+    k_jvv_diag<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, rec, ev);
+    k_assemble_jvv_diag<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, ev, dmv, tau, out);
     return cudaGetLastError();
   }
   static cudaError_t jtvp_rec(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* y,
@@ -1222,6 +1324,10 @@ cudaError_t launch_row_weights(const ElemParams& P, cudaStream_t s, const double
   return cudaGetLastError();
 }
 
+cudaError_t launch_jvv_diag(const ElemParams& P, cudaStream_t s, const float* rec, double tau, float* ev,
+                            const double* dmv, double* out) {
+  LH_DISPATCH(P, jvv_diag(P, s, rec, tau, ev, dmv, out))
+}
 cudaError_t launch_dt_estimate(const ElemParams& P, cudaStream_t s, const double* u, double* bmin) {
   LH_DISPATCH(P, dt_estimate(P, s, u, bmin))
 }

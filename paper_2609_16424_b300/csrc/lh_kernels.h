@@ -38,6 +38,10 @@ bool jvp_tc_supported(int dim, int k);
 long long halo_len(const ElemParams& P, int axis);
 template <class T>
 cudaError_t launch_halo(const ElemParams& P, cudaStream_t s, int face, int mode, const T* src, T* dst);
+// diagonal of the velocity block dR_v/dk_v = M_V + tau dF.1/dw_v from the linearisation
+// record [dim NV] (1 on fixed rows); ev: float element scratch of NE * dim * ND
+cudaError_t launch_jvv_diag(const ElemParams& P, cudaStream_t s, const float* rec, double tau, float* ev,
+                            const double* dmv, double* out);
 // Taylor-Green L1 velocity error terms (2D), one per (element, quadrature point) (lh_diag.cu)
 long long tg_error_terms(const ElemParams& P);
 cudaError_t launch_tg_error(const ElemParams& P, cudaStream_t s, const double* u, double* out);
@@ -98,8 +102,9 @@ cudaError_t launch_row_weights(const ElemParams& P, cudaStream_t s, const double
 cudaError_t launch_to_f32(cudaStream_t s, const double* x, float* y, long long n);
 cudaError_t launch_to_f64(cudaStream_t s, const float* x, double* y, long long n);
 // block upper-triangular preconditioner [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1] with
-// M_V^-1 = diagonal (kind 0) or exact Kronecker inverse (kind 1, lh_prec.cu); fixed velocity
-// rows identity.  Instantiated for (double, double), (double, float), (float, float),
+// M_V^-1 = diagonal (kind 0) or exact Kronecker inverse (kind 1, lh_prec.cu), or the
+// inverse of a per-dof velocity diagonal passed as diag_mv (kind 2: the diagonal of
+// dR_v/dk_v, launch_jvv_diag); fixed velocity rows identity.  Instantiated for (double, double), (double, float), (float, float),
 // (float, double) input/output types.
 template <class TR, class TZ>
 cudaError_t launch_prec(int kind, cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* diag_mv,

@@ -352,11 +352,34 @@ __global__ void k_precond(ElemParams P, const double* __restrict__ dmv, const do
   }
 }
 
+// the same with a per-dof velocity diagonal dv [dim NV] (the diagonal of dR_v/dk_v, 1 on
+// fixed rows): z_v = dv^-1 r_v, z_x = r_x + tau z_v, z_e = M_E^-1 r_e
+template <class TR, class TZ>
+__global__ void k_precond_dof(ElemParams P, const double* __restrict__ dv, const double* __restrict__ ime,
+                              const TR* __restrict__ r, TZ* __restrict__ z, double tau) {
+  const long long n1 = (long long)P.dim * P.NV;
+  const long long n = 2 * n1 + P.NEd;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i < n1) {
+    z[i] = TZ((double)r[i] + tau * (double)r[n1 + i] / dv[i]);
+  } else if (i < 2 * n1) {
+    z[i] = TZ((double)r[i] / dv[i - n1]);
+  } else {
+    z[i] = TZ((double)r[i] * ime[i - 2 * n1]);
+  }
+}
+
 template <class TR, class TZ>
 cudaError_t launch_prec(int kind, cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* diag_mv,
                         const double* inv_me, const TR* r, TZ* z, double tau) {
   if (kind == 1) return kron_apply<TR, TZ>(s, P, K, inv_me, r, z, tau);
   const long long n = 2LL * P.dim * P.NV + P.NEd;
+  if (kind == 2) {   // diag_mv is the per-dof velocity diagonal here
+    k_precond_dof<TR, TZ><<<nb(n, 256), 256, 0, s>>>(P, diag_mv, inv_me, r, z, tau);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   k_precond<TR, TZ><<<nb(n, 256), 256, 0, s>>>(P, diag_mv, inv_me, r, z, tau);
   count_launches(1);
   return cudaGetLastError();

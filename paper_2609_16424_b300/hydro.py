@@ -20,7 +20,8 @@ def _ptr(t):
 def newton_opts(**kw):
     """lh_newton_opts with the library defaults, overridden by keyword arguments
     (newton_rtol, newton_atol, gmres_rtol, newton_maxit, gmres_maxit, restart,
-    max_halvings, jvp_prec in {'fp64', 'fp32', 'tf32', 'bf16'}, precond in {'jacobi', 'kron'},
+    max_halvings, jvp_prec in {'fp64', 'fp32', 'tf32', 'bf16'}, precond in {'jacobi', 'kron',
+    'jvv_diag'},
     forcing, eta_max, scaled_norm);
     'tf32' and 'bf16' run the element contractions of J.w on the tensor cores."""
     o = _lib.NewtonOpts()
@@ -33,7 +34,7 @@ def newton_opts(**kw):
             val = {"fp64": _lib.LH_FP64, "fp32": _lib.LH_FP32, "tf32": _lib.LH_TF32,
                    "bf16": _lib.LH_BF16}.get(val, val)
         if key == "precond":
-            val = {"jacobi": 0, "kron": 1}.get(val, val)
+            val = {"jacobi": 0, "kron": 1, "jvv_diag": 2}.get(val, val)
         setattr(o, key, val)
     return o
 
@@ -242,6 +243,16 @@ class Mesh:
         self._stream()
         self._check(_L.lh_dt_estimate(self._h, _ptr(u), C.byref(dt)))
         return dt.value
+
+    def jvv_diagonal(self, u, k, tau, out=None):
+        """Diagonal of the velocity block dR_v/dk_v = M_V + tau dF/dv at (u, k, tau), [dim * NV]
+        (1 on fixed rows; the viscous part from the FP32 linearisation record)."""
+        self._vec(u, "u")
+        self._vec(k, "k")
+        out = torch.empty(self.dim * self.NV, dtype=torch.float64, device=self.device) if out is None else out
+        self._stream()
+        self._check(_L.lh_jvv_diagonal(self._h, _ptr(u), _ptr(k), float(tau), _ptr(out)))
+        return out
 
     def tg_velocity_error(self, u):
         """L1 velocity error of the 2D Taylor-Green vortex at state u (Sec. 4.1)."""

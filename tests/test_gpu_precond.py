@@ -1,0 +1,42 @@
+"""Diagonal of the velocity block M_V + tau dF/dv (the block of the paper's Eq. (23)) and
+the Jacobi preconditioner built on it (precond kind 2), against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import lh_synth
+from lhcase import Case
+from oracle import solver
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, (3, 3), 2), (2, (2, 2), 3), (3, (2, 2, 2), 1), (3, (2, 2, 2), 2)])
+def test_jvv_diagonal_matches_oracle(dim, n, k):
+    c = Case(dim, n, k, seed=7, vscale=2.0)
+    kk = lh_synth.normal_vector(c.u.size, 3, 0.2)
+    tau = 0.05
+    ref = solver.velocity_block_diagonal(c.hyd, c.u, kk, tau)
+    mass = solver.velocity_block_diagonal(c.hyd, c.u, kk, 0.0)
+    got = c.gm.jvv_diagonal(c.dev(c.u), c.dev(kk), tau).cpu().numpy()
+    visc = ref - mass
+    assert np.abs(visc).max() > 1e-3 * np.abs(mass).max()      # the viscous part is exercised
+    err = np.abs(got - ref).max()
+    assert err <= 5e-4 * np.abs(visc).max() + 1e-12 * np.abs(ref).max(), (err, np.abs(visc).max())
+
+
+def test_jvv_jacobi_newton_reaches_the_root():
+    import paper_2609_16424_b300 as lh
+    c = Case(3, (4, 4, 4), 2, seed=3, vscale=1.0)
+    u = c.dev(c.u)
+    outs = []
+    for pc in ("kron", "jvv_diag"):
+        ug, kg = u.clone(), torch.zeros_like(u)
+        st = c.gm.newton_step(ug, kg, 0.01, newton_rtol=1e-11, gmres_rtol=1e-8, gmres_maxit=300, restart=40,
+                              jvp_prec="fp32", precond=pc)
+        outs.append((ug.cpu().numpy(), st))
+    (a, sa), (b, sb) = outs
+    assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(a), (sa, sb)
+    with pytest.raises(lh.LHError) as ei:
+        c.gm.newton_step(u.clone(), None, 0.01, precond="jvv_diag")   # FP64 J.w has no record
+    assert ei.value.status == 1
