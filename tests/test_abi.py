@@ -64,6 +64,12 @@ def test_defaults_and_argument_checks_without_gpu():
     o = _lib.NewtonOpts()
     lh.lib.lh_newton_opts_init(C.byref(o))
     assert (o.newton_rtol, o.gmres_rtol, o.restart) == (1e-10, 1e-12, 30)
+    assert (o.precond, o.forcing, o.eta_max, o.scaled_norm) == (1, 0, 0.1, 0)
+    # the binding maps option names and rejects unknown ones (a typo must not pass silently)
+    o2 = lh.newton_opts(precond="jvv_diag", jvp_prec="bf16", scaled_norm=1)
+    assert (o2.precond, o2.jvp_prec, o2.scaled_norm) == (2, _lib.LH_BF16, 1)
+    with pytest.raises(TypeError):
+        lh.newton_opts(newton_rtoll=1e-6)
     # invalid descriptions are rejected before any CUDA call
     h = C.c_void_p()
     d.order = 7
@@ -75,14 +81,17 @@ def test_defaults_and_argument_checks_without_gpu():
     assert h.value is None
 
 
-@pytest.mark.parametrize("fn", ["lh_residual", "lh_jvp", "lh_jtvp", "lh_newton_step"])
+@pytest.mark.parametrize("fn", ["lh_residual", "lh_jvp", "lh_jtvp", "lh_newton_step", "lh_stage_solve",
+                                "lh_sdirk_step", "lh_jvv_diagonal", "lh_tg_velocity_error"])
 def test_null_mesh_is_rejected(fn):
     import paper_2609_16424_b300 as lh
     f = getattr(lh.lib, fn)
     nargs = len(f.argtypes)
     args = [None] * nargs
-    if fn in ("lh_residual", "lh_jvp", "lh_jtvp", "lh_newton_step"):
+    if fn in ("lh_residual", "lh_jvp", "lh_jtvp", "lh_newton_step", "lh_stage_solve", "lh_jvv_diagonal"):
         args[3] = 0.1
+    if fn == "lh_sdirk_step":
+        args[1], args[4] = 3, 0.1
     if fn in ("lh_jvp", "lh_jtvp"):
         args[6] = 0
     assert f(*args) == 1     # LH_EINVAL
