@@ -182,6 +182,9 @@ lh_status lh_mass_solve(lh_mesh* mesh, int which, const double* rhs, double* sol
  *   z = P^-1 r,  P^-1 = [I, tau M_V^-1, 0; 0, M_V^-1, 0; 0, 0, M_E^-1],
  * with M_V^-1 the diagonal of M_V (kind 0) or its exact Kronecker-product inverse (kind 1,
  * float arithmetic; exact for uniform rho0) on free velocity rows and identity on fixed rows.
+ * Kind 2 of lh_newton_opts.precond (the diagonal of M_V + tau dF/dv at the current Newton
+ * iterate) exists only inside lh_newton_step and is rejected here with LH_EINVAL; its
+ * diagonal is available from lh_jvv_diagonal.
  * r, z: device [n] double, not aliased.  Asynchronous. */
 lh_status lh_precond(lh_mesh* mesh, int kind, double tau, const double* r, double* z);
 
