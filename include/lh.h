@@ -284,6 +284,11 @@ lh_status lh_stage_solve(lh_mesh* mesh, const double* u_base, double* k, double 
 lh_status lh_sdirk_step(lh_mesh* mesh, int scheme, double* u, double* k_prev, double dt,
                         const lh_newton_opts* opts, lh_step_stats* stats);
 
+/* The Butcher tableau lh_sdirk_step uses for a scheme (host only, no GPU): *stages = s, A:
+ * HOST double[9] row-major 3 x 3 (entries beyond s x s are 0), b: HOST double[3].
+ * LH_EINVAL for a scheme other than 2-4. */
+lh_status lh_sdirk_tableau(int scheme, int* stages, double* A, double* b);
+
 /* Stage residual R(k; tau, u), the same operator and kernel as lh_residual, for callers
  * that must not allocate device memory when they call the library (for example code
  * inside a host application that owns all device memory through its own pool, or

@@ -1171,6 +1171,18 @@ void merge_stats(lh_step_stats& acc, const lh_step_stats& st, bool first) {
 
 }  // namespace
 
+lh_status lh_sdirk_tableau(int scheme, int* stages, double* A, double* b) {
+  if (!stages || !A || !b) return set_global_error(LH_EINVAL, "NULL argument to lh_sdirk_tableau");
+  Tableau T;
+  if (!sdirk_tableau(scheme, &T)) return set_global_error(LH_EINVAL, "scheme must be 2, 3 or 4");
+  *stages = T.s;
+  for (int i = 0; i < 3; ++i) {
+    b[i] = T.b[i];
+    for (int j = 0; j < 3; ++j) A[3 * i + j] = T.a[i][j];
+  }
+  return LH_OK;
+}
+
 lh_status lh_sdirk_step(lh_mesh* m, int scheme, double* u, double* k_prev, double dt,
                         const lh_newton_opts* opts_in, lh_step_stats* stats) {
   if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_sdirk_step");
