@@ -164,3 +164,21 @@ def test_scaled_norm_reaches_the_root_and_tightens_the_v_rows():
                        jvp_prec="fp32", scaled_norm=scaled)
         errs[scaled] = (rel(kk, sv), rel(kk, se))
     assert errs[1][0] < errs[0][0] and errs[1][0] <= 1e-4, errs
+
+
+@pytest.mark.parametrize("scheme,lo,hi", [(2, 1.7, 2.3), (3, 2.5, 3.5)])
+def test_taylor_green_convergence_rates(scheme, lo, hi):
+    """Sec. 4.1 table: Taylor-Green (p0 = 1) to t = 0.5 with Q_k-Q_{k-1} + SD_k (k = scheme),
+    dt fixed at 8x the explicit estimate (the paper's FS-CFL 2 step counts), Newton rtol
+    1e-9: the L1 velocity error falls at order k between h = 1/32 and 1/64."""
+    from paper_2609_16424_b300.states import taylor_green_problem
+    errs, steps = [], []
+    for inv_h in (32, 64):
+        gm, u = taylor_green_problem(inv_h, scheme, p0=1.0)
+        n, rej, hist = gm.advance(u, 0.5, fs_cfl=8.0, scheme=scheme, grow=False, max_attempts=400, jvp_prec="fp32",
+                                  newton_rtol=1e-9, gmres_rtol=1e-6, gmres_maxit=200, restart=30, newton_maxit=20)
+        assert sum(h for _, h, _, a in hist if a) == pytest.approx(0.5, rel=1e-12)
+        errs.append(gm.tg_velocity_error(u))
+        steps.append(n)
+    rate = np.log2(errs[0] / errs[1])
+    assert lo < rate < hi, (errs, steps)
