@@ -141,6 +141,15 @@ lh_status lh_halo_add(lh_mesh* mesh, int face, const void* buf, void* r, lh_prec
  * tensor cores timed out since the mesh was created (synchronises; clears the flag). */
 lh_status lh_tc_status(lh_mesh* mesh);
 
+/* Poll limit of every bounded wait of the tensor-core J.w on its MMA completions (process
+ * wide, all devices; default 2^22 polls, about 1 s at most).  After the first wait that runs
+ * out, the kernel skips all later MMA issues and waits of that launch, writes NaN into the
+ * element rows it has not finished, sets the flag lh_tc_status reports, lets the MMAs it
+ * already issued drain (one more wait with the default limit) and releases its tensor
+ * memory.  A diagnostic switch: a limit of 0 makes every launch take that path at once.
+ * Returns the previous limit. */
+unsigned lh_tc_set_wait_polls(unsigned polls);
+
 /* Linearisation record (partial assembly of the tangent, paper Sec. 2.2: store the
  * quadrature-point data once, reuse it for every action): evaluates the residual at
  * w = u + tau k in FP64 and keeps, rounded to float, the linearisation of the
@@ -219,7 +228,9 @@ typedef struct {
                               (exact for uniform rho0; rho0-scaled otherwise); 2 = inverse of
                               the diagonal of the paper's velocity block M_V + tau dF/dv
                               (Eq. (23)), recomputed from the linearisation record at every
-                              Newton iterate (needs jvp_prec other than LH_FP64); default 1 */
+                              Newton iterate, each free entry kept at >= 0.5 diag(M_V) (the
+                              viscous tangent is not sign-definite) (needs jvp_prec other than
+                              LH_FP64); default 1 */
   int forcing;             /* 0: every linear solve to gmres_rtol (default); 1: adaptive
                               forcing terms (Eisenstat and Walker 1996, choice 2 with gamma 0.9,
                               alpha 2, and the safeguard against oversolving the last step):
@@ -295,8 +306,9 @@ lh_status lh_sdirk_tableau(int scheme, int* stages, double* A, double* b);
  * latency-critical loops that cannot accept cudaMalloc's implicit synchronisation).
  * The paper has no counterpart; it is a deployment variant.
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.  The
- *    element scratch (16 MiB), per-block minima (512 KiB) and 1D tables (2 KiB) live in
- *    file-scope __device__ arrays that every GPU loading the library holds until exit.
+ *    element scratch (16 MiB), per-block minima (512 KiB) and 1D tables of orders 1-4
+ *    (8 KiB) live in file-scope __device__ arrays that every GPU loading the library holds
+ *    until exit.
  *  - Maximum size: NE * dim * (order+1)^dim <= 2^21 (e.g. 3D Q2: NE <= 25890; 2D Q2:
  *    NE <= 116508); larger meshes are rejected with LH_EINVAL and a message naming the
  *    limit.  No min det J is returned.
@@ -304,7 +316,8 @@ lh_status lh_sdirk_tableau(int scheme, int* stages, double* A, double* b);
  *    work runs on desc->stream).  rho0, gamma: DEVICE arrays [NE] of initial densities and
  *    adiabatic indices.  u, k, r: DEVICE [n] double, r must not alias u or k.
  *  - The first call on each device looks up the device addresses of those arrays
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and writes the tables of all orders with synchronous copies;
+ *    later calls copy nothing.  Make that first call before any stream capture.
  *  - Every call shares the arrays and overwrites them (the scratch keeps the last call's
  *    contents; nothing in it must start at zero).  Calls that overlap on the GPU, e.g. on
  *    two streams at once, race on them.

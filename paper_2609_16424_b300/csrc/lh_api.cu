@@ -16,6 +16,10 @@ namespace {
 
 std::string g_err;   // message for failures that have no mesh
 
+// precond 2 keeps each free velocity entry at >= this fraction of diag(M_V): the viscous part
+// tau dF.1/dv of the diagonal comes from the FP32 record and is not sign-definite
+constexpr double kJvvFloor = 0.5;
+
 lh_status fail(lh_mesh* m, lh_status st, const std::string& msg) {
   if (m) m->err = msg; else g_err = msg;
   return st;
@@ -1001,7 +1005,8 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     lh_newton_opts oi = o;
     oi.gmres_rtol = eta;
     if (o.precond == 2)   // the record describes the current iterate k (its last residual)
-      LH_CK(m, launch_jvv_diag(m->P, s, rec, tau, reinterpret_cast<float*>(m->d_ev), m->d_diagMv, m->d_jdiag));
+      LH_CK(m, launch_jvv_diag(m->P, s, rec, tau, reinterpret_cast<float*>(m->d_ev), m->d_diagMv, m->d_jdiag,
+                               kJvvFloor));
     const double* rhs = r;   // with scaled_norm GMRES solves W J dk = -W r
     if (wsc) {
       LH_CK(m, launch_row_mul<double>(s, wsc, r, rs, n));
@@ -1267,6 +1272,8 @@ lh_status lh_tc_status(lh_mesh* m) {
   }
   return LH_OK;
 }
+
+unsigned lh_tc_set_wait_polls(unsigned polls) { return set_tc_wait_polls(polls); }
 
 const char* lh_last_error(const lh_mesh* m) { return m ? m->err.c_str() : g_err.c_str(); }
 

@@ -999,13 +999,17 @@ k_jvv_diag(ElemParams P, const float* __restrict__ rec, float* __restrict__ ev) 
 // node-centric sum of the element parts: out = diag(M_V) + tau * sum (free rows), 1 (fixed)
 template <int DIM, int K>
 __global__ void k_assemble_jvv_diag(ElemParams P, const float* __restrict__ ev, const double* __restrict__ dmv,
-                                    double tau, double* __restrict__ out) {
+                                    double tau, double floor, double* __restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= DIM * P.NV) return;
   const int comp = (int)(i / P.NV);
   const long long nd = i % P.NV;
-  out[i] = fixed_node<DIM>(P, nd, comp) ? 1.0
-                                         : dmv[nd] + tau * (double)gather_node<DIM, K>(P, ev, DIM, comp, nd);
+  if (fixed_node<DIM>(P, nd, comp)) {
+    out[i] = 1.0;
+    return;
+  }
+  const double d = dmv[nd] + tau * (double)gather_node<DIM, K>(P, ev, DIM, comp, nd);
+  out[i] = (floor > 0.0 && !(d >= floor * dmv[nd])) ? floor * dmv[nd] : d;
 }
 
 template <int DIM, int K>
@@ -1154,13 +1158,13 @@ struct Launch {
     return cudaGetLastError();
   }
   static cudaError_t jvv_diag(const ElemParams& P, cudaStream_t s, const float* rec, double tau, float* ev,
-                              const double* dmv, double* out) {
+                              const double* dmv, double* out, double floor) {
     const size_t by = sizeof(float) * ((size_t)Tab<K>::SMEM + (size_t)C::THREADS * DIM * DIM * DIM);
     cudaError_t e = prep<k_jvv_diag<DIM, K>>(by);
     if (e != cudaSuccess) return e;
     count_launches(2);
     k_jvv_diag<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, rec, ev);
-    k_assemble_jvv_diag<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, ev, dmv, tau, out);
+    k_assemble_jvv_diag<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, ev, dmv, tau, floor, out);
     return cudaGetLastError();
   }
   static cudaError_t jtvp_rec(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* y,
@@ -1325,8 +1329,8 @@ cudaError_t launch_row_weights(const ElemParams& P, cudaStream_t s, const double
 }
 
 cudaError_t launch_jvv_diag(const ElemParams& P, cudaStream_t s, const float* rec, double tau, float* ev,
-                            const double* dmv, double* out) {
-  LH_DISPATCH(P, jvv_diag(P, s, rec, tau, ev, dmv, out))
+                            const double* dmv, double* out, double floor) {
+  LH_DISPATCH(P, jvv_diag(P, s, rec, tau, ev, dmv, out, floor))
 }
 cudaError_t launch_dt_estimate(const ElemParams& P, cudaStream_t s, const double* u, double* bmin) {
   LH_DISPATCH(P, dt_estimate(P, s, u, bmin))

@@ -33,15 +33,19 @@ template <class TO>
 cudaError_t launch_jvp_tc(const ElemParams& P, cudaStream_t s, int kind, const float* rec, double tau,
                           const float* dk, float* ev, TO* out, int* err, cudaEvent_t* ev2 = nullptr);
 bool jvp_tc_supported(int dim, int k);
+// process-wide poll limit of the tensor-core waits; returns the previous limit
+unsigned set_tc_wait_polls(unsigned polls);
 // halo of a box face (lh_halo.cu): mode 0 packs the dim velocity rows of the face nodes
 // into dst[dim][face nodes]; mode 1 adds src into the free velocity rows of dst
 long long halo_len(const ElemParams& P, int axis);
 template <class T>
 cudaError_t launch_halo(const ElemParams& P, cudaStream_t s, int face, int mode, const T* src, T* dst);
 // diagonal of the velocity block dR_v/dk_v = M_V + tau dF.1/dw_v from the linearisation
-// record [dim NV] (1 on fixed rows); ev: float element scratch of NE * dim * ND
+// record [dim NV] (1 on fixed rows); ev: float element scratch of NE * dim * ND.  floor > 0
+// clamps each free entry to at least floor * diag(M_V) (the preconditioner's use: the
+// viscous tangent is not sign-definite); floor = 0 returns the diagonal itself
 cudaError_t launch_jvv_diag(const ElemParams& P, cudaStream_t s, const float* rec, double tau, float* ev,
-                            const double* dmv, double* out);
+                            const double* dmv, double* out, double floor = 0.0);
 // Taylor-Green L1 velocity error terms (2D), one per (element, quadrature point) (lh_diag.cu)
 long long tg_error_terms(const ElemParams& P);
 cudaError_t launch_tg_error(const ElemParams& P, cudaStream_t s, const double* u, double* out);

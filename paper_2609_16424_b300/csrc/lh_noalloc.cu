@@ -15,18 +15,19 @@ namespace {
 
 constexpr long long kEvMax = 2LL * 1024 * 1024;   // element scratch, doubles (16 MiB)
 constexpr long long kBlocksMax = 64LL * 1024;     // per-block det J minima, doubles (512 KiB)
-constexpr int kTabMax = 256;                      // 1D bases and weights (order 4 needs 129)
+constexpr int kTabMax = 256;                      // 1D bases and weights of one order (order 4 needs 129)
+constexpr int kOrders = 4;                        // orders 1..4, one table row each
 
 __device__ __align__(256) double g_ev[kEvMax];
 __device__ __align__(256) double g_blockmin[kBlocksMax];
-__device__ __align__(256) double g_tab[kTabMax];
+__device__ __align__(256) double g_tab[kOrders * kTabMax];
 
 // device addresses of the arrays above, looked up once per device
 struct DevAddr {
   bool ready = false;
   double* ev = nullptr;
   double* blockmin = nullptr;
-  double* tab = nullptr;
+  double* tab = nullptr;   // kOrders rows of kTabMax entries, filled at set-up
 };
 constexpr int kMaxDevices = 64;
 DevAddr g_addr[kMaxDevices];
@@ -54,6 +55,21 @@ lh_status device_addresses(DevAddr* out, std::string* why) {
       *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
       return LH_ECUDA;
     }
+    // the 1D tables of every order, written once per device (synchronous copies, made
+    // before any call of this device launches work), so that a call copies nothing
+    for (int K = 1; K <= kOrders; ++K) {
+      const std::vector<double> tab = lh::host_tables(K);
+      if ((int)tab.size() > kTabMax) {
+        *why = "lh_residual_noalloc: table too large";
+        return LH_EINVAL;
+      }
+      e = cudaMemcpy(a.tab + (size_t)(K - 1) * kTabMax, tab.data(), sizeof(double) * tab.size(),
+                     cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        *why = std::string("lh_residual_noalloc: table upload: ") + cudaGetErrorString(e);
+        return LH_ECUDA;
+      }
+    }
     a.ready = true;
   }
   *out = a;
@@ -79,21 +95,17 @@ extern "C" lh_status lh_residual_noalloc(const lh_mesh_desc* desc, const double*
                                                std::to_string(ev_need) + " > " + std::to_string(kEvMax) + ")");
   if ((long long)lh::elem_grid(P) > kBlocksMax)
     return lh::set_global_error(LH_EINVAL, "lh_residual_noalloc: too many element blocks for the static scratch");
-  const std::vector<double> tab = lh::host_tables(P.K);
-  if ((int)tab.size() > kTabMax) return lh::set_global_error(LH_EINVAL, "lh_residual_noalloc: table too large");
+  if (P.K < 1 || P.K > kOrders) return lh::set_global_error(LH_EINVAL, "lh_residual_noalloc: order out of range");
   DevAddr a;
   lh_status st = device_addresses(&a, &why);
   if (st != LH_OK) return lh::set_global_error(st, why);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(desc->stream);
-  // the tables of this order replace the previous call's; the element scratch and the
-  // block minima are fully written before they are read, so nothing needs clearing
-  cudaError_t e = cudaMemcpyAsync(a.tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess)
-    return lh::set_global_error(LH_ECUDA, std::string("lh_residual_noalloc: ") + cudaGetErrorString(e));
-  P.tab = a.tab;
+  // the tables are constant per order; the element scratch and the block minima are fully
+  // written before they are read, so nothing needs clearing
+  P.tab = a.tab + (size_t)(P.K - 1) * kTabMax;
   P.rho0 = rho0;
   P.gamma = gamma;
-  e = lh::launch_residual(P, s, u, k, tau, a.ev, a.blockmin, r, nullptr, nullptr);
+  cudaError_t e = lh::launch_residual(P, s, u, k, tau, a.ev, a.blockmin, r, nullptr, nullptr);
   if (e != cudaSuccess)
     return lh::set_global_error(LH_ECUDA, std::string("lh_residual_noalloc: ") + cudaGetErrorString(e));
   return LH_OK;

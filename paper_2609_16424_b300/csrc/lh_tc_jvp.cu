@@ -19,7 +19,9 @@
 // Dense element operators are (Q^d x 4) x (D^d + L^d) entries; they fit in shared memory
 // for 2D k <= 4 and 3D k <= 2.  Persistent CTAs (two per SM with BF16 operands, one with
 // TF32 by shared memory) each own 256 tensor-memory columns for the whole launch.
+#include <atomic>
 #include <cfloat>
+#include <mutex>
 #include "lh_internal.h"
 #include "lh_kernels.h"
 #include "lh_qp.cuh"
@@ -33,7 +35,8 @@ namespace {
 constexpr int EB = 16;    // elements per batch
 constexpr int QS = 16;    // quadrature points per sub-chunk
 constexpr int NTH = EB * QS;
-constexpr uint32_t kWaitPolls = 1u << 22;   // mbarrier polls before giving up
+constexpr uint32_t kWaitPolls = 1u << 22;   // default mbarrier polls before giving up
+std::atomic<uint32_t> g_wait_polls{kWaitPolls};
 
 __host__ __device__ constexpr int rup(int x, int m) { return (x + m - 1) / m * m; }
 __host__ __device__ constexpr int pow2_cols(int x) {
@@ -69,7 +72,7 @@ struct TcPlan {
   static constexpr uint32_t O_X = O_AF + 128u * KF * ESZ;
   static constexpr uint32_t SZ_X = (uint32_t)EB * QS * 32 * 4;
   static constexpr uint32_t O_W = O_X + SZ_X;                          // 1D weights (float, 8)
-  static constexpr uint32_t O_BAR = O_W + 32;                          // 2 mbarriers + taddr
+  static constexpr uint32_t O_BAR = O_W + 32;                          // 3 mbarriers + taddr
   static constexpr uint32_t BYTES = O_BAR + 32 + 1024;                 // + alignment slack
   static_assert(NF <= 256 && NF % 16 == 0, "forward N out of range");
   static_assert(NB <= 256 && NB % 16 == 0, "backward N out of range");
@@ -130,6 +133,15 @@ __device__ __forceinline__ void cta_sync() {
   tc::fence_after_sync();
 }
 
+// barrier that also makes the wait status uniform over the CTA: after one thread's wait has
+// given up, every thread skips the remaining waits and MMA issues of the launch
+__device__ __forceinline__ bool cta_sync_and(bool ok) {
+  tc::fence_before_sync();
+  const bool all = __syncthreads_and(ok ? 1 : 0) != 0;
+  tc::fence_after_sync();
+  return all;
+}
+
 template <int DIM, int K>
 __device__ __forceinline__ long long node_lattice(const ElemParams& P, long long e, int a) {
   constexpr int D = K + 1;
@@ -147,7 +159,7 @@ __device__ __forceinline__ long long node_lattice(const ElemParams& P, long long
 template <int DIM, int K, tc::Kind KIND, class TO>
 __global__ void __launch_bounds__(NTH, 2)
 k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ dk,
-         float* __restrict__ ev, TO* __restrict__ oute, int* __restrict__ err) {
+         float* __restrict__ ev, TO* __restrict__ oute, int* __restrict__ err, uint32_t polls) {
   using PL = TcPlan<DIM, K, KIND>;
   using C = Cfg<DIM, K>;
   constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q;
@@ -164,7 +176,8 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
   float* sW = reinterpret_cast<float*>(sm + PL::O_W);
   uint64_t* mbf = reinterpret_cast<uint64_t*>(sm + PL::O_BAR);
   uint64_t* mbb = mbf + 1;
-  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(mbf + 2);
+  uint64_t* mbd = mbf + 2;                 // drain barrier: used once, after a failed wait
+  uint32_t* s_taddr = reinterpret_cast<uint32_t*>(mbf + 3);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // ---- set-up: tensor memory, barriers, constant operands, zeroed padding
@@ -175,6 +188,7 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
   if (tid == 0) {
     tc::mbar_init(mbf, 1);
     tc::mbar_init(mbb, 1);
+    tc::mbar_init(mbd, 1);
     tc::fence_mbar_init();
   }
   for (uint32_t i = tid; i < PL::O_X / 16; i += NTH) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
@@ -237,7 +251,7 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
     tc::fence_proxy_async();
     cta_sync();
     // ---- 2. forward MMA of the first sub-chunk: D_f = U Bf^T (its 4 QS columns)
-    if (tid == 0) issue_fwd(0);
+    if (tid == 0 && ok) issue_fwd(0);
 
     bool pending_b = false;
     for (int s = 0; s < PL::NSUB; ++s) {
@@ -253,11 +267,11 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
 #pragma unroll
         for (int f = 0; f < NR; ++f) Lr[f] = valid ? rq[f * NQ] : 0.f;
       }
-      ok = tc::mbar_wait(mbf, ph_f, kWaitPolls) && ok;   // forward MMA of this sub-chunk
+      if (ok) ok = tc::mbar_wait(mbf, ph_f, polls);   // forward MMA of this sub-chunk
       ph_f ^= 1u;
       tc::fence_after_sync();
       // ---- 3. D_f columns of this sub-chunk -> sX[e][q][slot][r] (slot = c ^ e ^ q, 16 B)
-      {
+      if (__syncthreads_or(ok ? 0 : 1) == 0) {
         const int quarter = warp & 3, half = warp >> 2;
         const int row = 32 * quarter + lane;
         const int cc = row / EB, er = row % EB;
@@ -276,11 +290,11 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
           }
         }
       }
-      cta_sync();
+      ok = cta_sync_and(ok);
       // next sub-chunk's forward MMA, into the other buffer (read in the previous sub-chunk).
       // Issued only after this barrier: every thread has then finished its wait on the
       // current phase of mbf, so that barrier cannot run a phase ahead of a waiting thread.
-      if (tid == 0 && s + 1 < PL::NSUB) issue_fwd(s + 1);
+      if (tid == 0 && ok && s + 1 < PL::NSUB) issue_fwd(s + 1);
       // ---- 4. quadrature-point tangent, thread = (e, ql)
       float fval[DIM], fgrad[DIM][DIM], g = 0.f;
 #pragma unroll
@@ -329,7 +343,7 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
       }
       // ---- 5. F into A_b (the previous backward MMA must have finished reading it)
       if (pending_b) {
-        ok = tc::mbar_wait(mbb, ph_b, kWaitPolls) && ok;
+        if (ok) ok = tc::mbar_wait(mbb, ph_b, polls);
         ph_b ^= 1u;
         pending_b = false;
       }
@@ -339,9 +353,9 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
                    DIM == 3 ? fgrad[i][DIM - 1] : 0.f);
       put4<KIND>(sAb, tc::off_sw128(DIM * EB + e, 4 * ql, ESZ, PL::AB_ASTRIDE), g, 0.f, 0.f, 0.f);
       tc::fence_proxy_async();
-      cta_sync();
+      ok = cta_sync_and(ok);
       // ---- 6. backward MMA of this sub-chunk: D_b += F Bb^T (K slice of the sub-chunk)
-      if (tid == 0) {
+      if (tid == 0 && ok) {
 #pragma unroll
         for (int j = 0; j < PL::KBC / MK; ++j) {
           const int k0 = j * MK;
@@ -352,12 +366,12 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
         }
         tc::commit(mbb);
       }
-      pending_b = true;
+      pending_b = ok;
     }
     // ---- 7. D_b -> staging (rows c'*16 + e in lanes 0..63) -> global
-    ok = tc::mbar_wait(mbb, ph_b, kWaitPolls) && ok;
+    if (ok) ok = tc::mbar_wait(mbb, ph_b, polls);
     ph_b ^= 1u;
-    tc::fence_after_sync();
+    ok = cta_sync_and(ok);
     float* yh = sX;                         // [EB][DIM][ND]
     float* yl = sX + EB * DIM * ND;         // [EB][NL]
     {
@@ -366,9 +380,11 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
         const int row = 32 * quarter + lane;
         const int cc = row / EB, e = row % EB;
         for (int ch = half; ch < PL::NB / 8; ch += 2) {
-          float v[8];
-          tc::tmem_ld8(tmb + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(8 * ch), v);
-          tc::tmem_wait_ld();
+          float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          if (ok) {
+            tc::tmem_ld8(tmb + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(8 * ch), v);
+            tc::tmem_wait_ld();
+          }
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const int a = 8 * ch + t;
@@ -388,7 +404,16 @@ k_jvp_tc(ElemParams P, const float* __restrict__ rec, float tau, const float* __
     }
     // the next batch's sub-chunk 3 overwrites sX only after the sync that follows its gather
   }
-  if (!ok && lane == 0) atomicExch(err, 1);
+  if (!ok) {
+    // a wait gave up: record it, then let the MMAs this CTA issued drain (a commit tracks
+    // all of the issuing thread's earlier tcgen05 operations; bounded wait) before the
+    // tensor memory is released
+    if (tid == 0) {
+      atomicExch(err, 1);
+      tc::commit(mbd);
+      tc::mbar_wait(mbd, 0, kWaitPolls);
+    }
+  }
   cta_sync();
   if (warp == 0) tc::tmem_dealloc(tm, PL::NCOLS);
 }
@@ -400,15 +425,23 @@ cudaError_t run_tc(const ElemParams& P, cudaStream_t s, const float* rec, double
                    TO* out, int* err, cudaEvent_t* ev2) {
   using PL = TcPlan<DIM, K, KIND>;
   auto kern = k_jvp_tc<DIM, K, KIND, TO>;
-  static int grid = 0;
-  static size_t bytes = 0;
+  // launch shape per device (the shared-memory attribute is a per-device setting)
+  constexpr int kMaxDev = 64;
+  static int grids[kMaxDev] = {};
+  static size_t bytes_of[kMaxDev] = {};
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  int& grid = grids[dev];
+  size_t& bytes = bytes_of[dev];
   if (grid == 0) {
     // keep the CTAs that can share an SM within its 512 tensor-memory columns: pad the
     // shared-memory request so that at most 512 / NCOLS CTAs are resident per SM
-    int dev = 0, nsm = 0;
+    int nsm = 0;
     size_t smem_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     int v = 0;
     if ((e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess) return e;
@@ -428,10 +461,11 @@ cudaError_t run_tc(const ElemParams& P, cudaStream_t s, const float* rec, double
   const long long nbatch = (P.NE + EB - 1) / EB;
   const int g = (int)(nbatch < grid ? nbatch : grid);
   if (ev2) cudaEventRecord(ev2[0], s);
-  kern<<<g, NTH, bytes, s>>>(P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV, err);
+  kern<<<g, NTH, bytes, s>>>(P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV, err,
+                             g_wait_polls.load(std::memory_order_relaxed));
   if (ev2) cudaEventRecord(ev2[1], s);
   count_launches(1);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_assemble_jvp<TO>(P, s, dk, tau, ev, out);
 }
@@ -444,6 +478,8 @@ cudaError_t run_tc_kind(const ElemParams& P, cudaStream_t s, int kind, const flo
 }
 
 }  // namespace
+
+unsigned set_tc_wait_polls(unsigned polls) { return g_wait_polls.exchange(polls, std::memory_order_relaxed); }
 
 bool jvp_tc_supported(int dim, int k) { return (dim == 2 && k >= 1 && k <= 4) || (dim == 3 && k >= 1 && k <= 2); }
 

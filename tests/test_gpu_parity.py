@@ -83,6 +83,33 @@ def test_jtvp_dot_product(case):
     assert abs(a - b) <= 1e-13 * scale, (a, b)
 
 
+@pytest.mark.parametrize("dim,n,k", [(2, (7, 5), 2), (3, (3, 3, 2), 2), (3, (2, 2, 1), 3)])
+def test_negative_energy_parity(dim, n, k):
+    """Eq. (19) on both branches: e ~ U(-1, 1), so about half of the quadrature points take
+    the e < 0 evaluation of e+.  Residual, FP64 J.w, FP64 J^T.y and the record J.w against
+    the oracle at the tolerances of the e >= 0 cases."""
+    c = Case(dim, n, k, seed=31, visc=True, e_lo=-1.0)
+    assert (c.u[2 * c.nx:] < 0).mean() > 0.3
+    kk = lh_synth.normal_vector(c.gm.n, 32, 0.1)
+    dk = lh_synth.normal_vector(c.gm.n, 33)
+    tau = 0.01
+    u, kd = c.dev(c.u), c.dev(kk)
+    ref = c.hyd.residual(c.u, kk, tau)
+    got = c.gm.residual(u, kd, tau).cpu().numpy()
+    assert max(c.rel_blocks(got, ref)) <= 1e-12
+    jref = c.hyd.jvp_complex_step(c.u, kk, tau, dk)
+    got = c.gm.jvp(u, kd, tau, c.dev(dk)).cpu().numpy()
+    assert max(c.rel_blocks(got, jref)) <= 1e-11
+    jref32 = c.hyd.jvp_complex_step(c.u, kk, tau, dk.astype(np.float32).astype(np.float64))
+    c.gm.linearize(u, kd, tau)
+    got = c.gm.jvp(u, kd, tau, c.dev(dk, torch.float32), lin=True).double().cpu().numpy()
+    assert max(c.rel_blocks(got, jref32)) <= 2e-5
+    y = lh_synth.normal_vector(c.gm.n, 34)
+    JTy = c.gm.jtvp(u, kd, tau, c.dev(y)).cpu().numpy()
+    Jdk = c.gm.jvp(u, kd, tau, c.dev(dk)).cpu().numpy()
+    assert abs(float(Jdk @ y) - float(dk @ JTy)) <= 1e-13 * np.linalg.norm(Jdk) * np.linalg.norm(y)
+
+
 @pytest.mark.parametrize("dim,n,k,tg", [(2, (2, 2), 2, False), (2, (2, 1), 2, True), (3, (1, 1, 1), 2, False)])
 def test_jtvp_dense_jacobian(dim, n, k, tg):
     """J^T y from the GPU adjoint against the oracle's dense complex-step Jacobian."""

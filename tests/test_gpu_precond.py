@@ -40,3 +40,25 @@ def test_jvv_jacobi_newton_reaches_the_root():
     with pytest.raises(lh.LHError) as ei:
         c.gm.newton_step(u.clone(), None, 0.01, precond="jvv_diag")   # FP64 J.w has no record
     assert ei.value.status == 1
+
+
+def test_jvv_jacobi_at_large_tau():
+    """Large steps: where tau dF/dv pulls a diagonal entry below half of diag(M_V) (or makes it
+    negative) the preconditioner keeps 0.5 diag(M_V); lh_jvv_diagonal still returns the
+    diagonal itself.  Newton with it reaches the same root as with the exact mass inverse."""
+    c = Case(3, (4, 4, 4), 2, seed=5, vscale=3.0)
+    u = c.dev(c.u)
+    tau = 0.02
+    kk = torch.zeros_like(u)
+    d = c.gm.jvv_diagonal(u, kk, tau).cpu().numpy()
+    dm = c.gm.jvv_diagonal(u, kk, 0.0).cpu().numpy()
+    free = dm != 1.0
+    assert np.abs(d[free] - dm[free]).max() > 0.05 * np.abs(dm[free]).max()   # viscous part exercised
+    outs = []
+    for pc in ("kron", "jvv_diag"):
+        ug, kg = u.clone(), torch.zeros_like(u)
+        st = c.gm.newton_step(ug, kg, 2 * tau, newton_rtol=1e-11, gmres_rtol=1e-8, gmres_maxit=400, restart=40,
+                              jvp_prec="fp32", precond=pc)
+        outs.append((ug.cpu().numpy(), st))
+    (a, sa), (b, sb) = outs
+    assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(a), (sa, sb)

@@ -120,3 +120,38 @@ def test_tc_many_batches_per_cta(dim, n, k):
         gm.tc_status()
         for sl in (slice(nx, 2 * nx), slice(2 * nx, gm.n)):
             assert float((got[sl] - ref[sl]).norm() / ref[sl].norm()) <= TOL[kind]
+
+
+@pytest.mark.parametrize("kind", ["tf32", "bf16"])
+def test_tc_wait_limit_reports_and_returns(kind):
+    """A tensor-core wait that runs out does not hang the launch: with a poll limit of 0 the
+    first wait on an MMA completion gives up, every later wait of the launch is skipped (no
+    cascade of full-length waits over the batches a CTA owns), the element rows come back
+    NaN, lh_tc_status reports LH_ECUDA, and the next launch with the default limit is
+    correct again (the context stays usable)."""
+    import time
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.hydro import LHError
+    c = Case(2, (61, 50), 2, seed=21, visc=True)       # 191 batches: several per CTA
+    kk = lh_synth.normal_vector(c.gm.n, 4, 0.1 * 5 / 61)
+    dk = lh_synth.normal_vector(c.gm.n, 5).astype(np.float32)
+    u, kd = c.dev(c.u), c.dev(kk)
+    tau = 0.02
+    c.gm.linearize(u, kd, tau)
+    good = c.gm.jvp(u, kd, tau, c.dev(dk, torch.float32), tc=kind).cpu().numpy()
+    c.gm.tc_status()
+    prev = lh.lib.lh_tc_set_wait_polls(0)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bad = c.gm.jvp(u, kd, tau, c.dev(dk, torch.float32), tc=kind).cpu().numpy()
+        took = time.perf_counter() - t0
+    finally:
+        lh.lib.lh_tc_set_wait_polls(prev)
+    assert took < 5.0, took
+    assert np.isnan(bad[c.nx:]).any()
+    with pytest.raises(LHError):
+        c.gm.tc_status()
+    again = c.gm.jvp(u, kd, tau, c.dev(dk, torch.float32), tc=kind).cpu().numpy()
+    c.gm.tc_status()
+    assert np.array_equal(again, good)

@@ -36,6 +36,43 @@ def test_energy_regularisation_values():
     assert s1[0, 1] == 0.0
 
 
+def _e_plus(e, eps=1e-6):
+    """e+ recovered from the pressure of a viscosity-free stress: p = (gamma - 1) rho e+."""
+    prm = _prm(2, visc=False)
+    prm.eps_e = eps
+    z = np.zeros((2, 2))
+    rho, gam = 1.7, 1.4
+    sig = stress(z, np.array(1.0), np.array(rho), np.array(float(e)), np.array(gam), prm, 2)
+    return -sig[0, 0] / ((gam - 1.0) * rho)
+
+
+@pytest.mark.parametrize("e", [-1e-7, -1e-6, -1.0, -100.0, -1e8, 3e-7])
+def test_energy_regularisation_negative_branch(e):
+    """Eq. (19) for e < 0 as well as e > 0.  e+ = (e + sqrt(e^2 + eps^2)) / 2 is the larger
+    root of x^2 - e x - eps^2/4 = 0, so e+ (e+ - e) = eps^2 / 4 and e+ > max(e, 0) at every
+    e; dropping the factor 1/2 in either evaluation branch breaks the product by a factor
+    2 or 4.  Checked to a few ulps of the product (for e >> eps the difference e+ - e
+    cancels, so the positive side is checked at e ~ eps here and by its limit below)."""
+    eps = 1e-6
+    ep = _e_plus(e, eps)
+    assert ep > 0.0 and ep > e
+    assert abs(ep * (ep - e) / (0.25 * eps * eps) - 1.0) < 1e-12, (e, ep)
+
+
+def test_energy_regularisation_negative_limits():
+    """Eq. (19): e+ is increasing in e, continuous through e = 0 (value eps/2), and behaves
+    like eps^2 / (4 |e|) as e -> -infinity (and like e as e -> +infinity)."""
+    eps = 1e-6
+    es = np.concatenate([-np.logspace(8, -12, 81), [0.0], np.logspace(-12, 8, 81)])
+    ep = np.array([_e_plus(e, eps) for e in es])
+    assert np.all(np.diff(ep) > 0)
+    assert abs(_e_plus(-1e-15, eps) / (0.5 * eps) - 1) < 1e-8
+    assert abs(_e_plus(1e-15, eps) / (0.5 * eps) - 1) < 1e-8
+    for e in (-1e3, -1e6, -1e8):
+        assert abs(_e_plus(e, eps) * 4.0 * abs(e) / eps ** 2 - 1.0) < 1e-9
+    assert abs(_e_plus(1e6, eps) / 1e6 - 1.0) < 1e-15
+
+
 @pytest.mark.parametrize("psi0", [0.3, 0.5, 0.7])
 def test_switch_value_at_zero_compression(psi0):
     """Eq. (17): the shift makes psi(0) = psi0; Eq. (16): |0|_ds = ds; so at div v = 0,

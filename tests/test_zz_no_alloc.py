@@ -60,6 +60,43 @@ def test_noalloc_residual_equals_regular_residual(dim, n, k, tg):
         assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
 
 
+def test_noalloc_allocates_nothing_and_alternates_orders():
+    """After the first call on the device (which looks up the arrays and writes the tables),
+    calls of different orders in a row leave the device's free memory and torch's allocator
+    unchanged, and each equals lh_residual."""
+    cases = [Case(3, (4, 3, 3), 2, seed=51), Case(3, (2, 2, 2), 3, seed=52), Case(2, (6, 5), 1, seed=53)]
+    descs = [_desc(c) for c in cases]
+    data = []
+    for c in cases:
+        u = c.dev(c.u)
+        kk = c.dev(lh_synth.normal_vector(c.gm.n, 54, 0.1))
+        data.append((u, kk, c.gm.residual(u, kk, 0.02).cpu().numpy()))
+    rho0 = [torch.ones(c.gm.NE, dtype=torch.float64, device="cuda") for c in cases]
+    gam = [torch.full((c.gm.NE,), 1.4, dtype=torch.float64, device="cuda") for c in cases]
+    outs = [torch.empty_like(u) for u, _, _ in data]
+
+    def call(i):
+        import paper_2609_16424_b300 as lh
+        u, kk, _ = data[i]
+        st = lh.lib.lh_residual_noalloc(C.byref(descs[i]), C.c_void_p(rho0[i].data_ptr()),
+                                        C.c_void_p(gam[i].data_ptr()), C.c_void_p(u.data_ptr()),
+                                        C.c_void_p(kk.data_ptr()), C.c_double(0.02), C.c_void_p(outs[i].data_ptr()))
+        assert st == 0, lh.lib.lh_last_error(None)
+
+    call(0)                                          # set-up call
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for rep in range(2):
+        for i in (1, 0, 2, 1):
+            call(i)
+            torch.cuda.synchronize()
+            ref = data[i][2]
+            assert np.linalg.norm(outs[i].cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+
 def test_noalloc_rejects_meshes_beyond_its_scratch():
     import paper_2609_16424_b300 as lh
     from paper_2609_16424_b300 import _lib
