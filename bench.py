@@ -35,6 +35,18 @@ NEWTON = {"newton_rtol": 1e-5, "gmres_rtol": 1e-4, "gmres_maxit": 200, "restart"
 L2_FLUSH_BYTES = 512 << 20
 
 
+def _hbm_peak():
+    """Measured copy bandwidth of this GPU pool (GB/s), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+HBM_PEAK_GBS, HBM_PEAK_SOURCE = _hbm_peak()
+
+
 def sf_macs(dim, k):
     """Multiply-adds of the sum-factorised contractions per element and field component."""
     D, Q = k + 1, 2 * k
@@ -129,22 +141,10 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
-def blast_state(mesh, energy):
-    """Corner point blast on the undeformed box: e = energy / (rho0 |K0|) in element 0."""
-    import torch
-    x0 = mesh.initial_nodes()
-    u = torch.zeros(mesh.n, dtype=torch.float64, device=mesh.device)
-    nx = x0.numel()
-    u[:nx] = x0
-    vol0 = 1.0 / mesh.NE
-    nl = mesh.NEd // mesh.NE
-    u[2 * nx:2 * nx + nl] = energy / vol0
-    return u
-
-
 def setup_ours(device):
     import torch
     import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import blast_state
     W = WORKLOAD
     mesh = lh.Mesh(W["dim"], W["n"], (0.0,) * 3, (1.0,) * 3, W["k"], gamma=W["gamma"], visc=True,
                    device=device)
@@ -185,10 +185,25 @@ def timed_steps(mesh, u_s, k_s, dt, steps, prec, flush, profile=False):
     return times, stats, launches, prof
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the unchanged kernel inside
-# the timed Newton steps of this workload (profiles/k_residual_blast3d_24_q2q1.md); None for
-# kernels without a capture
-NCU_TRAFFIC_BYTES = {"k_residual<3,2>": 13393920 + 61006336}
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a launch inside the timed Newton steps of
+# this workload, with the digest of the CUDA sources it was built from.  The figure is
+# reported only while the sources still have that digest (csrc_digest()).
+NCU_TRAFFIC = {"k_residual<3,2>": {"bytes": 13393920 + 61006336, "csrc": None}}
+
+
+def csrc_digest():
+    """sha256 (16 hex digits) over the library's CUDA sources and the C header."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(ROOT, "paper_2609_16424_b300", "csrc", "*"))) + [
+        os.path.join(ROOT, "include", "lh.h")]
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def tc_mma_flops(dim, k, ne, kind):
@@ -272,6 +287,46 @@ def oracle_residual_rate(u_np, k_np, tau, budget_s=15.0):
                 break
         t = (time.perf_counter() - t0) / reps
     return om.n_unknowns / t / 1e9, reps, t, r
+
+
+def _oracle_worker(args):
+    """One oracle process: residual evaluations of the bench state for about budget_s."""
+    u_np, k_np, tau, budget_s = args
+    with one_thread():
+        from oracle.fem import Mesh as OMesh
+        from oracle.hydro import Hydro, Params
+        W = WORKLOAD
+        om = OMesh(W["n"], (0.0,) * 3, (1.0,) * 3, W["k"])
+        hyd = Hydro(om, Params(om, gamma=W["gamma"], visc=True))
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            hyd.residual(u_np, k_np, tau)
+            reps += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        return reps, time.perf_counter() - t0, om.n_unknowns
+
+
+def oracle_all_cores(u_np, k_np, tau, budget_s=8.0, max_procs=32, gb_per_proc=2.0):
+    """The oracle on all host cores: one single-threaded process per core (spawned), each
+    evaluating the residual of the full bench state; rate = all evaluations x n / the slowest
+    process's time.  Processes are capped by max_procs and by available memory (~1.5 GB each)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    procs = min(cores, max_procs)
+    try:
+        import psutil
+        procs = max(1, min(procs, int(psutil.virtual_memory().available / (gb_per_proc * 2 ** 30))))
+    except ImportError:
+        pass
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(u_np, k_np, tau, budget_s)] * procs)
+    reps = sum(r[0] for r in res)
+    t = max(r[1] for r in res)
+    n = res[0][2]
+    return n * reps / t / 1e9, procs, cores, reps, t
 
 
 def aggregate_ranks(total_ms, units, device):
@@ -403,9 +458,14 @@ def run_ours(args, rank, world, device):
                 "share_of_step": round(dom_ms / sum(times), 4),
                 "algorithmic_flops_per_launch": dom_flops}
 
-    roofline["traffic"] = NCU_TRAFFIC_BYTES.get(roofline["kernel"])
-    if roofline["traffic"] is not None:
-        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch"
+    cap = NCU_TRAFFIC.get(roofline["kernel"])
+    if cap is not None and cap["csrc"] == csrc_digest():
+        roofline["traffic"] = cap["bytes"]
+        roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of this build"
+    else:
+        roofline["traffic_source"] = ("no ncu capture of this build of the kernel" if cap is None else
+                                      "null: the kernel sources changed since the ncu capture")
+    roofline["csrc_digest"] = csrc_digest()
     e2e_val, e2e_ms, e2e_bytes = e2e_steps(mesh, u_s, k_s, dt, max(2, min(args.steps, 5)), prec)
     out = {
         "metric": "GDoF/s of J.w & residual over the implicit step (FP64 residual, FP32 J.w)",
@@ -453,13 +513,53 @@ def run_ours(args, rank, world, device):
                 "h2d_bytes_per_step": e2e_bytes, "d2h_bytes_per_step": e2e_bytes},
         "clocks": clk.summary(),
     }
+    if not args.headline_only and world == 1:
+        w0 = time.perf_counter()
+        out["config5_48cube"] = {
+            "workload": "48^3 hex point blast / perturbed state, Q_k-Q_{k-1}, k = 1..4",
+            "element_kernels": sweep_rows([1, 2, 3, 4], flush, fp64_peak, fp32_peak, device),
+            "implicit_steps": config5_steps([1, 2, 3, 4], {1: 20, 2: 20, 3: 3, 4: 2}, 20, flush, device),
+            "newton": NEWTON, "hbm_peak_gbs": HBM_PEAK_GBS, "hbm_peak_source": HBM_PEAK_SOURCE,
+            "fp64_peak_tflops": round(fp64_peak, 3), "fp32_peak_tflops": round(fp32_peak, 2),
+            "note": "element kernels on the seeded perturbed state, L2 flushed before each call; implicit "
+                    "steps consecutive from the corner deposit at dt = 2 x explicit estimate; plain FP64 "
+                    "steps 20 at k = 1, 2 and 3 / 2 at k = 3 / 4 (seconds per step)"}
+        out["config3_interface"] = run_interface(args)
+        out["config1_taylor_green"] = tg_fp64_steps()
+        out["extras_wall_s"] = round(time.perf_counter() - w0, 1)
     if not args.no_cpu_baseline:
         import numpy as np
-        rate, reps_c, t_c, _ = oracle_residual_rate(u_s.cpu().numpy(), k_s.cpu().numpy(), tau)
+        u_np, k_np = u_s.cpu().numpy(), k_s.cpu().numpy()
+        rate, reps_c, t_c, _ = oracle_residual_rate(u_np, k_np, tau)
         out["cpu_baseline"] = {"value": round(rate, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
                                "sample": f"oracle residual on the full bench state ({W['name']}, n={n}), "
                                          f"{reps_c} evaluations, {t_c:.2f} s each, 1 thread"}
+        if not args.headline_only:
+            ra, procs, cores, reps_a, t_a = oracle_all_cores(u_np, k_np, tau)
+            out["cpu_baseline_all_cores"] = {
+                "value": round(ra, 6), "unit": "GDoF/s", "cores": procs, "host_cores": cores, "kind": "oracle",
+                "sample": f"{procs} single-threaded oracle processes, each evaluating the residual of the full "
+                          f"bench state; {reps_a} evaluations in {t_a:.1f} s"}
     return out
+
+
+def tg_fp64_steps():
+    """2D Taylor-Green vortex, plain FP64 (8x8 Q2-Q1, p0 = 100, no viscosity, energy source):
+    10 implicit midpoint steps at dt = 0.01, Newton-GMRES relative tolerance 1e-10."""
+    import torch
+    from paper_2609_16424_b300.states import taylor_green_problem
+    mesh, u = taylor_green_problem(8, 2, p0=100.0, device="cuda:0")
+    k = torch.zeros_like(u)
+    times, its, gm = [], 0, 0
+    for _ in range(10):
+        ms, st = _ms(lambda: mesh.newton_step(u, k, 0.01, jvp_prec="fp64", newton_rtol=1e-10, gmres_rtol=1e-12,
+                                              gmres_maxit=400, restart=60))
+        times.append(ms)
+        its += st["newton_its"]
+        gm += st["gmres_its_total"]
+    return {"workload": "tg2d_8x8_q2q1 (p0 = 100), FP64, dt 0.01, 10 steps", "n_unknowns": mesh.n,
+            "ms_per_step": round(sum(times) / 10, 3), "newton_its_per_step": its / 10, "gmres_its_per_step": gm / 10,
+            "l1_velocity_error": mesh.tg_velocity_error(u)}
 
 
 def sweep_state(mesh, n, k, seed):
@@ -501,9 +601,32 @@ def run_sweep(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     fp64 = lh.probe_fma("fp64")
     fp32 = lh.probe_fma("fp32")
+    rows = sweep_rows(args.orders, flush, fp64, fp32, dev)
+    return {"metric": "48^3 throughput sweep (element kernels, FP64 residual / FP64 J.w / FP32 record J.w / "
+                      "TF32 and BF16 tensor-core record J.w)",
+            "fp64_peak_tflops": round(fp64, 3), "fp32_peak_tflops": round(fp32, 2), "rows": rows,
+            "data": "synthetic perturbed state (seeded), L2 flushed before each call"}
+
+
+def record_bytes(dim, k, ne):
+    """Algorithmic DRAM bytes of one record J.w element launch: the record (read once), the
+    float direction (each element's dofs, lattice-shared nodes counted once) and the float
+    element output (written once)."""
+    import ctypes as C
+    import paper_2609_16424_b300 as lh
+    nr = C.c_int()
+    lh.lib.lh_record_len(dim, C.byref(nr))
+    nq = (2 * k) ** dim
+    return ne * (4 * nr.value * nq + 4 * (dim * (k + 1) ** dim + k ** dim))
+
+
+def sweep_rows(orders, flush, fp64, fp32, dev):
+    """Element-kernel times and roofline fractions on the 48^3 perturbed state, per order."""
+    import torch
+    import paper_2609_16424_b300 as lh
     rows = []
     n = (48, 48, 48)
-    for k in args.orders:
+    for k in orders:
         mesh = lh.Mesh(3, n, (0, 0, 0), (1, 1, 1), k, gamma=1.4, h_coarse=1.0 / 24, device=dev)
         u = sweep_state(mesh, n, k, 100 + k)
         kk = torch.zeros_like(u)
@@ -555,13 +678,55 @@ def run_sweep(args):
             row[name] = {"elem_kernel_ms": round(t, 4), "gdofs": round(mesh.n / (t * 1e-3) / 1e9, 3),
                          "tflops": round(tf, 3), "frac": round(tf / peak, 4), "pipe": pipe,
                          "flops_per_element": fl[flk]}
+            if flk == "jvp_rec":
+                by = record_bytes(3, k, ne)
+                row[name]["hbm_gbs"] = round(by / (t * 1e-3) / 1e9, 1)
+                row[name]["hbm_frac"] = round(by / (t * 1e-3) / 1e9 / HBM_PEAK_GBS, 4)
+                row[name]["algorithmic_bytes"] = by
         rows.append(row)
         del mesh, u, kk, dk, dkf, r, od, of
         torch.cuda.empty_cache()
-    return {"metric": "48^3 throughput sweep (element kernels, FP64 residual / FP64 J.w / FP32 record J.w / "
-                      "TF32 and BF16 tensor-core record J.w)",
-            "fp64_peak_tflops": round(fp64, 3), "fp32_peak_tflops": round(fp32, 2), "rows": rows,
-            "data": "synthetic perturbed state (seeded), L2 flushed before each call"}
+    return rows
+
+
+def config5_steps(orders, fp64_steps, steps, flush, dev):
+    """Implicit midpoint steps on the 48^3 point blast (Q_k-Q_{k-1}, gamma 1.4, smooth
+    viscosity with h_coarse = 1/24, walls), consecutive from the corner deposit after one
+    developing step, dt = 2 x the explicit estimate recomputed before each step (outside the
+    timed region); per step CUDA-event time of the whole Newton-GMRES solve."""
+    import torch
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import blast_state
+    out = []
+    n = (48, 48, 48)
+    for k in orders:
+        row = {"order": f"Q{k}-Q{k - 1}"}
+        for prec, nsteps in (("fp32", steps), ("fp64", fp64_steps.get(k, 0))):
+            if nsteps <= 0:
+                continue
+            mesh = lh.Mesh(3, n, (0, 0, 0), (1, 1, 1), k, gamma=1.4, h_coarse=1.0 / 24, device=dev)
+            u = blast_state(mesh, 0.25)
+            kk = torch.zeros_like(u)
+            mesh.newton_step(u, kk, 2.0 * mesh.dt_estimate(u), jvp_prec=prec, **NEWTON)
+            times, its, gm, ev = [], 0, 0, 0
+            for _ in range(nsteps):
+                dt = 2.0 * mesh.dt_estimate(u)
+                flush.fill_(1.0)
+                ms, st = _ms(lambda: mesh.newton_step(u, kk, dt, jvp_prec=prec, **NEWTON))
+                times.append(ms)
+                its += st["newton_its"]
+                gm += st["gmres_its_total"]
+                ev += st["residual_evals"] + st["jvp_evals"]
+            row["n_unknowns"] = mesh.n
+            row[prec] = {"steps": nsteps, "ms_per_step": round(sum(times) / nsteps, 3),
+                         "newton_its_per_step": round(its / nsteps, 3), "gmres_its_per_step": round(gm / nsteps, 3),
+                         "gdofs": round(mesh.n * ev / (sum(times) * 1e-3) / 1e9, 4)}
+            del mesh, u, kk
+            torch.cuda.empty_cache()
+        if "fp32" in row and "fp64" in row:
+            row["fp64_over_fp32"] = round(row["fp64"]["ms_per_step"] / row["fp32"]["ms_per_step"], 3)
+        out.append(row)
+    return out
 
 
 def _ms(fn):
@@ -864,6 +1029,8 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64", "tf32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="timed steps only (profiling runs)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the 48^3, interface and Taylor-Green extras and the all-cores oracle")
     ap.add_argument("--sweep", action="store_true", help="48^3 order sweep of the element kernels")
     ap.add_argument("--orders", type=int, nargs="+", default=[1, 2, 3, 4])
     ap.add_argument("--mlp", action="store_true", help="learned initial guess vs extrapolation")

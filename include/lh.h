@@ -295,6 +295,66 @@ lh_status lh_stage_solve(lh_mesh* mesh, const double* u_base, double* k, double 
 lh_status lh_sdirk_step(lh_mesh* mesh, int scheme, double* u, double* k_prev, double dt,
                         const lh_newton_opts* opts, lh_step_stats* stats);
 
+/* ---- Time loop with the paper's implicit time step control (Sec. 4, "implicit time step
+ * control"; the first step at FS-CFL times the explicit estimate of lh_dt_estimate).
+ * After a step whose largest stage solve took <= grow_its Newton iterations dt grows by
+ * `grow`; with more, up to reject_its - 1, dt is kept; a step with >= reject_its iterations,
+ * or whose solve fails (LH_ENOCONV, LH_ETANGLED, LH_ENONFINITE), is rejected: the state goes
+ * back to the start of the step and the step is retried with shrink * dt.  The last step is
+ * clipped to reach t_end exactly.
+ * Initial guess: each step starts from the previous step's last-stage increment (zero at
+ * the first step, or k_prev's content on entry).  The paper leaves the initial guess open;
+ * a predicted guess (for example the learned proposal of lh_mlp_*) is formed by the caller
+ * into k_prev between calls of lh_newton_step, since it needs the caller's network and the
+ * increments of earlier steps; this loop does not call a predictor. */
+typedef struct {
+  int scheme;              /* 2 = implicit midpoint, 3 = SD3, 4 = SD4 (lh_sdirk_step); default 2 */
+  double fs_cfl;           /* first dt = fs_cfl * lh_dt_estimate(u); default 2 */
+  double dt0;              /* if > 0, the first dt instead (fs_cfl ignored); default 0 */
+  double grow, shrink;     /* dt factors; defaults 1.05 and 0.85 */
+  int grow_its;            /* <= this many Newton iterations: grow; default 1 */
+  int reject_its;          /* >= this many: reject; default 4 */
+  int enlarge;             /* 0: never grow dt (rejections still shrink it); default 1 */
+  int max_steps;           /* accepted steps at most; default 1000000 */
+  int max_attempts;        /* attempts (accepted or not) at most, <= 0: no limit; default 0 */
+  double dt_min;           /* LH_ENOCONV once the controller's dt falls below this; default 0 */
+} lh_advance_opts;
+
+typedef struct {           /* one attempt of the time loop */
+  double dt;               /* the controller's dt at the attempt */
+  double h;                /* the step taken (dt, or less for the last step) */
+  int newton_its;          /* largest stage Newton count, or -1 if the solve failed */
+  int accepted;
+} lh_advance_attempt;
+
+typedef struct {
+  int steps, rejected, attempts;
+  double t;                /* time reached (t_end unless a limit ended the loop) */
+  double dt_next;          /* the controller's dt after the last attempt */
+  long long newton_its, gmres_its;   /* totals over the accepted steps */
+} lh_advance_stats;
+
+void lh_advance_opts_init(lh_advance_opts* opts);
+
+/* Advance u from t = 0 to t_end (in place) with the control above.  u: device [n];
+ * k_prev: device [n] first initial guess on entry and the last accepted step's increment on
+ * exit, or NULL (zero first guess, kept internally).  nopts: the Newton-GMRES options of
+ * every stage solve (NULL: defaults).  hist: HOST array of hist_cap attempts (may be NULL);
+ * the first min(attempts, hist_cap) attempts are written.  Allocates 2 n doubles of trial
+ * state on the first call.  Synchronises.  Errors other than the rejectable solve failures
+ * end the loop and are returned with u at the last accepted step; LH_ENOCONV also if dt
+ * falls below dt_min. */
+lh_status lh_advance(lh_mesh* mesh, double* u, double* k_prev, double t_end, const lh_newton_opts* nopts,
+                     const lh_advance_opts* aopts, lh_advance_stats* stats, lh_advance_attempt* hist,
+                     int hist_cap);
+
+/* The same loop without a mesh (host only, no GPU): each attempt's Newton count is taken in
+ * order from counts[0 .. ncounts) (a negative entry: the solve failed; past the end: 2), the
+ * explicit estimate is dt_est.  Lets the controller be checked without solving anything. */
+lh_status lh_advance_replay(const int* counts, int ncounts, double dt_est, double t_end,
+                            const lh_advance_opts* aopts, lh_advance_stats* stats, lh_advance_attempt* hist,
+                            int hist_cap);
+
 /* The Butcher tableau lh_sdirk_step uses for a scheme (host only, no GPU): *stages = s, A:
  * HOST double[9] row-major 3 x 3 (entries beyond s x s are 0), b: HOST double[3].
  * LH_EINVAL for a scheme other than 2-4. */
@@ -381,6 +441,10 @@ lh_status lh_profile_read(lh_mesh* mesh, double* ms, long long* count);
  * 3: tangent from the linearisation record (reduced-precision J.w).
  * Needs no GPU.  *ops is a HOST pointer. */
 lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops);
+
+/* Floats per quadrature point in the linearisation record of lh_linearize (dim 2 or 3).
+ * Needs no GPU.  *len is a HOST pointer. */
+lh_status lh_record_len(int dim, int* len);
 
 /* Host check of the linearisation record: on `trials` random points near the undeformed
  * element (seeded), compares the tangent formed from the record (lin_record + the linear

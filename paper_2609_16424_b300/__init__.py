@@ -16,7 +16,8 @@ if not os.path.exists(_lib.LIB_PATH):
 
 lib = _lib.load()
 
-from .hydro import Mesh, LHError, probe_fma, newton_opts, launch_count  # noqa: E402
+from .hydro import Mesh, LHError, probe_fma, newton_opts, advance_opts, advance_replay, launch_count  # noqa: E402
 from .autograd import StageResidual  # noqa: E402
 
-__all__ = ["Mesh", "LHError", "probe_fma", "newton_opts", "launch_count", "StageResidual", "lib"]
+__all__ = ["Mesh", "LHError", "probe_fma", "newton_opts", "advance_opts", "advance_replay", "launch_count",
+           "StageResidual", "lib"]

@@ -13,8 +13,8 @@ STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "L
 # every symbol include/lh.h declares
 SYMBOLS = ["lh_mesh_desc_init", "lh_mesh_create", "lh_mesh_destroy", "lh_sizes", "lh_set_stream",
            "lh_initial_nodes", "lh_residual", "lh_jvp", "lh_jtvp", "lh_mass_apply", "lh_mass_solve",
-           "lh_dt_estimate", "lh_energies", "lh_tg_velocity_error", "lh_newton_opts_init", "lh_newton_step", "lh_stage_solve", "lh_sdirk_step", "lh_sdirk_tableau", "lh_last_error",
-           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_linearize", "lh_jvv_diagonal", "lh_qp_tangent_check", "lh_qp_adjoint_check", "lh_tc_status", "lh_tc_set_wait_polls", "lh_halo_len", "lh_halo_pack", "lh_halo_add", "lh_residual_noalloc", "lh_precond",
+           "lh_dt_estimate", "lh_energies", "lh_tg_velocity_error", "lh_newton_opts_init", "lh_newton_step", "lh_advance_opts_init", "lh_advance", "lh_advance_replay", "lh_stage_solve", "lh_sdirk_step", "lh_sdirk_tableau", "lh_last_error",
+           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_record_len", "lh_linearize", "lh_jvv_diagonal", "lh_qp_tangent_check", "lh_qp_adjoint_check", "lh_tc_status", "lh_tc_set_wait_polls", "lh_halo_len", "lh_halo_pack", "lh_halo_add", "lh_residual_noalloc", "lh_precond",
            "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_params", "lh_mlp_forward",
            "lh_mlp_grad", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_features", "lh_mlp_apply_prediction"]
 PROF_KINDS = ["residual", "jvp_fp64", "jvp_fp32", "jtvp", "mass_h1", "jvp_tc"]
@@ -43,6 +43,21 @@ class StepStats(C.Structure):
                 ("rfinal", C.c_double), ("min_detj", C.c_double), ("newton_its_max", C.c_int)]
 
 
+class AdvanceOpts(C.Structure):
+    _fields_ = [("scheme", C.c_int), ("fs_cfl", C.c_double), ("dt0", C.c_double), ("grow", C.c_double),
+                ("shrink", C.c_double), ("grow_its", C.c_int), ("reject_its", C.c_int), ("enlarge", C.c_int),
+                ("max_steps", C.c_int), ("max_attempts", C.c_int), ("dt_min", C.c_double)]
+
+
+class AdvanceAttempt(C.Structure):
+    _fields_ = [("dt", C.c_double), ("h", C.c_double), ("newton_its", C.c_int), ("accepted", C.c_int)]
+
+
+class AdvanceStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("rejected", C.c_int), ("attempts", C.c_int), ("t", C.c_double),
+                ("dt_next", C.c_double), ("newton_its", C.c_longlong), ("gmres_its", C.c_longlong)]
+
+
 def load(path=LIB_PATH):
     """Load liblh.so and declare the signatures.  Raises OSError if it is missing."""
     lib = C.CDLL(path)
@@ -67,6 +82,11 @@ def load(path=LIB_PATH):
         "lh_newton_opts_init": (None, [C.POINTER(NewtonOpts)]),
         "lh_newton_step": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(StepStats)]),
         "lh_stage_solve": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(StepStats)]),
+        "lh_advance_opts_init": (None, [C.POINTER(AdvanceOpts)]),
+        "lh_advance": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(AdvanceOpts), C.POINTER(AdvanceStats),
+                           C.POINTER(AdvanceAttempt), i]),
+        "lh_advance_replay": (i, [ip, i, d, d, C.POINTER(AdvanceOpts), C.POINTER(AdvanceStats),
+                                  C.POINTER(AdvanceAttempt), i]),
         "lh_sdirk_step": (i, [vp, i, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(StepStats)]),
         "lh_sdirk_tableau": (i, [i, ip, dp, dp]),
         "lh_last_error": (C.c_char_p, [vp]),
@@ -75,6 +95,7 @@ def load(path=LIB_PATH):
         "lh_profile_read": (i, [vp, dp, llp]),
         "lh_launch_count": (C.c_longlong, []),
         "lh_qp_flops": (i, [i, i, i, llp]),
+        "lh_record_len": (i, [i, ip]),
         "lh_linearize": (i, [vp, vp, vp, d]),
         "lh_tc_status": (i, [vp]),
         "lh_tc_set_wait_polls": (C.c_uint, [C.c_uint]),

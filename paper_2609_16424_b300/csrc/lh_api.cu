@@ -687,6 +687,7 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_fconst) cudaFree(m->d_fconst);
   if (m->d_rec) cudaFree(m->d_rec);
   if (m->d_stage) cudaFree(m->d_stage);
+  if (m->d_adv) cudaFree(m->d_adv);
   if (m->d_wscale) cudaFree(m->d_wscale);
   if (m->d_jdiag) cudaFree(m->d_jdiag);
   for (int a = 0; a < 3; ++a) {
@@ -1229,6 +1230,162 @@ lh_status lh_sdirk_step(lh_mesh* m, int scheme, double* u, double* k_prev, doubl
   if (k_prev) LH_CK(m, cudaMemcpyAsync(k_prev, K[T.s - 1], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   LH_CK(m, cudaStreamSynchronize(s));
   if (stats) *stats = acc;
+  return LH_OK;
+}
+
+}  // extern "C"
+
+// ---- time loop with the Newton-count step control of Sec. 4 -----------------------------
+namespace {
+
+bool check_advance_opts(const lh_advance_opts& a, std::string* why) {
+  if (a.scheme < 2 || a.scheme > 4) return *why = "scheme must be 2, 3 or 4", false;
+  if (!(a.grow >= 1.0) || !(a.shrink > 0.0 && a.shrink < 1.0)) return *why = "need grow >= 1, 0 < shrink < 1", false;
+  if (a.reject_its < 1 || a.grow_its >= a.reject_its) return *why = "need grow_its < reject_its, reject_its >= 1", false;
+  if (!(a.dt0 >= 0.0) || !(a.fs_cfl > 0.0 || a.dt0 > 0.0)) return *why = "need fs_cfl > 0 or dt0 > 0", false;
+  if (a.max_steps < 1) return *why = "max_steps must be >= 1", false;
+  return true;
+}
+
+// The loop itself, shared by lh_advance and lh_advance_replay.  step(h, &its, &gmres)
+// attempts a step of size h on trial storage and returns LH_OK (its = largest stage Newton
+// count), a rejectable failure (LH_ENOCONV, LH_ETANGLED, LH_ENONFINITE) or a fatal status;
+// commit() makes the trial state current.
+template <class Step, class Commit>
+lh_status advance_loop(double dt, double t_end, const lh_advance_opts& a, Step step, Commit commit,
+                       lh_advance_stats* out, lh_advance_attempt* hist, int hist_cap, std::string* why) {
+  lh_advance_stats S;
+  std::memset(&S, 0, sizeof(S));
+  lh_status ret = LH_OK;
+  const double t_tol = 1e-14 * std::fmax(1.0, std::fabs(t_end));
+  while (S.t < t_end - t_tol && S.steps < a.max_steps && (a.max_attempts <= 0 || S.attempts < a.max_attempts)) {
+    if (!(dt >= a.dt_min) || !(dt > 0.0)) {
+      *why = "time step control: dt fell below dt_min";
+      ret = LH_ENOCONV;
+      break;
+    }
+    const double h = std::fmin(dt, t_end - S.t);
+    int its = -1, gm = 0;
+    const lh_status st = step(h, &its, &gm);
+    if (st != LH_OK && st != LH_ENOCONV && st != LH_ETANGLED && st != LH_ENONFINITE) {
+      ret = st;
+      break;
+    }
+    if (st != LH_OK) its = -1;
+    const bool accepted = its >= 0 && its < a.reject_its;
+    if (hist && S.attempts < hist_cap) hist[S.attempts] = lh_advance_attempt{dt, h, its, accepted ? 1 : 0};
+    ++S.attempts;
+    if (!accepted) {
+      ++S.rejected;
+      dt *= a.shrink;
+      continue;
+    }
+    const lh_status cs = commit();
+    if (cs != LH_OK) {
+      ret = cs;
+      break;
+    }
+    S.t += h;
+    ++S.steps;
+    S.newton_its += its;
+    S.gmres_its += gm;
+    if (its <= a.grow_its && a.enlarge) dt *= a.grow;
+  }
+  S.dt_next = dt;
+  if (out) *out = S;
+  return ret;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lh_advance_opts_init(lh_advance_opts* a) {
+  if (!a) return;
+  std::memset(a, 0, sizeof(*a));
+  a->scheme = 2;
+  a->fs_cfl = 2.0;
+  a->grow = 1.05;
+  a->shrink = 0.85;
+  a->grow_its = 1;
+  a->reject_its = 4;
+  a->enlarge = 1;
+  a->max_steps = 1000000;
+}
+
+lh_status lh_advance(lh_mesh* m, double* u, double* k_prev, double t_end, const lh_newton_opts* nopts,
+                     const lh_advance_opts* aopts, lh_advance_stats* stats, lh_advance_attempt* hist, int hist_cap) {
+  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_advance");
+  if (!(t_end >= 0.0)) return fail(m, LH_EINVAL, "lh_advance: t_end must be >= 0");
+  lh_advance_opts a;
+  if (aopts) a = *aopts; else lh_advance_opts_init(&a);
+  std::string why;
+  if (!check_advance_opts(a, &why)) return fail(m, LH_EINVAL, "lh_advance: " + why);
+  lh_newton_opts o;
+  if (nopts) o = *nopts; else lh_newton_opts_init(&o);
+  lh_status st = check_newton_opts(m, o);
+  if (st != LH_OK) return st;
+  const long long n = m->n;
+  const size_t bytes = sizeof(double) * (size_t)n;
+  if (!m->d_adv && cudaMalloc(&m->d_adv, 3 * bytes) != cudaSuccess)
+    return fail(m, LH_ENOMEM, "cannot allocate the trial state of lh_advance");
+  cudaStream_t s = m->stream;
+  double* u_try = m->d_adv;
+  double* k_try = m->d_adv + n;
+  double* k_cur = k_prev ? k_prev : m->d_adv + 2 * n;
+  if (!k_prev) LH_CK(m, cudaMemsetAsync(k_cur, 0, bytes, s));
+  double dt = a.dt0;
+  if (!(dt > 0.0)) {
+    double est = 0.0;
+    if ((st = lh_dt_estimate(m, u, &est)) != LH_OK) return st;
+    dt = a.fs_cfl * est;
+  }
+  auto step = [&](double h, int* its, int* gm) -> lh_status {
+    if (cudaMemcpyAsync(u_try, u, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(k_try, k_cur, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(m, LH_ECUDA, "lh_advance: trial copy failed");
+    lh_step_stats S;
+    std::memset(&S, 0, sizeof(S));
+    const lh_status r = a.scheme == 2 ? lh_newton_step(m, u_try, k_try, h, &o, &S)
+                                      : lh_sdirk_step(m, a.scheme, u_try, k_try, h, &o, &S);
+    *its = S.newton_its_max;
+    *gm = S.gmres_its_total;
+    return r;
+  };
+  auto commit = [&]() -> lh_status {
+    if (cudaMemcpyAsync(u, u_try, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(k_cur, k_try, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(m, LH_ECUDA, "lh_advance: commit copy failed");
+    return LH_OK;
+  };
+  st = advance_loop(dt, t_end, a, step, commit, stats, hist, hist_cap, &why);
+  LH_CK(m, cudaStreamSynchronize(s));
+  if (st == LH_ENOCONV && !why.empty()) return fail(m, st, "lh_advance: " + why);
+  return st;
+}
+
+lh_status lh_advance_replay(const int* counts, int ncounts, double dt_est, double t_end,
+                            const lh_advance_opts* aopts, lh_advance_stats* stats, lh_advance_attempt* hist,
+                            int hist_cap) {
+  if ((ncounts > 0 && !counts) || ncounts < 0 || !(dt_est > 0.0) || !(t_end >= 0.0))
+    return set_global_error(LH_EINVAL, "lh_advance_replay: invalid argument");
+  lh_advance_opts a;
+  if (aopts) a = *aopts; else lh_advance_opts_init(&a);
+  std::string why;
+  if (!check_advance_opts(a, &why)) return set_global_error(LH_EINVAL, "lh_advance_replay: " + why);
+  int next = 0;
+  auto step = [&](double, int* its, int* gm) -> lh_status {
+    const int c = next < ncounts ? counts[next] : 2;
+    ++next;
+    *gm = 0;
+    if (c < 0) return LH_ENOCONV;
+    *its = c;
+    return LH_OK;
+  };
+  auto commit = []() -> lh_status { return LH_OK; };
+  const double dt = a.dt0 > 0.0 ? a.dt0 : a.fs_cfl * dt_est;
+  const lh_status st = advance_loop(dt, t_end, a, step, commit, stats, hist, hist_cap, &why);
+  if (st != LH_OK) return set_global_error(st, "lh_advance_replay: " + why);
   return LH_OK;
 }
 

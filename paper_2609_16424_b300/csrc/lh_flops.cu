@@ -103,6 +103,12 @@ long long count(int kind, bool visc) {
 
 }  // namespace
 
+extern "C" lh_status lh_record_len(int dim, int* len) {
+  if (!len || (dim != 2 && dim != 3)) return LH_EINVAL;
+  *len = dim == 2 ? lh::lin_len<2>() : lh::lin_len<3>();
+  return LH_OK;
+}
+
 extern "C" lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops) {
   if (!ops || (dim != 2 && dim != 3) || kind < 0 || kind > 3) return LH_EINVAL;
   *ops = dim == 2 ? count<2>(kind, visc != 0) : count<3>(kind, visc != 0);

@@ -85,6 +85,7 @@ struct lh_mesh {
   float* d_fconst = nullptr;       // [3 NE] float rho0 detJ0, gamma - 1, gamma (gamma - 1)
   float* d_rec = nullptr;          // linearisation record [NE][rec_len][NQ] (lazily allocated)
   double* d_stage = nullptr;       // SDIRK stage increments k_1..k_3 and stage base state [4 n] (lazily)
+  double* d_adv = nullptr;         // lh_advance trial state u, k and the internal increment [3 n] (lazily)
   double* d_wscale = nullptr;      // row weights of the scaled Newton norm [n] (lazily)
   double* d_jdiag = nullptr;       // diagonal of dR_v/dk_v for preconditioner kind 2 [dim NV] (lazily)
   const double* rec_u = nullptr;   // arguments of the last lh_linearize (for the LH_FP32_LIN check)

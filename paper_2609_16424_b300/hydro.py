@@ -39,6 +39,38 @@ def newton_opts(**kw):
     return o
 
 
+def advance_opts(**kw):
+    """lh_advance_opts with the library defaults, overridden by keyword arguments (scheme,
+    fs_cfl, dt0, grow, shrink, grow_its, reject_its, enlarge, max_steps, max_attempts, dt_min)."""
+    a = _lib.AdvanceOpts()
+    _L.lh_advance_opts_init(C.byref(a))
+    fields = {f for f, _ in _lib.AdvanceOpts._fields_}
+    for key, val in kw.items():
+        if key not in fields:
+            raise TypeError(f"unknown time-loop option {key!r}")
+        setattr(a, key, val)
+    return a
+
+
+def _attempts(hist, count):
+    return [(hist[i].dt, hist[i].h, None if hist[i].newton_its < 0 else hist[i].newton_its, bool(hist[i].accepted))
+            for i in range(count)]
+
+
+def advance_replay(counts, dt_est, t_end, hist_cap=100000, **kw):
+    """The time loop of Mesh.advance on the host with scripted Newton counts (None: a failed
+    solve), no mesh and no GPU (lh_advance_replay).  Returns (steps, rejected, attempts, t)."""
+    arr = (C.c_int * max(1, len(counts)))(*[-1 if c is None else int(c) for c in counts])
+    hist = (_lib.AdvanceAttempt * hist_cap)()
+    stats = _lib.AdvanceStats()
+    a = advance_opts(**kw)
+    st = _L.lh_advance_replay(arr, len(counts), float(dt_est), float(t_end), C.byref(a), C.byref(stats), hist,
+                              hist_cap)
+    if st != _lib.LH_OK:
+        raise LHError(st, _L.lh_last_error(None).decode())
+    return stats.steps, stats.rejected, _attempts(hist, min(stats.attempts, hist_cap)), stats.t
+
+
 def launch_count():
     """CUDA kernels launched by liblh.so in this process so far."""
     return int(_L.lh_launch_count())
@@ -281,46 +313,31 @@ class Mesh:
         self._check(_L.lh_profile_read(self._h, ms, cnt))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_lib.PROF_KINDS)}
 
-    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=100000, scheme=2, max_attempts=None, grow=True,
-                **kw):
+    def advance(self, u, t_end, fs_cfl=2.0, k=None, max_steps=1000000, scheme=2, max_attempts=None, grow=True,
+                hist_cap=None, **kw):
         """SDIRK steps (scheme 2: implicit midpoint, 3: SD3, 4: SD4) from t = 0 to t_end with
-        the Newton-count time step control of the paper's Sec. 4 ("Implicit time step
-        control"): the first dt is fs_cfl times the explicit estimate; after a step with <= 1
-        Newton iteration dt grows by 5%, with 2-3 it is kept, with >= 4 the step is rejected
-        and repeated with 0.85 dt (also after a failed solve).  A multi-stage step counts the
-        most iterations any of its stages took.  grow=False never enlarges dt (steps of
-        FS-CFL times the first estimate, reduced only by rejections).  u is advanced in
-        place; the loop also ends after max_attempts attempts (accepted or not), if given.
-        Returns (steps, rejected, attempts) with attempts = [(controller dt, step taken,
-        Newton iterations or None, accepted)]."""
-        k = torch.zeros_like(u) if k is None else k
-        dt = fs_cfl * self.dt_estimate(u)
-        t, steps, rejected, hist = 0.0, 0, 0, []
-        while t < t_end - 1e-14 * max(1.0, t_end) and steps < max_steps and (
-                max_attempts is None or len(hist) < max_attempts):
-            h = min(dt, t_end - t)
-            u_try, k_try = u.clone(), k.clone()
-            try:
-                if scheme == 2:
-                    st = self.newton_step(u_try, k_try, h, **kw)
-                else:
-                    st = self.sdirk_step(u_try, k_try, h, scheme=scheme, **kw)
-                its = st["newton_its_max"]
-            except LHError:
-                its = None
-            if its is None or its >= 4:
-                hist.append((dt, h, its, False))
-                rejected += 1
-                dt = 0.85 * dt
-                continue
-            hist.append((dt, h, its, True))
-            u.copy_(u_try)
-            k.copy_(k_try)
-            t += h
-            steps += 1
-            if its <= 1 and grow:
-                dt = 1.05 * dt
-        return steps, rejected, hist
+        the Newton-count time step control of the paper's Sec. 4, run by lh_advance: the first
+        dt is fs_cfl times the explicit estimate; after a step with <= 1 Newton iteration dt
+        grows by 5%, with 2-3 it is kept, with >= 4 the step is rejected and repeated with
+        0.85 dt (also after a failed solve).  A multi-stage step counts the most iterations
+        any of its stages took.  grow=False never enlarges dt.  u (and k, the first initial
+        guess, if given) advance in place; the loop also ends after max_attempts attempts.
+        kw: Newton-GMRES options.  Returns (steps, rejected, attempts) with attempts =
+        [(controller dt, step taken, Newton iterations or None, accepted)]."""
+        self._vec(u, "u")
+        if k is not None:
+            self._vec(k, "k")
+        a = advance_opts(scheme=scheme, fs_cfl=fs_cfl, enlarge=int(bool(grow)), max_steps=max_steps,
+                         max_attempts=max_attempts or 0)
+        cap = hist_cap or (max_attempts or 100000)
+        hist = (_lib.AdvanceAttempt * cap)()
+        stats = _lib.AdvanceStats()
+        o = newton_opts(**kw)
+        self._stream()
+        st = _L.lh_advance(self._h, _ptr(u), _ptr(k) if k is not None else None, float(t_end), C.byref(o),
+                           C.byref(a), C.byref(stats), hist, cap)
+        self._check(st)
+        return stats.steps, stats.rejected, _attempts(hist, min(stats.attempts, cap))
 
     def newton_step(self, u, k_prev, dt, opts=None, **kw):
         """One implicit midpoint step in place on u (and k_prev, if given).  Returns the

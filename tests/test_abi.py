@@ -40,6 +40,11 @@ int main(void) {
   printf("%zu %zu\n", sizeof(lh_newton_opts), offsetof(lh_newton_opts, jvp_prec));
   printf("%zu %zu %zu\n", sizeof(lh_step_stats), offsetof(lh_step_stats, min_detj),
          offsetof(lh_step_stats, newton_its_max));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lh_advance_opts), offsetof(lh_advance_opts, dt0),
+         offsetof(lh_advance_opts, max_attempts), offsetof(lh_advance_opts, dt_min), sizeof(lh_advance_attempt),
+         offsetof(lh_advance_attempt, accepted));
+  printf("%zu %zu %zu\n", sizeof(lh_advance_stats), offsetof(lh_advance_stats, t),
+         offsetof(lh_advance_stats, gmres_its));
   return 0;
 }
 ''')
@@ -53,6 +58,10 @@ int main(void) {
     assert [int(x) for x in out[1].split()] == [C.sizeof(N), N.jvp_prec.offset]
     S = _lib.StepStats
     assert [int(x) for x in out[2].split()] == [C.sizeof(S), S.min_detj.offset, S.newton_its_max.offset]
+    A, H, T = _lib.AdvanceOpts, _lib.AdvanceAttempt, _lib.AdvanceStats
+    assert [int(x) for x in out[3].split()] == [C.sizeof(A), A.dt0.offset, A.max_attempts.offset, A.dt_min.offset,
+                                                 C.sizeof(H), H.accepted.offset]
+    assert [int(x) for x in out[4].split()] == [C.sizeof(T), T.t.offset, T.gmres_its.offset]
 
 
 def test_defaults_and_argument_checks_without_gpu():
@@ -82,14 +91,17 @@ def test_defaults_and_argument_checks_without_gpu():
 
 
 @pytest.mark.parametrize("fn", ["lh_residual", "lh_jvp", "lh_jtvp", "lh_newton_step", "lh_stage_solve",
-                                "lh_sdirk_step", "lh_jvv_diagonal", "lh_tg_velocity_error"])
+                                "lh_sdirk_step", "lh_jvv_diagonal", "lh_tg_velocity_error", "lh_advance"])
 def test_null_mesh_is_rejected(fn):
     import paper_2609_16424_b300 as lh
     f = getattr(lh.lib, fn)
     nargs = len(f.argtypes)
     args = [None] * nargs
-    if fn in ("lh_residual", "lh_jvp", "lh_jtvp", "lh_newton_step", "lh_stage_solve", "lh_jvv_diagonal"):
+    if fn in ("lh_residual", "lh_jvp", "lh_jtvp", "lh_newton_step", "lh_stage_solve", "lh_jvv_diagonal",
+              "lh_advance"):
         args[3] = 0.1
+    if fn == "lh_advance":
+        args[8] = 0
     if fn == "lh_sdirk_step":
         args[1], args[4] = 3, 0.1
     if fn in ("lh_jvp", "lh_jtvp"):
