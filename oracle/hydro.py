@@ -33,7 +33,8 @@ class Params:
     """Physical and model parameters (defaults from Sec. 3.4)."""
 
     def __init__(self, mesh, rho0=1.0, gamma=1.4, visc=True, q1=0.5, q2=1.0, psi0=0.5,
-                 eps_e=1e-6, h0=None, h_coarse=None, bc_mask=None, tg_source=False):
+                 eps_e=1e-6, h0=None, h_coarse=None, bc_mask=None, tg_source=False,
+                 visc_model='imp', q1_exp=0.5, q2_exp=2.0, vorticity=False):
         ne = mesh.NE
         self.rho0 = np.broadcast_to(np.asarray(rho0, dtype=float), (ne,)).copy()
         self.gamma = np.broadcast_to(np.asarray(gamma, dtype=float), (ne,)).copy()
@@ -44,6 +45,13 @@ class Params:
         self.h_coarse = float(h_coarse) if h_coarse else self.h0
         self.bc_mask = (1 << (2 * mesh.d)) - 1 if bc_mask is None else int(bc_mask)
         self.tg_source = bool(tg_source)
+        # the original tensor viscosity mu_exp (Sec. 3.4) for explicit runs: 'exp'
+        if visc_model not in ('imp', 'exp'):
+            raise ValueError("visc_model must be 'imp' or 'exp'")
+        self.visc_model = visc_model
+        self.q1_exp, self.q2_exp = float(q1_exp), float(q2_exp)
+        self.l0_exp = self.h0 / mesh.k
+        self.vorticity = bool(vorticity)
 
 
 def det(J):
@@ -74,7 +82,7 @@ def inv(J):
     return A / dt[..., None, None]
 
 
-def stress(grad_v, detJ, rho, e, gamma, prm, d):
+def stress(grad_v, detJ, rho, e, gamma, prm, d, return_mu=False):
     """Total stress sigma = -p I + mu_imp eps(v) at quadrature points (Sec. 3.4).
 
     grad_v: physical velocity gradient [..., d, d] ((grad v)_{cb} = dv_c/dx_b);
@@ -91,6 +99,7 @@ def stress(grad_v, detJ, rho, e, gamma, prm, d):
     c_s = np.sqrt(gamma * (gamma - 1.0) * e_plus)
     eye = np.eye(d)
     sigma = -p[..., None, None] * eye
+    mu = np.zeros_like(p)
     if prm.visc:
         # Eq. (14): isotropic current length scale by volume scaling
         h = prm.h0 * (detJ / prm.detJ0) ** (1.0 / d)
@@ -108,7 +117,46 @@ def stress(grad_v, detJ, rho, e, gamma, prm, d):
         # Eq. (11): sigma_a = mu eps(v), eps(v) = sym(grad v)
         eps_v = 0.5 * (grad_v + np.swapaxes(grad_v, -1, -2))
         sigma = sigma + mu[..., None, None] * eps_v
-    return sigma
+    return (sigma, mu) if return_mu else sigma
+
+
+def stress_exp(grad_v, J, J0inv, rho, e, gamma, prm, d, return_mu=False):
+    """Total stress sigma = -p I + mu_exp eps(v) with the original tensor viscosity (Sec. 3.4,
+    the equation for mu_exp; its ingredients are defined in Dobrev et al. 2012, Sec. 6.2,
+    which the paper cites and does not print; the readings here):
+
+      (lambda_1, s_1): smallest eigenvalue of eps(v) and its unit eigenvector;
+      l = l0 |J J0^{-1} s_1|: the initial length l0 = h0 / k carried by the deformation
+          (J J0^{-1} = dx / dx0) along s_1;
+      psi_1 = 1 if lambda_1 < 0 (compression) else 0;
+      psi_0 = 1, or |div v| / (sqrt(d) |grad v|_F) in [0, 1] with the vorticity switch on
+          (1 for isotropic compression, 0 for divergence-free flow);
+      mu_exp = rho (q2 l^2 |lambda_1| + q1 psi_1 psi_0 l c_s).
+
+    e+, p and c_s as in Eqs. (19)-(20).  grad_v, J, J0inv: [..., d, d]; rho, e, gamma: [...].
+    Real arithmetic only (the eigen-decomposition is not analytic)."""
+    root = np.sqrt(e * e + prm.eps_e ** 2)
+    e_plus = np.where(e < 0, 0.5 * prm.eps_e ** 2 / np.where(e < 0, root - e, 1.0), 0.5 * (e + root))
+    p = (gamma - 1.0) * rho * e_plus
+    c_s = np.sqrt(gamma * (gamma - 1.0) * e_plus)
+    sigma = -p[..., None, None] * np.eye(d)
+    if not prm.visc:
+        return (sigma, np.zeros_like(p)) if return_mu else sigma
+    eps_v = 0.5 * (grad_v + np.swapaxes(grad_v, -1, -2))
+    lam, vec = np.linalg.eigh(eps_v)                  # ascending eigenvalues
+    lam1, s1 = lam[..., 0], vec[..., :, 0]
+    Fd = np.einsum('...ij,...jk->...ik', J, J0inv)
+    ell = prm.l0_exp * np.linalg.norm(np.einsum('...ij,...j->...i', Fd, s1), axis=-1)
+    psi1 = (lam1 < 0).astype(float)
+    if prm.vorticity:
+        gnorm = np.sqrt(np.sum(grad_v * grad_v, axis=(-2, -1)))
+        psi0 = np.where(gnorm > 0, np.abs(np.trace(grad_v, axis1=-2, axis2=-1))
+                        / (np.sqrt(d) * np.where(gnorm > 0, gnorm, 1.0)), 1.0)
+    else:
+        psi0 = 1.0
+    mu = rho * (prm.q2_exp * ell ** 2 * np.abs(lam1) + prm.q1_exp * psi1 * psi0 * ell * c_s)
+    sigma = sigma + mu[..., None, None] * eps_v
+    return (sigma, mu) if return_mu else sigma
 
 
 def tg_source(xq):
@@ -131,6 +179,7 @@ class Hydro:
         x0 = mesh.initial_nodes()
         J0 = np.einsum('ecn,qrn->eqcr', mesh.gather(x0), mesh.Gh)
         self.detJ0 = det(J0)                                 # [NE, NQ]
+        self.J0inv = inv(J0)
         prm.detJ0 = self.detJ0
         # rho |J| is conserved pointwise: rho alpha detJ = rho0 alpha detJ0 (Sec. 2.1)
         self.mq = prm.rho0[:, None] * mesh.alpha[None, :] * self.detJ0   # [NE, NQ]
@@ -197,7 +246,10 @@ class Hydro:
         """
         m = self.m
         J, detJ, gradw, grad_v, eq, rho = self.qp_state(x, v, e)
-        sigma = stress(grad_v, detJ, rho, eq, self.p.gamma[:, None], self.p, m.d)
+        if self.p.visc_model == 'exp':
+            sigma = stress_exp(grad_v, J, self.J0inv, rho, eq, self.p.gamma[:, None], self.p, m.d)
+        else:
+            sigma = stress(grad_v, detJ, rho, eq, self.p.gamma[:, None], self.p, m.d)
         # sigma : grad w_{c,a} = sum_b sigma_{cb} (grad w_a)_b for the vector basis w_a e_c
         sig_gw = np.einsum('eqcb,eqbn->eqcn', sigma, gradw)
         dx = m.alpha[None, :] * detJ                              # current-domain weights
