@@ -939,6 +939,46 @@ def run_tg_table(args):
             "runs": rows}
 
 
+def run_accuracy_per_time(args):
+    """Accuracy per unit run time on the 2D Taylor-Green vortex (p0 = 1, t = 0.5; the paper's
+    Sec. 4.1 table): explicit RK2-average / SSP RK3 / RK4 at CFL args.xcfl of the explicit
+    estimate (with the explicit step control) against the implicit SD2 / SD3 / SD4 at FS-CFL
+    args.icfl with the Newton-count control, for Q2-Q1 / Q3-Q2 / Q4-Q3 on h = 1/16 .. 1/128.
+    No viscosity (the paper sets it to zero for this problem).  L1 velocity error, steps and
+    wall time of each run; both paths run on the GPU."""
+    import torch
+    from paper_2609_16424_b300.states import taylor_green_problem
+    torch.cuda.set_device(0)
+    rows, t_start = [], time.perf_counter()
+    for k in args.tg_orders:
+        for inv_h in args.tg_h:
+            for path in ("explicit", "implicit"):
+                if time.perf_counter() - t_start > args.tg_budget:
+                    rows.append({"k": k, "inv_h": inv_h, "path": path, "status": "skipped (time budget)"})
+                    continue
+                mesh, u = taylor_green_problem(inv_h, k, p0=1.0, device="cuda:0")
+                torch.cuda.synchronize()
+                w0 = time.perf_counter()
+                if path == "explicit":
+                    st = mesh.explicit_advance(u, 0.5, cfl=args.xcfl, scheme=k, visc_model="imp")
+                    steps, rejected = st["steps"], st["rejected"]
+                else:
+                    steps, rejected, _ = mesh.advance(u, 0.5, fs_cfl=args.icfl, scheme=k, jvp_prec=args.prec,
+                                                      **dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol))
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - w0
+                rows.append({"k": k, "inv_h": inv_h, "path": path,
+                             "scheme": (f"RK{k}" if path == "explicit" else f"SD{k}"), "n_unknowns": mesh.n,
+                             "l1_error": mesh.tg_velocity_error(u), "steps": steps, "rejected": rejected,
+                             "wall_s": round(wall, 4), "paper": PAPER_TG.get((k, 2.0, inv_h)) if path == "implicit"
+                             else None})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                del mesh, u
+    return {"metric": "Taylor-Green L1 error vs wall time, explicit RK vs implicit SDIRK (GPU)",
+            "explicit_cfl": args.xcfl, "implicit_fs_cfl": args.icfl, "jvp_prec": args.prec,
+            "newton": dict(TG_NEWTON, newton_rtol=args.tg_newton_rtol), "runs": rows}
+
+
 def run_precond_compare(args):
     """Velocity-block preconditioners of the Newton-GMRES step (FP32 J.w, Newton rtol 1e-5,
     GMRES 1e-4): the exact mass inverse (kron, the benchmark's), the Jacobi of M_V alone
@@ -1041,6 +1081,10 @@ def main():
                     help="three-state interface problem, 50 steps at 10x explicit dt")
     ap.add_argument("--t-end", type=float, default=0.1)
     ap.add_argument("--precond-compare", action="store_true", help="velocity-block preconditioners")
+    ap.add_argument("--accuracy-per-time", action="store_true",
+                    help="Taylor-Green: explicit RK vs implicit SDIRK, error and wall time")
+    ap.add_argument("--xcfl", type=float, default=0.5, help="explicit CFL (of the explicit estimate)")
+    ap.add_argument("--icfl", type=float, default=8.0, help="implicit FS-CFL (of the explicit estimate)")
     ap.add_argument("--tg-table", action="store_true", help="Taylor-Green convergence table, SD2/SD3/SD4")
     ap.add_argument("--tg-orders", type=int, nargs="+", default=[2, 3, 4])
     ap.add_argument("--tg-cfl", type=float, nargs="+", default=[8.0, 2.0])
@@ -1068,6 +1112,8 @@ def main():
         out = run_tg_table(args)
     elif args.precond_compare:
         out = run_precond_compare(args)
+    elif args.accuracy_per_time:
+        out = run_accuracy_per_time(args)
     elif args.impl == "reference":
         out = run_reference(args, rank)
     else:

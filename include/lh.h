@@ -153,8 +153,9 @@ unsigned lh_tc_set_wait_polls(unsigned polls);
 /* Linearisation record (partial assembly of the tangent, paper Sec. 2.2: store the
  * quadrature-point data once, reuse it for every action): evaluates the residual at
  * w = u + tau k in FP64 and keeps, rounded to float, the linearisation of the
- * quadrature-point map at every point ([NE][31 (3D) or 24 (2D)][quadrature points]:
- * J^-1, grad v, and the scalars of the pressure and viscosity chain of Eqs. (11)-(20)).
+ * quadrature-point map at every point ([NE][25 (3D) or 18 (2D)][quadrature points]:
+ * J^-1, grad v, and the pressure and linearised viscosity scalars of Eqs. (11)-(20): W, p,
+ * dp/de, mu and the three coefficients of dmu in theta = d detJ / detJ, d(div v) and de).
  * Later lh_jvp calls with LH_FP32_LIN, LH_TF32 or LH_BF16 and the same u, k (pointers)
  * and tau apply the linearised map instead of re-evaluating the point kernel.
  * lh_newton_step with a reduced-precision J.w writes the record at every Newton iterate
@@ -354,6 +355,68 @@ lh_status lh_advance(lh_mesh* mesh, double* u, double* k_prev, double t_end, con
 lh_status lh_advance_replay(const int* counts, int ncounts, double dt_est, double t_end,
                             const lh_advance_opts* aopts, lh_advance_stats* stats, lh_advance_attempt* hist,
                             int hist_cap);
+
+/* ---- Explicit path: the paper's comparison method (Sec. 2.2, Sec. 4.1: ORIG-E / dFEM-E)
+ * Eqs. (6a)-(6b) integrated explicitly: M_V dv/dt = -F.1 (dv/dt = 0 on fixed rows),
+ * M_E de/dt = F^T v + b, dx/dt = v, with F's quadrature data formed once per stage and
+ * applied twice (Sec. 2.2).  M_V is inverted by conjugate gradients preconditioned with the
+ * Kronecker-product inverse of lh_precond kind 1 (exact for uniform rho0, so a few
+ * iterations reach rounding); M_E^-1 is exact.  Viscosity: the smooth mu_imp of Eqs.
+ * (13)-(18) (visc_model 0) or the original tensor viscosity mu_exp of Sec. 3.4 (visc_model
+ * 1; the paper defers its ingredients to Dobrev et al. 2012, Sec. 6.2; readings:
+ * mu = rho (q2 l^2 |lambda_1| + q1 psi_1 psi_0 l c_s), (lambda_1, s_1) the smallest
+ * eigenpair of eps(v), l = l0 |J J0^-1 s_1|, psi_1 = [lambda_1 < 0], psi_0 = 1 or, with
+ * the vorticity switch, |div v| / (sqrt(dim) |grad v|_F)).  Integrators (Sec. 4.1; the
+ * schemes are defined in Dobrev et al. 2012, Sec. 7.1): scheme 2 = RK2-average
+ *   v_h = v + dt/2 a(U), e_h = e + dt/2 g(U, v_h), x_h = x + dt/2 v_h;
+ *   v' = v + dt a(U_h), vbar = (v + v') / 2, e' = e + dt g(U_h, vbar), x' = x + dt vbar
+ * with a = -M_V^-1 F.1 and g(U, w) = M_E^-1 (F(U)^T w + b) (total energy changes by
+ * exactly dt 1^T b per step); 3 = SSP RK3 (Shu-Osher); 4 = classical RK4, both on
+ * dU/dt = (v, a(U), g(U, v)).  All in FP64. */
+typedef struct {
+  int scheme;              /* 2 = RK2-average, 3 = RK3 SSP, 4 = RK4; default 2 */
+  int visc_model;          /* 0 = mu_imp (the mesh's q1, q2, psi0), 1 = mu_exp; default 1 */
+  double q1_exp, q2_exp;   /* mu_exp coefficients; defaults 0.5 and 2 */
+  double l0_exp;           /* mu_exp initial length l0; 0 = h0 / order (default) */
+  int vorticity;           /* mu_exp vorticity switch psi_0; default 0 (psi_0 = 1) */
+  double cfl;              /* lh_explicit_advance: dt = cfl x the explicit estimate; default 0.5 */
+  double mass_rtol;        /* relative tolerance of the M_V solves; default 1e-13 */
+  int mass_maxit;          /* CG iterations per M_V solve at most; default 200 */
+} lh_explicit_opts;
+
+typedef struct {
+  int steps, rejected;     /* accepted / repeated steps (lh_explicit_advance) */
+  double t;                /* time reached */
+  double dt_last;          /* the controller's dt after the last step */
+  long long force_evals;   /* evaluations of F's quadrature data */
+  long long mass_iters;    /* CG iterations over all M_V solves */
+} lh_explicit_stats;
+
+void lh_explicit_opts_init(lh_explicit_opts* opts);
+
+/* F's two applications at state u (device [n]): f1 = F(u).1 (device [dim N_V], every row
+ * assembled, fixed rows included) and ftw = F(u)^T w + b (device [N_E]; w: device [dim N_V]
+ * velocity field, or NULL for the velocity of u; b the Taylor-Green source if enabled).
+ * Either output may be NULL.  dt_est (HOST, may be NULL; then no synchronisation): the
+ * explicit estimate min_q h_min / (c_s + mu / (rho h_min)) of lh_dt_estimate with the
+ * viscosity model of opts.  Allocates the explicit work arrays on first use. */
+lh_status lh_force(lh_mesh* mesh, const double* u, const double* w, const lh_explicit_opts* opts, double* f1,
+                   double* ftw, double* dt_est);
+
+/* One explicit step of size dt in place on u (device [n]).  Synchronises.  LH_ENOCONV if a
+ * mass solve did not reach mass_rtol (u is then unchanged); LH_ENONFINITE if the new state is
+ * not finite (u unchanged). */
+lh_status lh_explicit_step(lh_mesh* mesh, double* u, double dt, const lh_explicit_opts* opts,
+                           lh_explicit_stats* stats);
+
+/* Explicit run from t = 0 to t_end in place on u with the step control of the explicit
+ * method (reading of Dobrev et al. 2012, Sec. 7.3, which the paper cites): the first dt is
+ * cfl x the estimate at u; after each step the estimate at the new state (cfl x) is
+ * compared with the step taken: below it, the step is repeated with 0.85 dt; above 1.25 dt,
+ * the next dt is 1.02 dt.  The last step is clipped to reach t_end.  max_steps bounds the
+ * accepted steps.  Synchronises. */
+lh_status lh_explicit_advance(lh_mesh* mesh, double* u, double t_end, int max_steps, const lh_explicit_opts* opts,
+                              lh_explicit_stats* stats);
 
 /* The Butcher tableau lh_sdirk_step uses for a scheme (host only, no GPU): *stages = s, A:
  * HOST double[9] row-major 3 x 3 (entries beyond s x s are 0), b: HOST double[3].

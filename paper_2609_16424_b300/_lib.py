@@ -13,7 +13,8 @@ STATUS_NAMES = {0: "LH_OK", 1: "LH_EINVAL", 2: "LH_ECUDA", 3: "LH_ENOMEM", 4: "L
 # every symbol include/lh.h declares
 SYMBOLS = ["lh_mesh_desc_init", "lh_mesh_create", "lh_mesh_destroy", "lh_sizes", "lh_set_stream",
            "lh_initial_nodes", "lh_residual", "lh_jvp", "lh_jtvp", "lh_mass_apply", "lh_mass_solve",
-           "lh_dt_estimate", "lh_energies", "lh_tg_velocity_error", "lh_newton_opts_init", "lh_newton_step", "lh_advance_opts_init", "lh_advance", "lh_advance_replay", "lh_stage_solve", "lh_sdirk_step", "lh_sdirk_tableau", "lh_last_error",
+           "lh_dt_estimate", "lh_energies", "lh_tg_velocity_error", "lh_newton_opts_init", "lh_newton_step", "lh_advance_opts_init", "lh_advance", "lh_advance_replay",
+           "lh_explicit_opts_init", "lh_force", "lh_explicit_step", "lh_explicit_advance", "lh_stage_solve", "lh_sdirk_step", "lh_sdirk_tableau", "lh_last_error",
            "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_record_len", "lh_linearize", "lh_jvv_diagonal", "lh_qp_tangent_check", "lh_qp_adjoint_check", "lh_tc_status", "lh_tc_set_wait_polls", "lh_halo_len", "lh_halo_pack", "lh_halo_add", "lh_residual_noalloc", "lh_precond",
            "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_params", "lh_mlp_forward",
            "lh_mlp_grad", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_features", "lh_mlp_apply_prediction"]
@@ -58,6 +59,17 @@ class AdvanceStats(C.Structure):
                 ("dt_next", C.c_double), ("newton_its", C.c_longlong), ("gmres_its", C.c_longlong)]
 
 
+class ExplicitOpts(C.Structure):
+    _fields_ = [("scheme", C.c_int), ("visc_model", C.c_int), ("q1_exp", C.c_double), ("q2_exp", C.c_double),
+                ("l0_exp", C.c_double), ("vorticity", C.c_int), ("cfl", C.c_double), ("mass_rtol", C.c_double),
+                ("mass_maxit", C.c_int)]
+
+
+class ExplicitStats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("rejected", C.c_int), ("t", C.c_double), ("dt_last", C.c_double),
+                ("force_evals", C.c_longlong), ("mass_iters", C.c_longlong)]
+
+
 def load(path=LIB_PATH):
     """Load liblh.so and declare the signatures.  Raises OSError if it is missing."""
     lib = C.CDLL(path)
@@ -83,6 +95,10 @@ def load(path=LIB_PATH):
         "lh_newton_step": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(StepStats)]),
         "lh_stage_solve": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(StepStats)]),
         "lh_advance_opts_init": (None, [C.POINTER(AdvanceOpts)]),
+        "lh_explicit_opts_init": (None, [C.POINTER(ExplicitOpts)]),
+        "lh_force": (i, [vp, vp, vp, C.POINTER(ExplicitOpts), vp, vp, dp]),
+        "lh_explicit_step": (i, [vp, vp, d, C.POINTER(ExplicitOpts), C.POINTER(ExplicitStats)]),
+        "lh_explicit_advance": (i, [vp, vp, d, i, C.POINTER(ExplicitOpts), C.POINTER(ExplicitStats)]),
         "lh_advance": (i, [vp, vp, vp, d, C.POINTER(NewtonOpts), C.POINTER(AdvanceOpts), C.POINTER(AdvanceStats),
                            C.POINTER(AdvanceAttempt), i]),
         "lh_advance_replay": (i, [ip, i, d, d, C.POINTER(AdvanceOpts), C.POINTER(AdvanceStats),

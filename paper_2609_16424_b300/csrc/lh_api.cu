@@ -688,6 +688,7 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_rec) cudaFree(m->d_rec);
   if (m->d_stage) cudaFree(m->d_stage);
   if (m->d_adv) cudaFree(m->d_adv);
+  if (m->d_xwork) cudaFree(m->d_xwork);
   if (m->d_wscale) cudaFree(m->d_wscale);
   if (m->d_jdiag) cudaFree(m->d_jdiag);
   for (int a = 0; a < 3; ++a) {
@@ -1231,6 +1232,299 @@ lh_status lh_sdirk_step(lh_mesh* m, int scheme, double* u, double* k_prev, doubl
   LH_CK(m, cudaStreamSynchronize(s));
   if (stats) *stats = acc;
   return LH_OK;
+}
+
+}  // extern "C"
+
+// ---- explicit path ------------------------------------------------------------------------
+namespace {
+
+bool check_explicit_opts(const lh_explicit_opts& o, std::string* why) {
+  if (o.scheme < 2 || o.scheme > 4) return *why = "scheme must be 2, 3 or 4", false;
+  if (o.visc_model != 0 && o.visc_model != 1) return *why = "visc_model must be 0 or 1", false;
+  if (!(o.q1_exp >= 0.0) || !(o.q2_exp >= 0.0) || !(o.l0_exp >= 0.0)) return *why = "negative mu_exp parameter", false;
+  if (!(o.cfl > 0.0)) return *why = "cfl must be > 0", false;
+  if (!(o.mass_rtol > 0.0) || o.mass_maxit < 1) return *why = "need mass_rtol > 0, mass_maxit >= 1", false;
+  return true;
+}
+
+lh::ExpC exp_consts(const lh_mesh* m, const lh_explicit_opts& o) {
+  lh::ExpC X;
+  X.l0 = o.l0_exp > 0.0 ? o.l0_exp : m->P.h0 / m->P.K;
+  X.q1 = o.q1_exp;
+  X.q2 = o.q2_exp;
+  for (int c = 0; c < 3; ++c) X.inv_h[c] = 1.0 / m->P.h[c];
+  X.vorticity = o.vorticity;
+  return X;
+}
+
+// explicit work arrays (lazily): S [NQ dim^2], f1, a, w1, w2, p, Ap [dim NV each],
+// fe, de, b [NEd each], r_full, z_full, U_i, u_save, K_1..K_4 [n each]
+struct XWork {
+  double *Sq, *f1, *a, *w1, *w2, *p, *Ap, *fe, *de, *b, *rf, *zf, *Ui, *usave, *K[4];
+};
+
+lh_status xwork(lh_mesh* m, XWork* W) {
+  const long long n = m->n, n1 = (long long)m->P.dim * m->P.NV, ne = m->P.NEd;
+  const long long nsq = m->NQ * m->P.dim * m->P.dim;
+  const long long need = nsq + 6 * n1 + 3 * ne + 8 * n;
+  if (!m->d_xwork) {
+    if (cudaMalloc(&m->d_xwork, sizeof(double) * (size_t)need) != cudaSuccess)
+      return fail(m, LH_ENOMEM, "cannot allocate the explicit work arrays");
+  }
+  double* q = m->d_xwork;
+  W->Sq = q; q += nsq;
+  W->f1 = q; q += n1;
+  W->a = q; q += n1;
+  W->w1 = q; q += n1;
+  W->w2 = q; q += n1;
+  W->p = q; q += n1;
+  W->Ap = q; q += n1;
+  W->fe = q; q += ne;
+  W->de = q; q += ne;
+  W->b = q; q += ne;
+  W->rf = q; q += n;
+  W->zf = q; q += n;
+  W->Ui = q; q += n;
+  W->usave = q; q += n;
+  for (int i = 0; i < 4; ++i) { W->K[i] = q; q += n; }
+  return LH_OK;
+}
+
+// F's point data and F.1 at u (and b); with est non-NULL also the explicit estimate (sync)
+lh_status x_force(lh_mesh* m, const lh_explicit_opts& o, const XWork& W, const double* u, double* est,
+                  lh_explicit_stats* S) {
+  const lh::ExpC X = exp_consts(m, o);
+  LH_CK(m, launch_force(m->P, m->stream, o.visc_model, X, u, W.Sq, m->d_ev, W.f1, m->P.tg ? W.b : nullptr,
+                        est ? m->d_blockmin : nullptr));
+  if (S) ++S->force_evals;
+  if (est) {
+    LH_CK(m, launch_min(m->stream, m->d_blockmin, m->nblocks_elem, m->d_scalar + 2));
+    LH_CK(m, cudaMemcpyAsync(est, m->d_scalar + 2, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    LH_CK(m, cudaStreamSynchronize(m->stream));
+  }
+  return LH_OK;
+}
+
+// a = -M_V^-1 f1 on free rows (0 on fixed rows): CG preconditioned with the Kronecker
+// inverse (lh_precond kind 1 applied to a state-shaped vector whose x and e rows are zero)
+lh_status x_accel(lh_mesh* m, const lh_explicit_opts& o, const XWork& W, lh_explicit_stats* S) {
+  cudaStream_t s = m->stream;
+  const long long n = m->n, n1 = (long long)m->P.dim * m->P.NV;
+  double* r = W.rf + n1;
+  double* z = W.zf + n1;
+  LH_CK(m, cudaMemsetAsync(W.rf, 0, sizeof(double) * n, s));
+  LH_CK(m, launch_axpby(s, -1.0, W.f1, 0.0, r, n1));
+  LH_CK(m, launch_copy_fixed(m->P, s, nullptr, r));
+  LH_CK(m, cudaMemsetAsync(W.a, 0, sizeof(double) * n1, s));
+  double bb, rz, pAp, rr;
+  lh_status st;
+  if ((st = dot_host(m, r, r, n1, &bb)) != LH_OK) return st;
+  if (bb == 0.0) return LH_OK;
+  LH_CK(m, (launch_prec<double, double>(1, s, m->P, m->kron, m->d_diagMv, m->d_invMe, W.rf, W.zf, 0.0)));
+  LH_CK(m, cudaMemcpyAsync(W.p, z, sizeof(double) * n1, cudaMemcpyDeviceToDevice, s));
+  if ((st = dot_host(m, r, z, n1, &rz)) != LH_OK) return st;
+  for (int it = 0; it < o.mass_maxit; ++it) {
+    LH_CK(m, launch_mass_h1(m->P, s, W.p, m->d_ev, W.Ap));
+    LH_CK(m, launch_copy_fixed(m->P, s, W.p, W.Ap));
+    if ((st = dot_host(m, W.p, W.Ap, n1, &pAp)) != LH_OK) return st;
+    const double alpha = rz / pAp;
+    LH_CK(m, launch_axpby(s, alpha, W.p, 1.0, W.a, n1));
+    LH_CK(m, launch_axpby(s, -alpha, W.Ap, 1.0, r, n1));
+    if (S) ++S->mass_iters;
+    if ((st = dot_host(m, r, r, n1, &rr)) != LH_OK) return st;
+    if (std::sqrt(rr) <= o.mass_rtol * std::sqrt(bb)) return LH_OK;
+    LH_CK(m, (launch_prec<double, double>(1, s, m->P, m->kron, m->d_diagMv, m->d_invMe, W.rf, W.zf, 0.0)));
+    double rz2;
+    if ((st = dot_host(m, r, z, n1, &rz2)) != LH_OK) return st;
+    LH_CK(m, launch_axpby(s, 1.0, z, rz2 / rz, W.p, n1));
+    rz = rz2;
+  }
+  return fail(m, LH_ENOCONV, "explicit step: the M_V solve did not reach mass_rtol");
+}
+
+// de = M_E^-1 (F^T w + b) from the stored point data
+lh_status x_edot(lh_mesh* m, const XWork& W, const double* w, double* de) {
+  LH_CK(m, launch_force_t(m->P, m->stream, W.Sq, w, m->P.tg ? W.b : nullptr, W.fe));
+  LH_CK(m, launch_mul(m->stream, m->d_invMe, W.fe, de, m->P.NEd));
+  return LH_OK;
+}
+
+// one explicit step in place on u; force_ready: F's data at u are already in W
+lh_status x_step(lh_mesh* m, double* u, double dt, const lh_explicit_opts& o, const XWork& W, bool force_ready,
+                 lh_explicit_stats* S) {
+  cudaStream_t s = m->stream;
+  const long long n = m->n, n1 = (long long)m->P.dim * m->P.NV, ne = m->P.NEd;
+  lh_status st;
+  if (o.scheme == 2) {   // RK2-average
+    double* uh = W.Ui;
+    if (!force_ready && (st = x_force(m, o, W, u, nullptr, S)) != LH_OK) return st;
+    if ((st = x_accel(m, o, W, S)) != LH_OK) return st;
+    double* vh = uh + n1;
+    LH_CK(m, cudaMemcpyAsync(vh, u + n1, sizeof(double) * n1, cudaMemcpyDeviceToDevice, s));
+    LH_CK(m, launch_axpby(s, 0.5 * dt, W.a, 1.0, vh, n1));
+    if ((st = x_edot(m, W, vh, W.de)) != LH_OK) return st;
+    LH_CK(m, cudaMemcpyAsync(uh, u, sizeof(double) * n1, cudaMemcpyDeviceToDevice, s));
+    LH_CK(m, launch_axpby(s, 0.5 * dt, vh, 1.0, uh, n1));
+    LH_CK(m, cudaMemcpyAsync(uh + 2 * n1, u + 2 * n1, sizeof(double) * ne, cudaMemcpyDeviceToDevice, s));
+    LH_CK(m, launch_axpby(s, 0.5 * dt, W.de, 1.0, uh + 2 * n1, ne));
+    if ((st = x_force(m, o, W, uh, nullptr, S)) != LH_OK) return st;
+    if ((st = x_accel(m, o, W, S)) != LH_OK) return st;
+    double* vbar = W.w1;
+    LH_CK(m, cudaMemcpyAsync(vbar, u + n1, sizeof(double) * n1, cudaMemcpyDeviceToDevice, s));
+    LH_CK(m, launch_axpby(s, 0.5 * dt, W.a, 1.0, vbar, n1));
+    if ((st = x_edot(m, W, vbar, W.de)) != LH_OK) return st;
+    LH_CK(m, launch_axpby(s, dt, vbar, 1.0, u, n1));
+    LH_CK(m, launch_axpby(s, dt, W.a, 1.0, u + n1, n1));
+    LH_CK(m, launch_axpby(s, dt, W.de, 1.0, u + 2 * n1, ne));
+    return LH_OK;
+  }
+  // RK3 SSP / RK4 on dU/dt = (v, a(U), g(U, v)); Butcher tableaux (explicit, lower triangular)
+  static const double A3[3][3] = {{0, 0, 0}, {1, 0, 0}, {0.25, 0.25, 0}};
+  static const double b3[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+  static const double A4[4][4] = {{0, 0, 0, 0}, {0.5, 0, 0, 0}, {0, 0.5, 0, 0}, {0, 0, 1, 0}};
+  static const double b4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+  const int ns = o.scheme == 3 ? 3 : 4;
+  for (int i = 0; i < ns; ++i) {
+    const double* Ui = u;
+    if (i > 0) {
+      LH_CK(m, cudaMemcpyAsync(W.Ui, u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      for (int j = 0; j < i; ++j) {
+        const double aij = o.scheme == 3 ? A3[i][j] : A4[i][j];
+        if (aij != 0.0) LH_CK(m, launch_axpby(s, dt * aij, W.K[j], 1.0, W.Ui, n));
+      }
+      Ui = W.Ui;
+    }
+    if (!(i == 0 && force_ready) && (st = x_force(m, o, W, Ui, nullptr, S)) != LH_OK) return st;
+    if ((st = x_accel(m, o, W, S)) != LH_OK) return st;
+    LH_CK(m, cudaMemcpyAsync(W.K[i], Ui + n1, sizeof(double) * n1, cudaMemcpyDeviceToDevice, s));
+    LH_CK(m, cudaMemcpyAsync(W.K[i] + n1, W.a, sizeof(double) * n1, cudaMemcpyDeviceToDevice, s));
+    if ((st = x_edot(m, W, Ui + n1, W.K[i] + 2 * n1)) != LH_OK) return st;
+  }
+  for (int i = 0; i < ns; ++i) LH_CK(m, launch_axpby(s, dt * (o.scheme == 3 ? b3[i] : b4[i]), W.K[i], 1.0, u, n));
+  return LH_OK;
+}
+
+lh_status x_prepare(lh_mesh* m, const lh_explicit_opts* in, lh_explicit_opts* o, XWork* W) {
+  if (in) *o = *in; else lh_explicit_opts_init(o);
+  std::string why;
+  if (!check_explicit_opts(*o, &why)) return fail(m, LH_EINVAL, "explicit path: " + why);
+  lh_status st = ensure_work(m, m->restart_alloc > 0 ? m->restart_alloc : 30);
+  if (st != LH_OK) return st;
+  return xwork(m, W);
+}
+
+lh_status finite_or_restore(lh_mesh* m, double* u, const double* usave) {
+  double nrm;
+  lh_status st = dot_host(m, u, u, m->n, &nrm);
+  if (st != LH_OK) return st;
+  if (std::isfinite(nrm)) return LH_OK;
+  LH_CK(m, cudaMemcpyAsync(u, usave, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  return fail(m, LH_ENONFINITE, "explicit step: the new state is not finite");
+}
+
+}  // namespace
+
+extern "C" {
+
+void lh_explicit_opts_init(lh_explicit_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->scheme = 2;
+  o->visc_model = 1;
+  o->q1_exp = 0.5;
+  o->q2_exp = 2.0;
+  o->cfl = 0.5;
+  o->mass_rtol = 1e-13;
+  o->mass_maxit = 200;
+}
+
+lh_status lh_force(lh_mesh* m, const double* u, const double* w, const lh_explicit_opts* opts, double* f1,
+                   double* ftw, double* dt_est) {
+  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_force");
+  lh_explicit_opts o;
+  XWork W;
+  lh_status st = x_prepare(m, opts, &o, &W);
+  if (st != LH_OK) return st;
+  if ((st = x_force(m, o, W, u, dt_est, nullptr)) != LH_OK) return st;
+  const long long n1 = (long long)m->P.dim * m->P.NV;
+  if (f1) LH_CK(m, cudaMemcpyAsync(f1, W.f1, sizeof(double) * n1, cudaMemcpyDeviceToDevice, m->stream));
+  if (ftw) LH_CK(m, launch_force_t(m->P, m->stream, W.Sq, w ? w : u + n1, m->P.tg ? W.b : nullptr, ftw));
+  return LH_OK;
+}
+
+lh_status lh_explicit_step(lh_mesh* m, double* u, double dt, const lh_explicit_opts* opts, lh_explicit_stats* stats) {
+  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_explicit_step");
+  if (!(dt > 0.0)) return fail(m, LH_EINVAL, "dt must be > 0");
+  lh_explicit_opts o;
+  XWork W;
+  lh_status st = x_prepare(m, opts, &o, &W);
+  if (st != LH_OK) return st;
+  lh_explicit_stats S;
+  std::memset(&S, 0, sizeof(S));
+  LH_CK(m, cudaMemcpyAsync(W.usave, u, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+  st = x_step(m, u, dt, o, W, false, &S);
+  if (st == LH_ENOCONV) {
+    LH_CK(m, cudaMemcpyAsync(u, W.usave, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+    LH_CK(m, cudaStreamSynchronize(m->stream));
+  }
+  if (st == LH_OK) st = finite_or_restore(m, u, W.usave);
+  S.steps = st == LH_OK ? 1 : 0;
+  S.t = st == LH_OK ? dt : 0.0;
+  S.dt_last = dt;
+  if (stats) *stats = S;
+  return st;
+}
+
+lh_status lh_explicit_advance(lh_mesh* m, double* u, double t_end, int max_steps, const lh_explicit_opts* opts,
+                              lh_explicit_stats* stats) {
+  if (!m || !u) return fail(m, LH_EINVAL, "NULL argument to lh_explicit_advance");
+  if (!(t_end >= 0.0) || max_steps < 1) return fail(m, LH_EINVAL, "need t_end >= 0 and max_steps >= 1");
+  lh_explicit_opts o;
+  XWork W;
+  lh_status st = x_prepare(m, opts, &o, &W);
+  if (st != LH_OK) return st;
+  lh_explicit_stats S;
+  std::memset(&S, 0, sizeof(S));
+  double est = 0.0;
+  if ((st = x_force(m, o, W, u, &est, &S)) != LH_OK) return st;
+  bool ready = true;   // W holds F's data at u
+  double dt = o.cfl * est;
+  const double t_tol = 1e-14 * std::fmax(1.0, t_end);
+  while (S.t < t_end - t_tol && S.steps < max_steps) {
+    if (!(dt > 0.0) || !std::isfinite(dt)) {
+      st = fail(m, LH_ENONFINITE, "explicit advance: the time-step estimate is not positive");
+      break;
+    }
+    const double h = std::fmin(dt, t_end - S.t);
+    LH_CK(m, cudaMemcpyAsync(W.usave, u, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+    st = x_step(m, u, h, o, W, ready, &S);
+    if (st == LH_OK) st = finite_or_restore(m, u, W.usave);
+    if (st == LH_OK) st = x_force(m, o, W, u, &est, &S);   // estimate at the new state (F reused next step)
+    if (st != LH_OK && st != LH_ENONFINITE) break;
+    const double dt_new = o.cfl * est;
+    if (st == LH_ENONFINITE || !(dt_new >= h)) {   // repeat the step with a smaller dt
+      LH_CK(m, cudaMemcpyAsync(u, W.usave, sizeof(double) * m->n, cudaMemcpyDeviceToDevice, m->stream));
+      ready = false;
+      dt *= 0.85;
+      ++S.rejected;
+      st = LH_OK;
+      if (S.rejected > 1000) {
+        st = fail(m, LH_ENOCONV, "explicit advance: more than 1000 repeated steps");
+        break;
+      }
+      continue;
+    }
+    ready = true;
+    S.t += h;
+    ++S.steps;
+    if (dt_new > 1.25 * dt) dt *= 1.02;
+  }
+  LH_CK(m, cudaStreamSynchronize(m->stream));
+  S.dt_last = dt;
+  if (stats) *stats = S;
+  return st;
 }
 
 }  // extern "C"

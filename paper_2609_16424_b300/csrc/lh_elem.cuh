@@ -1,0 +1,238 @@
+// Device helpers shared by the element kernels (lh_kernels.cu, lh_explicit.cu): the
+// per-element shared-memory plan, element and lattice indexing, quadrature-point constants,
+// boundary masks, block reductions, the node-centric gather of element rows (G^T of the
+// paper's Sec. 2.2, Eq. (8)) and small launch helpers.
+#pragma once
+#include <atomic>
+#include <cfloat>
+#include "lh_internal.h"
+#include "lh_kernels.h"
+#include "lh_qp.cuh"
+#include "lh_contract.cuh"
+
+namespace lh {
+
+// Per-element shared-memory plan (units of T).
+template <int DIM, int K, int NCH, int NCV, int NCL, int NCO>
+struct Plan {
+  using C = Cfg<DIM, K>;
+  using SC = H1Scratch<DIM, K, NCH>;
+  static constexpr int IN = NCH * C::ND + NCV * C::ND + NCL * C::NL;
+  static constexpr int T1 = SC::T1;
+  static constexpr int T2 = SC::T2;
+  static constexpr int SF = (DIM + 1) * (NCO > 1 ? NCO : 1) * C::NQ;
+  static constexpr int PER = IN + T1 + T2 + SF;
+  static constexpr int HEAD = ((Tab<K>::SMEM + C::THREADS + 1) / 2) * 2;   // tables + reduction
+  static constexpr size_t bytes(size_t szT) { return szT * (size_t)(HEAD + C::EPB * PER); }
+};
+
+struct ElemIdx {
+  long long e;
+  int ex, ey, ez;
+  bool valid;
+};
+
+template <int DIM, int K>
+__device__ __forceinline__ ElemIdx elem_index(const ElemParams& P) {
+  using C = Cfg<DIM, K>;
+  ElemIdx r;
+  const int eb = threadIdx.x / C::NQ;
+  r.e = (long long)blockIdx.x * C::EPB + eb;
+  r.valid = r.e < P.NE;
+  const long long e = r.valid ? r.e : 0;
+  r.ex = (int)(e % P.n0);
+  r.ey = (int)((e / P.n0) % P.n1);
+  r.ez = DIM == 3 ? (int)(e / ((long long)P.n0 * P.n1)) : 0;
+  return r;
+}
+
+// global lattice node of local H1 node a of element (ex, ey, ez)
+template <int DIM, int K>
+__device__ __forceinline__ long long node_of(const ElemParams& P, const ElemIdx& E, int a) {
+  constexpr int D = K + 1;
+  const int a0 = a % D, a1 = (a / D) % D, a2 = a / (D * D);
+  const long long i0 = (long long)E.ex * K + a0, i1 = (long long)E.ey * K + a1;
+  if constexpr (DIM == 2) return i0 + (long long)P.N0 * i1;
+  const long long i2 = (long long)E.ez * K + a2;
+  return i0 + (long long)P.N0 * (i1 + (long long)P.N1 * i2);
+}
+
+template <int DIM, int K, class T>
+__device__ __forceinline__ QpC<T> qp_consts(const ElemParams& P, const ElemIdx& E, const T* sW, int lt) {
+  constexpr int Q = 2 * K;
+  QpC<T> c;
+  const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+  T a = sW[q0] * sW[q1];
+  if constexpr (DIM == 3) a *= sW[q2];
+  c.alpha = a;
+  const double rho0 = E.valid ? P.rho0[E.e] : 1.0;
+  const double gam = E.valid ? P.gamma[E.e] : 1.4;
+  c.mq = T(rho0 * P.detJ0) * a;
+  c.inv_detJ0 = T(1.0 / P.detJ0);
+  c.gm1 = T(gam - 1.0);
+  c.ggm1 = T(gam * (gam - 1.0));
+  c.h0 = T(P.h0);
+  c.inv_hc = T(P.inv_hc);
+  c.q1 = T(P.q1);
+  c.q2 = T(P.q2);
+  c.scoef = T(P.scoef);
+  c.eps2 = T(P.eps2);
+  c.visc = P.visc != 0;
+  return c;
+}
+
+// true if velocity component comp of lattice node nd is fixed (v.n = 0 on a masked face)
+template <int DIM>
+__device__ __forceinline__ bool fixed_node(const ElemParams& P, long long nd_, int comp) {
+  const int nd = (int)nd_;
+  int ic, Nc;
+  if (comp == 0) {
+    ic = nd % P.N0;
+    Nc = P.N0;
+  } else if (comp == 1) {
+    ic = (nd / P.N0) % P.N1;
+    Nc = P.N1;
+  } else {
+    ic = nd / (P.N0 * P.N1);
+    Nc = P.N2;
+  }
+  const bool lo = ((P.bc >> (2 * comp)) & 1u) && ic == 0;
+  const bool hi = ((P.bc >> (2 * comp + 1)) & 1u) && ic == Nc - 1;
+  return lo || hi;
+}
+
+template <class T>
+__device__ __forceinline__ void load_tables(const ElemParams& P, T* s, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = T(P.tab[i]);
+}
+
+// min over the block (thread 0 holds the result); red has blockDim.x entries
+__device__ __forceinline__ double block_min(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 1; s < (int)blockDim.x; s <<= 1) {
+    const int i = threadIdx.x;
+    double o = DBL_MAX;
+    if ((i % (2 * s)) == 0 && i + s < (int)blockDim.x) o = red[i + s];
+    __syncthreads();
+    if ((i % (2 * s)) == 0) red[i] = fmin(red[i], o);
+    __syncthreads();
+  }
+  return red[0];
+}
+
+template <int DIM, int K, class T>
+__device__ __forceinline__ T gather_node(const ElemParams& P, const T* __restrict__ ev, int ncomp, int comp,
+                                         long long nd_) {
+  // 32-bit lattice arithmetic (node counts stay far below 2^31); per axis at most two
+  // elements share the node: option 0 (the lower element, or the only one) and option 1
+  // (the upper element), summed in the fixed order lower-then-upper per axis
+  constexpr int D = K + 1, ND = Cfg<DIM, K>::ND;
+  const int nd = (int)nd_;
+  const int ic[3] = {nd % P.N0, (nd / P.N0) % P.N1, DIM == 3 ? nd / (P.N0 * P.N1) : 0};
+  const int nel[3] = {P.n0, P.n1, P.n2};
+  int e0[3], l0[3], e1[3], l1[3];
+  bool v0[3], v1[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d >= DIM) {
+      e0[d] = 0; l0[d] = 0; v0[d] = true; e1[d] = 0; l1[d] = 0; v1[d] = false;
+      continue;
+    }
+    const int q = ic[d] / K, r = ic[d] % K;
+    if (r != 0) {
+      e0[d] = q; l0[d] = r; v0[d] = true;
+      e1[d] = 0; l1[d] = 0; v1[d] = false;
+    } else {
+      e0[d] = q - 1; l0[d] = K; v0[d] = q >= 1;
+      e1[d] = q; l1[d] = 0; v1[d] = q < nel[d];
+    }
+  }
+  T s = T(0);
+#pragma unroll
+  for (int b2 = 0; b2 < 2; ++b2)
+#pragma unroll
+    for (int b1 = 0; b1 < 2; ++b1)
+#pragma unroll
+      for (int b0 = 0; b0 < 2; ++b0) {
+        const bool ok = (b0 ? v1[0] : v0[0]) && (b1 ? v1[1] : v0[1]) && (b2 ? v1[2] : v0[2]);
+        if (!ok) continue;
+        const int ex = b0 ? e1[0] : e0[0], ey = b1 ? e1[1] : e0[1], ez = b2 ? e1[2] : e0[2];
+        const int a = (b0 ? l1[0] : l0[0]) + D * ((b1 ? l1[1] : l0[1]) + D * (b2 ? l1[2] : l0[2]));
+        const long long e = ex + (long long)P.n0 * (ey + (long long)P.n1 * ez);
+        s += ev[(e * ncomp + comp) * ND + a];
+      }
+  return s;
+}
+
+// dynamic shared-memory limit of a kernel, set once per device (a per-device attribute)
+template <auto KERN>
+static cudaError_t prep(size_t bytes) {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(done.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    done.fetch_or(bit, std::memory_order_release);
+  }
+  return cudaSuccess;
+}
+
+static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static inline void mark(cudaEvent_t* ev2, int i, cudaStream_t s) {
+  if (ev2) cudaEventRecord(ev2[i], s);
+}
+
+// out[comp * NV + node] = sum of the element rows of that node (element scratch [e][ncomp][ND])
+template <int DIM, int K>
+__global__ void k_assemble_sum(ElemParams P, const double* __restrict__ ev, int ncomp, double* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)ncomp * P.NV) return;
+  const int comp = (int)(i / P.NV);
+  out[i] = gather_node<DIM, K>(P, ev, ncomp, comp, i % P.NV);
+}
+
+// smallest singular value of a DIM x DIM matrix (the explicit time-step estimate's
+// h_min = sigma_min(J) / K)
+template <int DIM>
+__device__ __forceinline__ double sigma_min(const double (&J)[DIM][DIM]) {
+  // smallest eigenvalue of the symmetric J^T J, then its square root
+  double M[DIM][DIM];
+  for (int i = 0; i < DIM; ++i)
+    for (int j = 0; j < DIM; ++j) {
+      double s = 0;
+      for (int r = 0; r < DIM; ++r) s += J[r][i] * J[r][j];
+      M[i][j] = s;
+    }
+  if constexpr (DIM == 2) {
+    const double tr = M[0][0] + M[1][1];
+    const double dd = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+    const double disc = sqrt(fmax(0.25 * tr * tr - dd, 0.0));
+    return sqrt(fmax(0.5 * tr - disc, 0.0));
+  } else {
+    // eigenvalues of a symmetric 3x3 matrix by the trigonometric solution of its
+    // characteristic cubic (Smith 1961)
+    const double p1 = M[0][1] * M[0][1] + M[0][2] * M[0][2] + M[1][2] * M[1][2];
+    const double q = (M[0][0] + M[1][1] + M[2][2]) / 3.0;
+    const double p2 = (M[0][0] - q) * (M[0][0] - q) + (M[1][1] - q) * (M[1][1] - q) +
+                      (M[2][2] - q) * (M[2][2] - q) + 2.0 * p1;
+    const double p = sqrt(p2 / 6.0);
+    if (p <= 1e-300) return sqrt(fmax(q, 0.0));
+    double Bm[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) Bm[i][j] = (M[i][j] - (i == j ? q : 0.0)) / p;
+    const double detB = Bm[0][0] * (Bm[1][1] * Bm[2][2] - Bm[1][2] * Bm[2][1]) -
+                        Bm[0][1] * (Bm[1][0] * Bm[2][2] - Bm[1][2] * Bm[2][0]) +
+                        Bm[0][2] * (Bm[1][0] * Bm[2][1] - Bm[1][1] * Bm[2][0]);
+    const double r = fmin(fmax(0.5 * detB, -1.0), 1.0);
+    const double phi = acos(r) / 3.0;
+    const double lmin = q + 2.0 * p * cos(phi + 2.0 * 3.14159265358979323846 / 3.0);
+    return sqrt(fmax(lmin, 0.0));
+  }
+}
+
+}  // namespace lh

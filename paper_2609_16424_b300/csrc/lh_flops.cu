@@ -155,10 +155,10 @@ void tangent_check(bool visc, int trials, unsigned seed, double* max_double, dou
     lh::QpPrimal<DIM, double> pr;
     lh::qp_forward<DIM>(J, Gv, e, c, So, Eo, det, &pr);
     double Ld[lh::lin_len<DIM>()], dSd[DIM][DIM], dEd, dWd;
-    lh::lin_record<DIM, double>(pr, c.gm1, visc, 0, 0, 0, Ld);
+    lh::lin_record<DIM, double>(pr, c.gm1, c.q1, c.q2, visc, 0, 0, 0, Ld);
     lh::qp_tangent_lin<DIM, double>(Ld, dJ, dGv, de, c.q1, c.q2, visc, dSd, dEd, dWd);
     float Lf[lh::lin_len<DIM>()], dJf[DIM][DIM], dGf[DIM][DIM], dSf[DIM][DIM], dEf, dWf;
-    lh::lin_record<DIM, float>(pr, c.gm1, visc, 0, 0, 0, Lf);
+    lh::lin_record<DIM, float>(pr, c.gm1, c.q1, c.q2, visc, 0, 0, 0, Lf);
     for (int i = 0; i < DIM; ++i)
       for (int j = 0; j < DIM; ++j) {
         dJf[i][j] = (float)dJ[i][j];

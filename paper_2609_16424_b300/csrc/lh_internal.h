@@ -28,6 +28,14 @@ struct ElemParams {
   const float* fggm1;      // device [NE]: gamma (gamma - 1)
 };
 
+// parameters of the original tensor viscosity mu_exp of the explicit path (lh_qp_exp.cuh);
+// J0^-1 of the undeformed box is diag(1 / h_c)
+struct ExpC {
+  double l0, q1, q2;
+  double inv_h[3];
+  int vorticity;
+};
+
 // shared set-up helpers (lh_api.cu)
 bool check_desc(const lh_mesh_desc* d, std::string* why);
 void fill_params(const lh_mesh_desc& d, ElemParams* out);
@@ -35,8 +43,9 @@ std::vector<double> host_tables(int K);   // [B | G | Bl | w | zh | zl] for orde
 lh_status set_global_error(lh_status st, const std::string& msg);   // for lh_last_error(NULL)
 
 // floats per quadrature point in the linearisation record (lh_qp.cuh, lin_record): J^-1,
-// grad v, 13 scalars of the stress and viscosity chain (and the Taylor-Green source in 2D)
-inline int rec_len(int dim) { return dim == 3 ? 31 : 24; }
+// grad v, 7 scalars of the stress and linearised viscosity chain (and the Taylor-Green
+// source in 2D)
+inline int rec_len(int dim) { return dim == 3 ? 25 : 18; }
 
 // Kronecker factors of the H1 mass inverse (lh_prec.cu); device pointers owned by the mesh
 struct KronPrec {
@@ -85,6 +94,7 @@ struct lh_mesh {
   float* d_fconst = nullptr;       // [3 NE] float rho0 detJ0, gamma - 1, gamma (gamma - 1)
   float* d_rec = nullptr;          // linearisation record [NE][rec_len][NQ] (lazily allocated)
   double* d_stage = nullptr;       // SDIRK stage increments k_1..k_3 and stage base state [4 n] (lazily)
+  double* d_xwork = nullptr;       // explicit path work arrays (lazily, lh_api.cu XWork)
   double* d_adv = nullptr;         // lh_advance trial state u, k and the internal increment [3 n] (lazily)
   double* d_wscale = nullptr;      // row weights of the scaled Newton norm [n] (lazily)
   double* d_jdiag = nullptr;       // diagonal of dR_v/dk_v for preconditioner kind 2 [dim NV] (lazily)

@@ -120,5 +120,16 @@ cudaError_t launch_jvp_f32_to_f64(const ElemParams& P, cudaStream_t s, const dou
 cudaError_t launch_jacobi_h1(cudaStream_t s, long long nv, int dim, const double* diag, const double* r, double* z);
 cudaError_t launch_mul(cudaStream_t s, const double* a, const double* b, double* y, long long n);
 cudaError_t launch_probe_fma(int prec, double* tflops);
+// explicit path (lh_explicit.cu): F's point data S = alpha detJ sigma J^-T at state u
+// ([NE][dim^2][NQ]), F.1 assembled into f1 [dim NV] (ev: element scratch NE dim ND),
+// the Taylor-Green source rows into bsrc [NEd] (2D, if P.tg and bsrc), the per-block
+// minimum of the explicit time-step estimate into blockmin (if not NULL); vm 0 = mu_imp,
+// 1 = mu_exp.  launch_force_t: out [NEd] = F^T w (+ bsrc if not NULL) from the stored S.
+cudaError_t launch_force(const ElemParams& P, cudaStream_t s, int vm, const ExpC& X, const double* u, double* Sq,
+                         double* ev, double* f1, double* bsrc, double* blockmin);
+cudaError_t launch_force_t(const ElemParams& P, cudaStream_t s, const double* Sq, const double* w, const double* bsrc,
+                           double* out);
+// dst = src (or 0 if src is NULL) on the fixed rows of a velocity array [dim NV]
+cudaError_t launch_copy_fixed(const ElemParams& P, cudaStream_t s, const double* src, double* dst);
 
 }  // namespace lh

@@ -153,18 +153,28 @@ __host__ __device__ __forceinline__ void qp_forward(const S (&J)[DIM][DIM], cons
 // paper Sec. 2.2: the point data are stored once per Newton iterate and reused by every
 // Jacobian action).  Fields per point, float:
 //   [0, D^2) J^-1, [D^2, 2 D^2) grad v, then W = alpha detJ, p, pe = (gamma-1) rho e+',
-//   cs, ke = e+' / (2 e+) (so dcs = cs ke de), h, ds, 1/ds, 1/|.|_ds, psi, g = (1 - t^2)/2
-//   (t the tanh of Eq. (17)), mu, rho h; in 2D also the Taylor-Green source s and its
-//   gradient at x_q.  e+' = e+ / sqrt(e^2 + eps^2) in both branches of Eq. (19).
+//   mu, and the three coefficients of the linearised viscosity chain of Eqs. (13)-(18),
+//   dmu = a_th theta + a_div d(div v) + a_e de  (theta = tr(J^-1 dJ) = d detJ / detJ);
+//   in 2D also the Taylor-Green source s and its gradient at x_q.
+// The chain (tq = theta / dim, e+' = e+ / sqrt(e^2 + eps^2) in both branches of Eq. (19),
+// ke = e+' / (2 e+) = 1 / (2 sqrt(e^2 + eps^2)), rh = rho h, delta_v = h div v):
+//   d delta_v = tq delta_v + h d(div v),   d delta_s = delta_s (tq + ke de),
+//   d|.|  = tq |.| + (delta_v h d(div v) + delta_s^2 ke de) / |.|,
+//   d arg = -(h d(div v) - delta_v ke de) / (2 delta_s),   d psi = (1 - t^2)/2 d arg,
+//   dmu   = mu (1/dim - 1) theta + rh [q2 d|.| + q1 (c_s ke psi de + c_s d psi)]
+// collects into
+//   a_th  = mu (1/dim - 1) + rh q2 |.| / dim = rh (q2 |.| (2/dim - 1) + q1 c_s psi (1/dim - 1)),
+//   a_div = rh h (q2 delta_v / |.| - q1 c_s (1 - t^2) / (4 delta_s)),
+//   a_e   = rh ke (q2 delta_s^2 / |.| + q1 c_s psi + q1 c_s (1 - t^2) delta_v / (4 delta_s)),
+// formed from the residual's own intermediates.
 template <int DIM>
-__host__ __device__ constexpr int lin_len() { return DIM == 3 ? 31 : 24; }
+__host__ __device__ constexpr int lin_len() { return DIM == 3 ? 25 : 18; }
 
-enum LinField : int { LF_W = 0, LF_P, LF_PE, LF_CS, LF_KE, LF_H, LF_DS, LF_IDS, LF_IAB, LF_PSI, LF_G, LF_MU, LF_RH,
-                      LF_TGS, LF_TGX, LF_TGY };
+enum LinField : int { LF_W = 0, LF_P, LF_PE, LF_MU, LF_ATH, LF_ADIV, LF_AE, LF_TGS, LF_TGX, LF_TGY };
 
 template <int DIM, class R = float>
-__host__ __device__ __forceinline__ void lin_record(const QpPrimal<DIM, double>& pr, double gm1, bool visc,
-                                                    double tgs, double tgx, double tgy,
+__host__ __device__ __forceinline__ void lin_record(const QpPrimal<DIM, double>& pr, double gm1, double q1, double q2,
+                                                    bool visc, double tgs, double tgx, double tgy,
                                                     R (&L)[lin_len<DIM>()]) {
   constexpr int O = 2 * DIM * DIM;
 #pragma unroll
@@ -174,23 +184,28 @@ __host__ __device__ __forceinline__ void lin_record(const QpPrimal<DIM, double>&
       L[i * DIM + j] = R(pr.Jinv[i][j]);
       L[DIM * DIM + i * DIM + j] = R(pr.Lv[i][j]);
     }
-  const R ep = R(pr.ep), epd = ep / R(pr.sq);      // e+ and d e+ / d e
+  // the chain is formed in the record's precision R (float on the GPU: no FP64 divisions
+  // in the residual kernel), from the double intermediates rounded once
+  const R isq = R(1) / R(pr.sq);
   L[O + LF_W] = R(pr.W);
   L[O + LF_P] = R(pr.p);
-  L[O + LF_PE] = R(gm1) * R(pr.rho) * epd;
-  L[O + LF_CS] = R(pr.cs);
-  L[O + LF_KE] = epd / (R(2) * ep);
+  L[O + LF_PE] = R(gm1 * pr.rho) * R(pr.ep) * isq;
   if (visc) {
-    L[O + LF_H] = R(pr.h);
-    L[O + LF_DS] = R(pr.ds);
-    L[O + LF_IDS] = R(1) / R(pr.ds);
-    L[O + LF_IAB] = R(1) / R(pr.ab);
-    L[O + LF_PSI] = R(0.5 + 0.5 * pr.t);
-    L[O + LF_G] = R(0.5 * (1.0 - pr.t * pr.t));   // in double: 1 - t^2 cancels as |t| -> 1
+    double div = 0.0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) div += pr.Lv[i][i];
+    const R h = R(pr.h), dv = R(pr.h * div), rh = R(pr.rho * pr.h), ds = R(pr.ds), ab = R(pr.ab), cs = R(pr.cs);
+    const R ke = R(0.5) * isq, iab = R(1) / ab;
+    const R g4 = R(0.25 * (1.0 - pr.t * pr.t)) / ds;   // (1 - t^2) / (4 delta_s), 1 - t^2 in double
+    const R psi = R(0.5 + 0.5 * pr.t);
+    const R q1r = R(q1), q2r = R(q2);
     L[O + LF_MU] = R(pr.mu);
-    L[O + LF_RH] = R(pr.rho * pr.h);
+    // a_th = mu (1/dim - 1) + rh q2 |.| / dim with mu = rh (q2 |.| + q1 c_s psi), cancellation-free
+    L[O + LF_ATH] = rh * (q2r * ab * R(2.0 / DIM - 1.0) + q1r * cs * psi * R(1.0 / DIM - 1.0));
+    L[O + LF_ADIV] = rh * h * (q2r * dv * iab - q1r * cs * g4);
+    L[O + LF_AE] = rh * ke * (q2r * ds * ds * iab + q1r * cs * (psi + g4 * dv));
   } else {
-    for (int f = LF_H; f <= LF_RH; ++f) L[O + f] = R(0);
+    L[O + LF_MU] = L[O + LF_ATH] = L[O + LF_ADIV] = L[O + LF_AE] = R(0);
   }
   if constexpr (DIM == 2) {
     L[O + LF_TGS] = R(tgs);
@@ -247,24 +262,11 @@ __host__ __device__ __forceinline__ void qp_tangent_lin(const T (&L)[lin_len<DIM
   const T dp = -p * th + L[O + LF_PE] * de;
   T mu = T(0.), dmu = T(0.);
   if (visc) {
-    const T cs = L[O + LF_CS], dcs = cs * L[O + LF_KE] * de;
-    const T h = L[O + LF_H], ds = L[O + LF_DS], ids = L[O + LF_IDS];
-    T div = T(0.), ddiv = T(0.);
+    T ddiv = dL[0][0];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-      div += Lv[i][i];
-      ddiv += dL[i][i];
-    }
-    const T dv = h * div;
-    const T tq = th * (T(1.) / DIM);
-    const T ddv = h * (tq * div + ddiv);
-    const T dds = ds * (tq + L[O + LF_KE] * de);
-    const T dab = (dv * ddv + ds * dds) * L[O + LF_IAB];
-    const T darg = -T(0.5) * ids * (ddv - dv * dds * ids);
-    const T dpsi = L[O + LF_G] * darg;
-    const T dX = q2 * dab + q1 * (dcs * L[O + LF_PSI] + cs * dpsi);
+    for (int i = 1; i < DIM; ++i) ddiv += dL[i][i];
     mu = L[O + LF_MU];
-    dmu = mu * th * (T(1.) / DIM - T(1.)) + L[O + LF_RH] * dX;
+    dmu = L[O + LF_ATH] * th + L[O + LF_ADIV] * ddiv + L[O + LF_AE] * de;
   }
   T sg[DIM][DIM], dsg[DIM][DIM];
 #pragma unroll
@@ -392,27 +394,10 @@ __host__ __device__ __forceinline__ void qp_tangent_lin_adj(const T (&L)[lin_len
     }
   }
   T ebv = T(0);
-  if (visc) {
-    const T cs = L[O + LF_CS], ke = L[O + LF_KE], h = L[O + LF_H], ds = L[O + LF_DS], ids = L[O + LF_IDS];
-    const T iab = L[O + LF_IAB], psi = L[O + LF_PSI], G = L[O + LF_G], rh = L[O + LF_RH];
-    T div = T(0);
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) div += Lv[i][i];
-    const T dv = h * div;
-    // dmu = mu theta (1/dim - 1) + rh dX
-    thb += mu * (T(1) / DIM - T(1)) * dmub;
-    const T dXb = rh * dmub;
-    // dX = q2 dab + q1 (psi dcs + cs dpsi)
-    const T dabb = q2 * dXb, dcsb = q1 * psi * dXb, dpsib = q1 * cs * dXb;
-    const T dargb = G * dpsib;
-    // darg = -1/2 ids (ddv - dv dds ids);  dab = iab (dv ddv + ds dds)
-    const T ddvb = -T(0.5) * ids * dargb + iab * dv * dabb;
-    const T ddsb = T(0.5) * ids * ids * dv * dargb + iab * ds * dabb;
-    // dds = ds (tq + ke de);  ddv = h (tq div + ddiv);  tq = theta / dim
-    const T tqb = ds * ddsb + h * div * ddvb;
-    ebv += ds * ke * ddsb + cs * ke * dcsb;   // dcs = cs ke de
-    const T ddivb = h * ddvb;
-    thb += tqb * (T(1) / DIM);
+  if (visc) {   // dmu = a_th theta + a_div tr(dL) + a_e de
+    thb += L[O + LF_ATH] * dmub;
+    ebv += L[O + LF_AE] * dmub;
+    const T ddivb = L[O + LF_ADIV] * dmub;
 #pragma unroll
     for (int i = 0; i < DIM; ++i) dLb[i][i] += ddivb;
   }

@@ -52,6 +52,26 @@ def advance_opts(**kw):
     return a
 
 
+def explicit_opts(**kw):
+    """lh_explicit_opts with the library defaults, overridden by keyword arguments (scheme,
+    visc_model in {'imp', 'exp', 0, 1}, q1_exp, q2_exp, l0_exp, vorticity, cfl, mass_rtol,
+    mass_maxit)."""
+    o = _lib.ExplicitOpts()
+    _L.lh_explicit_opts_init(C.byref(o))
+    fields = {f for f, _ in _lib.ExplicitOpts._fields_}
+    for key, val in kw.items():
+        if key not in fields:
+            raise TypeError(f"unknown explicit option {key!r}")
+        if key == "visc_model":
+            val = {"imp": 0, "exp": 1}.get(val, val)
+        setattr(o, key, val)
+    return o
+
+
+def _stats_dict(st):
+    return {f: getattr(st, f) for f, _ in st._fields_}
+
+
 def _attempts(hist, count):
     return [(hist[i].dt, hist[i].h, None if hist[i].newton_its < 0 else hist[i].newton_its, bool(hist[i].accepted))
             for i in range(count)]
@@ -338,6 +358,41 @@ class Mesh:
                            C.byref(a), C.byref(stats), hist, cap)
         self._check(st)
         return stats.steps, stats.rejected, _attempts(hist, min(stats.attempts, cap))
+
+    def force(self, u, w=None, estimate=False, **kw):
+        """F(u).1 [dim NV] and F(u)^T w + b [N_E] (w = the velocity of u if None), and with
+        estimate=True the explicit time-step estimate, for the explicit path (kw: explicit
+        options, e.g. visc_model='exp').  Returns (f1, ftw) or (f1, ftw, dt_est)."""
+        self._vec(u, "u")
+        if w is not None:
+            self._vec(w, "w", n=self.dim * self.NV)
+        f1 = torch.empty(self.dim * self.NV, dtype=torch.float64, device=self.device)
+        ftw = torch.empty(self.NEd, dtype=torch.float64, device=self.device)
+        est = C.c_double()
+        o = explicit_opts(**kw)
+        self._stream()
+        self._check(_L.lh_force(self._h, _ptr(u), _ptr(w) if w is not None else None, C.byref(o), _ptr(f1),
+                                _ptr(ftw), C.byref(est) if estimate else None))
+        return (f1, ftw, est.value) if estimate else (f1, ftw)
+
+    def explicit_step(self, u, dt, **kw):
+        """One explicit step (scheme 2: RK2-average, 3: RK3 SSP, 4: RK4) in place on u."""
+        self._vec(u, "u")
+        o, st = explicit_opts(**kw), _lib.ExplicitStats()
+        self._stream()
+        self._check(_L.lh_explicit_step(self._h, _ptr(u), float(dt), C.byref(o), C.byref(st)))
+        return _stats_dict(st)
+
+    def explicit_advance(self, u, t_end, max_steps=10000000, **kw):
+        """Explicit run from t = 0 to t_end in place on u with the explicit step control
+        (first dt = cfl x estimate; repeat with 0.85 dt when the estimate at the new state is
+        below the step; grow 2% when it is above 1.25 dt).  Returns the run statistics."""
+        self._vec(u, "u")
+        o, st = explicit_opts(**kw), _lib.ExplicitStats()
+        self._stream()
+        self._check(_L.lh_explicit_advance(self._h, _ptr(u), float(t_end), int(max_steps), C.byref(o),
+                                           C.byref(st)))
+        return _stats_dict(st)
 
     def newton_step(self, u, k_prev, dt, opts=None, **kw):
         """One implicit midpoint step in place on u (and k_prev, if given).  Returns the

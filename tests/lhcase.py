@@ -10,13 +10,14 @@ from oracle.hydro import Hydro, Params
 
 class Case:
     def __init__(self, dim, n, k, seed=0, visc=True, tg=False, lo=None, hi=None, rho0=1.0, gamma=1.4,
-                 h_coarse=0.0, vscale=1.0, e_lo=0.0):
+                 h_coarse=0.0, vscale=1.0, e_lo=0.0, visc_model='imp'):
         import paper_2609_16424_b300 as lh
         lo = lo or (0.0,) * dim
         hi = hi or (1.0,) * dim
         self.dim, self.n, self.k = dim, tuple(n), k
         m = OMesh(n, lo, hi, k)
-        prm = Params(m, rho0=rho0, gamma=gamma, visc=visc, tg_source=tg, h_coarse=h_coarse or None)
+        prm = Params(m, rho0=rho0, gamma=gamma, visc=visc, tg_source=tg, h_coarse=h_coarse or None,
+                     visc_model=visc_model)
         self.hyd = Hydro(m, prm)
         self.u = problems.perturbed_state(self.hyd, lh_synth.perturbed_draws(n, k, seed, e_lo=e_lo),
                                          vscale=vscale)
