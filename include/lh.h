@@ -501,9 +501,19 @@ lh_status lh_profile_read(lh_mesh* mesh, double* ms, long long* count);
 /* Arithmetic operations (+ - * / sqrt tanh cbrt cos sin, one each) of one evaluation of
  * the quadrature-point kernel, counted by running the kernel's code on the host with a
  * counting scalar.  kind 0: stress (residual), 1: tangent (J.w), 2: adjoint (J^T.y),
- * 3: tangent from the linearisation record (reduced-precision J.w).
+ * 3: tangent from the linearisation record (reduced-precision J.w); 4: the float
+ * operations the residual's stress (kind 0) costs in the double-word arithmetic it runs in
+ * on the GPU (each double-word sum, product, quotient, root and tanh weighed by its count
+ * of float operations).
  * Needs no GPU.  *ops is a HOST pointer. */
 lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops);
+
+/* Host check of the double-word (float pair) arithmetic the residual's point kernel runs
+ * in (needs no GPU): `trials` seeded cases of which = 0 sum / difference, 1 product,
+ * 2 quotient, 3 square root, 4 cube root (relative errors against double), 5 tanh on
+ * [-25, 25] (absolute error), 6-9 the whole quadrature-point stress (S, E, det J) in
+ * double-word against double, 2D / 2D viscous / 3D / 3D viscous.  *max_err: HOST. */
+lh_status lh_dd_check(int which, int trials, unsigned seed, double* max_err);
 
 /* Floats per quadrature point in the linearisation record of lh_linearize (dim 2 or 3).
  * Needs no GPU.  *len is a HOST pointer. */

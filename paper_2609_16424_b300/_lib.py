@@ -15,7 +15,7 @@ SYMBOLS = ["lh_mesh_desc_init", "lh_mesh_create", "lh_mesh_destroy", "lh_sizes",
            "lh_initial_nodes", "lh_residual", "lh_jvp", "lh_jtvp", "lh_mass_apply", "lh_mass_solve",
            "lh_dt_estimate", "lh_energies", "lh_tg_velocity_error", "lh_newton_opts_init", "lh_newton_step", "lh_advance_opts_init", "lh_advance", "lh_advance_replay",
            "lh_explicit_opts_init", "lh_force", "lh_explicit_step", "lh_explicit_advance", "lh_stage_solve", "lh_sdirk_step", "lh_sdirk_tableau", "lh_last_error",
-           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_record_len", "lh_linearize", "lh_jvv_diagonal", "lh_qp_tangent_check", "lh_qp_adjoint_check", "lh_tc_status", "lh_tc_set_wait_polls", "lh_halo_len", "lh_halo_pack", "lh_halo_add", "lh_residual_noalloc", "lh_precond",
+           "lh_probe_fma", "lh_profile_enable", "lh_profile_read", "lh_launch_count", "lh_qp_flops", "lh_record_len", "lh_dd_check", "lh_linearize", "lh_jvv_diagonal", "lh_qp_tangent_check", "lh_qp_adjoint_check", "lh_tc_status", "lh_tc_set_wait_polls", "lh_halo_len", "lh_halo_pack", "lh_halo_add", "lh_residual_noalloc", "lh_precond",
            "lh_mlp_create", "lh_mlp_destroy", "lh_mlp_num_params", "lh_mlp_params", "lh_mlp_forward",
            "lh_mlp_grad", "lh_mlp_train_step", "lh_mlp_last_error", "lh_mlp_features", "lh_mlp_apply_prediction"]
 PROF_KINDS = ["residual", "jvp_fp64", "jvp_fp32", "jtvp", "mass_h1", "jvp_tc"]
@@ -112,6 +112,7 @@ def load(path=LIB_PATH):
         "lh_launch_count": (C.c_longlong, []),
         "lh_qp_flops": (i, [i, i, i, llp]),
         "lh_record_len": (i, [i, ip]),
+        "lh_dd_check": (i, [i, i, C.c_uint, dp]),
         "lh_linearize": (i, [vp, vp, vp, d]),
         "lh_tc_status": (i, [vp]),
         "lh_tc_set_wait_polls": (C.c_uint, [C.c_uint]),

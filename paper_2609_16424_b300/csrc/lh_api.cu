@@ -497,6 +497,17 @@ void fill_params(const lh_mesh_desc& d, ElemParams* out) {
   P.visc = d.visc;
   P.tg = d.tg_source;
   P.bc = d.bc_mask;
+  auto split = [](double x, float (&w)[2]) {
+    w[0] = (float)x;
+    w[1] = (float)(x - (double)w[0]);
+  };
+  split(1.0 / P.detJ0, P.dw_inv_detJ0);
+  split(P.h0, P.dw_h0);
+  split(P.inv_hc, P.dw_inv_hc);
+  split(P.q1, P.dw_q1);
+  split(P.q2, P.dw_q2);
+  split(P.scoef, P.dw_scoef);
+  split(P.eps2, P.dw_eps2);
 }
 
 std::vector<double> host_tables(int K) { return build_tables(K); }

@@ -16,25 +16,27 @@
 namespace {
 
 long long g_ops = 0;
+// per-kind counts (kind 4 weighs them by the float operations of the double-word arithmetic)
+long long g_add = 0, g_mul = 0, g_div = 0, g_sqrt = 0, g_tanh = 0, g_cbrt = 0;
 
 struct Cnt {
   double v;
   Cnt() : v(0) {}
   Cnt(double a) : v(a) {}
 };
-inline Cnt operator+(Cnt a, Cnt b) { ++g_ops; return Cnt(a.v + b.v); }
-inline Cnt operator-(Cnt a, Cnt b) { ++g_ops; return Cnt(a.v - b.v); }
-inline Cnt operator*(Cnt a, Cnt b) { ++g_ops; return Cnt(a.v * b.v); }
-inline Cnt operator/(Cnt a, Cnt b) { ++g_ops; return Cnt(a.v / b.v); }
+inline Cnt operator+(Cnt a, Cnt b) { ++g_ops; ++g_add; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_ops; ++g_add; return Cnt(a.v - b.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_ops; ++g_mul; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_ops; ++g_div; return Cnt(a.v / b.v); }
 inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
 inline bool operator>=(Cnt a, Cnt b) { return a.v >= b.v; }   // branches are not counted
-inline Cnt& operator+=(Cnt& a, Cnt b) { ++g_ops; a.v += b.v; return a; }
-inline Cnt& operator-=(Cnt& a, Cnt b) { ++g_ops; a.v -= b.v; return a; }
-inline Cnt& operator*=(Cnt& a, Cnt b) { ++g_ops; a.v *= b.v; return a; }
+inline Cnt& operator+=(Cnt& a, Cnt b) { ++g_ops; ++g_add; a.v += b.v; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { ++g_ops; ++g_add; a.v -= b.v; return a; }
+inline Cnt& operator*=(Cnt& a, Cnt b) { ++g_ops; ++g_mul; a.v *= b.v; return a; }
 // found by argument-dependent lookup from the templated kernel code
-inline Cnt lsqrt(Cnt a) { ++g_ops; return Cnt(std::sqrt(a.v)); }
-inline Cnt ltanh(Cnt a) { ++g_ops; return Cnt(std::tanh(a.v)); }
-inline Cnt lcbrt(Cnt a) { ++g_ops; return Cnt(std::cbrt(a.v)); }
+inline Cnt lsqrt(Cnt a) { ++g_ops; ++g_sqrt; return Cnt(std::sqrt(a.v)); }
+inline Cnt ltanh(Cnt a) { ++g_ops; ++g_tanh; return Cnt(std::tanh(a.v)); }
+inline Cnt lcbrt(Cnt a) { ++g_ops; ++g_cbrt; return Cnt(std::cbrt(a.v)); }
 inline Cnt lcos(Cnt a) { ++g_ops; return Cnt(std::cos(a.v)); }
 inline Cnt lsin(Cnt a) { ++g_ops; return Cnt(std::sin(a.v)); }
 
@@ -46,6 +48,13 @@ namespace {
 
 using lh::Dual;
 using lh::QpC;
+
+// float operations (+, -, *, fma, /, sqrt, cbrt, rint, ldexp: one each) of the double-word
+// primitives of lh_dd.cuh: sum 2 TwoSum + 2 FastTwoSum + 2 adds; product TwoProd + 2 + 1 +
+// FastTwoSum; quotient 2 divisions + product + sum + FastTwoSum; square and cube roots one
+// Newton correction; tanh = exp (range reduction, degree-12 Horner) + sum, difference, quotient
+constexpr long long kDwAdd = 20, kDwMul = 8, kDwDiv = 33, kDwSqrt = 28, kDwCbrt = 36;
+constexpr long long kDwTanh = 8 + (2 + 22 + 22 + 21 + 12 * (kDwMul + kDwAdd) + 2) + 2 * kDwAdd + kDwDiv;
 
 QpC<Cnt> consts(bool visc) {
   QpC<Cnt> c;
@@ -59,15 +68,18 @@ template <int DIM>
 long long count(int kind, bool visc) {
   const QpC<Cnt> c = consts(visc);
   g_ops = 0;
-  if (kind == 0) {
+  if (kind == 0 || kind == 4) {
     Cnt J[DIM][DIM], Gv[DIM][DIM], S[DIM][DIM], E, det;
     for (int i = 0; i < DIM; ++i)
       for (int j = 0; j < DIM; ++j) {
         J[i][j] = i == j ? 0.1 : 0.01;
         Gv[i][j] = 0.1 * (i + 1) - 0.05 * j;
       }
-    g_ops = 0;
+    g_ops = g_add = g_mul = g_div = g_sqrt = g_tanh = g_cbrt = 0;
     lh::qp_forward<DIM>(J, Gv, Cnt(2.0), c, S, E, det);
+    if (kind == 4)   // float operations of the same code in double-word arithmetic (lh_dd.cuh)
+      return g_add * kDwAdd + g_mul * kDwMul + g_div * kDwDiv + g_sqrt * kDwSqrt + g_cbrt * kDwCbrt +
+             g_tanh * kDwTanh;
   } else if (kind == 1) {
     Dual<Cnt> J[DIM][DIM], Gv[DIM][DIM], S[DIM][DIM], E, det;
     for (int i = 0; i < DIM; ++i)
@@ -110,7 +122,7 @@ extern "C" lh_status lh_record_len(int dim, int* len) {
 }
 
 extern "C" lh_status lh_qp_flops(int dim, int kind, int visc, long long* ops) {
-  if (!ops || (dim != 2 && dim != 3) || kind < 0 || kind > 3) return LH_EINVAL;
+  if (!ops || (dim != 2 && dim != 3) || kind < 0 || kind > 4) return LH_EINVAL;
   *ops = dim == 2 ? count<2>(kind, visc != 0) : count<3>(kind, visc != 0);
   return LH_OK;
 }
@@ -158,7 +170,7 @@ void tangent_check(bool visc, int trials, unsigned seed, double* max_double, dou
     lh::lin_record<DIM, double>(pr, c.gm1, c.q1, c.q2, visc, 0, 0, 0, Ld);
     lh::qp_tangent_lin<DIM, double>(Ld, dJ, dGv, de, c.q1, c.q2, visc, dSd, dEd, dWd);
     float Lf[lh::lin_len<DIM>()], dJf[DIM][DIM], dGf[DIM][DIM], dSf[DIM][DIM], dEf, dWf;
-    lh::lin_record<DIM, float>(pr, c.gm1, c.q1, c.q2, visc, 0, 0, 0, Lf);
+    lh::lin_record<DIM, float>(pr, c.gm1, (float)c.q1, (float)c.q2, visc, 0, 0, 0, Lf);
     for (int i = 0; i < DIM; ++i)
       for (int j = 0; j < DIM; ++j) {
         dJf[i][j] = (float)dJ[i][j];
@@ -229,3 +241,98 @@ extern "C" lh_status lh_qp_adjoint_check(int dim, int visc, int trials, unsigned
   *max_rel = dim == 2 ? adjoint_check<2>(visc != 0, trials, seed) : adjoint_check<3>(visc != 0, trials, seed);
   return LH_OK;
 }
+
+// ---- host check of the double-word arithmetic and of the residual's point kernel in it
+namespace {
+double rel(double got, double ref) { return std::fabs(got - ref) / std::fmax(std::fabs(ref), 1e-300); }
+
+template <int DIM>
+double dd_point_check(bool visc, int trials, Lcg& g) {
+  lh::QpC<double> c;
+  c.alpha = 0.3; c.mq = 1.3 * 0.3 * 0.002; c.inv_detJ0 = 500.0; c.gm1 = 0.4; c.ggm1 = 0.56;
+  c.h0 = 0.05; c.inv_hc = 20.0; c.q1 = 0.5; c.q2 = 1.0; c.scoef = 0.3; c.eps2 = 1e-12; c.visc = visc;
+  lh::QpC<lh::DD> cd;
+  cd.alpha = lh::DD(c.alpha); cd.mq = lh::DD(c.mq); cd.inv_detJ0 = lh::DD(c.inv_detJ0); cd.gm1 = lh::DD(c.gm1);
+  cd.ggm1 = lh::DD(c.ggm1); cd.h0 = lh::DD(c.h0); cd.inv_hc = lh::DD(c.inv_hc); cd.q1 = lh::DD(c.q1);
+  cd.q2 = lh::DD(c.q2); cd.scoef = lh::DD(c.scoef); cd.eps2 = lh::DD(c.eps2); cd.visc = visc;
+  const double s = DIM == 3 ? 0.126 : 0.045;
+  double worst = 0.0;
+  for (int tr = 0; tr < trials; ++tr) {
+    double J[DIM][DIM], Gv[DIM][DIM];
+    lh::DD Jd[DIM][DIM], Gd[DIM][DIM];
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        // inputs representable in double-word exactly: round through the pair
+        Jd[i][j] = lh::DD(s * ((i == j) + 0.2 * g.next()));
+        Gd[i][j] = lh::DD(g.next() * (tr % 3 == 0 ? 30.0 : 1.0));
+        J[i][j] = lh::to_double(Jd[i][j]);
+        Gv[i][j] = lh::to_double(Gd[i][j]);
+      }
+    const lh::DD ed = lh::DD(g.next() * (tr % 5 == 0 ? 1e-5 : 2.0));
+    const double e = lh::to_double(ed);
+    double S[DIM][DIM], E, det;
+    lh::DD Sd[DIM][DIM], Ed, detd;
+    lh::QpPrimal<DIM, double> pr;
+    lh::qp_forward<DIM>(J, Gv, e, c, S, E, det, &pr);
+    lh::qp_forward<DIM>(Jd, Gd, ed, cd, Sd, Ed, detd);
+    // error scale: the size of the stress terms before cancellation, W |J^-1| (|p| + mu_max |grad v|)
+    // with mu_max = rho h (q2 (h |grad v| + delta_s) + q1 c_s); divergence and trace
+    // cancellations make any finite precision lose relative accuracy below that scale
+    double nj = 0.0, nl = 0.0;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        nj += pr.Jinv[i][j] * pr.Jinv[i][j];
+        nl += pr.Lv[i][j] * pr.Lv[i][j];
+      }
+    nj = std::sqrt(nj);
+    nl = std::sqrt(nl);
+    const double mu_max = visc ? pr.rho * pr.h * (c.q2 * (pr.h * nl + pr.ds) + c.q1 * pr.cs) : 0.0;
+    const double scale = std::fabs(pr.W) * nj * (std::fabs(pr.p) + mu_max * nl);
+    double d = 0.0;
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        const double x = lh::to_double(Sd[i][j]) - S[i][j];
+        d += x * x;
+      }
+    worst = std::max({worst, std::sqrt(d) / scale, rel(lh::to_double(detd), det),
+                      std::fabs(lh::to_double(Ed) - E) / (scale * nl / nj + 1e-300)});
+  }
+  return worst;
+}
+}  // namespace
+
+extern "C" lh_status lh_dd_check(int which, int trials, unsigned seed, double* max_err) {
+  if (!max_err || trials < 1 || which < 0 || which > 9) return LH_EINVAL;
+  Lcg g{0x2545F4914F6CDD1DULL ^ seed};
+  double worst = 0.0;
+  using lh::DD;
+  if (which >= 6) {
+    *max_err = which == 6 ? dd_point_check<2>(false, trials, g) : which == 7 ? dd_point_check<2>(true, trials, g)
+             : which == 8 ? dd_point_check<3>(false, trials, g) : dd_point_check<3>(true, trials, g);
+    return LH_OK;
+  }
+  for (int t = 0; t < trials; ++t) {
+    const double a = g.next() * std::ldexp(1.0, (int)(g.next() * 20)), b = g.next() * std::ldexp(1.0, (int)(g.next() * 20));
+    const DD A(a), B(b);
+    const double ad = lh::to_double(A), bd = lh::to_double(B);
+    switch (which) {
+      case 0: {   // sum and difference (relative to the operands' size: cancellation is exact)
+        worst = std::max(worst, std::fabs(lh::to_double(A + B) - (ad + bd)) / (std::fabs(ad) + std::fabs(bd)));
+        worst = std::max(worst, std::fabs(lh::to_double(A - B) - (ad - bd)) / (std::fabs(ad) + std::fabs(bd)));
+        break;
+      }
+      case 1: worst = std::max(worst, rel(lh::to_double(A * B), ad * bd)); break;
+      case 2: worst = std::max(worst, rel(lh::to_double(A / B), ad / bd)); break;
+      case 3: worst = std::max(worst, rel(lh::to_double(lh::lsqrt(DD(std::fabs(ad)))), std::sqrt(std::fabs(ad)))); break;
+      case 4: worst = std::max(worst, rel(lh::to_double(lh::lcbrt(DD(std::fabs(ad)))), std::cbrt(std::fabs(ad)))); break;
+      case 5: {   // tanh on [-25, 25] (absolute error: |tanh| <= 1)
+        const DD z(25.0 * g.next());
+        worst = std::max(worst, std::fabs(lh::to_double(lh::ltanh(z)) - std::tanh(lh::to_double(z))));
+        break;
+      }
+    }
+  }
+  *max_err = worst;
+  return LH_OK;
+}
+

@@ -23,6 +23,9 @@ struct ElemParams {
   unsigned bc;
   // float copies for the FP32 tangent kernels (no conversions on the FP64 pipe there)
   float fh0, finv_hc, fq1, fq2, fscoef, feps2, finv_detJ0;
+  // double-word (hi, lo float pairs) copies of the mesh constants for the residual's point
+  // kernel on the FP32 pipe: 1 / detJ0, h0, 1 / h_coarse, q1, q2, scoef, eps_e^2
+  float dw_inv_detJ0[2], dw_h0[2], dw_inv_hc[2], dw_q1[2], dw_q2[2], dw_scoef[2], dw_eps2[2];
   const float* fmq0;       // device [NE]: rho0 detJ0
   const float* fgm1;       // device [NE]: gamma - 1
   const float* fggm1;      // device [NE]: gamma (gamma - 1)

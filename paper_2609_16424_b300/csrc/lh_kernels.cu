@@ -24,10 +24,11 @@ __global__ void __launch_bounds__(Cfg<DIM, K>::THREADS)
 k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk, double tau,
            double* __restrict__ ev, double* __restrict__ Re, double* __restrict__ blockmin,
            float* __restrict__ rec) {
-  // Element contractions in double-float (DF, FP32 pipe), the quadrature-point kernel and
-  // everything written out in FP64.  Positions enter the contractions relative to the
-  // element's first node (the reference gradients of the basis sum to zero, so J is
-  // unchanged), which keeps J accurate to ~2^-46 relative on fine meshes.
+  // Element contractions (DF) and the quadrature-point kernel (DD) in double-word arithmetic
+  // on the FP32 pipe; gathers, the element outputs and the det J minimum in FP64.  Positions
+  // enter the contractions relative to the element's first node (the reference gradients of
+  // the basis sum to zero, so J is unchanged), which keeps J accurate to ~2^-46 relative on
+  // fine meshes.
   using C = Cfg<DIM, K>;
   constexpr int D = C::D, Q = C::Q, ND = C::ND, NL = C::NL, NQ = C::NQ;
   constexpr int NCH = 2 * DIM;
@@ -39,16 +40,16 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
   const DF* sB = sdf + TB::B;
   const DF* sG = sdf + TB::G;
   const DF* sBl = sdf + TB::BL;
-  const double* sW = smem + TB::W;
+  const DF* sW = sdf + TB::W;
   double* red = smem + TB::SMEM;
-  for (int i = threadIdx.x; i < TB::SMEM; i += blockDim.x) {
-    if (i < TB::W) sdf[i] = DF(P.tab[i]);
-    else smem[i] = P.tab[i];
-  }
+  for (int i = threadIdx.x; i < TB::SMEM; i += blockDim.x) sdf[i] = DF(P.tab[i]);
   const int eb = threadIdx.x / NQ, lt = threadIdx.x % NQ;
   DF* s_h = sdf + PL::HEAD + eb * PL::PER;   // [2 DIM][ND]: w_x - w_x(node 0), w_v
   DF* s_kv = s_h + NCH * ND;                 // [DIM][ND]: k_v
   DF* s_l = s_kv + DIM * ND;                 // [2][NL]: w_e, k_e
+  // [3] per element: rho0 detJ0, gamma - 1, gamma (gamma - 1), in the reduction buffer (which
+  // the final det J minimum overwrites only after many barriers)
+  DF* s_c = reinterpret_cast<DF*>(red) + 3 * eb;
   DF* t1 = s_l + 2 * NL;
   DF* t2 = t1 + PL::T1;
   DF* sf = t2 + PL::T2;
@@ -86,6 +87,12 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
     s_l[i] = DF(we);
     s_l[NL + i] = DF(ke);
   }
+  if (lt == 0) {   // per-element material constants, split once per element
+    const double rho0 = E.valid ? P.rho0[E.e] : 1.0, gam = E.valid ? P.gamma[E.e] : 1.4;
+    s_c[0] = DF(rho0 * P.detJ0);
+    s_c[1] = DF(gam - 1.0);
+    s_c[2] = DF(gam * (gam - 1.0));
+  }
   __syncthreads();
   DF hvd[NCH], hgd[NCH][DIM];
   // positions at the quadrature points are only needed by the 2D Taylor-Green source
@@ -94,29 +101,44 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
   l2_fwd<DIM, K, DIM, DF, D>(s_kv, t1, t2, sB, lt, kvd);
   DF lqd[2];
   l2_fwd<DIM, K, 2, DF>(s_l, t1, t2, sBl, lt, lqd);
-  double hv[DIM], kvq[DIM], lq[2] = {to_double(lqd[0]), to_double(lqd[1])};
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) {
-    hv[c] = DIM == 2 ? to_double(hvd[c]) + x0[c] : 0.0;
-    kvq[c] = to_double(kvd[c]);
+  // quadrature-point constants in double-word (mesh constants split on the host)
+  QpC<DD> c;
+  {
+    const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+    DD a = dd_of(sW[q0]) * dd_of(sW[q1]);
+    if constexpr (DIM == 3) a = a * dd_of(sW[q2]);
+    c.alpha = a;
+    c.mq = dd_of(s_c[0]) * a;
+    c.gm1 = dd_of(s_c[1]);
+    c.ggm1 = dd_of(s_c[2]);
+    c.inv_detJ0 = DD(P.dw_inv_detJ0[0], P.dw_inv_detJ0[1]);
+    c.h0 = DD(P.dw_h0[0], P.dw_h0[1]);
+    c.inv_hc = DD(P.dw_inv_hc[0], P.dw_inv_hc[1]);
+    c.q1 = DD(P.dw_q1[0], P.dw_q1[1]);
+    c.q2 = DD(P.dw_q2[0], P.dw_q2[1]);
+    c.scoef = DD(P.dw_scoef[0], P.dw_scoef[1]);
+    c.eps2 = DD(P.dw_eps2[0], P.dw_eps2[1]);
+    c.visc = P.visc != 0;
   }
-
-  const QpC<double> c = qp_consts<DIM, K, double>(P, E, sW, lt);
-  double J[DIM][DIM], Gv[DIM][DIM];
+  DD J[DIM][DIM], Gv[DIM][DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
 #pragma unroll
     for (int r = 0; r < DIM; ++r) {
-      J[i][r] = to_double(hgd[i][r]);
-      Gv[i][r] = to_double(hgd[DIM + i][r]);
+      J[i][r] = dd_of(hgd[i][r]);
+      Gv[i][r] = dd_of(hgd[DIM + i][r]);
     }
   if (!E.valid) {
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) J[i][i] = 1.0;   // keep the idle lanes finite
+    for (int i = 0; i < DIM; ++i) J[i][i] = DD(1.f);   // keep the idle lanes finite
   }
-  double So[DIM][DIM], Eo, detJ;
-  QpPrimal<DIM, double> pr;
-  qp_forward<DIM>(J, Gv, lq[0], c, So, Eo, detJ, rec ? &pr : nullptr);
+  DD So[DIM][DIM], Eo, detJd;
+  QpPrimal<DIM, DD> pr;
+  qp_forward<DIM>(J, Gv, dd_of(lqd[0]), c, So, Eo, detJd, rec ? &pr : nullptr);
+  const double detJ = to_double(detJd);
+  double hv[DIM];
+#pragma unroll
+  for (int cc = 0; cc < DIM; ++cc) hv[cc] = DIM == 2 ? to_double(hvd[cc]) + x0[cc] : 0.0;
   if (rec && E.valid) {   // linearisation record of the tangent (float, [NE][fields][NQ])
     double tgs = 0.0, tgx = 0.0, tgy = 0.0;
     if constexpr (DIM == 2) {
@@ -126,7 +148,7 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
       }
     }
     float L[lin_len<DIM>()];
-    lin_record<DIM>(pr, c.gm1, c.q1, c.q2, c.visc, tgs, tgx, tgy, L);
+    lin_record<DIM, float, DD>(pr, c.gm1, P.fq1, P.fq2, c.visc, tgs, tgx, tgy, L);
     float* rq = rec + E.e * lin_len<DIM>() * NQ + lt;
 #pragma unroll
     for (int f = 0; f < lin_len<DIM>(); ++f) rq[f * NQ] = L[f];
@@ -134,18 +156,18 @@ k_residual(ElemParams P, const double* __restrict__ u, const double* __restrict_
   DF fval[DIM], Sd[DIM][DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
-    fval[i] = DF(c.mq * kvq[i]);
+    fval[i] = df_of(c.mq * dd_of(kvd[i]));
 #pragma unroll
-    for (int r = 0; r < DIM; ++r) Sd[i][r] = DF(So[i][r]);
+    for (int r = 0; r < DIM; ++r) Sd[i][r] = df_of(So[i][r]);
   }
-  double g = c.mq * lq[1] - Eo;
+  DD g = c.mq * dd_of(lqd[1]) - Eo;
   if constexpr (DIM == 2) {
-    if (P.tg) g -= c.alpha * detJ * tg_source<double, double>(hv[0], hv[1]);
+    if (P.tg) g = g - c.alpha * detJd * DD(tg_source<double, double>(hv[0], hv[1]));
   }
   h1_bwd<DIM, K, DIM>(fval, Sd, sf, t1, t2, sB, sG, lt, s_h);
   if (E.valid)
     for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = to_double(s_h[i]);
-  DF gv[1] = {DF(g)};
+  DF gv[1] = {df_of(g)};
   l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
   if (E.valid)
     for (int i = lt; i < NL; i += NQ) Re[E.e * NL + i] = to_double(s_l[i]);

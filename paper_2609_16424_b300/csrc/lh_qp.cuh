@@ -3,6 +3,7 @@
 // hand-written adjoint (reverse mode) for the transpose action.
 #pragma once
 #include "lh_common.cuh"
+#include "lh_dd.cuh"
 
 namespace lh {
 
@@ -172,38 +173,46 @@ __host__ __device__ constexpr int lin_len() { return DIM == 3 ? 25 : 18; }
 
 enum LinField : int { LF_W = 0, LF_P, LF_PE, LF_MU, LF_ATH, LF_ADIV, LF_AE, LF_TGS, LF_TGX, LF_TGY };
 
-template <int DIM, class R = float>
-__host__ __device__ __forceinline__ void lin_record(const QpPrimal<DIM, double>& pr, double gm1, double q1, double q2,
-                                                    bool visc, double tgs, double tgx, double tgy,
-                                                    R (&L)[lin_len<DIM>()]) {
+// conversion of a primal intermediate (double or double-word) to the record's precision
+template <class R>
+__host__ __device__ __forceinline__ R rcv(double x) { return R(x); }
+template <class R>
+__host__ __device__ __forceinline__ R rcv(const DD& x) {
+  if constexpr (sizeof(R) == sizeof(float)) return x.hi;   // hi is x rounded to float
+  else return R(to_double(x));
+}
+
+template <int DIM, class R = float, class PT = double>
+__host__ __device__ __forceinline__ void lin_record(const QpPrimal<DIM, PT>& pr, PT gm1, R q1, R q2, bool visc,
+                                                    double tgs, double tgx, double tgy, R (&L)[lin_len<DIM>()]) {
   constexpr int O = 2 * DIM * DIM;
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      L[i * DIM + j] = R(pr.Jinv[i][j]);
-      L[DIM * DIM + i * DIM + j] = R(pr.Lv[i][j]);
+      L[i * DIM + j] = rcv<R>(pr.Jinv[i][j]);
+      L[DIM * DIM + i * DIM + j] = rcv<R>(pr.Lv[i][j]);
     }
-  // the chain is formed in the record's precision R (float on the GPU: no FP64 divisions
-  // in the residual kernel), from the double intermediates rounded once
-  const R isq = R(1) / R(pr.sq);
-  L[O + LF_W] = R(pr.W);
-  L[O + LF_P] = R(pr.p);
-  L[O + LF_PE] = R(gm1 * pr.rho) * R(pr.ep) * isq;
+  // the chain is formed in the record's precision R (float on the GPU), from the primal
+  // intermediates rounded once; 1 - t^2 and psi in the primal precision (1 - t^2 cancels)
+  const R isq = R(1) / rcv<R>(pr.sq);
+  L[O + LF_W] = rcv<R>(pr.W);
+  L[O + LF_P] = rcv<R>(pr.p);
+  L[O + LF_PE] = rcv<R>(gm1 * pr.rho) * rcv<R>(pr.ep) * isq;
   if (visc) {
-    double div = 0.0;
+    PT div = pr.Lv[0][0];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) div += pr.Lv[i][i];
-    const R h = R(pr.h), dv = R(pr.h * div), rh = R(pr.rho * pr.h), ds = R(pr.ds), ab = R(pr.ab), cs = R(pr.cs);
+    for (int i = 1; i < DIM; ++i) div = div + pr.Lv[i][i];
+    const R h = rcv<R>(pr.h), dv = rcv<R>(pr.h * div), rh = rcv<R>(pr.rho * pr.h), ds = rcv<R>(pr.ds);
+    const R ab = rcv<R>(pr.ab), cs = rcv<R>(pr.cs);
     const R ke = R(0.5) * isq, iab = R(1) / ab;
-    const R g4 = R(0.25 * (1.0 - pr.t * pr.t)) / ds;   // (1 - t^2) / (4 delta_s), 1 - t^2 in double
-    const R psi = R(0.5 + 0.5 * pr.t);
-    const R q1r = R(q1), q2r = R(q2);
-    L[O + LF_MU] = R(pr.mu);
+    const R g4 = rcv<R>(PT(0.25) * (PT(1) - pr.t * pr.t)) / ds;   // (1 - t^2) / (4 delta_s)
+    const R psi = rcv<R>(PT(0.5) + PT(0.5) * pr.t);
+    L[O + LF_MU] = rcv<R>(pr.mu);
     // a_th = mu (1/dim - 1) + rh q2 |.| / dim with mu = rh (q2 |.| + q1 c_s psi), cancellation-free
-    L[O + LF_ATH] = rh * (q2r * ab * R(2.0 / DIM - 1.0) + q1r * cs * psi * R(1.0 / DIM - 1.0));
-    L[O + LF_ADIV] = rh * h * (q2r * dv * iab - q1r * cs * g4);
-    L[O + LF_AE] = rh * ke * (q2r * ds * ds * iab + q1r * cs * (psi + g4 * dv));
+    L[O + LF_ATH] = rh * (q2 * ab * R(2.0 / DIM - 1.0) + q1 * cs * psi * R(1.0 / DIM - 1.0));
+    L[O + LF_ADIV] = rh * h * (q2 * dv * iab - q1 * cs * g4);
+    L[O + LF_AE] = rh * ke * (q2 * ds * ds * iab + q1 * cs * (psi + g4 * dv));
   } else {
     L[O + LF_MU] = L[O + LF_ATH] = L[O + LF_ADIV] = L[O + LF_AE] = R(0);
   }

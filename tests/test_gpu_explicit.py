@@ -22,6 +22,7 @@ CASES = [
     (2, (4, 3), 2, False, True),     # Taylor-Green source, no viscosity
     (2, (3, 2), 3, True, False),
     (2, (2, 2), 4, True, False),
+    (2, (3, 3), 3, False, True),     # Taylor-Green source at Q3-Q2
     (3, (3, 2, 2), 1, True, False),
     (3, (2, 2, 2), 2, True, False),
     (3, (2, 1, 1), 3, True, False),
@@ -55,7 +56,7 @@ def test_force_and_estimate_parity(param, model):
 
 @pytest.mark.parametrize("scheme", [2, 3, 4])
 @pytest.mark.parametrize("model", ["imp", "exp"])
-@pytest.mark.parametrize("param", [CASES[1], CASES[2], CASES[6]], ids=[IDS[1], IDS[2], IDS[6]])
+@pytest.mark.parametrize("param", [CASES[1], CASES[2], CASES[5], CASES[7]], ids=[IDS[1], IDS[2], IDS[5], IDS[7]])
 def test_explicit_step_parity(param, model, scheme):
     c = _case(param, model)
     dt = 0.2 * dt_estimate(c.hyd, c.u)
