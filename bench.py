@@ -206,6 +206,64 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
+def fp32_ops_residual(dim, k, visc=True):
+    """Float operations per element of the residual kernel as it runs: the sum-factorised
+    contractions in double-float (a multiply-add costs 15 float operations: TwoProd with its
+    cross terms 4, the accumulation TwoSum + FastTwoSum 11) and the point kernel in
+    double-word arithmetic (lh_qp_flops kind 4), the per-point glue (dim + 4 products, one
+    sum) weighed the same way (8 and 20 float operations)."""
+    import ctypes as C
+    import paper_2609_16424_b300 as lh
+    grad, valgrad, val = sf_macs(dim, k)
+    macs = 2 * dim * grad + dim * val(k + 1) + 2 * val(k) + dim * valgrad + val(k)
+    ops = C.c_longlong()
+    lh.lib.lh_qp_flops(dim, 4, int(visc), C.byref(ops))
+    return 15 * macs + (2 * k) ** dim * (ops.value + 8 * (dim + 4) + 20)
+
+
+def dominant_roofline(kind, launch_ms, ne, k, prec, fp64_peak, fp32_peak):
+    """Roofline of the step's dominant element kernel (3D, order k).
+    residual: float operations of its double-word arithmetic against the FP32 pipe's
+    operation rate (half the FMA FLOP/s probe; an FMA is one operation), with the
+    FP64-accurate algorithmic FLOP/s beside it against the FP64 FMA probe.
+    FP32 record J.w: the larger of its FP32-FLOP fraction and its HBM fraction (algorithmic
+    bytes: record, direction, element output)."""
+    t = launch_ms * 1e-3
+    name = {"residual": "k_residual<3,2>", "jvp_fp64": "k_jvp<3,2,double,double>",
+            "jvp_fp32": "k_jvp_rec<3,2,double>", "jvp_tc": f"k_jvp_tc<3,2,{prec}>"}.get(kind, kind)
+    out = {"kernel": name, "launch_ms": round(launch_ms, 5), "peak_source": "measured FMA probe (lh_probe_fma) "
+           "this run" if kind != "jvp_fp32" else None}
+    if kind == "residual":
+        ops = fp32_ops_residual(3, k) * ne
+        fl = flops_per_element(3, k, "residual") * ne
+        out.update({"bound": "alu", "pipe": "fp32 (double-word arithmetic)", "unit": "Top/s",
+                    "achieved": round(ops / t / 1e12, 4), "peak": round(fp32_peak / 2, 3),
+                    "frac": round(ops / t / 1e12 / (fp32_peak / 2), 4), "fp32_ops_per_launch": ops,
+                    "fp64_accurate_tflops": round(fl / t / 1e12, 4), "fp64_fma_peak_tflops": round(fp64_peak, 3),
+                    "algorithmic_flops_per_launch": fl})
+        return out
+    if kind == "jvp_fp32":
+        fl = flops_per_element(3, k, "jvp_rec") * ne
+        by = record_bytes(3, k, ne)
+        ff, fb = fl / t / 1e12 / fp32_peak, by / t / 1e9 / HBM_PEAK_GBS
+        if fb >= ff:
+            out.update({"bound": "hbm", "unit": "GB/s", "achieved": round(by / t / 1e9, 1), "peak": HBM_PEAK_GBS,
+                        "frac": round(fb, 4), "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({HBM_PEAK_SOURCE})"})
+        else:
+            out.update({"bound": "alu", "pipe": "fp32", "unit": "TFLOP/s", "achieved": round(fl / t / 1e12, 4),
+                        "peak": round(fp32_peak, 3), "frac": round(ff, 4),
+                        "peak_source": "measured FMA probe (lh_probe_fma) this run"})
+        out.update({"algorithmic_bytes_per_launch": by, "algorithmic_flops_per_launch": fl,
+                    "hbm_frac": round(fb, 4), "fp32_flop_frac": round(ff, 4)})
+        return out
+    fl = flops_per_element(3, k, {"jvp_fp64": "jvp", "jvp_tc": "jvp_rec"}[kind]) * ne
+    peak = fp64_peak if kind == "jvp_fp64" else fp32_peak
+    out.update({"bound": "alu", "pipe": "fp64" if kind == "jvp_fp64" else "fp32", "unit": "TFLOP/s",
+                "achieved": round(fl / t / 1e12, 4), "peak": round(peak, 3), "frac": round(fl / t / 1e12 / peak, 4),
+                "algorithmic_flops_per_launch": fl})
+    return out
+
+
 def tc_mma_flops(dim, k, ne, kind):
     """Tensor-core flops one k_jvp_tc launch issues (dense, padded element operators:
     per batch of 16 elements one 128 x NF x KF forward MMA and 128 x NB x 64 backward MMAs
@@ -443,22 +501,11 @@ def run_ours(args, rank, world, device):
     # dominant kernel of the timed steps
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_kind, (dom_ms, dom_cnt) = dom[0], dom[1]
-    # inside the Newton step the FP32 J.w runs from the linearisation record
-    dom_flops = ne * {"residual": fl["residual"], "jvp_fp64": fl["jvp"], "jvp_fp32": fl["jvp_rec"],
-                      "jvp_tc": fl["jvp_rec"]}[dom_kind]
-    dom_peak = fp64_peak if dom_kind in ("residual", "jvp_fp64") else fp32_peak
-    achieved = dom_flops / (dom_ms / dom_cnt * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": {"residual": "k_residual<3,2>", "jvp_fp64": "k_jvp<3,2,double,double>",
-                                           "jvp_fp32": "k_jvp_rec<3,2,double>",
-                                           "jvp_tc": f"k_jvp_tc<3,2,{prec}>"}.get(dom_kind, dom_kind),
-                "pipe": "fp64" if dom_peak is fp64_peak else "fp32",
-                "achieved": round(achieved, 4), "peak": round(dom_peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / dom_peak, 4), "peak_source": "measured FMA probe (lh_probe_fma) this run",
-                "traffic": None, "launch_ms": round(dom_ms / dom_cnt, 5), "launches": dom_cnt,
-                "share_of_step": round(dom_ms / sum(times), 4),
-                "algorithmic_flops_per_launch": dom_flops}
+    roofline = dominant_roofline(dom_kind, dom_ms / dom_cnt, ne, W["k"], prec, fp64_peak, fp32_peak)
+    roofline.update({"launches": dom_cnt, "share_of_step": round(dom_ms / sum(times), 4)})
 
     cap = NCU_TRAFFIC.get(roofline["kernel"])
+    roofline["traffic"] = None
     if cap is not None and cap["csrc"] == csrc_digest():
         roofline["traffic"] = cap["bytes"]
         roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of this build"
@@ -992,17 +1039,19 @@ def run_precond_compare(args):
     rows = []
 
     def probe(name, m, u, dt, kk, reps=5):
-        for pc in ("kron", "jvv_diag", "jacobi"):
+        for pc, extra in (("kron", {}), ("jvv_diag", {}), ("jacobi", {}), ("cheb", {"cheb_degree": 2}),
+                          ("cheb", {"cheb_degree": 3}), ("cheb", {"cheb_degree": 5})):
             ts, st = [], None
             for _ in range(reps):
                 ug, kg = u.clone(), kk.clone()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                st = m.newton_step(ug, kg, dt, jvp_prec="fp32", precond=pc, **NEWTON)
+                st = m.newton_step(ug, kg, dt, jvp_prec="fp32", precond=pc, **extra, **NEWTON)
                 torch.cuda.synchronize()
                 ts.append((time.perf_counter() - t0) * 1e3)
-            rows.append({"case": name, "precond": pc, "ms": round(statistics.median(ts), 3),
-                         "newton": st["newton_its"], "gmres": st["gmres_its_total"]})
+            rows.append({"case": name, "precond": pc + (f"{extra['cheb_degree']}" if extra else ""),
+                         "ms": round(statistics.median(ts), 3), "newton": st["newton_its"],
+                         "gmres": st["gmres_its_total"], "jvp_evals": st["jvp_evals"]})
 
     W = WORKLOAD
     m = lh.Mesh(3, W["n"], (0,) * 3, (1,) * 3, W["k"], gamma=W["gamma"], device="cuda:0")

@@ -231,7 +231,12 @@ typedef struct {
                               (Eq. (23)), recomputed from the linearisation record at every
                               Newton iterate, each free entry kept at >= 0.5 diag(M_V) (the
                               viscous tangent is not sign-definite) (needs jvp_prec other than
-                              LH_FP64); default 1 */
+                              LH_FP64); 3 = a Chebyshev iteration (the matrix-free smoother the
+                              paper's Sec. 5 points to) on the velocity Schur block
+                              S = M_V + tau dF.1/dv + tau^2 dF.1/dx (the block Eq. (23)'s velocity
+                              part approximates, with the exact elimination of the x rows),
+                              Jacobi-scaled by the diagonal of kind 2, S applied by the record
+                              J.w (reduced-precision J.w only); default 1 */
   int forcing;             /* 0: every linear solve to gmres_rtol (default); 1: adaptive
                               forcing terms (Eisenstat and Walker 1996, choice 2 with gamma 0.9,
                               alpha 2, and the safeguard against oversolving the last step):
@@ -245,6 +250,11 @@ typedef struct {
                               row-scaled system W J dk = -W R), so the v and e rows are not
                               weighted by mass factors that shrink with the mesh size; stats
                               r0 / rfinal are then in that norm */
+  int cheb_degree;         /* precond 3: degree of the Chebyshev polynomial (>= 1; degree m
+                              costs m - 1 Jacobian actions per application); default 3 */
+  double cheb_ratio;       /* precond 3: the Chebyshev interval is [b / ratio, b], b = 1.1 x the
+                              largest eigenvalue of D^-1 S estimated by 5 power steps at every
+                              Newton iterate; default 20 */
 } lh_newton_opts;
 
 typedef struct {

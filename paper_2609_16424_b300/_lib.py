@@ -35,7 +35,8 @@ class NewtonOpts(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_atol", C.c_double), ("gmres_rtol", C.c_double),
                 ("newton_maxit", C.c_int), ("gmres_maxit", C.c_int), ("restart", C.c_int),
                 ("max_halvings", C.c_int), ("jvp_prec", C.c_int), ("precond", C.c_int),
-                ("forcing", C.c_int), ("eta_max", C.c_double), ("scaled_norm", C.c_int)]
+                ("forcing", C.c_int), ("eta_max", C.c_double), ("scaled_norm", C.c_int),
+                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double)]
 
 
 class StepStats(C.Structure):

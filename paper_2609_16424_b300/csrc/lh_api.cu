@@ -269,7 +269,12 @@ struct KrylovOp {
   const double* wsc = nullptr;   // row weights W of the scaled norm: the operator is W J P^-1
 
   lh_status apply(const T* x, T* y) {
-    LH_CK(m, (launch_prec<T, T>(pk, m->stream, m->P, m->kron, prec_diag(m, pk), m->d_invMe, x, z, tau)));
+    if (pk == 3) {
+      lh_status st = cheb(x, z);
+      if (st != LH_OK) return st;
+    } else {
+      LH_CK(m, (launch_prec<T, T>(pk, m->stream, m->P, m->kron, prec_diag(m, pk), m->d_invMe, x, z, tau)));
+    }
     if constexpr (sizeof(T) == sizeof(double)) {
       LH_CK(m, launch_jvp_f64(m->P, m->stream, u, k, tau, z, m->d_ev, y, prof_pair(m, LH_PROF_JVP64)));
     } else {
@@ -285,6 +290,34 @@ struct KrylovOp {
     return launch_jvp_tc<float>(m->P, m->stream, tck, m->d_rec, tau, x, reinterpret_cast<float*>(m->d_ev), y,
                                 tc_err(m), prof_pair(m, LH_PROF_JVPTC));
   }
+  // z = P^-1 x with the Chebyshev velocity block (kind 3, FP32 record J.w); float input
+  template <class TZ>
+  lh_status cheb(const T* x, TZ* out) {
+    if constexpr (sizeof(T) != sizeof(float)) {
+      return fail(m, LH_EINVAL, "precond 3 needs the FP32 Krylov basis");
+    } else {
+      cudaStream_t s = m->stream;
+      const long long n = m->n, n1 = (long long)m->P.dim * m->P.NV, ld = m->ldf;
+      float* res = m->d_cheb;
+      float* d = res + ld;
+      float* zc = d + ld;
+      float* wdir = zc + ld;
+      float* jw = wdir + ld;
+      const double a = m->cheb_b / m->cheb_ratio, b = m->cheb_b;
+      const double theta = 0.5 * (b + a), delta = 0.5 * (b - a), sigma = theta / delta;
+      LH_CK(m, launch_cheb_init<float>(s, n1, m->d_jdiag, x, res, d, zc, 1.0 / theta));
+      double rho_old = 1.0 / sigma;
+      for (int it = 1; it < m->cheb_degree; ++it) {
+        LH_CK(m, launch_cheb_dir(s, n1, n, d, wdir, tau));
+        LH_CK(m, jvp_f32(wdir, jw));
+        const double rho = 1.0 / (2.0 * sigma - rho_old);
+        LH_CK(m, launch_cheb_step(s, n1, m->d_jdiag, jw, res, d, zc, rho * rho_old, 2.0 * rho / delta));
+        rho_old = rho;
+      }
+      LH_CK(m, (launch_cheb_out<float, TZ>(s, n1, n, m->d_invMe, x, zc, out, tau)));
+      return LH_OK;
+    }
+  }
   // y = J d for a double vector d (restarts)
   lh_status jac(const double* d, T* y) {
     if constexpr (sizeof(T) == sizeof(double)) {
@@ -297,6 +330,40 @@ struct KrylovOp {
     return LH_OK;
   }
 };
+
+// Upper end of the spectrum of D^-1 S for the Chebyshev interval of preconditioner kind 3:
+// five power steps from the diagonal itself, S applied by the record J.w; b = 1.1 x the
+// estimate (tmp: double scratch of dim NV)
+lh_status cheb_bounds(lh_mesh* m, const lh_newton_opts& o, double tau, int tck, double* tmp) {
+  cudaStream_t s = m->stream;
+  const long long n = m->n, n1 = (long long)m->P.dim * m->P.NV, ld = m->ldf;
+  float* v = m->d_cheb;
+  float* y = v + ld;
+  float* wdir = v + 3 * ld;
+  float* jw = v + 4 * ld;
+  KrylovOp<float> op{m, 3, tck, nullptr, nullptr, tau, nullptr};
+  lh_status st;
+  LH_CK(m, launch_to_f32(s, m->d_jdiag, v + n1, n1));
+  double nv2 = 0.0, lam = 0.0;
+  LH_CK(m, launch_to_f64(s, v + n1, tmp, n1));
+  if ((st = dot_host(m, tmp, tmp, n1, &nv2)) != LH_OK) return st;
+  LH_CK(m, (launch_scale<float, float>(s, 1.0 / std::sqrt(nv2), v + n1, 0.0, nullptr, v + n1, n1)));
+  for (int it = 0; it < 5; ++it) {
+    LH_CK(m, launch_cheb_dir(s, n1, n, v, wdir, tau));
+    LH_CK(m, op.jvp_f32(wdir, jw));
+    LH_CK(m, launch_cheb_scale(s, n1, m->d_jdiag, jw, y));
+    LH_CK(m, launch_to_f64(s, y + n1, tmp, n1));
+    double ny2 = 0.0;
+    if ((st = dot_host(m, tmp, tmp, n1, &ny2)) != LH_OK) return st;
+    if (!(ny2 > 0.0) || !std::isfinite(ny2)) return fail(m, LH_ENONFINITE, "precond 3: power iteration failed");
+    lam = std::sqrt(ny2);
+    LH_CK(m, (launch_scale<float, float>(s, 1.0 / lam, y + n1, 0.0, nullptr, v + n1, n1)));
+  }
+  m->cheb_b = 1.1 * lam;
+  m->cheb_ratio = o.cheb_ratio;
+  m->cheb_degree = o.cheb_degree;
+  return LH_OK;
+}
 
 // Restarted, right-preconditioned GMRES on J dk = -r from dk = 0 (paper Sec. 3.5, Eq. (22)).
 // Classical Gram-Schmidt applied twice (CGS2), each pass one fused reduction (V^T w and
@@ -390,7 +457,12 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
     }
     LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
     LH_CK(m, launch_gemv<T>(s, V, j, ld, dh, 0.0, ulin, len));
-    LH_CK(m, (launch_prec<T, double>(op.pk, s, m->P, m->kron, prec_diag(m, op.pk), m->d_invMe, ulin, zd, op.tau)));
+    if (op.pk == 3) {
+      if ((st = op.template cheb<double>(ulin, zd)) != LH_OK) return st;
+    } else {
+      LH_CK(m, (launch_prec<T, double>(op.pk, s, m->P, m->kron, prec_diag(m, op.pk), m->d_invMe, ulin, zd,
+                                       op.tau)));
+    }
     LH_CK(m, launch_axpby(s, 1.0, zd, 1.0, dk, n));
     if (done || total >= o.gmres_maxit) break;
     // restart from the true linear residual -r - J dk
@@ -549,6 +621,8 @@ void lh_newton_opts_init(lh_newton_opts* o) {
   o->forcing = 0;
   o->eta_max = 0.1;
   o->scaled_norm = 0;
+  o->cheb_degree = 3;
+  o->cheb_ratio = 20.0;
 }
 
 lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
@@ -699,6 +773,7 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_rec) cudaFree(m->d_rec);
   if (m->d_stage) cudaFree(m->d_stage);
   if (m->d_adv) cudaFree(m->d_adv);
+  if (m->d_cheb) cudaFree(m->d_cheb);
   if (m->d_xwork) cudaFree(m->d_xwork);
   if (m->d_wscale) cudaFree(m->d_wscale);
   if (m->d_jdiag) cudaFree(m->d_jdiag);
@@ -929,9 +1004,11 @@ static lh_status check_newton_opts(lh_mesh* m, const lh_newton_opts& o) {
     return fail(m, LH_EINVAL, "unsupported jvp_prec");
   if ((o.jvp_prec == LH_TF32 || o.jvp_prec == LH_BF16) && !jvp_tc_supported(m->P.dim, m->P.K))
     return fail(m, LH_EINVAL, "tensor-core J.w supports 2D orders 1-4 and 3D orders 1-2");
-  if (o.precond != 0 && o.precond != 1 && o.precond != 2) return fail(m, LH_EINVAL, "precond must be 0, 1 or 2");
-  if (o.precond == 2 && o.jvp_prec == LH_FP64)
-    return fail(m, LH_EINVAL, "precond 2 (diagonal of the velocity block) needs a reduced-precision J.w");
+  if (o.precond < 0 || o.precond > 3) return fail(m, LH_EINVAL, "precond must be 0, 1, 2 or 3");
+  if (o.precond >= 2 && o.jvp_prec == LH_FP64)
+    return fail(m, LH_EINVAL, "precond 2 and 3 (velocity block) need a reduced-precision J.w");
+  if (o.precond == 3 && (o.cheb_degree < 1 || o.cheb_degree > 16 || !(o.cheb_ratio > 1.0)))
+    return fail(m, LH_EINVAL, "precond 3: need 1 <= cheb_degree <= 16 and cheb_ratio > 1");
   if (o.forcing != 0 && o.forcing != 1) return fail(m, LH_EINVAL, "forcing must be 0 or 1");
   if (o.forcing && !(o.eta_max >= o.gmres_rtol && o.eta_max < 1.0))
     return fail(m, LH_EINVAL, "eta_max must be in [gmres_rtol, 1)");
@@ -973,9 +1050,11 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
   float* zf = wf + ldf;
   float* uf = zf + ldf;
 
-  if (o.precond == 2 && !m->d_jdiag &&
+  if (o.precond >= 2 && !m->d_jdiag &&
       cudaMalloc(&m->d_jdiag, sizeof(double) * (size_t)m->P.dim * m->P.NV) != cudaSuccess)
     return fail(m, LH_ENOMEM, "cannot allocate the velocity-block diagonal");
+  if (o.precond == 3 && !m->d_cheb && cudaMalloc(&m->d_cheb, sizeof(float) * 5 * (size_t)ldf) != cudaSuccess)
+    return fail(m, LH_ENOMEM, "cannot allocate the Chebyshev work vectors");
   const double* wsc = nullptr;
   if (o.scaled_norm) {
     if (!m->d_wscale) {
@@ -1017,9 +1096,10 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     // ---- linear solve J dk = -r (Eq. (22)) at the current iterate k
     lh_newton_opts oi = o;
     oi.gmres_rtol = eta;
-    if (o.precond == 2)   // the record describes the current iterate k (its last residual)
+    if (o.precond >= 2)   // the record describes the current iterate k (its last residual)
       LH_CK(m, launch_jvv_diag(m->P, s, rec, tau, reinterpret_cast<float*>(m->d_ev), m->d_diagMv, m->d_jdiag,
                                kJvvFloor));
+    if (o.precond == 3 && (st = cheb_bounds(m, o, tau, tck, zd)) != LH_OK) return st;
     const double* rhs = r;   // with scaled_norm GMRES solves W J dk = -W r
     if (wsc) {
       LH_CK(m, launch_row_mul<double>(s, wsc, r, rs, n));

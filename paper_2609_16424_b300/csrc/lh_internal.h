@@ -100,6 +100,9 @@ struct lh_mesh {
   double* d_xwork = nullptr;       // explicit path work arrays (lazily, lh_api.cu XWork)
   double* d_adv = nullptr;         // lh_advance trial state u, k and the internal increment [3 n] (lazily)
   double* d_wscale = nullptr;      // row weights of the scaled Newton norm [n] (lazily)
+  float* d_cheb = nullptr;         // Chebyshev work vectors of preconditioner kind 3 [5 ldf] (lazily)
+  double cheb_b = 1.0, cheb_ratio = 20.0;   // Chebyshev interval [b / ratio, b] at the current iterate
+  int cheb_degree = 3;
   double* d_jdiag = nullptr;       // diagonal of dR_v/dk_v for preconditioner kind 2 [dim NV] (lazily)
   const double* rec_u = nullptr;   // arguments of the last lh_linearize (for the LH_FP32_LIN check)
   const double* rec_k = nullptr;

@@ -113,6 +113,18 @@ cudaError_t launch_to_f64(cudaStream_t s, const float* x, double* y, long long n
 template <class TR, class TZ>
 cudaError_t launch_prec(int kind, cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* diag_mv,
                         const double* inv_me, const TR* r, TZ* z, double tau);
+// Chebyshev pieces of preconditioner kind 3 (lh_prec.cu); state-shaped float vectors whose
+// velocity rows [n1, 2 n1) are used; dv the per-dof velocity diagonal [n1]
+template <class TR>
+cudaError_t launch_cheb_init(cudaStream_t s, long long n1, const double* dv, const TR* r, float* res, float* d,
+                             float* z, double inv_theta);
+cudaError_t launch_cheb_dir(cudaStream_t s, long long n1, long long n, const float* d, float* w, double tau);
+cudaError_t launch_cheb_step(cudaStream_t s, long long n1, const double* dv, const float* jw, float* res, float* d,
+                             float* z, double c1, double c2);
+template <class TR, class TZ>
+cudaError_t launch_cheb_out(cudaStream_t s, long long n1, long long n, const double* ime, const TR* r, const float* z,
+                            TZ* out, double tau);
+cudaError_t launch_cheb_scale(cudaStream_t s, long long n1, const double* dv, const float* x, float* y);
 // J.w with float arithmetic, float input and double output (inside the FP64 Krylov solver)
 cudaError_t launch_jvp_f32_to_f64(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                                   const float* dk, float* ev, double* out, cudaEvent_t* ev2 = nullptr);

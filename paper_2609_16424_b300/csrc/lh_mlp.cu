@@ -6,9 +6,11 @@
 // averaged onto the shared H1 nodes.
 //
 // Network: Linear -> GELU -> ... -> Linear, exact GELU z Phi(z), mean-squared-error loss,
-// Adam with bias correction.  Matrix products run on the tensor cores (mma.sync m16n8k16,
-// operands rounded to BF16, FP32 accumulation); master weights, biases, activations and the
-// optimiser state are FP32.  Every reduction has a fixed order (deterministic).
+// Adam with bias correction.  Matrix products run on the 5th-generation tensor cores
+// (tcgen05.mma kind::f16 issued by one thread, operands rounded to BF16 and staged in shared
+// memory, FP32 accumulators in tensor memory read back by tcgen05.ld for the bias / GELU
+// epilogue); master weights, biases, activations and the optimiser state are FP32.  Every
+// reduction has a fixed order (deterministic).
 #include <cuda_bf16.h>
 #include <algorithm>
 #include <cstdint>
@@ -19,23 +21,14 @@
 #include <vector>
 #include "lh_internal.h"
 #include "lh_kernels.h"
+#include "lh_tc.cuh"
 
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 16, kPad = 8;
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+// tile of one CTA: 128 rows (tensor-memory lanes) x 64 columns, K staged 64 at a time
+constexpr int kTM = 128, kTN = 64, kTK = 64;
+constexpr uint32_t kSboA = (uint32_t)(kTK / 8) * 128u;   // bytes between 8-row groups (K-major interleaved)
+constexpr uint32_t kWaitPolls = 1u << 22;                 // mbarrier polls before giving up
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
@@ -44,63 +37,104 @@ __device__ __forceinline__ float gelu_grad(float z) {
 
 // C[m][n] (=|+=) act( sum_k A(m,k) B(k,n) + bias[n] ), A(m,k) = A[m*lam + k*lak],
 // B(k,n) = B[k*lbk + n*lbn]; Z (optional) receives the pre-activation.  act: 0 none, 1 GELU.
-// Block 128 threads = 4 warps; block tile 64 x 64; each warp 16 rows x 64 columns.
+// Block 128 threads; tile kTM x kTN.  The threads stage A and B as BF16 in the K-major
+// interleaved layout (8-row x 16-byte core matrices; the staging loop runs along whichever
+// index has unit stride, so either operand may be K- or MN-major in memory); thread 0
+// issues four K = 16 MMAs per stage into the FP32 accumulator in tensor memory and commits
+// to an mbarrier that every thread waits on (bounded: after a timeout the tile's outputs are
+// NaN and *err is set).  Each warp reads its 32 accumulator lanes for the epilogue.
 __global__ void __launch_bounds__(128)
-k_gemm_bf16(int M, int N, int K, const float* __restrict__ A, long long lam, long long lak,
-            const float* __restrict__ B, long long lbk, long long lbn, const float* __restrict__ bias, int act,
-            float* __restrict__ Z, float* __restrict__ C, long long ldc, int accumulate) {
-  __shared__ __align__(16) __nv_bfloat16 sA[kBM][kBK + kPad];
-  __shared__ __align__(16) __nv_bfloat16 sB[kBN][kBK + kPad];
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t2 = (lane & 3) * 2;
-  float acc[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-  for (int k0 = 0; k0 < K; k0 += kBK) {
-    for (int idx = threadIdx.x; idx < kBM * kBK; idx += blockDim.x) {
-      const int r = idx / kBK, c = idx % kBK;
+k_gemm_tc(int M, int N, int K, const float* __restrict__ A, long long lam, long long lak,
+          const float* __restrict__ B, long long lbk, long long lbn, const float* __restrict__ bias, int act,
+          float* __restrict__ Z, float* __restrict__ C, long long ldc, int accumulate, int* __restrict__ err) {
+  using namespace lh;
+  __shared__ __align__(1024) unsigned char sA[kTM * kTK * 2];
+  __shared__ __align__(1024) unsigned char sB[kTN * kTK * 2];
+  __shared__ uint64_t mbar, mdrain;
+  __shared__ uint32_t taddr;
+  const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(&taddr, kTN);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mdrain, 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tm = taddr;
+  const uint32_t idesc = tc::instr_desc(tc::KIND_BF16, kTM, kTN);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < K; k0 += kTK) {
+    // stage A [kTM x kTK] and B [kTN x kTK] (rows m resp. n, K index c)
+    const bool a_k_fast = lak == 1;
+    for (int idx = tid; idx < kTM * kTK; idx += 128) {
+      const int r = a_k_fast ? idx / kTK : idx % kTM, c = a_k_fast ? idx % kTK : idx / kTM;
       const int gm = m0 + r, gk = k0 + c;
       const float v = (gm < M && gk < K) ? A[gm * lam + gk * lak] : 0.f;
-      sA[r][c] = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16*>(sA + tc::off_il(r, c, 2, 128u, kSboA)) = __float2bfloat16_rn(v);
     }
-    for (int idx = threadIdx.x; idx < kBN * kBK; idx += blockDim.x) {
-      const int r = idx / kBK, c = idx % kBK;
+    const bool b_k_fast = lbk == 1;
+    for (int idx = tid; idx < kTN * kTK; idx += 128) {
+      const int r = b_k_fast ? idx / kTK : idx % kTN, c = b_k_fast ? idx % kTK : idx / kTN;
       const int gn = n0 + r, gk = k0 + c;
       const float v = (gn < N && gk < K) ? B[gk * lbk + gn * lbn] : 0.f;
-      sB[r][c] = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16*>(sB + tc::off_il(r, c, 2, 128u, kSboA)) = __float2bfloat16_rn(v);
     }
-    __syncthreads();
-    const int ar = warp * 16 + g;
-    uint32_t a[4];
-    a[0] = *reinterpret_cast<const uint32_t*>(&sA[ar][t2]);
-    a[1] = *reinterpret_cast<const uint32_t*>(&sA[ar + 8][t2]);
-    a[2] = *reinterpret_cast<const uint32_t*>(&sA[ar][t2 + 8]);
-    a[3] = *reinterpret_cast<const uint32_t*>(&sA[ar + 8][t2 + 8]);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    tc::fence_after_sync();
+    if (!ok) break;
+    if (tid == 0) {
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      uint32_t b[2];
-      b[0] = *reinterpret_cast<const uint32_t*>(&sB[nt * 8 + g][t2]);
-      b[1] = *reinterpret_cast<const uint32_t*>(&sB[nt * 8 + g][t2 + 8]);
-      mma_bf16(acc[nt], a, b);
+      for (int j = 0; j < kTK / 16; ++j) {
+        const uint32_t ko = (uint32_t)(j * 2) * 128u;   // two core matrices (16 K entries) per MMA
+        tc::mma<tc::KIND_BF16>(tm, tc::smem_desc(tc::smem_u32(sA) + ko, 128u, kSboA, tc::SW_NONE),
+                               tc::smem_desc(tc::smem_u32(sB) + ko, 128u, kSboA, tc::SW_NONE), idesc,
+                               k0 > 0 || j > 0);
+      }
+      tc::commit(&mbar);
     }
-    __syncthreads();
+    ok = tc::mbar_wait(&mbar, phase, kWaitPolls);   // the stage is read: shared memory reusable
+    phase ^= 1u;
   }
+  tc::fence_before_sync();
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  tc::fence_after_sync();
+  if (!ok && tid == 0) {   // record the timeout, let issued MMAs drain before releasing tensor memory
+    atomicExch(err, 1);
+    tc::commit(&mdrain);
+    tc::mbar_wait(&mdrain, 0, kWaitPolls);
+  }
+  const int r = m0 + 32 * warp + lane;
+#pragma unroll 1
+  for (int ch = 0; ch < kTN / 8; ++ch) {
+    float v[8];
+    if (ok) {
+      tc::tmem_ld8(tm + ((uint32_t)(32 * warp) << 16) + (uint32_t)(8 * ch), v);
+      tc::tmem_wait_ld();
+    }
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int r = m0 + warp * 16 + g + (h >= 2 ? 8 : 0);
-      const int c = n0 + nt * 8 + t2 + (h & 1);
+    for (int t = 0; t < 8; ++t) {
+      const int c = n0 + 8 * ch + t;
       if (r >= M || c >= N) continue;
-      float z = acc[nt][h] + (bias ? bias[c] : 0.f);
+      float z = ok ? v[t] + (bias ? bias[c] : 0.f) : __int_as_float(0x7fc00000);
       if (Z) Z[r * ldc + c] = z;
       const float y = act == 1 ? gelu(z) : z;
       if (accumulate) C[r * ldc + c] += y;
       else C[r * ldc + c] = y;
     }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tm, kTN);
 }
 
 // dZ = dH * GELU'(Z)
@@ -274,6 +308,7 @@ struct lh_mlp {
   float* d_act = nullptr;    // activations / pre-activations workspace
   long long act_cap = 0;
   double* d_part = nullptr;  // loss partials
+  int* d_err = nullptr;      // set by a tensor-core GEMM whose bounded wait timed out
   std::string err;
   std::vector<long long> woff, boff;   // parameter offsets per layer
   std::vector<int> din, dout;          // layer shapes
@@ -292,11 +327,21 @@ lh_status mfail(lh_mlp* m, lh_status st, const std::string& msg) {
     if (e__ != cudaSuccess) return mfail(m, LH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
   } while (0)
 
+// the flag of the tensor-core GEMMs' bounded waits (synchronises; clears the flag)
+lh_status check_tc(lh_mlp* m) {
+  int flag = 0;
+  MLP_CK(m, cudaMemcpyAsync(&flag, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  MLP_CK(m, cudaStreamSynchronize(m->stream));
+  if (!flag) return LH_OK;
+  MLP_CK(m, cudaMemsetAsync(m->d_err, 0, sizeof(int), m->stream));
+  return mfail(m, LH_ECUDA, "MLP: a bounded wait on the tensor cores timed out (results are NaN)");
+}
+
 cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float* A, long long lam, long long lak, const float* B,
                  long long lbk, long long lbn, const float* bias, int act, float* Z, float* C, long long ldc,
-                 int accumulate) {
-  dim3 grid(nb(N, kBN), nb(M, kBM));
-  k_gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, lam, lak, B, lbk, lbn, bias, act, Z, C, ldc, accumulate);
+                 int accumulate, int* err) {
+  dim3 grid(nb(N, kTN), nb(M, kTM));
+  k_gemm_tc<<<grid, 128, 0, s>>>(M, N, K, A, lam, lak, B, lbk, lbn, bias, act, Z, C, ldc, accumulate, err);
   lh::count_launches(1);
   return cudaGetLastError();
 }
@@ -332,7 +377,7 @@ lh_status forward(lh_mlp* m, const float* X, int M, float** Hs, float** Zs) {
     const bool last = l == L - 1;
     float* out = last ? Zs[l] : Hs[l + 1];
     MLP_CK(m, gemm(s, M, m->dout[l], m->din[l], Hs[l], m->din[l], 1, m->d_w + m->woff[l], 1, m->din[l],
-                   m->d_w + m->boff[l], last ? 0 : 1, last ? nullptr : Zs[l], out, m->dout[l], 0));
+                   m->d_w + m->boff[l], last ? 0 : 1, last ? nullptr : Zs[l], out, m->dout[l], 0, m->d_err));
   }
   return LH_OK;
 }
@@ -370,7 +415,8 @@ lh_status lh_mlp_create(int n_in, int hidden, int layers, int n_out, const float
   const size_t bytes = sizeof(float) * o;
   if (cudaMalloc(&m->d_w, bytes) != cudaSuccess || cudaMalloc(&m->d_g, bytes) != cudaSuccess ||
       cudaMalloc(&m->d_m, bytes) != cudaSuccess || cudaMalloc(&m->d_v, bytes) != cudaSuccess ||
-      cudaMalloc(&m->d_part, sizeof(double) * 1024) != cudaSuccess) {
+      cudaMalloc(&m->d_part, sizeof(double) * 1024) != cudaSuccess ||
+      cudaMalloc(&m->d_err, sizeof(int)) != cudaSuccess || cudaMemset(m->d_err, 0, sizeof(int)) != cudaSuccess) {
     lh_mlp_destroy(m);
     return mfail(nullptr, LH_ENOMEM, "lh_mlp_create: device allocation failed");
   }
@@ -394,6 +440,7 @@ lh_status lh_mlp_destroy(lh_mlp* m) {
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (m->d_part) cudaFree(m->d_part);
+  if (m->d_err) cudaFree(m->d_err);
   delete m;
   return LH_OK;
 }
@@ -404,7 +451,7 @@ lh_status lh_mlp_params(lh_mlp* m, float* host_out) {
   if (!m || !host_out) return mfail(m, LH_EINVAL, "NULL argument to lh_mlp_params");
   MLP_CK(m, cudaMemcpyAsync(host_out, m->d_w, sizeof(float) * m->n_params, cudaMemcpyDeviceToHost, m->stream));
   MLP_CK(m, cudaStreamSynchronize(m->stream));
-  return LH_OK;
+  return check_tc(m);
 }
 
 lh_status lh_mlp_forward(lh_mlp* m, const float* X, int M, float* Y) {
@@ -438,12 +485,12 @@ lh_status lh_mlp_grad(lh_mlp* m, const float* X, const float* T, int M, float* g
   for (int l = L - 1; l >= 0; --l) {
     const int N = m->dout[l], K = m->din[l];
     // dW_l = dZ^T H_l  ([N][K], reduction over the M rows), db_l = column sums of dZ
-    MLP_CK(m, gemm(s, N, K, M, dA, 1, N, Hs[l], K, 1, nullptr, 0, nullptr, m->d_g + m->woff[l], K, 0));
+    MLP_CK(m, gemm(s, N, K, M, dA, 1, N, Hs[l], K, 1, nullptr, 0, nullptr, m->d_g + m->woff[l], K, 0, m->d_err));
     k_colsum<<<N, 256, 0, s>>>(dA, M, N, m->d_g + m->boff[l]);
     lh::count_launches(1);
     if (l == 0) break;
     // dH_l = dZ W_l ([M][K]); dZ_{l-1} = dH_l * GELU'(Z_{l-1})
-    MLP_CK(m, gemm(s, M, K, N, dA, N, 1, m->d_w + m->woff[l], K, 1, nullptr, 0, nullptr, dB, K, 0));
+    MLP_CK(m, gemm(s, M, K, N, dA, N, 1, m->d_w + m->woff[l], K, 1, nullptr, 0, nullptr, dB, K, 0, m->d_err));
     k_gelu_back<<<nb((long long)M * K, 256), 256, 0, s>>>(dB, Zs[l - 1], dA, (long long)M * K);
     lh::count_launches(1);
     MLP_CK(m, cudaGetLastError());
@@ -455,6 +502,7 @@ lh_status lh_mlp_grad(lh_mlp* m, const float* X, const float* T, int M, float* g
     double sum = 0.0;
     for (int i = 0; i < pb; ++i) sum += part[i];
     *loss = sum / (double)ny;
+    if ((st = check_tc(m)) != LH_OK) return st;
   }
   if (grad_out)
     MLP_CK(m, cudaMemcpyAsync(grad_out, m->d_g, sizeof(float) * m->n_params, cudaMemcpyDeviceToDevice, s));

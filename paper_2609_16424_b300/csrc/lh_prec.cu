@@ -216,17 +216,34 @@ k_kron_xy(ElemParams P, const float* __restrict__ Ax_free, const float* __restri
   const float* Ax = c == 0 ? Ax_fixed : Ax_free;
   const float* Ay = c == 1 ? Ay_fixed : Ay_free;
   const long long plane = (long long)c * nv + (long long)N0 * N1 * zp;
-  for (int i = t; i < kNP * kNP; i += kXYThreads) {
+  // all global loads of the stage first (independent, in flight together), then the stores:
+  // a loop that alternates loads and shared-memory stores serialises their latencies
+  constexpr int NL = (kNP * kNP + kXYThreads - 1) / kXYThreads;
+  float ax[NL], ay[NL];
+  double rv[NL], sv[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int i = t + l * kXYThreads;
     const int a = i / kNP, b = i % kNP;
-    sAx[a][b] = (a < N0 && b < N0) ? __ldg(Ax + a * N0 + b) : 0.f;
-    sAy[a][b] = (a < N1 && b < N1) ? __ldg(Ay + a * N1 + b) : 0.f;
+    const bool in = i < kNP * kNP;
+    ax[l] = (in && a < N0 && b < N0) ? __ldg(Ax + a * N0 + b) : 0.f;
+    ay[l] = (in && a < N1 && b < N1) ? __ldg(Ay + a * N1 + b) : 0.f;
     const int y = a, x = b;   // plane read coalesced along x, stored transposed
-    float v = 0.f;
-    if (x < N0 && y < N1) {
+    rv[l] = sv[l] = 0.0;
+    if (in && x < N0 && y < N1) {
       const long long node = (long long)x + (long long)N0 * y + (plane - (long long)c * nv);
-      v = (float)((double)r[n1 + (long long)c * nv + node] * scale[node]);
+      rv[l] = (double)r[n1 + (long long)c * nv + node];
+      sv[l] = scale[node];
     }
-    sPT[x][y] = v;
+  }
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const int i = t + l * kXYThreads;
+    if (i >= kNP * kNP) break;
+    const int a = i / kNP, b = i % kNP;
+    sAx[a][b] = ax[l];
+    sAy[a][b] = ay[l];
+    sPT[b][a] = (float)(rv[l] * sv[l]);
   }
   __syncthreads();
   constexpr int NT = kNP / 4;
@@ -369,6 +386,94 @@ __global__ void k_precond_dof(ElemParams P, const double* __restrict__ dv, const
     z[i] = TZ((double)r[i] * ime[i - 2 * n1]);
   }
 }
+
+// ---- Chebyshev iteration on the velocity Schur block (preconditioner kind 3) -------------
+// S = dR_v/dk_v + tau dR_v/dk_x = M_V + tau dF.1/dv + tau^2 dF.1/dx, applied through the
+// record J.w to directions [tau d | d | 0]; Jacobi-scaled by D = the clamped diagonal of
+// M_V + tau dF/dv (1 on fixed rows).  Vectors are state-shaped; only velocity rows are used.
+template <class TR>
+__global__ void k_cheb_init(long long n1, const double* __restrict__ dv, const TR* __restrict__ r,
+                            float* __restrict__ res, float* __restrict__ d, float* __restrict__ z, float inv_theta) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n1) return;
+  const float rv = (float)r[n1 + j];
+  const float dj = inv_theta * (float)(rv / dv[j]);
+  res[n1 + j] = rv;
+  d[n1 + j] = dj;
+  z[n1 + j] = dj;
+}
+
+__global__ void k_cheb_dir(long long n1, long long n, const float* __restrict__ d, float* __restrict__ w, float tau) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  w[i] = i < n1 ? tau * d[n1 + i] : (i < 2 * n1 ? d[i] : 0.f);
+}
+
+__global__ void k_cheb_step(long long n1, const double* __restrict__ dv, const float* __restrict__ jw,
+                            float* __restrict__ res, float* __restrict__ d, float* __restrict__ z, float c1, float c2) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n1) return;
+  const float rj = res[n1 + j] - jw[n1 + j];
+  res[n1 + j] = rj;
+  const float dj = c1 * d[n1 + j] + c2 * (float)(rj / dv[j]);
+  d[n1 + j] = dj;
+  z[n1 + j] += dj;
+}
+
+template <class TR, class TZ>
+__global__ void k_cheb_out(long long n1, long long n, const double* __restrict__ ime, const TR* __restrict__ r,
+                           const float* __restrict__ z, TZ* __restrict__ out, double tau) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i < n1) out[i] = TZ((double)r[i] + tau * (double)z[n1 + i]);
+  else if (i < 2 * n1) out[i] = TZ(z[i]);
+  else out[i] = TZ((double)r[i] * ime[i - 2 * n1]);
+}
+
+// velocity rows only: y_v = D^-1 x_v (the power iteration of the Chebyshev bounds)
+__global__ void k_cheb_scale(long long n1, const double* __restrict__ dv, const float* __restrict__ x,
+                             float* __restrict__ y) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n1) return;
+  y[n1 + j] = (float)(x[n1 + j] / dv[j]);
+}
+
+template <class TR>
+cudaError_t launch_cheb_init(cudaStream_t s, long long n1, const double* dv, const TR* r, float* res, float* d,
+                             float* z, double inv_theta) {
+  k_cheb_init<TR><<<nb(n1, 256), 256, 0, s>>>(n1, dv, r, res, d, z, (float)inv_theta);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_cheb_dir(cudaStream_t s, long long n1, long long n, const float* d, float* w, double tau) {
+  k_cheb_dir<<<nb(n, 256), 256, 0, s>>>(n1, n, d, w, (float)tau);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_cheb_step(cudaStream_t s, long long n1, const double* dv, const float* jw, float* res, float* d,
+                             float* z, double c1, double c2) {
+  k_cheb_step<<<nb(n1, 256), 256, 0, s>>>(n1, dv, jw, res, d, z, (float)c1, (float)c2);
+  count_launches(1);
+  return cudaGetLastError();
+}
+template <class TR, class TZ>
+cudaError_t launch_cheb_out(cudaStream_t s, long long n1, long long n, const double* ime, const TR* r, const float* z,
+                            TZ* out, double tau) {
+  k_cheb_out<TR, TZ><<<nb(n, 256), 256, 0, s>>>(n1, n, ime, r, z, out, tau);
+  count_launches(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_cheb_scale(cudaStream_t s, long long n1, const double* dv, const float* x, float* y) {
+  k_cheb_scale<<<nb(n1, 256), 256, 0, s>>>(n1, dv, x, y);
+  count_launches(1);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cheb_init<float>(cudaStream_t, long long, const double*, const float*, float*, float*,
+                                             float*, double);
+template cudaError_t launch_cheb_out<float, float>(cudaStream_t, long long, long long, const double*, const float*,
+                                                   const float*, float*, double);
+template cudaError_t launch_cheb_out<float, double>(cudaStream_t, long long, long long, const double*, const float*,
+                                                    const float*, double*, double);
 
 template <class TR, class TZ>
 cudaError_t launch_prec(int kind, cudaStream_t s, const ElemParams& P, const KronPrec& K, const double* diag_mv,

@@ -21,8 +21,7 @@ def newton_opts(**kw):
     """lh_newton_opts with the library defaults, overridden by keyword arguments
     (newton_rtol, newton_atol, gmres_rtol, newton_maxit, gmres_maxit, restart,
     max_halvings, jvp_prec in {'fp64', 'fp32', 'tf32', 'bf16'}, precond in {'jacobi', 'kron',
-    'jvv_diag'},
-    forcing, eta_max, scaled_norm);
+    'jvv_diag', 'cheb'}, forcing, eta_max, scaled_norm, cheb_degree, cheb_ratio);
     'tf32' and 'bf16' run the element contractions of J.w on the tensor cores."""
     o = _lib.NewtonOpts()
     _L.lh_newton_opts_init(C.byref(o))
@@ -34,7 +33,7 @@ def newton_opts(**kw):
             val = {"fp64": _lib.LH_FP64, "fp32": _lib.LH_FP32, "tf32": _lib.LH_TF32,
                    "bf16": _lib.LH_BF16}.get(val, val)
         if key == "precond":
-            val = {"jacobi": 0, "kron": 1, "jvv_diag": 2}.get(val, val)
+            val = {"jacobi": 0, "kron": 1, "jvv_diag": 2, "cheb": 3}.get(val, val)
         setattr(o, key, val)
     return o
 
