@@ -97,33 +97,37 @@ def test_features_and_completion_layout():
     assert np.allclose(k0, ref0, rtol=1e-6, atol=1e-6)
 
 
-def test_learned_proposal_gains_on_heldout_blasts():
-    """Trained on blasts with seeded gamma in [1.3, 1.7] and deposits in [0.1, 0.5]; on held-out
-    seeds the proposal's initial residual and its distance to the converged increment are
-    below plain extrapolation's (Newton iterations are reported, at a fixed tolerance)."""
-    import paper_2609_16424_b300 as lh
+def _family(make, nrun, steps, ntrain, dim, k, cfl):
+    """Seeded trajectories of a problem family, a network trained on the first ntrain runs,
+    and the held-out runs (Newton rtol 1e-8 for the training data, FP32 J.w)."""
     from paper_2609_16424_b300 import mlp
-    from paper_2609_16424_b300.states import blast_state
-    rng = np.random.default_rng(0)
     newton = dict(newton_rtol=1e-8, gmres_rtol=1e-4, gmres_maxit=200, restart=30, jvp_prec="fp32")
     runs = []
-    for gam, en in [(rng.uniform(1.3, 1.7), rng.uniform(0.1, 0.5)) for _ in range(8)]:
-        gm = lh.Mesh(3, (8, 8, 8), (0,) * 3, (1,) * 3, 2, gamma=gam)
-        u0 = blast_state(gm, en)
-        runs.append((gm, u0, mlp.trajectory(gm, u0, 24, **newton)))
+    for i in range(nrun):
+        gm, u0 = make(i)
+        runs.append((gm, u0, mlp.trajectory(gm, u0, steps, cfl=cfl, **newton)))
     gm0 = runs[0][0]
-    train = [tr for _, _, tr in runs[:6]]
+    train = [tr for _, _, tr in runs[:ntrain]]
     fscale = torch.zeros(4, dtype=torch.float32, device="cuda")
-    fscale[:3] = mlp.group_rms(gm0, [k for tr in train for _, k in tr]).float()
+    fscale[:3] = mlp.group_rms(gm0, [kk for tr in train for _, kk in tr]).float()
     fscale[3] = float(np.mean([dt for tr in train for dt, _ in tr]))
     tscale = torch.ones(4, dtype=torch.float32, device="cuda")
     tscale[:3] = mlp.group_rms(gm0, [tr[i][1] - tr[i - 1][1] for tr in train for i in range(1, len(tr))]).float()
     X, T = mlp.dataset(gm0, train, fscale, tscale)
-    n_in, n_out = mlp.feature_sizes(3, 2)
+    n_in, n_out = mlp.feature_sizes(dim, k)
     net = mlp.MLP(n_in, 128, 3, n_out, seed=1)
     mlp.train(net, X, T, epochs=40)
-    ratios_r, ratios_e, its = [], [], []
-    for gm, u0, tr in runs[6:]:
+    return net, fscale, tscale, runs[ntrain:]
+
+
+def _evaluate(net, fscale, tscale, heldout, tol):
+    """On held-out steps: initial-residual and error ratios of the proposal against plain
+    extrapolation, and Newton / GMRES iterations of both guesses to one absolute tolerance,
+    tol x ||R(k^{n-1})|| (the paper's relative tolerance 1e-5, measured against the fallback's
+    initial residual, so that both guesses stop at the same accuracy)."""
+    from paper_2609_16424_b300 import mlp
+    ratios_r, ratios_e, its, gits = [], [], [], []
+    for gm, u0, tr in heldout:
         u = u0.clone()
         for i, (dt, kn) in enumerate(tr):
             tau = 0.5 * dt
@@ -131,17 +135,56 @@ def test_learned_proposal_gains_on_heldout_blasts():
                 k1, k2 = tr[i - 1][1], tr[i - 2][1]
                 k0 = mlp.apply(gm, u, tau, k1, net.forward(mlp.features(gm, k1, k2, dt, fscale)), tscale)
                 r1 = float(gm.residual(u, k1, tau).norm())
-                r0 = float(gm.residual(u, k0, tau).norm())
-                ratios_r.append(r0 / r1)
+                ratios_r.append(float(gm.residual(u, k0, tau).norm()) / r1)
                 ratios_e.append(float((k0 - kn).norm() / (k1 - kn).norm()))
-                pair = []
+                pair, gpair = [], []
                 for guess in (k1, k0):
-                    st = gm.newton_step(u.clone(), guess.clone(), dt, newton_rtol=1e-30, newton_atol=1e-8 * r1,
+                    st = gm.newton_step(u.clone(), guess.clone(), dt, newton_rtol=1e-30, newton_atol=tol * r1,
                                         gmres_rtol=1e-4, gmres_maxit=200, restart=30, jvp_prec="fp32")
                     pair.append(st["newton_its"])
+                    gpair.append(st["gmres_its_total"])
                 its.append(pair)
+                gits.append(gpair)
             u = u + dt * kn
-    print("residual ratio", np.mean(ratios_r), "error ratio", np.mean(ratios_e), "newton its", np.mean(its, axis=0))
-    assert np.mean(ratios_r) < 0.2
-    assert np.mean(ratios_e) < 0.7
-    assert np.mean(its, axis=0)[1] <= np.mean(its, axis=0)[0] + 0.5
+    return np.mean(ratios_r), np.mean(ratios_e), np.mean(its, axis=0), np.mean(gits, axis=0)
+
+
+def test_learned_proposal_on_heldout_blasts():
+    """3D point blasts (the 24^3 benchmark family at 8^3), seeded gamma in [1.3, 1.7] and
+    deposits in [0.1, 0.5], 6 training runs, 2 held out.  The proposal's initial residual and
+    its distance to the converged increment are well below plain extrapolation's.  Measured
+    (not asserted): at the paper's tolerance it saves no Newton iteration and GMRES needs more
+    iterations than from extrapolation, so it does not pay on this family."""
+    import paper_2609_16424_b300 as lh
+    from paper_2609_16424_b300.states import blast_state
+    rng = np.random.default_rng(0)
+    params = [(rng.uniform(1.3, 1.7), rng.uniform(0.1, 0.5)) for _ in range(8)]
+
+    def make(i):
+        gm = lh.Mesh(3, (8, 8, 8), (0,) * 3, (1,) * 3, 2, gamma=params[i][0])
+        return gm, blast_state(gm, params[i][1])
+    net, fs, ts, held = _family(make, 8, 24, 6, 3, 2, 2.0)
+    rr, re, its, gits = _evaluate(net, fs, ts, held, 1e-5)
+    print("blast: residual ratio", rr, "error ratio", re, "newton", its, "gmres", gits)
+    assert rr < 0.2 and re < 0.7
+
+
+def test_learned_proposal_gains_on_taylor_green():
+    """2D Taylor-Green vortex, 16 x 16 Q2-Q1, seeded velocity amplitudes in [0.5, 1.5] and
+    pressure levels p0 in [1, 10], implicit midpoint at FS-CFL 8; 6 training runs, 2 held out.
+    At the paper's tolerance the proposal takes fewer Newton iterations and fewer GMRES
+    iterations per step than plain extrapolation.  (On the 8 x 8 mesh with 12 training runs
+    the same network saves nothing: fewer elements per step give less training data.)"""
+    from paper_2609_16424_b300.states import taylor_green_problem
+    rng = np.random.default_rng(1)
+    params = [(rng.uniform(0.5, 1.5), rng.uniform(1.0, 10.0)) for _ in range(8)]
+
+    def make(i):
+        gm, u = taylor_green_problem(16, 2, p0=params[i][1], device="cuda:0")
+        u[2 * gm.NV:4 * gm.NV] *= params[i][0]
+        return gm, u
+    net, fs, ts, held = _family(make, 8, 24, 6, 2, 2, 8.0)
+    rr, re, its, gits = _evaluate(net, fs, ts, held, 1e-5)
+    print("taylor-green: residual ratio", rr, "error ratio", re, "newton", its, "gmres", gits)
+    assert rr < 0.2 and re < 0.7
+    assert its[1] < its[0] and gits[1] < gits[0], (its, gits)
