@@ -172,9 +172,10 @@ def test_learned_proposal_on_heldout_blasts():
 def test_learned_proposal_gains_on_taylor_green():
     """2D Taylor-Green vortex, 16 x 16 Q2-Q1, seeded velocity amplitudes in [0.5, 1.5] and
     pressure levels p0 in [1, 10], implicit midpoint at FS-CFL 8; 6 training runs, 2 held out.
-    At the paper's tolerance the proposal takes fewer Newton iterations and fewer GMRES
-    iterations per step than plain extrapolation.  (On the 8 x 8 mesh with 12 training runs
-    the same network saves nothing: fewer elements per step give less training data.)"""
+    At the paper's tolerance the proposal takes fewer Newton iterations per step than plain
+    extrapolation.  GMRES iterations are reported, not asserted: on this family they drop,
+    but over 160 training and 39 held-out runs (bench.py --mlp) they grow, and the step is
+    slower than with extrapolation."""
     from paper_2609_16424_b300.states import taylor_green_problem
     rng = np.random.default_rng(1)
     params = [(rng.uniform(0.5, 1.5), rng.uniform(1.0, 10.0)) for _ in range(8)]
@@ -187,4 +188,4 @@ def test_learned_proposal_gains_on_taylor_green():
     rr, re, its, gits = _evaluate(net, fs, ts, held, 1e-5)
     print("taylor-green: residual ratio", rr, "error ratio", re, "newton", its, "gmres", gits)
     assert rr < 0.2 and re < 0.7
-    assert its[1] < its[0] and gits[1] < gits[0], (its, gits)
+    assert its[1] < its[0], (its, gits)
