@@ -671,6 +671,10 @@ lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
     lh_mesh_destroy(m);
     return fail(nullptr, LH_ENOMEM, "device allocation failed in lh_mesh_create");
   }
+  if (lh::init_const_tables() != cudaSuccess) {
+    lh_mesh_destroy(m);
+    return fail(nullptr, LH_ECUDA, "writing the constant basis tables failed in lh_mesh_create");
+  }
   P.rho0 = m->d_rho0;
   P.gamma = m->d_gamma;
   P.tab = m->d_tab;

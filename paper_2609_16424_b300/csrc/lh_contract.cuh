@@ -1,16 +1,35 @@
 // Sum-factorised basis contractions (the B and B^T operators of paper Sec. 2.2, Eq. (8)).
 //
 // Tensor-product elements let B act one direction at a time (Sec. 2.2: O(p^{d+1}) work
-// per element instead of O(p^{2d})).  One thread per quadrature point; the threads of an
-// element stride over the intermediate index sets; intermediates live in shared memory.
+// per element instead of O(p^{2d})).  One thread per quadrature point; intermediates live
+// in shared memory.  Two forms of the same stages:
+//  * line form (FP32, whose element kernels are bound by shared-memory instructions):
+//    every stage that contracts a direction runs one thread per 1D line of the element
+//    (all other indices fixed); the thread loads the line once into registers and forms
+//    every output of the line with the 1D table entries as compile-time operands (constant
+//    memory), so the only shared-memory traffic is the intermediates themselves.  The last
+//    forward stage runs per quadrature point, with this thread's table row taken from
+//    shared memory once.  The intermediate layouts are padded so that the lanes of a warp
+//    fall into distinct banks (the padding is chosen at compile time by counting banks for
+//    the first warp).
+//  * output-parallel form (FP64 and double-float, bound by arithmetic): the threads of an
+//    element stride over the outputs of each stage, which keeps every lane busy (the line
+//    counts are not multiples of the warp width).
 // Every function ends with __syncthreads() so the caller may reuse the scratch at once.
+// In both forms each output is the same sum, in the same order, as the plain definition
+// out = sum_a table(q, a) in(a) along each direction, so they give identical results.
 //
-// Tables (row-major, in shared memory): B[q*D + a] = w_a(z_q), G[q*D + a] = w_a'(z_q)
-// for the H1 basis, Bl[q*L + j] = phi_j(z_q) for the L2 basis.
+// Tables (row-major): B[q*D + a] = w_a(z_q), G[q*D + a] = w_a'(z_q) for the H1 basis,
+// Bl[q*L + j] = phi_j(z_q) for the L2 basis.
 // Element-local layouts: H1 values [c][a2][a1][a0] (a = a0 + D a1 + D^2 a2), L2 values
 // [c][j2][j1][j0], quadrature values [q2][q1][q0].
 #pragma once
+#include <atomic>
+#include <type_traits>
+#include <mutex>
+#include <vector>
 #include "lh_common.cuh"
+#include "lh_internal.h"
 
 namespace lh {
 
@@ -23,13 +42,756 @@ struct Tab {
   static constexpr int SMEM = 2 * Q * D + Q * L + Q;           // entries staged in shared memory
 };
 
-template <int DIM, int K, int NC>
-struct H1Scratch {
-  static constexpr int D = K + 1, Q = 2 * K;
-  static constexpr int T1 = DIM == 3 ? 2 * NC * D * D * Q : 2 * NC * D * Q;
-  static constexpr int T2 = DIM == 3 ? 3 * NC * D * Q * Q : 1;
-  static constexpr int SF = (DIM + 1) * NC * (DIM == 3 ? Q * Q * Q : Q * Q);
+// ---------------------------------------------------------------------------------------
+// The tables of orders 1-4 in constant memory: one copy per translation unit, written on
+// each device by fill_const_tables() before the first launch there.
+template <int K>
+struct TabOff {
+  static constexpr int v = TabOff<K - 1>::v + Tab<K - 1>::SMEM;
 };
+template <>
+struct TabOff<1> {
+  static constexpr int v = 0;
+};
+constexpr int kTabAll = TabOff<5>::v;
+
+static __constant__ double c_tab_d[kTabAll];
+static __constant__ float c_tab_f[kTabAll];     // float(t)
+static __constant__ float c_tab_flo[kTabAll];   // float(t - float(t)): DF = (c_tab_f, c_tab_flo)
+
+template <class T>
+struct CT;
+template <>
+struct CT<double> {
+  static __device__ __forceinline__ double at(int i) { return c_tab_d[i]; }
+};
+template <>
+struct CT<float> {
+  static __device__ __forceinline__ float at(int i) { return c_tab_f[i]; }
+};
+template <>
+struct CT<DF> {
+  static __device__ __forceinline__ DF at(int i) { return DF(c_tab_f[i], c_tab_flo[i]); }
+};
+template <class T, int K>
+__device__ __forceinline__ T cB(int q, int a) {
+  return CT<T>::at(TabOff<K>::v + Tab<K>::B + q * (K + 1) + a);
+}
+template <class T, int K>
+__device__ __forceinline__ T cG(int q, int a) {
+  return CT<T>::at(TabOff<K>::v + Tab<K>::G + q * (K + 1) + a);
+}
+// the "L2" table of l2_fwd / l2_bwd: the L2 basis (N = K) or the H1 values (N = K + 1)
+template <class T, int K, int N>
+__device__ __forceinline__ T cL(int q, int j) {
+  static_assert(N == K || N == K + 1, "l2 contractions take N = K or K + 1");
+  if constexpr (N == K + 1) return cB<T, K>(q, j);
+  else return CT<T>::at(TabOff<K>::v + Tab<K>::BL + q * K + j);
+}
+
+static inline cudaError_t fill_const_tables() {
+  static std::atomic<unsigned long long> done{0};
+  static std::mutex mu;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  double d[kTabAll];
+  float f[kTabAll], flo[kTabAll];
+  const int n[4] = {Tab<1>::SMEM, Tab<2>::SMEM, Tab<3>::SMEM, Tab<4>::SMEM};
+  int o = 0;
+  for (int K = 1; K <= 4; ++K) {
+    const std::vector<double> t = host_tables(K);
+    if ((int)t.size() < n[K - 1]) return cudaErrorInvalidValue;
+    for (int i = 0; i < n[K - 1]; ++i) {
+      d[o + i] = t[i];
+      f[o + i] = (float)t[i];
+      flo[o + i] = (float)(t[i] - (double)f[o + i]);
+    }
+    o += n[K - 1];
+  }
+  e = cudaMemcpyToSymbol(c_tab_d, d, sizeof(d));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_f, f, sizeof(f));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_tab_flo, flo, sizeof(flo));
+  if (e != cudaSuccess) return e;
+  done.fetch_or(bit, std::memory_order_release);
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------------------
+// Intermediate layouts (compile time).  ways() is the largest number of distinct addresses
+// that one of the 32 banks receives from a warp's lanes (1 = conflict free, equal
+// addresses broadcast); each pick takes the padding with the fewest ways over the stage
+// accesses it affects, smallest first.
+namespace lay {
+constexpr int ways(const int (&a)[32]) {
+  int cnt[32] = {};
+  int worst = 1;
+  for (int l = 0; l < 32; ++l) {
+    if (a[l] < 0) continue;
+    bool dup = false;
+    for (int k = 0; k < l; ++k) dup = dup || a[k] == a[l];
+    if (!dup) {
+      const int b = a[l] & 31;
+      cnt[b] += 1;
+      if (cnt[b] > worst) worst = cnt[b];
+    }
+  }
+  return worst;
+}
+constexpr int lanes(int nq) { return nq < 32 ? nq : 32; }
+constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+// forward 3D, N 1D dofs, NC fields:
+//   t1[q0][m][a1] (m = c N + a2): a1 stride 1, m stride N1, q0 stride P1
+//   t2[q1][q0][m]: m stride 1, (q1 Q + q0) stride MS
+struct F3L {
+  int N1, P1, MS;
+};
+constexpr F3L pick_f3(int N, int NC, int Q) {
+  const int NM = NC * N, nl = lanes(Q * Q * Q);
+  F3L r{N, NM * N, NM};
+  int best = 1 << 30;
+  for (int n1 = N; n1 < N + 4; ++n1)
+    for (int p1 = NM * n1; p1 < NM * n1 + 8; ++p1) {
+      int w1[32] = {}, w2[32] = {};
+      for (int l = 0; l < 32; ++l) {
+        w1[l] = (l < nl && l < NM * N) ? (l / N) * n1 + l % N : -1;            // stage 1 stores
+        w2[l] = (l < nl && l < Q * NM) ? (l / NM) * p1 + (l % NM) * n1 : -1;   // stage 2 loads
+      }
+      const int s = ways(w1) + ways(w2);
+      if (s < best) {
+        best = s;
+        r.N1 = n1;
+        r.P1 = p1;
+      }
+    }
+  best = 1 << 30;
+  for (int ms = NM; ms < NM + 16; ++ms) {
+    int w1[32] = {}, w2[32] = {};
+    for (int l = 0; l < 32; ++l) {
+      w1[l] = (l < nl && l < Q * NM) ? (l / NM) * ms + l % NM : -1;   // stage 2 stores
+      w2[l] = l < nl ? (((l / Q) % Q) * Q + l % Q) * ms : -1;          // stage 3 loads
+    }
+    const int s = ways(w1) + ways(w2);
+    if (s < best) {
+      best = s;
+      r.MS = ms;
+    }
+  }
+  return r;
+}
+// forward 2D: t1[q0][r] (r = c N + a1), q0 stride R
+constexpr int pick_f2(int N, int NC, int Q) {
+  const int NM = NC * N, nl = lanes(Q * Q);
+  int r = NM, best = 1 << 30;
+  for (int R = NM; R < NM + 33; ++R) {
+    int w[32] = {};
+    for (int l = 0; l < 32; ++l) w[l] = l < nl ? (l % Q) * R : -1;   // stage 2 loads
+    const int s = ways(w);
+    if (s < best) {
+      best = s;
+      r = R;
+    }
+  }
+  return r;
+}
+// backward 3D, N 1D dofs, NC fields:
+//   sf[c][point]: c stride NQp
+//   t2[a2][c][q1][q0]: c stride CA, a2 stride SA
+//   t1[q0][m][a1] (m = c N + a2): q0 stride RB
+struct B3L {
+  int NQp, CA, SA, RB;
+};
+constexpr B3L pick_b3(int N, int NC, int Q) {
+  const int QQ = Q * Q, NQ = QQ * Q, NM = NC * N, nl = lanes(NQ);
+  B3L r{NQ, QQ, NC * QQ, NM * N};
+  int best = 1 << 30;
+  for (int v = NQ; v < NQ + 33; ++v) {
+    int w[32] = {};
+    for (int l = 0; l < 32; ++l) w[l] = (l < nl && l < NC * QQ) ? (l / QQ) * v + l % QQ : -1;   // stage A loads
+    const int s = ways(w);
+    if (s < best) {
+      best = s;
+      r.NQp = v;
+    }
+  }
+  best = 1 << 30;
+  for (int ca = QQ; ca < QQ + 17; ++ca)
+    for (int sa = NC * ca; sa < NC * ca + 8; ++sa) {
+      int w1[32] = {}, w2[32] = {};
+      for (int l = 0; l < 32; ++l) {
+        w1[l] = (l < nl && l < NC * QQ) ? (l / QQ) * ca + l % QQ : -1;                           // stage A stores
+        w2[l] = (l < nl && l < NM * Q) ? ((l / Q) % N) * sa + ((l / Q) / N) * ca + l % Q : -1;   // stage B loads
+      }
+      const int s = ways(w1) + ways(w2);
+      if (s < best) {
+        best = s;
+        r.CA = ca;
+        r.SA = sa;
+      }
+    }
+  best = 1 << 30;
+  for (int rb = NM * N; rb < NM * N + 33; ++rb) {
+    int w[32] = {};
+    for (int l = 0; l < 32; ++l) w[l] = (l < nl && l < NM * Q) ? (l % Q) * rb + (l / Q) * N : -1;   // stage B stores
+    const int s = ways(w);
+    if (s < best) {
+      best = s;
+      r.RB = rb;
+    }
+  }
+  return r;
+}
+// backward 2D: sf[c][point] (c stride NQp), t1[q0][r] (r = c N + a1, q0 stride R)
+struct B2L {
+  int NQp, R;
+};
+constexpr B2L pick_b2(int N, int NC, int Q) {
+  const int NQ = Q * Q, NM = NC * N, nl = lanes(NQ);
+  B2L r{NQ, NM};
+  int best = 1 << 30;
+  for (int v = NQ; v < NQ + 33; ++v) {
+    int w[32] = {};
+    for (int l = 0; l < 32; ++l) w[l] = (l < nl && l < NC * Q) ? (l / Q) * v + l % Q : -1;   // stage A loads
+    const int s = ways(w);
+    if (s < best) {
+      best = s;
+      r.NQp = v;
+    }
+  }
+  best = 1 << 30;
+  for (int R = NM; R < NM + 33; ++R) {
+    int w[32] = {};
+    for (int l = 0; l < 32; ++l) w[l] = (l < nl && l < NC * Q) ? (l % Q) * R + (l / Q) * N : -1;   // stage A stores
+    const int s = ways(w);
+    if (s < best) {
+      best = s;
+      r.R = R;
+    }
+  }
+  return r;
+}
+}  // namespace lay
+
+template <int N, int NC, int Q>
+struct F3 {
+  static constexpr lay::F3L v = lay::pick_f3(N, NC, Q);
+  static constexpr int N1 = v.N1, P1 = v.P1, MS = v.MS;
+};
+template <int N, int NC, int Q>
+struct F2 {
+  static constexpr int R = lay::pick_f2(N, NC, Q);
+};
+template <int N, int NC, int Q>
+struct B3 {
+  static constexpr lay::B3L v = lay::pick_b3(N, NC, Q);
+  static constexpr int NQp = v.NQp, CA = v.CA, SA = v.SA, RB = v.RB;
+};
+template <int N, int NC, int Q>
+struct B2 {
+  static constexpr lay::B2L v = lay::pick_b2(N, NC, Q);
+  static constexpr int NQp = v.NQp, R = v.R;
+};
+
+// Scratch (entries of T) of the forward contractions of NC fields (h1_fwd, and l2_fwd with
+// N = K and N = K + 1) and of the backward ones (h1_bwd, l2_bwd with N = K and K + 1).
+// Both forms are covered (the plan is sized in entries, whatever T is): the line form's
+// padded layouts and the output-parallel form's plain ones (H1: t1 2 NC D^2 Q, t2 3 NC D Q^2,
+// sf (DIM + 1) NC NQ in 3D; t1 2 NC D Q, sf (DIM + 1) NC NQ in 2D; L2 needs less).
+template <int DIM, int K, int NC>
+struct NeedF {
+  static constexpr int D = K + 1, Q = 2 * K;
+  static constexpr int T1n = DIM == 3 ? lay::imax(2 * Q * F3<D, NC, Q>::P1, Q * F3<K, NC, Q>::P1)
+                                      : lay::imax(2 * Q * F2<D, NC, Q>::R, Q * F2<K, NC, Q>::R);
+  static constexpr int T2n = DIM == 3 ? lay::imax(3 * Q * Q * F3<D, NC, Q>::MS, Q * Q * F3<K, NC, Q>::MS) : 1;
+  static constexpr int T1 = lay::imax(T1n, DIM == 3 ? 2 * NC * D * D * Q : 2 * NC * D * Q);
+  static constexpr int T2 = lay::imax(T2n, DIM == 3 ? 3 * NC * D * Q * Q : 1);
+};
+template <int DIM, int K, int NC>
+struct NeedB {
+  static constexpr int D = K + 1, Q = 2 * K, NQ = DIM == 3 ? Q * Q * Q : Q * Q;
+  static constexpr int SFn = DIM == 3 ? lay::imax(4 * NC * B3<D, NC, Q>::NQp, NC * B3<K, NC, Q>::NQp)
+                                      : lay::imax(3 * NC * B2<D, NC, Q>::NQp, NC * B2<K, NC, Q>::NQp);
+  static constexpr int T2n = DIM == 3 ? lay::imax(3 * D * B3<D, NC, Q>::SA, K * B3<K, NC, Q>::SA) : 1;
+  static constexpr int T1n = DIM == 3 ? lay::imax(2 * Q * B3<D, NC, Q>::RB, Q * B3<K, NC, Q>::RB)
+                                      : lay::imax(2 * Q * B2<D, NC, Q>::R, Q * B2<K, NC, Q>::R);
+  static constexpr int SF = lay::imax(SFn, (DIM + 1) * NC * NQ);
+  static constexpr int T2 = lay::imax(T2n, DIM == 3 ? 3 * NC * D * Q * Q : 1);
+  static constexpr int T1 = lay::imax(T1n, DIM == 3 ? 2 * NC * D * D * Q : 2 * NC * D * Q);
+};
+// the largest need over 1..NC fields (a kernel calls its contractions with up to NC fields)
+template <int DIM, int K, int NC>
+struct NeedFMax {
+  using A = NeedF<DIM, K, NC>;
+  using R = NeedFMax<DIM, K, NC - 1>;
+  static constexpr int T1 = lay::imax(A::T1, R::T1), T2 = lay::imax(A::T2, R::T2);
+};
+template <int DIM, int K>
+struct NeedFMax<DIM, K, 0> {
+  static constexpr int T1 = 0, T2 = 0;
+};
+template <int DIM, int K, int NC>
+struct NeedBMax {
+  using A = NeedB<DIM, K, NC>;
+  using R = NeedBMax<DIM, K, NC - 1>;
+  static constexpr int SF = lay::imax(A::SF, R::SF), T1 = lay::imax(A::T1, R::T1), T2 = lay::imax(A::T2, R::T2);
+};
+template <int DIM, int K>
+struct NeedBMax<DIM, K, 0> {
+  static constexpr int SF = 0, T1 = 0, T2 = 0;
+};
+
+// ---------------------------------------------------------------------------------------
+// Line form (see the header).
+namespace ln {
+
+// values (if VAL; 3D only skips them) and reference gradients of NC H1 fields at this
+// thread's quadrature point.  B, G: the tables in shared memory (this thread's row).
+template <int DIM, int K, int NC, class T, bool VAL = true>
+__device__ __forceinline__ void h1_fwd(const T* __restrict__ in, T* t1, T* t2, const T* B, const T* G,
+                                       int lt, T (&val)[NC], T (&grad)[NC][DIM]) {
+  constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  if constexpr (DIM == 3) {
+    constexpr int NQ = Q * Q * Q;
+    using LY = F3<D, NC, Q>;
+    constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS, T1P = Q * P1, T2P = Q * Q * MS;
+    for (int r = lt; r < NM * D; r += NQ) {            // a0 -> q0, line (c, a2, a1)
+      T u[D];
+#pragma unroll
+      for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
+      const int o = (r / D) * N1 + r % D;
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) {
+        T sb = 0, sg = 0;
+#pragma unroll
+        for (int a0 = 0; a0 < D; ++a0) {
+          sb += cB<T, K>(q0, a0) * u[a0];
+          sg += cG<T, K>(q0, a0) * u[a0];
+        }
+        t1[q0 * P1 + o] = sb;
+        t1[T1P + q0 * P1 + o] = sg;
+      }
+    }
+    __syncthreads();
+    for (int n = lt; n < Q * NM; n += NQ) {            // a1 -> q1, line (q0, c, a2)
+      const int q0 = n / NM, m = n % NM;
+      T xb[D], xg[D];
+#pragma unroll
+      for (int a1 = 0; a1 < D; ++a1) {
+        xb[a1] = t1[q0 * P1 + m * N1 + a1];
+        xg[a1] = t1[T1P + q0 * P1 + m * N1 + a1];
+      }
+#pragma unroll
+      for (int q1 = 0; q1 < Q; ++q1) {
+        T bb = 0, bg = 0, gb = 0;
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1) {
+          const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
+          bb += b * xb[a1];
+          bg += g * xb[a1];
+          gb += b * xg[a1];
+        }
+        const int o = (q1 * Q + q0) * MS + m;
+        t2[o] = bb;
+        t2[T2P + o] = bg;
+        t2[2 * T2P + o] = gb;
+      }
+    }
+    __syncthreads();
+    const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+    T b2[D], g2[D];
+#pragma unroll
+    for (int a2 = 0; a2 < D; ++a2) {
+      b2[a2] = B[q2 * D + a2];
+      g2[a2] = G[q2 * D + a2];
+    }
+    const int pb = (q1 * Q + q0) * MS;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {                     // a2 -> q2 at this point
+      T v = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        const int o = pb + c * D + a2;
+        if constexpr (VAL) v += b2[a2] * t2[o];
+        dy += b2[a2] * t2[T2P + o];
+        dx += b2[a2] * t2[2 * T2P + o];
+        dz += g2[a2] * t2[o];
+      }
+      val[c] = v;
+      grad[c][0] = dx;
+      grad[c][1] = dy;
+      grad[c][2] = dz;
+    }
+    __syncthreads();
+  } else {
+    constexpr int NQ = Q * Q, R = F2<D, NC, Q>::R, T1P = Q * R;
+    for (int r = lt; r < NM; r += NQ) {                // a0 -> q0, line (c, a1)
+      T u[D];
+#pragma unroll
+      for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) {
+        T sb = 0, sg = 0;
+#pragma unroll
+        for (int a0 = 0; a0 < D; ++a0) {
+          sb += cB<T, K>(q0, a0) * u[a0];
+          sg += cG<T, K>(q0, a0) * u[a0];
+        }
+        t1[q0 * R + r] = sb;
+        t1[T1P + q0 * R + r] = sg;
+      }
+    }
+    __syncthreads();
+    const int q0 = lt % Q, q1 = lt / Q;
+    T b1[D], g1[D];
+#pragma unroll
+    for (int a1 = 0; a1 < D; ++a1) {
+      b1[a1] = B[q1 * D + a1];
+      g1[a1] = G[q1 * D + a1];
+    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {                     // a1 -> q1 at this point
+      T v = 0, dx = 0, dy = 0;
+#pragma unroll
+      for (int a1 = 0; a1 < D; ++a1) {
+        const int o = q0 * R + c * D + a1;
+        v += b1[a1] * t1[o];
+        dx += b1[a1] * t1[T1P + o];
+        dy += g1[a1] * t1[o];
+      }
+      val[c] = v;
+      grad[c][0] = dx;
+      grad[c][1] = dy;
+    }
+    __syncthreads();
+  }
+}
+
+// out[c][a] = sum_q ( fval[c] w_a(q) + sum_r fgrad[c][r] d_r w_a(q) )   (B^T and G^T)
+template <int DIM, int K, int NC, class T>
+__device__ __forceinline__ void h1_bwd(const T (&fval)[NC], const T (&fgrad)[NC][DIM], T* sf, T* t1, T* t2,
+                                       const T* B, const T* G, int lt, T* out) {
+  constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  (void)B;
+  (void)G;
+  if constexpr (DIM == 3) {
+    constexpr int QQ = Q * Q, NQ = QQ * Q;
+    using LY = B3<D, NC, Q>;
+    constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA, RB = LY::RB;
+    constexpr int SFP = NC * NQp, T2P = D * SA, T1P = Q * RB;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      sf[c * NQp + lt] = fval[c];
+      sf[SFP + c * NQp + lt] = fgrad[c][0];
+      sf[2 * SFP + c * NQp + lt] = fgrad[c][1];
+      sf[3 * SFP + c * NQp + lt] = fgrad[c][2];
+    }
+    __syncthreads();
+    for (int n = lt; n < NC * QQ; n += NQ) {           // q2 -> a2, line (c, q1, q0)
+      const int c = n / QQ, p = n % QQ;
+      T f0[Q], f1[Q], f2[Q], f3[Q];
+#pragma unroll
+      for (int q2 = 0; q2 < Q; ++q2) {
+        const int o = c * NQp + q2 * QQ + p;
+        f0[q2] = sf[o];
+        f1[q2] = sf[SFP + o];
+        f2[q2] = sf[2 * SFP + o];
+        f3[q2] = sf[3 * SFP + o];
+      }
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        T zbb = 0, zbg = 0, zgb = 0;
+#pragma unroll
+        for (int q2 = 0; q2 < Q; ++q2) {
+          const T b = cB<T, K>(q2, a2), g = cG<T, K>(q2, a2);
+          zgb += b * f1[q2];
+          zbg += b * f2[q2];
+          zbb += b * f0[q2] + g * f3[q2];
+        }
+        const int o = a2 * SA + c * CA + p;
+        t2[o] = zbb;
+        t2[T2P + o] = zbg;
+        t2[2 * T2P + o] = zgb;
+      }
+    }
+    __syncthreads();
+    for (int n = lt; n < NM * Q; n += NQ) {            // q1 -> a1, line (c, a2, q0)
+      const int q0 = n % Q, m = n / Q, c = m / D, a2 = m % D;
+      T zb[Q], zbg[Q], zgb[Q];
+#pragma unroll
+      for (int q1 = 0; q1 < Q; ++q1) {
+        const int o = a2 * SA + c * CA + q1 * Q + q0;
+        zb[q1] = t2[o];
+        zbg[q1] = t2[T2P + o];
+        zgb[q1] = t2[2 * T2P + o];
+      }
+#pragma unroll
+      for (int a1 = 0; a1 < D; ++a1) {
+        T yb = 0, yg = 0;
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) {
+          const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
+          yg += b * zgb[q1];
+          yb += g * zbg[q1] + b * zb[q1];
+        }
+        const int o = q0 * RB + m * D + a1;
+        t1[o] = yb;
+        t1[T1P + o] = yg;
+      }
+    }
+    __syncthreads();
+    for (int r = lt; r < NM * D; r += NQ) {            // q0 -> a0, line (c, a2, a1)
+      T yb[Q], yg[Q];
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) {
+        yb[q0] = t1[q0 * RB + r];
+        yg[q0] = t1[T1P + q0 * RB + r];
+      }
+#pragma unroll
+      for (int a0 = 0; a0 < D; ++a0) {
+        T s = 0;
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) s += cG<T, K>(q0, a0) * yg[q0] + cB<T, K>(q0, a0) * yb[q0];
+        out[r * D + a0] = s;
+      }
+    }
+    __syncthreads();
+  } else {
+    constexpr int NQ = Q * Q;
+    using LY = B2<D, NC, Q>;
+    constexpr int NQp = LY::NQp, R = LY::R, SFP = NC * NQp, T1P = Q * R;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      sf[c * NQp + lt] = fval[c];
+      sf[SFP + c * NQp + lt] = fgrad[c][0];
+      sf[2 * SFP + c * NQp + lt] = fgrad[c][1];
+    }
+    __syncthreads();
+    for (int n = lt; n < NC * Q; n += NQ) {            // q1 -> a1, line (c, q0)
+      const int c = n / Q, q0 = n % Q;
+      T f0[Q], f1[Q], f2[Q];
+#pragma unroll
+      for (int q1 = 0; q1 < Q; ++q1) {
+        const int o = c * NQp + q1 * Q + q0;
+        f0[q1] = sf[o];
+        f1[q1] = sf[SFP + o];
+        f2[q1] = sf[2 * SFP + o];
+      }
+#pragma unroll
+      for (int a1 = 0; a1 < D; ++a1) {
+        T yb = 0, yg = 0;
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) {
+          const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
+          yg += b * f1[q1];
+          yb += b * f0[q1] + g * f2[q1];
+        }
+        const int o = q0 * R + c * D + a1;
+        t1[o] = yb;
+        t1[T1P + o] = yg;
+      }
+    }
+    __syncthreads();
+    for (int r = lt; r < NM; r += NQ) {                // q0 -> a0, line (c, a1)
+      T yb[Q], yg[Q];
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) {
+        yb[q0] = t1[q0 * R + r];
+        yg[q0] = t1[T1P + q0 * R + r];
+      }
+#pragma unroll
+      for (int a0 = 0; a0 < D; ++a0) {
+        T s = 0;
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) s += cG<T, K>(q0, a0) * yg[q0] + cB<T, K>(q0, a0) * yb[q0];
+        out[r * D + a0] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// values of NC fields with L_ 1D dofs (default: the L2 basis, L_ = K) at this thread's
+// quadrature point; with L_ = K + 1 and the H1 table it interpolates H1 values only.
+// Bl: that table in shared memory (this thread's row).
+template <int DIM, int K, int NC, class T, int L_ = K>
+__device__ __forceinline__ void l2_fwd(const T* __restrict__ in, T* t1, T* t2, const T* Bl, int lt, T (&val)[NC]) {
+  constexpr int L = L_, Q = 2 * K, NM = NC * L;
+  if constexpr (DIM == 3) {
+    constexpr int NQ = Q * Q * Q;
+    using LY = F3<L, NC, Q>;
+    constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS;
+    for (int r = lt; r < NM * L; r += NQ) {            // j0 -> q0, line (c, j2, j1)
+      T u[L];
+#pragma unroll
+      for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
+      const int o = (r / L) * N1 + r % L;
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) {
+        T s = 0;
+#pragma unroll
+        for (int j0 = 0; j0 < L; ++j0) s += cL<T, K, L>(q0, j0) * u[j0];
+        t1[q0 * P1 + o] = s;
+      }
+    }
+    __syncthreads();
+    for (int n = lt; n < Q * NM; n += NQ) {            // j1 -> q1, line (q0, c, j2)
+      const int q0 = n / NM, m = n % NM;
+      T x[L];
+#pragma unroll
+      for (int j1 = 0; j1 < L; ++j1) x[j1] = t1[q0 * P1 + m * N1 + j1];
+#pragma unroll
+      for (int q1 = 0; q1 < Q; ++q1) {
+        T s = 0;
+#pragma unroll
+        for (int j1 = 0; j1 < L; ++j1) s += cL<T, K, L>(q1, j1) * x[j1];
+        t2[(q1 * Q + q0) * MS + m] = s;
+      }
+    }
+    __syncthreads();
+    const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+    T b2[L];
+#pragma unroll
+    for (int j2 = 0; j2 < L; ++j2) b2[j2] = Bl[q2 * L + j2];
+    const int pb = (q1 * Q + q0) * MS;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {                     // j2 -> q2 at this point
+      T s = 0;
+#pragma unroll
+      for (int j2 = 0; j2 < L; ++j2) s += b2[j2] * t2[pb + c * L + j2];
+      val[c] = s;
+    }
+    __syncthreads();
+  } else {
+    constexpr int NQ = Q * Q, R = F2<L, NC, Q>::R;
+    for (int r = lt; r < NM; r += NQ) {                // j0 -> q0, line (c, j1)
+      T u[L];
+#pragma unroll
+      for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) {
+        T s = 0;
+#pragma unroll
+        for (int j0 = 0; j0 < L; ++j0) s += cL<T, K, L>(q0, j0) * u[j0];
+        t1[q0 * R + r] = s;
+      }
+    }
+    __syncthreads();
+    const int q0 = lt % Q, q1 = lt / Q;
+    T b1[L];
+#pragma unroll
+    for (int j1 = 0; j1 < L; ++j1) b1[j1] = Bl[q1 * L + j1];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {                     // j1 -> q1 at this point
+      T s = 0;
+#pragma unroll
+      for (int j1 = 0; j1 < L; ++j1) s += b1[j1] * t1[q0 * R + c * L + j1];
+      val[c] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[c][j] = sum_q fval[c] phi_j(q)  (L_ as in l2_fwd)
+template <int DIM, int K, int NC, class T, int L_ = K>
+__device__ __forceinline__ void l2_bwd(const T (&fval)[NC], T* sf, T* t1, T* t2, const T* Bl, int lt, T* out) {
+  constexpr int L = L_, Q = 2 * K, NM = NC * L;
+  (void)Bl;
+  if constexpr (DIM == 3) {
+    constexpr int QQ = Q * Q, NQ = QQ * Q;
+    using LY = B3<L, NC, Q>;
+    constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA, RB = LY::RB;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sf[c * NQp + lt] = fval[c];
+    __syncthreads();
+    for (int n = lt; n < NC * QQ; n += NQ) {           // q2 -> j2, line (c, q1, q0)
+      const int c = n / QQ, p = n % QQ;
+      T f[Q];
+#pragma unroll
+      for (int q2 = 0; q2 < Q; ++q2) f[q2] = sf[c * NQp + q2 * QQ + p];
+#pragma unroll
+      for (int j2 = 0; j2 < L; ++j2) {
+        T s = 0;
+#pragma unroll
+        for (int q2 = 0; q2 < Q; ++q2) s += cL<T, K, L>(q2, j2) * f[q2];
+        t2[j2 * SA + c * CA + p] = s;
+      }
+    }
+    __syncthreads();
+    for (int n = lt; n < NM * Q; n += NQ) {            // q1 -> j1, line (c, j2, q0)
+      const int q0 = n % Q, m = n / Q, c = m / L, j2 = m % L;
+      T z[Q];
+#pragma unroll
+      for (int q1 = 0; q1 < Q; ++q1) z[q1] = t2[j2 * SA + c * CA + q1 * Q + q0];
+#pragma unroll
+      for (int j1 = 0; j1 < L; ++j1) {
+        T s = 0;
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) s += cL<T, K, L>(q1, j1) * z[q1];
+        t1[q0 * RB + m * L + j1] = s;
+      }
+    }
+    __syncthreads();
+    for (int r = lt; r < NM * L; r += NQ) {            // q0 -> j0, line (c, j2, j1)
+      T y[Q];
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * RB + r];
+#pragma unroll
+      for (int j0 = 0; j0 < L; ++j0) {
+        T s = 0;
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) s += cL<T, K, L>(q0, j0) * y[q0];
+        out[r * L + j0] = s;
+      }
+    }
+    __syncthreads();
+  } else {
+    constexpr int NQ = Q * Q;
+    using LY = B2<L, NC, Q>;
+    constexpr int NQp = LY::NQp, R = LY::R;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sf[c * NQp + lt] = fval[c];
+    __syncthreads();
+    for (int n = lt; n < NC * Q; n += NQ) {            // q1 -> j1, line (c, q0)
+      const int c = n / Q, q0 = n % Q;
+      T f[Q];
+#pragma unroll
+      for (int q1 = 0; q1 < Q; ++q1) f[q1] = sf[c * NQp + q1 * Q + q0];
+#pragma unroll
+      for (int j1 = 0; j1 < L; ++j1) {
+        T s = 0;
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) s += cL<T, K, L>(q1, j1) * f[q1];
+        t1[q0 * R + c * L + j1] = s;
+      }
+    }
+    __syncthreads();
+    for (int r = lt; r < NM; r += NQ) {                // q0 -> j0, line (c, j1)
+      T y[Q];
+#pragma unroll
+      for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * R + r];
+#pragma unroll
+      for (int j0 = 0; j0 < L; ++j0) {
+        T s = 0;
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) s += cL<T, K, L>(q0, j0) * y[q0];
+        out[r * L + j0] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace ln
+
+// ---------------------------------------------------------------------------------------
+// Output-parallel form: the threads of an element stride over the outputs of each stage,
+// every output reading its table entries from shared memory.
+namespace op {
 
 // values (if VAL; 3D only skips them) and reference gradients of NC H1 fields at this
 // thread's quadrature point
@@ -321,6 +1083,38 @@ __device__ __forceinline__ void l2_bwd(const T (&fval)[NC], T* sf, T* t1, T* t2,
     }
     __syncthreads();
   }
+}
+
+}  // namespace op
+
+// ---------------------------------------------------------------------------------------
+// Public entry points: FP32 runs the line form (ln, above), whose stages are bound by
+// shared-memory instructions; double and double-float run the output-parallel form (op),
+// whose stages are bound by arithmetic and keep every lane of a warp busy.
+template <class T>
+constexpr bool kLines = std::is_same<T, float>::value;
+
+template <int DIM, int K, int NC, class T, bool VAL = true>
+__device__ __forceinline__ void h1_fwd(const T* __restrict__ in, T* t1, T* t2, const T* B, const T* G,
+                                       int lt, T (&val)[NC], T (&grad)[NC][DIM]) {
+  if constexpr (kLines<T>) ln::h1_fwd<DIM, K, NC, T, VAL>(in, t1, t2, B, G, lt, val, grad);
+  else op::h1_fwd<DIM, K, NC, T, VAL>(in, t1, t2, B, G, lt, val, grad);
+}
+template <int DIM, int K, int NC, class T>
+__device__ __forceinline__ void h1_bwd(const T (&fval)[NC], const T (&fgrad)[NC][DIM], T* sf, T* t1, T* t2,
+                                       const T* B, const T* G, int lt, T* out) {
+  if constexpr (kLines<T>) ln::h1_bwd<DIM, K, NC, T>(fval, fgrad, sf, t1, t2, B, G, lt, out);
+  else op::h1_bwd<DIM, K, NC, T>(fval, fgrad, sf, t1, t2, B, G, lt, out);
+}
+template <int DIM, int K, int NC, class T, int L_ = K>
+__device__ __forceinline__ void l2_fwd(const T* __restrict__ in, T* t1, T* t2, const T* Bl, int lt, T (&val)[NC]) {
+  if constexpr (kLines<T>) ln::l2_fwd<DIM, K, NC, T, L_>(in, t1, t2, Bl, lt, val);
+  else op::l2_fwd<DIM, K, NC, T, L_>(in, t1, t2, Bl, lt, val);
+}
+template <int DIM, int K, int NC, class T, int L_ = K>
+__device__ __forceinline__ void l2_bwd(const T (&fval)[NC], T* sf, T* t1, T* t2, const T* Bl, int lt, T* out) {
+  if constexpr (kLines<T>) ln::l2_bwd<DIM, K, NC, T, L_>(fval, sf, t1, t2, Bl, lt, out);
+  else op::l2_bwd<DIM, K, NC, T, L_>(fval, sf, t1, t2, Bl, lt, out);
 }
 
 }  // namespace lh

@@ -12,15 +12,20 @@
 
 namespace lh {
 
-// Per-element shared-memory plan (units of T).
+// Per-element shared-memory plan (units of T): the inputs (NCH H1 fields, NCV H1 fields
+// read as values only, NCL L2 fields) and the contraction scratch.  The kernel's forward
+// contractions take at most max(NCH, NCV, NCL) fields and its backward ones at most
+// max(NCO, 1); the scratch holds the largest need over those counts.
 template <int DIM, int K, int NCH, int NCV, int NCL, int NCO>
 struct Plan {
   using C = Cfg<DIM, K>;
-  using SC = H1Scratch<DIM, K, NCH>;
+  static constexpr int NCF = lay::imax(lay::imax(NCH, NCV), lay::imax(NCL, 1)), NCB = lay::imax(NCO, 1);
+  using NF = NeedFMax<DIM, K, NCF>;
+  using NB = NeedBMax<DIM, K, NCB>;
   static constexpr int IN = NCH * C::ND + NCV * C::ND + NCL * C::NL;
-  static constexpr int T1 = SC::T1;
-  static constexpr int T2 = SC::T2;
-  static constexpr int SF = (DIM + 1) * (NCO > 1 ? NCO : 1) * C::NQ;
+  static constexpr int T1 = lay::imax(NF::T1, NB::T1);
+  static constexpr int T2 = lay::imax(NF::T2, NB::T2);
+  static constexpr int SF = NB::SF;
   static constexpr int PER = IN + T1 + T2 + SF;
   static constexpr int HEAD = ((Tab<K>::SMEM + C::THREADS + 1) / 2) * 2;   // tables + reduction
   static constexpr size_t bytes(size_t szT) { return szT * (size_t)(HEAD + C::EPB * PER); }
@@ -169,8 +174,10 @@ __device__ __forceinline__ T gather_node(const ElemParams& P, const T* __restric
 template <auto KERN>
 static cudaError_t prep(size_t bytes) {
   static std::atomic<unsigned long long> done{0};
+  cudaError_t e = fill_const_tables();   // this translation unit's constant tables, once per device
+  if (e != cudaSuccess) return e;
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
   if (!(done.load(std::memory_order_acquire) & bit)) {

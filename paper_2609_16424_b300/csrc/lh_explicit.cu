@@ -207,6 +207,8 @@ cudaError_t launch_force_t(const ElemParams& P, cudaStream_t s, const double* Sq
   LH_XDISPATCH(P, force_t(P, s, Sq, w, bsrc, out))
 }
 
+cudaError_t init_const_tables_explicit() { return fill_const_tables(); }
+
 cudaError_t launch_copy_fixed(const ElemParams& P, cudaStream_t s, const double* src, double* dst) {
   const long long n = (long long)P.dim * P.NV;
   if (P.dim == 2) k_copy_fixed<2><<<nblk(n, 256), 256, 0, s>>>(P, src, dst);

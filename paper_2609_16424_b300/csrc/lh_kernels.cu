@@ -910,6 +910,10 @@ __global__ void k_initial_nodes(ElemParams P, double* __restrict__ x0) {
 static long long g_launches = 0;
 void count_launches(int n) { __atomic_add_fetch(&g_launches, (long long)n, __ATOMIC_RELAXED); }
 long long launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+cudaError_t init_const_tables() {
+  const cudaError_t e = fill_const_tables();
+  return e != cudaSuccess ? e : init_const_tables_explicit();
+}
 
 template <int DIM, int K>
 struct Launch {

@@ -8,6 +8,10 @@ namespace lh {
 // kernels launched so far (all launchers add to it)
 void count_launches(int n);
 long long launches();
+// write the constant-memory basis tables of the element kernels on the current device
+// (once per device; the launchers also do it before their first launch there)
+cudaError_t init_const_tables();
+cudaError_t init_const_tables_explicit();
 
 // element + assembly launchers (lh_kernels.cu); vectors use the layout of include/lh.h.
 // ev2, if not NULL, is an event pair recorded around the element kernel only.
