@@ -255,6 +255,16 @@ typedef struct {
   double cheb_ratio;       /* precond 3: the Chebyshev interval is [b / ratio, b], b = 1.1 x the
                               largest eigenvalue of D^-1 S estimated by 5 power steps at every
                               Newton iterate; default 20 */
+  int arnoldi;             /* driver of the Arnoldi iterations of an FP32-basis GMRES: 1 = on
+                              the device (default): each restart cycle is one launch of a CUDA
+                              graph whose WHILE conditional node repeats one iteration (operator,
+                              both Gram-Schmidt passes, the exact-norm fallback, the Givens
+                              rotation and the stopping test, all in kernels) until the device
+                              ends the cycle; the host reads the cycle's Hessenberg matrix once.
+                              The first solve with a new operator kind runs on the host (the
+                              kernels' one-time set-up cannot be recorded).  0 = host loop, one
+                              read-back per iteration.  Same arithmetic either way (the Givens
+                              rotations in double on the device instead of the host). */
 } lh_newton_opts;
 
 typedef struct {

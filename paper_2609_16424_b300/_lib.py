@@ -36,7 +36,7 @@ class NewtonOpts(C.Structure):
                 ("newton_maxit", C.c_int), ("gmres_maxit", C.c_int), ("restart", C.c_int),
                 ("max_halvings", C.c_int), ("jvp_prec", C.c_int), ("precond", C.c_int),
                 ("forcing", C.c_int), ("eta_max", C.c_double), ("scaled_norm", C.c_int),
-                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double)]
+                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("arnoldi", C.c_int)]
 
 
 class StepStats(C.Structure):

@@ -2,6 +2,7 @@
 // Newton-GMRES implicit midpoint step (paper Sec. 3.5 and Sec. 4.1).
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -365,6 +366,249 @@ lh_status cheb_bounds(lh_mesh* m, const lh_newton_opts& o, double tau, int tck, 
   return LH_OK;
 }
 
+// ---- device-driven Arnoldi (FP32 basis) ----
+// bit of the operator kind (preconditioner, J.w form, row weights) in ArnGraph::warm
+unsigned long long arn_kind(const KrylovOp<float>& op) {
+  return 1ull << (((op.pk * 3) + (op.tck + 1)) * 2 + (op.wsc ? 1 : 0));
+}
+
+// gives up on the device-driven Arnoldi for this mesh (the host loop runs from then on)
+bool arn_off(lh_mesh* m) {
+  ArnGraph& G = m->arn;
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (G.graph) cudaGraphDestroy(G.graph);
+  G.exec = nullptr;
+  G.graph = nullptr;
+  G.off = true;
+  (void)cudaGetLastError();
+  return false;
+}
+
+// zero-initialised graph-node parameters (cudaGraphNodeParams has no default constructor:
+// its union holds dim3s)
+union ZeroNodeParams {
+  cudaGraphNodeParams p;
+  unsigned char raw[sizeof(cudaGraphNodeParams)];
+  ZeroNodeParams() { std::memset(raw, 0, sizeof(raw)); }
+};
+
+// One Arnoldi iteration, recorded into the WHILE body: y = J P^-1 v_j (v_j in d_vin), both
+// Gram-Schmidt passes with the column count read from the cycle state, v_{j+1} by the
+// Pythagorean norm, an IF node with the exact-norm fallback (run only when the second pass
+// still cancelled; its body is recorded on the second private stream), then the Givens
+// update that ends the loop.
+lh_status arn_body(lh_mesh* m, KrylovOp<float>& op, float* V, float* w, long long ld, long long len,
+                   cudaGraphConditionalHandle cond) {
+  cudaStream_t s = m->stream;
+  double* dh = m->d_scalar + 8;
+  double* dh2 = dh + 72;
+  ArnState* st = m->d_arn;
+  const int* jd = &st->j;
+  lh_status e = op.apply(m->d_vin, w);
+  if (e != LH_OK) return e;
+  LH_CK(m, launch_mdot_dev(s, V, jd, ld, w, len, 1, nullptr, m->d_part, m->d_counter, dh));
+  LH_CK(m, launch_gemv_sub_dev(s, V, jd, ld, dh, w, len, nullptr));
+  LH_CK(m, launch_mdot_dev(s, V, jd, ld, w, len, 1, nullptr, m->d_part, m->d_counter, dh2));
+  // the IF node after the second update, then its body
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t capg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  LH_CK(m, cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, nullptr, nullptr, nullptr));   // the WHILE body
+  cudaGraphConditionalHandle fix;
+  LH_CK(m, cudaGraphConditionalHandleCreate(&fix, capg, 0u, 0u));
+  LH_CK(m, launch_gemv_norm_dev(s, V, st, ld, dh2, w, m->d_vin, len, fix));
+  LH_CK(m, cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, &deps, nullptr, &nd));
+  ZeroNodeParams zp;
+  cudaGraphNodeParams& np = zp.p;
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = fix;
+  np.conditional.type = cudaGraphCondTypeIf;
+  np.conditional.size = 1;
+  cudaGraphNode_t ifn;
+  LH_CK(m, cudaGraphAddNode(&ifn, capg, deps, nullptr, nd, &np));
+  LH_CK(m, cudaStreamUpdateCaptureDependencies(s, &ifn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaStream_t s2 = m->arn.cap2;
+  LH_CK(m, cudaStreamBeginCaptureToGraph(s2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal));
+  const long long l0 = launches();
+  const cudaError_t e1 = launch_gemv_sub_dev(s2, V, jd, ld, dh2, w, len, nullptr);
+  const cudaError_t e2 = launch_mdot_dev(s2, w, nullptr, 0, w, len, 0, nullptr, m->d_part, m->d_counter, &st->hn2);
+  const cudaError_t e3 = launch_arn_scale(s2, st, w, V, ld, m->d_vin, len);
+  m->arn.per_fix = launches() - l0;   // the IF body runs only when the second pass cancelled
+  cudaGraph_t got = nullptr;
+  const cudaError_t e4 = cudaStreamEndCapture(s2, &got);
+  LH_CK(m, e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4);
+  LH_CK(m, launch_arn_givens(s, dh, dh2, st, cond));
+  return LH_OK;
+}
+
+// Records the cycle graph: a WHILE conditional node (condition 1 at every launch) whose body
+// is one Arnoldi iteration, captured on a private stream.  False (and the host loop from then
+// on) if any step is refused.
+bool arn_record(lh_mesh* m, KrylovOp<float>& op, float* V, float* w, long long ld, long long len) {
+  ArnGraph& G = m->arn;
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (G.graph) cudaGraphDestroy(G.graph);
+  G.exec = nullptr;
+  G.graph = nullptr;
+  if (!G.cap && cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking) != cudaSuccess) {
+    G.cap = nullptr;
+    return arn_off(m);
+  }
+  if (!G.cap2 && cudaStreamCreateWithFlags(&G.cap2, cudaStreamNonBlocking) != cudaSuccess) {
+    G.cap2 = nullptr;
+    return arn_off(m);
+  }
+  if (cudaGraphCreate(&G.graph, 0) != cudaSuccess) {
+    G.graph = nullptr;
+    return arn_off(m);
+  }
+  cudaGraphConditionalHandle cond;
+  if (cudaGraphConditionalHandleCreate(&cond, G.graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+    return arn_off(m);
+  ZeroNodeParams zp;
+  cudaGraphNodeParams& np = zp.p;
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, G.graph, nullptr, nullptr, 0, &np) != cudaSuccess) return arn_off(m);
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(G.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return arn_off(m);
+  cudaStream_t keep = m->stream;
+  const long long l0 = launches();
+  m->stream = G.cap;
+  const lh_status st = arn_body(m, op, V, w, ld, len, cond);
+  m->stream = keep;
+  cudaGraph_t got = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(G.cap, &got);
+  G.per_it = launches() - l0;
+  count_launches((int)-G.per_it);   // recorded, not run
+  G.per_it -= G.per_fix;            // kernels of every iteration (the IF body's are rare)
+  if (st != LH_OK || ce != cudaSuccess) return arn_off(m);
+  if (cudaGraphInstantiate(&G.exec, G.graph, 0) != cudaSuccess) {
+    G.exec = nullptr;
+    return arn_off(m);
+  }
+  G.V = V;
+  G.w = w;
+  G.z = op.z;
+  G.wsc = op.wsc;
+  G.ld = ld;
+  G.len = len;
+  G.n = m->n;
+  G.pk = op.pk;
+  G.tck = op.tck;
+  G.tau = op.tau;
+  G.cheb_b = m->cheb_b;
+  G.cheb_ratio = m->cheb_ratio;
+  G.cheb_degree = m->cheb_degree;
+  return true;
+}
+
+// GMRES of the header comment below with the Arnoldi iterations of each restart cycle in one
+// graph launch; *used = false (nothing done) when this path does not apply.
+lh_status gmres_dev(lh_mesh* m, const lh_newton_opts& o, KrylovOp<float>& op, const double* r, double nr,
+                    double* dk, float* V, float* w, float* ulin, double* zd, double* wd, lh_step_stats& S,
+                    bool* used) {
+  *used = false;
+  ArnGraph& G = m->arn;
+  if (o.arnoldi != 1 || G.off || m->prof.on || o.restart < 1 || o.restart > kArnMax || !(G.warm & arn_kind(op)))
+    return LH_OK;
+  const long long n = m->n, ld = m->ldf, len = (n + 3) / 4 * 4;
+  const int mres = o.restart;
+  cudaStream_t s = m->stream;
+  if (!m->d_arn && cudaMalloc(&m->d_arn, sizeof(ArnState)) != cudaSuccess) {
+    m->d_arn = nullptr;
+    arn_off(m);
+    return LH_OK;
+  }
+  if (!m->h_arn && cudaMallocHost(&m->h_arn, sizeof(ArnState)) != cudaSuccess) {
+    m->h_arn = nullptr;
+    arn_off(m);
+    return LH_OK;
+  }
+  if (!m->d_vin) {
+    if (cudaMalloc(&m->d_vin, sizeof(float) * ld) != cudaSuccess) {
+      m->d_vin = nullptr;
+      arn_off(m);
+      return LH_OK;
+    }
+    LH_CK(m, cudaMemsetAsync(m->d_vin, 0, sizeof(float) * ld, s));
+  }
+  const bool same = G.exec && G.V == V && G.w == w && G.z == op.z && G.wsc == op.wsc && G.ld == ld &&
+                    G.len == len && G.n == n && G.pk == op.pk && G.tck == op.tck && G.tau == op.tau &&
+                    (op.pk != 3 || (G.cheb_b == m->cheb_b && G.cheb_ratio == m->cheb_ratio &&
+                                    G.cheb_degree == m->cheb_degree));
+  if (!same && !arn_record(m, op, V, w, ld, len)) return LH_OK;
+  *used = true;
+  double* dh = m->d_scalar + 8;
+  ArnState* h = m->h_arn;
+  LH_CK(m, cudaMemsetAsync(dk, 0, sizeof(double) * n, s));
+  double beta = nr;
+  const double beta0 = nr;
+  LH_CK(m, (launch_scale<double, float>(s, -1.0 / beta, r, 0.0, nullptr, V, n)));
+  int total = 0;
+  lh_status st;
+  while (total < o.gmres_maxit) {
+    LH_CK(m, cudaMemcpyAsync(m->d_vin, V, sizeof(float) * len, cudaMemcpyDeviceToDevice, s));
+    h->j = 0;
+    h->stop = 0;
+    h->fix = 0;
+    h->mres = mres;
+    h->maxit = o.gmres_maxit - total;
+    h->pad_ = 0;
+    h->tol = o.gmres_rtol * beta0;
+    h->hn2 = 0.0;
+    for (int i = 0; i <= kArnMax; ++i) h->g[i] = 0.0;
+    h->g[0] = beta;
+    LH_CK(m, cudaMemcpyAsync(m->d_arn, h, offsetof(ArnState, cs), cudaMemcpyHostToDevice, s));
+    LH_CK(m, cudaGraphLaunch(G.exec, s));
+    LH_CK(m, cudaMemcpyAsync(h, m->d_arn, sizeof(ArnState), cudaMemcpyDeviceToHost, s));
+    LH_CK(m, cudaStreamSynchronize(s));
+    const int j = h->j;
+    count_launches((int)(j * G.per_it));
+    total += j;
+    S.jvp_evals += j;
+    S.reorth += j;
+    if (h->stop == 5) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite Krylov vector");
+    if (j < 1 || j > mres) return fail(m, LH_ECUDA, "device Arnoldi: inconsistent cycle state");
+    const bool done = h->stop == 1;
+    // y = H^-1 g (upper triangular j x j), dk += P^-1 V y
+    std::vector<double> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      double sum = h->g[i];
+      for (int l = i + 1; l < j; ++l) sum -= h->H[i * kArnMax + l] * y[l];
+      y[i] = sum / h->H[i * kArnMax + i];
+    }
+    LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    LH_CK(m, launch_gemv<float>(s, V, j, ld, dh, 0.0, ulin, len));
+    if (op.pk == 3) {
+      if ((st = op.template cheb<double>(ulin, zd)) != LH_OK) return st;
+    } else {
+      LH_CK(m, (launch_prec<float, double>(op.pk, s, m->P, m->kron, prec_diag(m, op.pk), m->d_invMe, ulin, zd,
+                                           op.tau)));
+    }
+    LH_CK(m, launch_axpby(s, 1.0, zd, 1.0, dk, n));
+    if (done || total >= o.gmres_maxit) break;
+    // restart from the true linear residual -r - J dk
+    if ((st = op.jac(dk, w)) != LH_OK) return st;
+    ++S.jvp_evals;
+    LH_CK(m, (launch_scale<double, double>(s, -1.0, r, -1.0, w, wd, n)));
+    double b2;
+    if ((st = dot_host(m, wd, wd, n, &b2)) != LH_OK) return st;
+    beta = std::sqrt(b2);
+    if (beta <= o.gmres_rtol * beta0) break;
+    LH_CK(m, (launch_scale<double, float>(s, 1.0 / beta, wd, 0.0, nullptr, V, n)));
+  }
+  S.gmres_its_total += total;
+  return LH_OK;
+}
+
 // Restarted, right-preconditioned GMRES on J dk = -r from dk = 0 (paper Sec. 3.5, Eq. (22)).
 // Classical Gram-Schmidt applied twice (CGS2), each pass one fused reduction (V^T w and
 // w.w); the norm of the projected vector by Pythagoras from the second pass, computed on
@@ -376,6 +620,11 @@ lh_status cheb_bounds(lh_mesh* m, const lh_newton_opts& o, double tau, int tck, 
 template <class T>
 lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const double* r, double nr, double* dk,
                 T* V, T* w, T* ulin, double* zd, double* wd, lh_step_stats& S) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    bool used = false;
+    const lh_status sd = gmres_dev(m, o, op, r, nr, dk, V, w, ulin, zd, wd, S, &used);
+    if (used || sd != LH_OK) return sd;
+  }
   const long long n = m->n;
   // FP32 basis: leading dimension ldf, reductions over n rounded up to 4 (zero tails);
   // FP64 basis: contiguous
@@ -482,6 +731,7 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
     LH_CK(m, (launch_scale<double, T>(s, 1.0 / beta, wd, 0.0, nullptr, V, n)));
   }
   S.gmres_its_total += total;
+  if constexpr (sizeof(T) == sizeof(float)) m->arn.warm |= arn_kind(op);   // its kernels have run once
   return LH_OK;
 }
 
@@ -623,6 +873,7 @@ void lh_newton_opts_init(lh_newton_opts* o) {
   o->scaled_norm = 0;
   o->cheb_degree = 3;
   o->cheb_ratio = 20.0;
+  o->arnoldi = 1;
 }
 
 lh_status lh_mesh_create(const lh_mesh_desc* d, lh_mesh** out) {
@@ -781,6 +1032,13 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_xwork) cudaFree(m->d_xwork);
   if (m->d_wscale) cudaFree(m->d_wscale);
   if (m->d_jdiag) cudaFree(m->d_jdiag);
+  if (m->arn.exec) cudaGraphExecDestroy(m->arn.exec);
+  if (m->arn.graph) cudaGraphDestroy(m->arn.graph);
+  if (m->arn.cap) cudaStreamDestroy(m->arn.cap);
+  if (m->arn.cap2) cudaStreamDestroy(m->arn.cap2);
+  if (m->d_arn) cudaFree(m->d_arn);
+  if (m->h_arn) cudaFreeHost(m->h_arn);
+  if (m->d_vin) cudaFree(m->d_vin);
   for (int a = 0; a < 3; ++a) {
     if (m->kron.At_free[a]) cudaFree(m->kron.At_free[a]);
     if (m->kron.At_fixed[a]) cudaFree(m->kron.At_fixed[a]);
@@ -1013,6 +1271,7 @@ static lh_status check_newton_opts(lh_mesh* m, const lh_newton_opts& o) {
     return fail(m, LH_EINVAL, "precond 2 and 3 (velocity block) need a reduced-precision J.w");
   if (o.precond == 3 && (o.cheb_degree < 1 || o.cheb_degree > 16 || !(o.cheb_ratio > 1.0)))
     return fail(m, LH_EINVAL, "precond 3: need 1 <= cheb_degree <= 16 and cheb_ratio > 1");
+  if (o.arnoldi != 0 && o.arnoldi != 1) return fail(m, LH_EINVAL, "arnoldi must be 0 or 1");
   if (o.forcing != 0 && o.forcing != 1) return fail(m, LH_EINVAL, "forcing must be 0 or 1");
   if (o.forcing && !(o.eta_max >= o.gmres_rtol && o.eta_max < 1.0))
     return fail(m, LH_EINVAL, "eta_max must be in [gmres_rtol, 1)");

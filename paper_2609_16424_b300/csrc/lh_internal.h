@@ -50,6 +50,29 @@ lh_status set_global_error(lh_status st, const std::string& msg);   // for lh_la
 // source in 2D)
 inline int rec_len(int dim) { return dim == 3 ? 25 : 18; }
 
+// Device-driven Arnoldi of the FP32-basis GMRES (lh_api.cu): the CUDA graph of one restart
+// cycle (a WHILE conditional node around one Arnoldi iteration) and what its recorded
+// kernels depend on; it is recorded again when any of that changes.
+struct ArnState;
+struct ArnGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;      // private streams, used only to record the body and the
+  cudaStream_t cap2 = nullptr;     // body of its IF node
+  long long per_it = 0;            // kernel launches per iteration (for the launch counter)
+  long long per_fix = 0;           // ... in the IF body of the exact-norm fallback
+  bool off = false;                // a graph call failed once: the host loop from then on
+  const void* V = nullptr;
+  const void* w = nullptr;
+  const void* z = nullptr;
+  const void* wsc = nullptr;
+  long long ld = 0, len = 0, n = 0;
+  int pk = -9, tck = -9, mres = 0, cheb_degree = 0;
+  double tau = 0.0, cheb_b = 0.0, cheb_ratio = 0.0;
+  // operator kinds whose kernels have run once outside a recording (one-time set-up done)
+  unsigned long long warm = 0;
+};
+
 // Kronecker factors of the H1 mass inverse (lh_prec.cu); device pointers owned by the mesh
 struct KronPrec {
   float* At_free[3] = {nullptr, nullptr, nullptr};    // transposed 1D inverses, N_d x N_d
@@ -110,6 +133,12 @@ struct lh_mesh {
   bool rec_valid = false;
   int restart_alloc = 0;
   lh::KronPrec kron;
+  // device-driven Arnoldi: cycle state (device) and its pinned host copy, the operator
+  // input v_j (FP32 [ldf]), and the recorded graph
+  lh::ArnState* d_arn = nullptr;
+  lh::ArnState* h_arn = nullptr;
+  float* d_vin = nullptr;
+  lh::ArnGraph arn;
   lh::Prof prof;
   std::string err;
 };

@@ -95,6 +95,45 @@ cudaError_t launch_gemv_norm(cudaStream_t s, const T* V, int m, long long ld, co
 template <class T>
 cudaError_t launch_gemv(cudaStream_t s, const T* V, int m, long long ld, const double* h, double beta, T* y,
                         long long n);
+// ---- device-side Arnoldi of the FP32-basis GMRES (one restart cycle per CUDA graph) ----
+// State of one restart cycle in device memory.  The host writes the header and g[0] before
+// the cycle and reads the whole struct after it.  H is the Hessenberg matrix after the
+// Givens rotations, row-major with row stride kArnMax.
+constexpr int kArnMax = 64;
+struct ArnState {
+  int j;             // columns built so far in this cycle (the next column to build)
+  int stop;          // 0 running; 1 converged or breakdown; 3 restart length reached;
+                     // 4 iteration budget reached; 5 non-finite Krylov vector
+  int fix;           // this iteration needs the exact norm (the second pass still cancelled)
+  int mres;          // restart length of the cycle (<= kArnMax)
+  int maxit;         // iterations this cycle may take (the budget left)
+  int pad_;
+  double tol;        // stop when |g[j+1]| <= tol
+  double hn2;        // squared norm of the projected vector (Pythagoras, or exact if fix)
+  double g[kArnMax + 1], cs[kArnMax], sn[kArnMax];
+  double H[(kArnMax + 1) * kArnMax];
+};
+// the multi-dot and updates above with the column count taken from the device (m = *jdev + 1)
+// and an optional device gate (the launch does nothing unless *gate != 0); float4 forms only
+// (n, ld multiples of 4, 16-byte aligned vectors)
+cudaError_t launch_mdot_dev(cudaStream_t s, const float* V, const int* jdev, long long ld, const float* w, long long n,
+                            int with_self, const int* gate, double* partials, unsigned* counter, double* out_dev);
+cudaError_t launch_gemv_sub_dev(cudaStream_t s, const float* V, const int* jdev, long long ld, const double* h,
+                                float* w, long long n, const int* gate);
+// v_{j+1} = V[(j+1) ld + .] = (w - V h) / hn as launch_gemv_norm (j = st->j), also copied to
+// vin; stores hn^2 by Pythagoras (h: j + 1 coefficients and w.w at h[j + 1]) in st->hn2 and
+// st->fix = 1 if it kept no more than 1e-4 of w.w (the exact norm is then taken), which it
+// also sets as the conditional `fix` of the enclosing graph
+cudaError_t launch_gemv_norm_dev(cudaStream_t s, float* V, ArnState* st, long long ld, const double* h,
+                                 const float* w, float* vin, long long n, cudaGraphConditionalHandle fix);
+// if st->fix: v_{j+1} = vin = w / sqrt(st->hn2) (st->hn2 then holds the exact w.w)
+cudaError_t launch_arn_scale(cudaStream_t s, const ArnState* st, const float* w, float* V, long long ld, float* vin,
+                             long long n);
+// column j of H from the two passes' coefficients, the Givens rotations, the residual
+// estimate |g[j+1]| and the stopping test; sets the WHILE condition of the enclosing graph
+cudaError_t launch_arn_givens(cudaStream_t s, const double* h1, const double* h2, ArnState* st,
+                              cudaGraphConditionalHandle cond);
+
 // y = a x + b z  (z float, may be NULL)
 template <class TX, class TY>
 cudaError_t launch_scale(cudaStream_t s, double a, const TX* x, double b, const float* z, TY* y, long long n);

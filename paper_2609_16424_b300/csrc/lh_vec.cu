@@ -29,9 +29,14 @@ static inline unsigned red_grid(long long n) {
 template <class T, bool VEC4>
 __global__ void __launch_bounds__(kRedThreads)
 k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, long long n, int with_self,
-       double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ out) {
+       double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ out,
+       const int* __restrict__ jdev, const int* __restrict__ gate) {
   // per-thread and warp sums in T (float: a few hundred terms, ~1e-7 relative), block and
-  // grid sums in double
+  // grid sums in double.  jdev: column count from the device (m = *jdev + 1, at most
+  // kArnMax); gate: the launch does nothing unless *gate != 0 (both only inside the
+  // device-driven Arnoldi).
+  if (gate && *gate == 0) return;
+  if (jdev) m = min(*jdev + 1, kArnMax);
   constexpr int kChunk = MdotChunk<T>::value;
   __shared__ double red[kRedThreads / 32][kChunkMax];
   __shared__ bool last;
@@ -137,12 +142,14 @@ cudaError_t launch_mdot(cudaStream_t s, const T* V, int m, long long ld, const T
                     reinterpret_cast<uintptr_t>(V) % 16 == 0 && reinterpret_cast<uintptr_t>(w) % 16 == 0;
   if constexpr (sizeof(T) == sizeof(float)) {
     if (vec4) {
-      k_mdot<T, true><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
+      k_mdot<T, true><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev,
+                                                           nullptr, nullptr);
       count_launches(1);
       return cudaGetLastError();
     }
   }
-  k_mdot<T, false><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev);
+  k_mdot<T, false><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, with_self, partials, counter, out_dev,
+                                                        nullptr, nullptr);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -187,8 +194,11 @@ __global__ void k_gemv_sub(const T* __restrict__ V, int m, long long ld, const d
 // float4 forms (n, ld multiples of 4, 16-byte aligned): y = beta y + sign * V h
 template <bool SUB>
 __global__ void k_gemv4(const float* __restrict__ V, int m, long long ld, const double* __restrict__ h, float beta,
-                        float* __restrict__ y, long long n4) {
+                        float* __restrict__ y, long long n4, const int* __restrict__ jdev = nullptr,
+                        const int* __restrict__ gate = nullptr) {
   __shared__ float hs[64];
+  if (gate && *gate == 0) return;
+  if (jdev) m = min(*jdev + 1, kArnMax);
   if ((int)threadIdx.x < m) hs[threadIdx.x] = SUB ? -(float)h[threadIdx.x] : (float)h[threadIdx.x];
   __syncthreads();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
@@ -309,6 +319,156 @@ template cudaError_t launch_gemv_sub<double>(cudaStream_t, const double*, int, l
                                              long long);
 template cudaError_t launch_gemv_sub<float>(cudaStream_t, const float*, int, long long, const double*, float*,
                                             long long);
+
+// ---- device-side Arnoldi (FP32 basis) ----
+static inline unsigned gemv_grid(long long n4) { return nblk(n4, 256) < 4736u ? nblk(n4, 256) : 4736u; }
+
+cudaError_t launch_mdot_dev(cudaStream_t s, const float* V, const int* jdev, long long ld, const float* w, long long n,
+                            int with_self, const int* gate, double* partials, unsigned* counter, double* out_dev) {
+  if (!vec4_ok(V, w, ld, n)) return cudaErrorInvalidValue;
+  k_mdot<float, true><<<red_grid(n), kRedThreads, 0, s>>>(V, 1, ld, w, n, with_self, partials, counter, out_dev, jdev,
+                                                          gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_sub_dev(cudaStream_t s, const float* V, const int* jdev, long long ld, const double* h,
+                                float* w, long long n, const int* gate) {
+  if (!vec4_ok(V, w, ld, n)) return cudaErrorInvalidValue;
+  const long long n4 = n / 4;
+  k_gemv4<true><<<gemv_grid(n4), 256, 0, s>>>(V, 1, ld, h, 1.f, w, n4, jdev, gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// as k_gemv4_norm with m = st->j + 1 coefficients; writes column m of V and vin.  Block 0
+// also stores hn^2 (Pythagoras) and whether the second pass still cancelled (hn^2 <= 1e-4
+// w.w, then the exact norm is taken) in the cycle state and as the IF condition `fix`.
+__global__ void k_gemv4_norm_dev(float* V, ArnState* st, long long ld, const double* __restrict__ h,
+                                 const float* __restrict__ w, float* __restrict__ vin, long long n4,
+                                 cudaGraphConditionalHandle fix) {
+  __shared__ float hs[64];
+  __shared__ float s_inv;
+  const int m = min(st->j + 1, kArnMax);
+  if (threadIdx.x == 0) {
+    double hh = 0.0;
+    for (int q = 0; q < m; ++q) hh += h[q] * h[q];
+    const double ww = h[m];
+    const double hn2 = ww - hh;
+    s_inv = hn2 > 0.0 ? (float)(1.0 / sqrt(hn2)) : 0.f;
+    if (blockIdx.x == 0) {
+      const int f = hn2 > 1e-4 * ww ? 0 : 1;
+      st->hn2 = hn2;
+      st->fix = f;
+      cudaGraphSetConditional(fix, (unsigned)f);
+    }
+  }
+  if ((int)threadIdx.x < m) hs[threadIdx.x] = -(float)h[threadIdx.x];
+  __syncthreads();
+  const float inv = s_inv;
+  const long long ld4 = ld / 4;
+  float4* y = reinterpret_cast<float4*>(V + (long long)m * ld);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    float4 t = reinterpret_cast<const float4*>(w)[i];
+    const float4* v = reinterpret_cast<const float4*>(V) + i;
+    for (int j = 0; j < m; ++j, v += ld4) {
+      const float4 x = *v;
+      const float c = hs[j];
+      t.x += c * x.x;
+      t.y += c * x.y;
+      t.z += c * x.z;
+      t.w += c * x.w;
+    }
+    const float4 o = make_float4(t.x * inv, t.y * inv, t.z * inv, t.w * inv);
+    y[i] = o;
+    reinterpret_cast<float4*>(vin)[i] = o;
+  }
+}
+
+cudaError_t launch_gemv_norm_dev(cudaStream_t s, float* V, ArnState* st, long long ld, const double* h,
+                                 const float* w, float* vin, long long n, cudaGraphConditionalHandle fix) {
+  if (!vec4_ok(V, w, ld, n) || reinterpret_cast<uintptr_t>(vin) % 16 != 0) return cudaErrorInvalidValue;
+  const long long n4 = n / 4;
+  k_gemv4_norm_dev<<<gemv_grid(n4), 256, 0, s>>>(V, st, ld, h, w, vin, n4, fix);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_arn_scale(const ArnState* __restrict__ st, const float* __restrict__ w, float* V, long long ld,
+                            float* __restrict__ vin, long long n4) {
+  if (st->fix == 0) return;
+  const double hn2 = st->hn2;
+  if (!(hn2 > 0.0)) return;
+  const float a = (float)(1.0 / sqrt(hn2));
+  const int m = min(st->j + 1, kArnMax);
+  float4* y = reinterpret_cast<float4*>(V + (long long)m * ld);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    const float4 x = reinterpret_cast<const float4*>(w)[i];
+    const float4 o = make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
+    y[i] = o;
+    reinterpret_cast<float4*>(vin)[i] = o;
+  }
+}
+
+cudaError_t launch_arn_scale(cudaStream_t s, const ArnState* st, const float* w, float* V, long long ld, float* vin,
+                             long long n) {
+  if (!vec4_ok(V, w, ld, n) || reinterpret_cast<uintptr_t>(vin) % 16 != 0) return cudaErrorInvalidValue;
+  const long long n4 = n / 4;
+  k_arn_scale<<<gemv_grid(n4), 256, 0, s>>>(st, w, V, ld, vin, n4);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// One Arnoldi column's bookkeeping, in the order of the host loop: H[i][j] = h1[i] + h2[i]
+// (both Gram-Schmidt passes), H[j+1][j] = hn, the previous Givens rotations, the new
+// rotation, g, and the stopping test.  The WHILE condition is 1 only while the cycle runs.
+__global__ void k_arn_givens(const double* __restrict__ h1, const double* __restrict__ h2, ArnState* st,
+                             cudaGraphConditionalHandle cond) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int j = st->j;
+  int stop = 0;
+  if (j < 0 || j >= st->mres || j >= kArnMax) {
+    stop = 3;   // cannot happen while the host sets mres <= kArnMax; ends the loop regardless
+  } else {
+    const double hn2 = st->hn2;
+    if (!isfinite(hn2)) {
+      stop = 5;
+    } else {
+      double c[kArnMax + 1];
+      for (int i = 0; i <= j; ++i) c[i] = h1[i] + h2[i];
+      const double hn = sqrt(fmax(hn2, 0.0));
+      c[j + 1] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double a = c[i], b = c[i + 1];
+        c[i] = st->cs[i] * a + st->sn[i] * b;
+        c[i + 1] = -st->sn[i] * a + st->cs[i] * b;
+      }
+      const double a = c[j], b = c[j + 1];
+      const double rad = hypot(a, b);
+      st->cs[j] = rad > 0 ? a / rad : 1.0;
+      st->sn[j] = rad > 0 ? b / rad : 0.0;
+      c[j] = rad;
+      c[j + 1] = 0.0;
+      for (int i = 0; i <= j + 1; ++i) st->H[i * kArnMax + j] = c[i];
+      const double gj = st->g[j];
+      st->g[j + 1] = -st->sn[j] * gj;
+      st->g[j] = st->cs[j] * gj;
+      st->j = j + 1;
+      if (fabs(st->g[j + 1]) <= st->tol || hn == 0.0) stop = 1;
+      else if (j + 1 >= st->mres) stop = 3;
+      else if (j + 1 >= st->maxit) stop = 4;
+    }
+  }
+  st->stop = stop;
+  cudaGraphSetConditional(cond, stop == 0 ? 1u : 0u);
+}
+
+cudaError_t launch_arn_givens(cudaStream_t s, const double* h1, const double* h2, ArnState* st,
+                              cudaGraphConditionalHandle cond) {
+  k_arn_givens<<<1, 32, 0, s>>>(h1, h2, st, cond);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 template <class T>
 __global__ void k_gemv(const T* __restrict__ V, int m, long long ld, const double* __restrict__ h, double beta,

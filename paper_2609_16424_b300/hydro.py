@@ -21,7 +21,7 @@ def newton_opts(**kw):
     """lh_newton_opts with the library defaults, overridden by keyword arguments
     (newton_rtol, newton_atol, gmres_rtol, newton_maxit, gmres_maxit, restart,
     max_halvings, jvp_prec in {'fp64', 'fp32', 'tf32', 'bf16'}, precond in {'jacobi', 'kron',
-    'jvv_diag', 'cheb'}, forcing, eta_max, scaled_norm, cheb_degree, cheb_ratio);
+    'jvv_diag', 'cheb'}, forcing, eta_max, scaled_norm, cheb_degree, cheb_ratio, arnoldi);
     'tf32' and 'bf16' run the element contractions of J.w on the tensor cores."""
     o = _lib.NewtonOpts()
     _L.lh_newton_opts_init(C.byref(o))

@@ -37,7 +37,8 @@ def test_struct_layout_matches_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(lh_mesh_desc), offsetof(lh_mesh_desc, rho0),
          offsetof(lh_mesh_desc, bc_mask), offsetof(lh_mesh_desc, tg_source), offsetof(lh_mesh_desc, stream));
-  printf("%zu %zu\n", sizeof(lh_newton_opts), offsetof(lh_newton_opts, jvp_prec));
+  printf("%zu %zu %zu\n", sizeof(lh_newton_opts), offsetof(lh_newton_opts, jvp_prec),
+         offsetof(lh_newton_opts, arnoldi));
   printf("%zu %zu %zu\n", sizeof(lh_step_stats), offsetof(lh_step_stats, min_detj),
          offsetof(lh_step_stats, newton_its_max));
   printf("%zu %zu %zu %zu %zu %zu\n", sizeof(lh_advance_opts), offsetof(lh_advance_opts, dt0),
@@ -55,7 +56,7 @@ int main(void) {
     assert [int(x) for x in out[0].split()] == [C.sizeof(D), D.rho0.offset, D.bc_mask.offset,
                                                  D.tg_source.offset, D.stream.offset]
     N = _lib.NewtonOpts
-    assert [int(x) for x in out[1].split()] == [C.sizeof(N), N.jvp_prec.offset]
+    assert [int(x) for x in out[1].split()] == [C.sizeof(N), N.jvp_prec.offset, N.arnoldi.offset]
     S = _lib.StepStats
     assert [int(x) for x in out[2].split()] == [C.sizeof(S), S.min_detj.offset, S.newton_its_max.offset]
     A, H, T = _lib.AdvanceOpts, _lib.AdvanceAttempt, _lib.AdvanceStats
