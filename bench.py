@@ -191,7 +191,8 @@ def timed_steps(mesh, u_s, k_s, dt, steps, prec, flush, profile=False, arnoldi=1
 # (dram__bytes_read.sum + dram__bytes_write.sum) of a launch inside the timed Newton steps of
 # this workload, with the digest of the CUDA sources it was built from.  The figure is
 # reported only while the sources still have that digest (csrc_digest()).
-NCU_TRAFFIC = {"k_residual<3,2>": {"bytes": 13393920 + 61006336, "csrc": None}}
+NCU_TRAFFIC = {"k_jvp_rec<3,2,float>": {"bytes": 91828224 + 441600, "csrc": "0461a2af659b64c4"},
+               "k_residual<3,2>": {"bytes": 13469696 + 40662784, "csrc": "0461a2af659b64c4"}}
 
 
 def csrc_digest():
@@ -425,7 +426,10 @@ def run_ours(args, rank, world, device):
         wall = time.perf_counter() - wall0
     # element-kernel durations: CUDA events around each launch in a repeat of the timed steps
     # (same state, kernels and inputs; the Arnoldi loop on the host, where events can be placed)
+    torch.cuda.nvtx.range_push("kernel_timing")
     times_p, _, _, prof = timed_steps(mesh, u_s, k_s, dt, args.steps, prec, flush, profile=True)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         torch.distributed.barrier()
     step_ms = sum(times) / len(times)
