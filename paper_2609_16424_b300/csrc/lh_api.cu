@@ -406,9 +406,9 @@ lh_status arn_body(lh_mesh* m, KrylovOp<float>& op, float* V, float* w, long lon
   const int* jd = &st->j;
   lh_status e = op.apply(m->d_vin, w);
   if (e != LH_OK) return e;
+  float* wp = op.z;   // the projected vector w' = w - V h1 (the operator's scratch is free again)
   LH_CK(m, launch_mdot_dev(s, V, jd, ld, w, len, 1, nullptr, m->d_part, m->d_counter, dh));
-  LH_CK(m, launch_gemv_sub_dev(s, V, jd, ld, dh, w, len, nullptr));
-  LH_CK(m, launch_mdot_dev(s, V, jd, ld, w, len, 1, nullptr, m->d_part, m->d_counter, dh2));
+  LH_CK(m, launch_mdot_sub(s, V, 0, jd, ld, w, dh, wp, len, m->d_part, m->d_counter, dh2));
   // the IF node after the second update, then its body
   cudaStreamCaptureStatus cs;
   cudaGraph_t capg = nullptr;
@@ -417,7 +417,7 @@ lh_status arn_body(lh_mesh* m, KrylovOp<float>& op, float* V, float* w, long lon
   LH_CK(m, cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, nullptr, nullptr, nullptr));   // the WHILE body
   cudaGraphConditionalHandle fix;
   LH_CK(m, cudaGraphConditionalHandleCreate(&fix, capg, 0u, 0u));
-  LH_CK(m, launch_gemv_norm_dev(s, V, st, ld, dh2, w, m->d_vin, len, fix));
+  LH_CK(m, launch_gemv_norm_dev(s, V, st, ld, dh2, wp, m->d_vin, len, fix));
   LH_CK(m, cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, &deps, nullptr, &nd));
   ZeroNodeParams zp;
   cudaGraphNodeParams& np = zp.p;
@@ -432,9 +432,9 @@ lh_status arn_body(lh_mesh* m, KrylovOp<float>& op, float* V, float* w, long lon
   LH_CK(m, cudaStreamBeginCaptureToGraph(s2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal));
   const long long l0 = launches();
-  const cudaError_t e1 = launch_gemv_sub_dev(s2, V, jd, ld, dh2, w, len, nullptr);
-  const cudaError_t e2 = launch_mdot_dev(s2, w, nullptr, 0, w, len, 0, nullptr, m->d_part, m->d_counter, &st->hn2);
-  const cudaError_t e3 = launch_arn_scale(s2, st, w, V, ld, m->d_vin, len);
+  const cudaError_t e1 = launch_gemv_sub_dev(s2, V, jd, ld, dh2, wp, len, nullptr);
+  const cudaError_t e2 = launch_mdot_dev(s2, wp, nullptr, 0, wp, len, 0, nullptr, m->d_part, m->d_counter, &st->hn2);
+  const cudaError_t e3 = launch_arn_scale(s2, st, wp, V, ld, m->d_vin, len);
   m->arn.per_fix = launches() - l0;   // the IF body runs only when the second pass cancelled
   cudaGraph_t got = nullptr;
   const cudaError_t e4 = cudaStreamEndCapture(s2, &got);
@@ -653,9 +653,15 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
       double* dh2 = dh + 72;   // the first pass writes up to 66 values at dh
       T* vn = V + (long long)(j + 1) * ld;
       LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh));
-      LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh, w, len));
-      LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh2));
-      LH_CK(m, launch_gemv_norm<T>(s, V, j + 1, ld, dh2, w, vn, len));
+      T* wp = w;   // the projected vector w' = w - V h1
+      if constexpr (sizeof(T) == sizeof(float)) {   // update fused into the second multi-dot, w' in z
+        wp = op.z;
+        LH_CK(m, launch_mdot_sub(s, V, j + 1, nullptr, ld, w, dh, wp, len, m->d_part, m->d_counter, dh2));
+      } else {
+        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh, w, len));
+        LH_CK(m, launch_mdot<T>(s, V, j + 1, ld, w, len, 1, m->d_part, m->d_counter, dh2));
+      }
+      LH_CK(m, launch_gemv_norm<T>(s, V, j + 1, ld, dh2, wp, vn, len));
       LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double) * (72 + j + 2), cudaMemcpyDeviceToHost, s));
       LH_CK(m, cudaStreamSynchronize(s));
       ++S.reorth;
@@ -667,12 +673,12 @@ lh_status gmres(lh_mesh* m, const lh_newton_opts& o, KrylovOp<T>& op, const doub
       const double ww2 = hcol[72 + j + 1];
       double hn2 = ww2 - hh2;
       if (!(hn2 > 1e-4 * ww2)) {   // the second pass still cancelled: take the exact norm
-        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh2, w, len));
-        LH_CK(m, launch_mdot<T>(s, w, 1, 0, w, len, 0, m->d_part, m->d_counter, dh));
+        LH_CK(m, launch_gemv_sub<T>(s, V, j + 1, ld, dh2, wp, len));
+        LH_CK(m, launch_mdot<T>(s, wp, 1, 0, wp, len, 0, m->d_part, m->d_counter, dh));
         LH_CK(m, cudaMemcpyAsync(hcol.data(), dh, sizeof(double), cudaMemcpyDeviceToHost, s));
         LH_CK(m, cudaStreamSynchronize(s));
         hn2 = hcol[0];
-        if (hn2 > 0.0) LH_CK(m, (launch_scale<T, T>(s, 1.0 / std::sqrt(hn2), w, 0.0, nullptr, vn, n)));
+        if (hn2 > 0.0) LH_CK(m, (launch_scale<T, T>(s, 1.0 / std::sqrt(hn2), wp, 0.0, nullptr, vn, n)));
       }
       if (!std::isfinite(hn2)) return fail(m, LH_ENONFINITE, "lh_newton_step: non-finite Krylov vector");
       const double hn = std::sqrt(std::fmax(hn2, 0.0));

@@ -44,10 +44,18 @@ __device__ __forceinline__ ElemIdx elem_index(const ElemParams& P) {
   const int eb = threadIdx.x / C::NQ;
   r.e = (long long)blockIdx.x * C::EPB + eb;
   r.valid = r.e < P.NE;
-  const long long e = r.valid ? r.e : 0;
-  r.ex = (int)(e % P.n0);
-  r.ey = (int)((e / P.n0) % P.n1);
-  r.ez = DIM == 3 ? (int)(e / ((long long)P.n0 * P.n1)) : 0;
+  // 32-bit lattice arithmetic: dim * N_V < 2^31 is checked at mesh creation, so NE fits
+  const unsigned e = r.valid ? (unsigned)r.e : 0u, n0 = (unsigned)P.n0, n1 = (unsigned)P.n1;
+  const unsigned t = e / n0;
+  r.ex = (int)(e - t * n0);
+  if constexpr (DIM == 3) {
+    const unsigned u = t / n1;
+    r.ey = (int)(t - u * n1);
+    r.ez = (int)u;
+  } else {
+    r.ey = (int)(t % n1);
+    r.ez = 0;
+  }
   return r;
 }
 
@@ -56,10 +64,11 @@ template <int DIM, int K>
 __device__ __forceinline__ long long node_of(const ElemParams& P, const ElemIdx& E, int a) {
   constexpr int D = K + 1;
   const int a0 = a % D, a1 = (a / D) % D, a2 = a / (D * D);
-  const long long i0 = (long long)E.ex * K + a0, i1 = (long long)E.ey * K + a1;
-  if constexpr (DIM == 2) return i0 + (long long)P.N0 * i1;
-  const long long i2 = (long long)E.ez * K + a2;
-  return i0 + (long long)P.N0 * (i1 + (long long)P.N1 * i2);
+  // node indices are below N_V < 2^31 (checked at mesh creation): 32-bit products
+  const unsigned i0 = (unsigned)E.ex * K + a0, i1 = (unsigned)E.ey * K + a1;
+  if constexpr (DIM == 2) return (long long)(i0 + (unsigned)P.N0 * i1);
+  const unsigned i2 = (unsigned)E.ez * K + a2;
+  return (long long)(i0 + (unsigned)P.N0 * (i1 + (unsigned)P.N1 * i2));
 }
 
 template <int DIM, int K, class T>

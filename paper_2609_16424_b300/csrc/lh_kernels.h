@@ -120,6 +120,12 @@ cudaError_t launch_mdot_dev(cudaStream_t s, const float* V, const int* jdev, lon
                             int with_self, const int* gate, double* partials, unsigned* counter, double* out_dev);
 cudaError_t launch_gemv_sub_dev(cudaStream_t s, const float* V, const int* jdev, long long ld, const double* h,
                                 float* w, long long n, const int* gate);
+// the first Gram-Schmidt update fused in front of the second multi-dot (float4 form):
+// wout = w - V hsub (m columns, or *jdev + 1 when jdev is given), out_dev[q] = V_q . wout for
+// q < m and out_dev[m] = wout . wout
+cudaError_t launch_mdot_sub(cudaStream_t s, const float* V, int m, const int* jdev, long long ld, const float* w,
+                            const double* hsub, float* wout, long long n, double* partials, unsigned* counter,
+                            double* out_dev);
 // v_{j+1} = V[(j+1) ld + .] = (w - V h) / hn as launch_gemv_norm (j = st->j), also copied to
 // vin; stores hn^2 by Pythagoras (h: j + 1 coefficients and w.w at h[j + 1]) in st->hn2 and
 // st->fix = 1 if it kept no more than 1e-4 of w.w (the exact norm is then taken), which it

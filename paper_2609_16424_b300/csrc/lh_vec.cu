@@ -9,6 +9,32 @@ namespace lh {
 
 static inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// s += sum_{j < m} hs[j] v[j * ld4] in the order j = 0, 1, ... (four columns' loads issued
+// together)
+__device__ __forceinline__ void cols4(float4& s, const float* hs, const float4* v, long long ld4, int m) {
+  int j = 0;
+  for (; j + 4 <= m; j += 4, v += 4 * ld4) {
+    const float4 x0 = v[0], x1 = v[ld4], x2 = v[2 * ld4], x3 = v[3 * ld4];
+    const float4 x[4] = {x0, x1, x2, x3};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float c = hs[j + u];
+      s.x += c * x[u].x;
+      s.y += c * x[u].y;
+      s.z += c * x[u].z;
+      s.w += c * x[u].w;
+    }
+  }
+  for (; j < m; ++j, v += ld4) {
+    const float4 x = *v;
+    const float c = hs[j];
+    s.x += c * x.x;
+    s.y += c * x.y;
+    s.z += c * x.z;
+    s.w += c * x.w;
+  }
+}
+
 // Fused deterministic multi-dot: out[j] = V_j . w for j < m, plus out[m] = w . w when
 // with_self.  Each block reduces a fixed contiguous chunk of the index range (one pass
 // over w for up to 8 vectors at a time, fixed-order warp and block trees) and writes its
@@ -26,11 +52,15 @@ static inline unsigned red_grid(long long n) {
   return (unsigned)g;
 }
 
-template <class T, bool VEC4>
+// SUB (float4 form only): the first Gram-Schmidt update fused in front of the multi-dot:
+// w' = w - V hsub (the same sums, in the same order, as k_gemv4<true>) is written to wout and
+// the outputs are V^T w' (and w'.w').
+template <class T, bool VEC4, bool SUB = false>
 __global__ void __launch_bounds__(kRedThreads)
 k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, long long n, int with_self,
        double* __restrict__ part, unsigned* __restrict__ counter, double* __restrict__ out,
-       const int* __restrict__ jdev, const int* __restrict__ gate) {
+       const int* __restrict__ jdev, const int* __restrict__ gate, const double* __restrict__ hsub = nullptr,
+       float* __restrict__ wout = nullptr) {
   // per-thread and warp sums in T (float: a few hundred terms, ~1e-7 relative), block and
   // grid sums in double.  jdev: column count from the device (m = *jdev + 1, at most
   // kArnMax); gate: the launch does nothing unless *gate != 0 (both only inside the
@@ -40,6 +70,12 @@ k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, lo
   constexpr int kChunk = MdotChunk<T>::value;
   __shared__ double red[kRedThreads / 32][kChunkMax];
   __shared__ bool last;
+  __shared__ float hsn[SUB ? 64 : 1];
+  static_assert(!SUB || (VEC4 && sizeof(T) == sizeof(float)), "the fused update is float4 only");
+  if constexpr (SUB) {
+    if ((int)threadIdx.x < m) hsn[threadIdx.x] = -(float)hsub[threadIdx.x];
+    __syncthreads();
+  }
   const int nout = m + (with_self ? 1 : 0);
   long long chunk = (n + gridDim.x - 1) / gridDim.x;
   if constexpr (VEC4) chunk = (chunk + 3) / 4 * 4;   // chunk boundaries on 16-byte boundaries
@@ -58,11 +94,22 @@ k_mdot(const T* __restrict__ V, int m, long long ld, const T* __restrict__ w, lo
     if constexpr (VEC4) {
       // four consecutive entries per load (ld, n multiples of 4, 16-byte aligned vectors)
       for (long long i = beg + 4 * threadIdx.x; i < end; i += 4 * blockDim.x) {
-        const float4 wi = w ? *reinterpret_cast<const float4*>(w + i) : make_float4(1.f, 1.f, 1.f, 1.f);
+        float4 wi;
+        if constexpr (SUB) {
+          if (c0 == 0) {   // w' at this position, kept for the later chunks of outputs
+            wi = *reinterpret_cast<const float4*>(w + i);
+            cols4(wi, hsn, reinterpret_cast<const float4*>(V + i), ld / 4, m);
+            *reinterpret_cast<float4*>(wout + i) = wi;
+          } else {
+            wi = *reinterpret_cast<const float4*>(wout + i);
+          }
+        } else {
+          wi = w ? *reinterpret_cast<const float4*>(w + i) : make_float4(1.f, 1.f, 1.f, 1.f);
+        }
 #pragma unroll
         for (int q = 0; q < kChunk; ++q)
           if (q < nq) {
-            const float4 v = *reinterpret_cast<const float4*>(vq[q] + i);
+            const float4 v = c0 + q == m ? wi : *reinterpret_cast<const float4*>(vq[q] + i);
             acc[q] += (v.x * wi.x + v.y * wi.y) + (v.z * wi.z + v.w * wi.w);
           }
       }
@@ -328,6 +375,16 @@ cudaError_t launch_mdot_dev(cudaStream_t s, const float* V, const int* jdev, lon
   if (!vec4_ok(V, w, ld, n)) return cudaErrorInvalidValue;
   k_mdot<float, true><<<red_grid(n), kRedThreads, 0, s>>>(V, 1, ld, w, n, with_self, partials, counter, out_dev, jdev,
                                                           gate);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mdot_sub(cudaStream_t s, const float* V, int m, const int* jdev, long long ld, const float* w,
+                            const double* hsub, float* wout, long long n, double* partials, unsigned* counter,
+                            double* out_dev) {
+  if (!vec4_ok(V, w, ld, n) || reinterpret_cast<uintptr_t>(wout) % 16 != 0 || m + 1 > 72) return cudaErrorInvalidValue;
+  k_mdot<float, true, true><<<red_grid(n), kRedThreads, 0, s>>>(V, m, ld, w, n, 1, partials, counter, out_dev, jdev,
+                                                                nullptr, hsub, wout);
   count_launches(1);
   return cudaGetLastError();
 }
