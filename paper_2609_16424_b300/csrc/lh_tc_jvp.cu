@@ -13,8 +13,9 @@
 //   D_b[(c', e)][a] += sum_(q, r) F[(c', e)][(q, r)] Bb[a][(q, r)]
 // with F = (m_q dv_q, S-tangent) for the H1 rows c' < dim and (g_q, 0, ..) for the L2 row
 // c' = dim.  Operands are TF32 or BF16 in shared memory, accumulators FP32 in tensor
-// memory.  The quadrature-point tangent (Eqs. (11)-(20) on dual numbers) runs in FP32 on
-// the CUDA cores between the two MMAs, one thread per (element, quadrature point).
+// memory.  Between the two MMAs the linearised point map of Eqs. (11)-(20), read from the
+// linearisation record the FP64 residual wrote, is applied in FP32 on the CUDA cores, one
+// thread per (element, quadrature point).
 //
 // Dense element operators are (Q^d x 4) x (D^d + L^d) entries; they fit in shared memory
 // for 2D k <= 4 and 3D k <= 2.  Persistent CTAs (two per SM with BF16 operands, one with
