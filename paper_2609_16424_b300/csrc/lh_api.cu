@@ -242,11 +242,24 @@ cudaEvent_t* prof_pair(lh_mesh* m, int kind) {
   return &p.ev[2 * p.n++];
 }
 
-// ||x||_2^2 into a host double (synchronises)
+// pinned host scratch for the small read-backs of the Newton loop and the GMRES coefficients
+// y (entries 16..16 + kArnMax); NULL if it cannot be allocated (pageable memory then)
+constexpr int kSmallHost = 16 + kArnMax;
+double* host_small(lh_mesh* m) {
+  if (!m->h_small && cudaMallocHost(&m->h_small, sizeof(double) * kSmallHost) != cudaSuccess) {
+    m->h_small = nullptr;
+    (void)cudaGetLastError();
+  }
+  return m->h_small;
+}
+
+// a . b into a host double (synchronises)
 lh_status dot_host(lh_mesh* m, const double* a, const double* b, long long n, double* out) {
   LH_CK(m, launch_mdot<double>(m->stream, a, 1, 0, b, n, 0, m->d_part, m->d_counter, m->d_scalar));
-  LH_CK(m, cudaMemcpyAsync(out, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  double* h = host_small(m);
+  LH_CK(m, cudaMemcpyAsync(h ? h : out, m->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
   LH_CK(m, cudaStreamSynchronize(m->stream));
+  if (h) *out = h[0];
   return LH_OK;
 }
 
@@ -579,13 +592,15 @@ lh_status gmres_dev(lh_mesh* m, const lh_newton_opts& o, KrylovOp<float>& op, co
     if (j < 1 || j > mres) return fail(m, LH_ECUDA, "device Arnoldi: inconsistent cycle state");
     const bool done = h->stop == 1;
     // y = H^-1 g (upper triangular j x j), dk += P^-1 V y
-    std::vector<double> y(j);
+    std::vector<double> yv(j);
+    double* hs = host_small(m);
+    double* y = hs ? hs + 16 : yv.data();   // pinned: the copy below does not stage
     for (int i = j - 1; i >= 0; --i) {
       double sum = h->g[i];
       for (int l = i + 1; l < j; ++l) sum -= h->H[i * kArnMax + l] * y[l];
       y[i] = sum / h->H[i * kArnMax + i];
     }
-    LH_CK(m, cudaMemcpyAsync(dh, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    LH_CK(m, cudaMemcpyAsync(dh, y, sizeof(double) * j, cudaMemcpyHostToDevice, s));
     LH_CK(m, launch_gemv<float>(s, V, j, ld, dh, 0.0, ulin, len));
     if (op.pk == 3) {
       if ((st = op.template cheb<double>(ulin, zd)) != LH_OK) return st;
@@ -749,6 +764,28 @@ lh_status ensure_rec(lh_mesh* m) {
 }
 
 // residual + min detJ (host) in one call; rec (optional) receives the linearisation record
+// the residual, its min det J and ||x||_2^2 with x = r (or W r in rs when wsc is given),
+// read back together (one synchronisation)
+lh_status residual_min_norm(lh_mesh* m, const double* u, const double* k, double tau, double* r, double* mindet,
+                            double* nr2, float* rec, const double* wsc, double* rs) {
+  cudaStream_t s = m->stream;
+  LH_CK(m, launch_residual(m->P, s, u, k, tau, m->d_ev, m->d_blockmin, r, prof_pair(m, LH_PROF_RESIDUAL), rec));
+  LH_CK(m, launch_min(s, m->d_blockmin, m->nblocks_elem, m->d_scalar + 1));
+  const double* x = r;
+  if (wsc) {
+    LH_CK(m, launch_row_mul<double>(s, wsc, r, rs, m->n));
+    x = rs;
+  }
+  LH_CK(m, launch_mdot<double>(s, x, 1, 0, x, m->n, 0, m->d_part, m->d_counter, m->d_scalar + 2));
+  double* h = host_small(m);
+  double tmp[2];
+  LH_CK(m, cudaMemcpyAsync(h ? h : tmp, m->d_scalar + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  LH_CK(m, cudaStreamSynchronize(s));
+  *mindet = (h ? h : tmp)[0];
+  *nr2 = (h ? h : tmp)[1];
+  return LH_OK;
+}
+
 lh_status residual_min(lh_mesh* m, const double* u, const double* k, double tau, double* r, double* mindet,
                        float* rec = nullptr) {
   LH_CK(m, launch_residual(m->P, m->stream, u, k, tau, m->d_ev, m->d_blockmin, r, prof_pair(m, LH_PROF_RESIDUAL),
@@ -1045,6 +1082,7 @@ lh_status lh_mesh_destroy(lh_mesh* m) {
   if (m->d_arn) cudaFree(m->d_arn);
   if (m->h_arn) cudaFreeHost(m->h_arn);
   if (m->d_vin) cudaFree(m->d_vin);
+  if (m->h_small) cudaFreeHost(m->h_small);
   for (int a = 0; a < 3; ++a) {
     if (m->kron.At_free[a]) cudaFree(m->kron.At_free[a]);
     if (m->kron.At_fixed[a]) cudaFree(m->kron.At_fixed[a]);
@@ -1334,11 +1372,6 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     wsc = m->d_wscale;
   }
   // squared norm of the stopping test: ||x||_2^2, or ||W x||_2^2 with scaled_norm (W x left in rs)
-  auto norm2 = [&](const double* x, double* out) -> lh_status {
-    if (!wsc) return dot_host(m, x, x, n, out);
-    LH_CK(m, launch_row_mul<double>(s, wsc, x, rs, n));
-    return dot_host(m, rs, rs, n, out);
-  };
 
   if (k_init) {
     LH_CK(m, cudaMemcpyAsync(k, k_init, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -1346,15 +1379,14 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
   }
   double mind, nr2;
-  if ((st = residual_min(m, u, k, tau, r, &mind, rec)) != LH_OK) return st;
+  if ((st = residual_min_norm(m, u, k, tau, r, &mind, &nr2, rec, wsc, rs)) != LH_OK) return st;
   ++S.residual_evals;
   if (!(mind > 0.0) && k_init) {   // a tangled initial guess: restart from k = 0
     LH_CK(m, cudaMemsetAsync(k, 0, sizeof(double) * n, s));
-    if ((st = residual_min(m, u, k, tau, r, &mind, rec)) != LH_OK) return st;
+    if ((st = residual_min_norm(m, u, k, tau, r, &mind, &nr2, rec, wsc, rs)) != LH_OK) return st;
     ++S.residual_evals;
   }
   if (!(mind > 0.0)) return fail(m, LH_ETANGLED, "Newton: det J <= 0 at the initial guess");
-  if ((st = norm2(r, &nr2)) != LH_OK) return st;
   double nr = std::sqrt(nr2);
   if (!std::isfinite(nr)) return fail(m, LH_ENONFINITE, "Newton: non-finite residual");
   S.r0 = nr;
@@ -1390,10 +1422,9 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     for (int hlv = 0; hlv <= o.max_halvings; ++hlv) {
       LH_CK(m, cudaMemcpyAsync(kt, k, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       LH_CK(m, launch_axpby(s, lam, dk, 1.0, kt, n));
-      if ((st = residual_min(m, u, kt, tau, rt, &mind, rec)) != LH_OK) return st;
+      if ((st = residual_min_norm(m, u, kt, tau, rt, &mind, &nr2, rec, wsc, rs)) != LH_OK) return st;
       ++S.residual_evals;
       if (mind > 0.0) {   // reject tangled trials (Sec. 3.5) and, as well, non-finite ones
-        if ((st = norm2(rt, &nr2)) != LH_OK) return st;
         if (std::isfinite(nr2)) {
           accepted = true;
           break;

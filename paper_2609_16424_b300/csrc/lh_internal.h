@@ -139,6 +139,7 @@ struct lh_mesh {
   lh::ArnState* h_arn = nullptr;
   float* d_vin = nullptr;
   lh::ArnGraph arn;
+  double* h_small = nullptr;       // pinned host scratch for the Newton loop's read-backs
   lh::Prof prof;
   std::string err;
 };
