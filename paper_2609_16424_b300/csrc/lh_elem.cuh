@@ -136,14 +136,12 @@ __device__ __forceinline__ double block_min(double v, double* red) {
 }
 
 template <int DIM, int K, class T>
-__device__ __forceinline__ T gather_node(const ElemParams& P, const T* __restrict__ ev, int ncomp, int comp,
-                                         long long nd_) {
+__device__ __forceinline__ T gather_node_ic(const ElemParams& P, const T* __restrict__ ev, int ncomp, int comp,
+                                            const int (&ic)[3]) {
   // 32-bit lattice arithmetic (node counts stay far below 2^31); per axis at most two
   // elements share the node: option 0 (the lower element, or the only one) and option 1
   // (the upper element), summed in the fixed order lower-then-upper per axis
   constexpr int D = K + 1, ND = Cfg<DIM, K>::ND;
-  const int nd = (int)nd_;
-  const int ic[3] = {nd % P.N0, (nd / P.N0) % P.N1, DIM == 3 ? nd / (P.N0 * P.N1) : 0};
   const int nel[3] = {P.n0, P.n1, P.n2};
   int e0[3], l0[3], e1[3], l1[3];
   bool v0[3], v1[3];
@@ -173,10 +171,51 @@ __device__ __forceinline__ T gather_node(const ElemParams& P, const T* __restric
         if (!ok) continue;
         const int ex = b0 ? e1[0] : e0[0], ey = b1 ? e1[1] : e0[1], ez = b2 ? e1[2] : e0[2];
         const int a = (b0 ? l1[0] : l0[0]) + D * ((b1 ? l1[1] : l0[1]) + D * (b2 ? l1[2] : l0[2]));
-        const long long e = ex + (long long)P.n0 * (ey + (long long)P.n1 * ez);
+        const long long e = (long long)((unsigned)ex + (unsigned)P.n0 * ((unsigned)ey + (unsigned)P.n1 * (unsigned)ez));
         s += ev[(e * ncomp + comp) * ND + a];
       }
   return s;
+}
+
+template <int DIM, int K, class T>
+__device__ __forceinline__ T gather_node(const ElemParams& P, const T* __restrict__ ev, int ncomp, int comp,
+                                         long long nd_) {
+  const int nd = (int)nd_;
+  const int ic[3] = {nd % P.N0, (nd / P.N0) % P.N1, DIM == 3 ? nd / (P.N0 * P.N1) : 0};
+  return gather_node_ic<DIM, K>(P, ev, ncomp, comp, ic);
+}
+
+// velocity component comp of lattice node (ic) is fixed (v.n = 0 on a masked face)
+template <int DIM>
+__device__ __forceinline__ bool fixed_node_ic(const ElemParams& P, const int (&ic)[3], int comp) {
+  const int Nc = comp == 0 ? P.N0 : comp == 1 ? P.N1 : P.N2;
+  const int c = ic[comp];
+  return (((P.bc >> (2 * comp)) & 1u) && c == 0) || (((P.bc >> (2 * comp + 1)) & 1u) && c == Nc - 1);
+}
+
+// Launch shape of the node-centric assembly kernels: blocks of kAsmX nodes along x, one
+// (y, z plane, component) row per block, grid-strided in y and z past the grid limits, so
+// that a thread finds its node without integer division.
+constexpr int kAsmX = 64;
+static inline dim3 asm_grid(const ElemParams& P) {
+  const long long zc = (long long)(P.dim == 3 ? P.N2 : 1) * P.dim;
+  return dim3((unsigned)((P.N0 + kAsmX - 1) / kAsmX), (unsigned)(P.N1 < 65535 ? P.N1 : 65535),
+              (unsigned)(zc < 65535 ? zc : 65535));
+}
+// f(comp, ic, nd) for every node row this thread owns under asm_grid
+template <int DIM, class F>
+__device__ __forceinline__ void for_asm_nodes(const ElemParams& P, F&& f) {
+  const int ix = (int)blockIdx.x * kAsmX + (int)threadIdx.x;
+  if (ix >= P.N0) return;
+  const int nz = DIM == 3 ? P.N2 : 1;
+  for (int zc = blockIdx.z; zc < nz * DIM; zc += gridDim.z) {
+    const int comp = zc / nz, iz = zc - comp * nz;
+    for (int iy = blockIdx.y; iy < P.N1; iy += gridDim.y) {
+      const int ic[3] = {ix, iy, iz};
+      const long long nd = (long long)((unsigned)ix + (unsigned)P.N0 * ((unsigned)iy + (unsigned)P.N1 * (unsigned)iz));
+      f(comp, ic, nd);
+    }
+  }
 }
 
 // dynamic shared-memory limit of a kernel, set once per device (a per-device attribute)

@@ -712,40 +712,33 @@ k_dt_estimate(ElemParams P, const double* __restrict__ u, double* __restrict__ b
 template <int DIM, int K>
 __global__ void k_assemble_residual(ElemParams P, const double* __restrict__ u, const double* __restrict__ kk,
                                     double tau, const double* __restrict__ ev, double* __restrict__ r) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= DIM * P.NV) return;
-  const int comp = (int)(i / P.NV);
-  const long long nd = i % P.NV;
-  const long long iv = DIM * P.NV + i;
-  r[i] = kk[i] - (u[iv] + tau * kk[iv]);
-  r[iv] = fixed_node<DIM>(P, nd, comp) ? kk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd);
+  for_asm_nodes<DIM>(P, [&](int comp, const int (&ic)[3], long long nd) {
+    const long long i = comp * P.NV + nd, iv = DIM * P.NV + i;
+    r[i] = kk[i] - (u[iv] + tau * kk[iv]);
+    r[iv] = fixed_node_ic<DIM>(P, ic, comp) ? kk[iv] : gather_node_ic<DIM, K>(P, ev, DIM, comp, ic);
+  });
 }
 
 template <int DIM, int K, class T, class TO>
 __global__ void k_assemble_jvp(ElemParams P, const T* __restrict__ dk, double tau, const T* __restrict__ ev,
                                TO* __restrict__ out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= DIM * P.NV) return;
-  const int nv = (int)P.NV, i32 = (int)i;
-  const int comp = i32 / nv;
-  const long long nd = i32 - comp * nv;
-  const long long iv = DIM * P.NV + i;
-  out[i] = TO(dk[i] - T(tau) * dk[iv]);
-  out[iv] = TO(fixed_node<DIM>(P, nd, comp) ? dk[iv] : gather_node<DIM, K>(P, ev, DIM, comp, nd));
+  for_asm_nodes<DIM>(P, [&](int comp, const int (&ic)[3], long long nd) {
+    const long long i = comp * P.NV + nd, iv = DIM * P.NV + i;
+    out[i] = TO(dk[i] - T(tau) * dk[iv]);
+    out[iv] = TO(fixed_node_ic<DIM>(P, ic, comp) ? dk[iv] : gather_node_ic<DIM, K>(P, ev, DIM, comp, ic));
+  });
 }
 
 template <int DIM, int K, class T>
 __global__ void k_assemble_jtvp(ElemParams P, const T* __restrict__ y, double tau,
                                   const T* __restrict__ ev, T* __restrict__ out) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= DIM * P.NV) return;
-  const int comp = (int)(i / P.NV);
-  const long long nd = i % P.NV;
-  const long long iv = DIM * P.NV + i;
-  out[i] = y[i] + gather_node<DIM, K>(P, ev, 2 * DIM, comp, nd);
-  T s = T(-tau) * y[i] + gather_node<DIM, K>(P, ev, 2 * DIM, DIM + comp, nd);
-  if (fixed_node<DIM>(P, nd, comp)) s += y[iv];
-  out[iv] = s;
+  for_asm_nodes<DIM>(P, [&](int comp, const int (&ic)[3], long long nd) {
+    const long long i = comp * P.NV + nd, iv = DIM * P.NV + i;
+    out[i] = y[i] + gather_node_ic<DIM, K>(P, ev, 2 * DIM, comp, ic);
+    T s = T(-tau) * y[i] + gather_node_ic<DIM, K>(P, ev, 2 * DIM, DIM + comp, ic);
+    if (fixed_node_ic<DIM>(P, ic, comp)) s += y[iv];
+    out[iv] = s;
+  });
 }
 
 // =====================================================================================
@@ -930,7 +923,7 @@ struct Launch {
     k_residual<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, ev, Re, bmin, rec);
     mark(ev2, 1, s);
     count_launches(2);
-    k_assemble_residual<DIM, K><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, u, k, tau, ev, r);
+    k_assemble_residual<DIM, K><<<asm_grid(P), kAsmX, 0, s>>>(P, u, k, tau, ev, r);
     return cudaGetLastError();
   }
   template <class T, class TO>
@@ -944,7 +937,7 @@ struct Launch {
     k_jvp<DIM, K, T, TO><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, dk, ev, out + 2 * DIM * P.NV);
     mark(ev2, 1, s);
     count_launches(2);
-    k_assemble_jvp<DIM, K, T, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    k_assemble_jvp<DIM, K, T, TO><<<asm_grid(P), kAsmX, 0, s>>>(P, dk, tau, ev, out);
     return cudaGetLastError();
   }
   template <class TO>
@@ -958,14 +951,14 @@ struct Launch {
     k_jvp_rec<DIM, K, TO><<<grid(P), C::THREADS, by, s>>>(P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV);
     mark(ev2, 1, s);
     count_launches(2);
-    k_assemble_jvp<DIM, K, float, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    k_assemble_jvp<DIM, K, float, TO><<<asm_grid(P), kAsmX, 0, s>>>(P, dk, tau, ev, out);
     return cudaGetLastError();
   }
   template <class TO>
   static cudaError_t assemble_jvp(const ElemParams& P, cudaStream_t s, const float* dk, double tau, const float* ev,
                                   TO* out) {
     count_launches(1);
-    k_assemble_jvp<DIM, K, float, TO><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, dk, tau, ev, out);
+    k_assemble_jvp<DIM, K, float, TO><<<asm_grid(P), kAsmX, 0, s>>>(P, dk, tau, ev, out);
     return cudaGetLastError();
   }
   static cudaError_t jvv_diag(const ElemParams& P, cudaStream_t s, const float* rec, double tau, float* ev,
@@ -988,7 +981,7 @@ struct Launch {
     k_jtvp_rec<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, rec, (float)tau, y, ev, out + 2 * DIM * P.NV);
     mark(ev2, 1, s);
     count_launches(2);
-    k_assemble_jtvp<DIM, K, float><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, y, tau, ev, out);
+    k_assemble_jtvp<DIM, K, float><<<asm_grid(P), kAsmX, 0, s>>>(P, y, tau, ev, out);
     return cudaGetLastError();
   }
   static cudaError_t jtvp(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
@@ -1001,7 +994,7 @@ struct Launch {
     k_jtvp<DIM, K><<<grid(P), C::THREADS, by, s>>>(P, u, k, tau, y, ev, out + 2 * DIM * P.NV);
     mark(ev2, 1, s);
     count_launches(2);
-    k_assemble_jtvp<DIM, K, double><<<nblk(DIM * P.NV, 256), 256, 0, s>>>(P, y, tau, ev, out);
+    k_assemble_jtvp<DIM, K, double><<<asm_grid(P), kAsmX, 0, s>>>(P, y, tau, ev, out);
     return cudaGetLastError();
   }
   static cudaError_t mass_h1(const ElemParams& P, cudaStream_t s, const double* f, double* ev, double* out,
