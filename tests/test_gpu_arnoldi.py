@@ -64,3 +64,28 @@ def test_device_arnoldi_rejects_bad_option():
     with pytest.raises(lh.LHError) as ei:
         c.gm.newton_step(u.clone(), torch.zeros_like(u), 0.01, jvp_prec="fp32", arnoldi=2)
     assert ei.value.status == 1
+
+
+def test_device_arnoldi_rerecords_on_new_step_size_and_per_mesh():
+    """The recorded cycle depends on tau (= dt / 2): steps of changing dt re-record it, and two
+    meshes used alternately each keep their own; both must still match the host loop."""
+    ca = Case(3, (4, 4, 4), 2, seed=11, vscale=1.0)
+    cb = Case(2, (8, 6), 2, seed=12, vscale=1.0)
+    kw = dict(newton_rtol=1e-10, gmres_rtol=1e-6, gmres_maxit=300, restart=30, jvp_prec="fp32")
+    dts = (0.01, 0.007, 0.013, 0.007)
+
+    def run(arnoldi):
+        ua, ka = ca.dev(ca.u), torch.zeros(ca.u.size, dtype=torch.float64, device="cuda")
+        ub, kb = cb.dev(cb.u), torch.zeros(cb.u.size, dtype=torch.float64, device="cuda")
+        its = []
+        for dt in dts:
+            sa = ca.gm.newton_step(ua, ka, dt, arnoldi=arnoldi, **kw)
+            sb = cb.gm.newton_step(ub, kb, 0.5 * dt, arnoldi=arnoldi, **kw)
+            its.append((sa["gmres_its_total"], sb["gmres_its_total"]))
+        return ua.cpu().numpy(), ub.cpu().numpy(), its
+
+    a0, b0, i0 = run(0)
+    a1, b1, i1 = run(1)
+    assert i0 == i1, (i0, i1)
+    assert np.linalg.norm(a1 - a0) <= 1e-10 * np.linalg.norm(a0)
+    assert np.linalg.norm(b1 - b0) <= 1e-10 * np.linalg.norm(b0)
