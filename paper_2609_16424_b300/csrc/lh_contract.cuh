@@ -349,442 +349,619 @@ struct NeedBMax<DIM, K, 0> {
 // Line form (see the header).
 namespace ln {
 
-// values (if VAL; 3D only skips them) and reference gradients of NC H1 fields at this
-// thread's quadrature point.  B, G: the tables in shared memory (this thread's row).
+// The line form's stages, one function per stage (no barriers inside); the entry points
+// below put __syncthreads() between them, and the fused entry points run the H1 and L2
+// stages of one direction in the same barrier phase (disjoint scratch).
+
+// ---- forward, NC H1 fields: values (if VAL) and reference gradients at this point
+template <int DIM, int K, int NC, class T>
+struct H1F {
+  static constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  // a0 -> q0, one thread per line (c, a2, a1) [3D] or (c, a1) [2D]
+  static __device__ __forceinline__ void s1(const T* __restrict__ in, T* t1, int lt) {
+    if constexpr (DIM == 3) {
+      constexpr int NQ = Q * Q * Q;
+      using LY = F3<D, NC, Q>;
+      constexpr int N1 = LY::N1, P1 = LY::P1, T1P = Q * P1;
+      for (int r = lt; r < NM * D; r += NQ) {
+        T u[D];
+#pragma unroll
+        for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
+        const int o = (r / D) * N1 + r % D;
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) {
+          T sb = 0, sg = 0;
+#pragma unroll
+          for (int a0 = 0; a0 < D; ++a0) {
+            sb += cB<T, K>(q0, a0) * u[a0];
+            sg += cG<T, K>(q0, a0) * u[a0];
+          }
+          t1[q0 * P1 + o] = sb;
+          t1[T1P + q0 * P1 + o] = sg;
+        }
+      }
+    } else {
+      constexpr int NQ = Q * Q, R = F2<D, NC, Q>::R, T1P = Q * R;
+      for (int r = lt; r < NM; r += NQ) {
+        T u[D];
+#pragma unroll
+        for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) {
+          T sb = 0, sg = 0;
+#pragma unroll
+          for (int a0 = 0; a0 < D; ++a0) {
+            sb += cB<T, K>(q0, a0) * u[a0];
+            sg += cG<T, K>(q0, a0) * u[a0];
+          }
+          t1[q0 * R + r] = sb;
+          t1[T1P + q0 * R + r] = sg;
+        }
+      }
+    }
+  }
+  // a1 -> q1 (3D only), one thread per line (q0, c, a2)
+  static __device__ __forceinline__ void s2(const T* t1, T* t2, int lt) {
+    if constexpr (DIM == 3) {
+      constexpr int NQ = Q * Q * Q;
+      using LY = F3<D, NC, Q>;
+      constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS, T1P = Q * P1, T2P = Q * Q * MS;
+      for (int n = lt; n < Q * NM; n += NQ) {
+        const int q0 = n / NM, m = n % NM;
+        T xb[D], xg[D];
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1) {
+          xb[a1] = t1[q0 * P1 + m * N1 + a1];
+          xg[a1] = t1[T1P + q0 * P1 + m * N1 + a1];
+        }
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) {
+          T bb = 0, bg = 0, gb = 0;
+#pragma unroll
+          for (int a1 = 0; a1 < D; ++a1) {
+            const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
+            bb += b * xb[a1];
+            bg += g * xb[a1];
+            gb += b * xg[a1];
+          }
+          const int o = (q1 * Q + q0) * MS + m;
+          t2[o] = bb;
+          t2[T2P + o] = bg;
+          t2[2 * T2P + o] = gb;
+        }
+      }
+    }
+  }
+  // the last direction at this thread's point (src: t2 in 3D, t1 in 2D); B, G: the tables in
+  // shared memory (this thread's row)
+  template <bool VAL>
+  static __device__ __forceinline__ void s3(const T* src, const T* B, const T* G, int lt, T (&val)[NC],
+                                            T (&grad)[NC][DIM]) {
+    if constexpr (DIM == 3) {
+      using LY = F3<D, NC, Q>;
+      constexpr int MS = LY::MS, T2P = Q * Q * MS;
+      const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+      T b2[D], g2[D];
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        b2[a2] = B[q2 * D + a2];
+        g2[a2] = G[q2 * D + a2];
+      }
+      const int pb = (q1 * Q + q0) * MS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T v = 0, dx = 0, dy = 0, dz = 0;
+#pragma unroll
+        for (int a2 = 0; a2 < D; ++a2) {
+          const int o = pb + c * D + a2;
+          if constexpr (VAL) v += b2[a2] * src[o];
+          dy += b2[a2] * src[T2P + o];
+          dx += b2[a2] * src[2 * T2P + o];
+          dz += g2[a2] * src[o];
+        }
+        val[c] = v;
+        grad[c][0] = dx;
+        grad[c][1] = dy;
+        grad[c][2] = dz;
+      }
+    } else {
+      constexpr int R = F2<D, NC, Q>::R, T1P = Q * R;
+      const int q0 = lt % Q, q1 = lt / Q;
+      T b1[D], g1[D];
+#pragma unroll
+      for (int a1 = 0; a1 < D; ++a1) {
+        b1[a1] = B[q1 * D + a1];
+        g1[a1] = G[q1 * D + a1];
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T v = 0, dx = 0, dy = 0;
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1) {
+          const int o = q0 * R + c * D + a1;
+          v += b1[a1] * src[o];
+          dx += b1[a1] * src[T1P + o];
+          dy += g1[a1] * src[o];
+        }
+        val[c] = v;
+        grad[c][0] = dx;
+        grad[c][1] = dy;
+      }
+    }
+  }
+};
+
+// ---- forward, NC fields with L 1D dofs: values at this point (table cL<T, K, L>)
+template <int DIM, int K, int NC, class T, int L>
+struct L2F {
+  static constexpr int Q = 2 * K, NM = NC * L;
+  static __device__ __forceinline__ void s1(const T* __restrict__ in, T* t1, int lt) {
+    if constexpr (DIM == 3) {
+      constexpr int NQ = Q * Q * Q;
+      using LY = F3<L, NC, Q>;
+      constexpr int N1 = LY::N1, P1 = LY::P1;
+      for (int r = lt; r < NM * L; r += NQ) {            // j0 -> q0, line (c, j2, j1)
+        T u[L];
+#pragma unroll
+        for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
+        const int o = (r / L) * N1 + r % L;
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) {
+          T s = 0;
+#pragma unroll
+          for (int j0 = 0; j0 < L; ++j0) s += cL<T, K, L>(q0, j0) * u[j0];
+          t1[q0 * P1 + o] = s;
+        }
+      }
+    } else {
+      constexpr int NQ = Q * Q, R = F2<L, NC, Q>::R;
+      for (int r = lt; r < NM; r += NQ) {                // j0 -> q0, line (c, j1)
+        T u[L];
+#pragma unroll
+        for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) {
+          T s = 0;
+#pragma unroll
+          for (int j0 = 0; j0 < L; ++j0) s += cL<T, K, L>(q0, j0) * u[j0];
+          t1[q0 * R + r] = s;
+        }
+      }
+    }
+  }
+  static __device__ __forceinline__ void s2(const T* t1, T* t2, int lt) {
+    if constexpr (DIM == 3) {
+      constexpr int NQ = Q * Q * Q;
+      using LY = F3<L, NC, Q>;
+      constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS;
+      for (int n = lt; n < Q * NM; n += NQ) {            // j1 -> q1, line (q0, c, j2)
+        const int q0 = n / NM, m = n % NM;
+        T x[L];
+#pragma unroll
+        for (int j1 = 0; j1 < L; ++j1) x[j1] = t1[q0 * P1 + m * N1 + j1];
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) {
+          T s = 0;
+#pragma unroll
+          for (int j1 = 0; j1 < L; ++j1) s += cL<T, K, L>(q1, j1) * x[j1];
+          t2[(q1 * Q + q0) * MS + m] = s;
+        }
+      }
+    }
+  }
+  // Bl: the table in shared memory (this thread's row)
+  static __device__ __forceinline__ void s3(const T* src, const T* Bl, int lt, T (&val)[NC]) {
+    if constexpr (DIM == 3) {
+      constexpr int MS = F3<L, NC, Q>::MS;
+      const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
+      T b2[L];
+#pragma unroll
+      for (int j2 = 0; j2 < L; ++j2) b2[j2] = Bl[q2 * L + j2];
+      const int pb = (q1 * Q + q0) * MS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int j2 = 0; j2 < L; ++j2) s += b2[j2] * src[pb + c * L + j2];
+        val[c] = s;
+      }
+    } else {
+      constexpr int R = F2<L, NC, Q>::R;
+      const int q0 = lt % Q, q1 = lt / Q;
+      T b1[L];
+#pragma unroll
+      for (int j1 = 0; j1 < L; ++j1) b1[j1] = Bl[q1 * L + j1];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        T s = 0;
+#pragma unroll
+        for (int j1 = 0; j1 < L; ++j1) s += b1[j1] * src[q0 * R + c * L + j1];
+        val[c] = s;
+      }
+    }
+  }
+};
+
+// ---- backward, NC H1 fields: out[c][a] = sum_q (fval w_a + fgrad . grad w_a)
+template <int DIM, int K, int NC, class T>
+struct H1B {
+  static constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  // phase 0: the point values into sf
+  static __device__ __forceinline__ void p0(const T (&fval)[NC], const T (&fgrad)[NC][DIM], T* sf, int lt) {
+    if constexpr (DIM == 3) {
+      constexpr int NQp = B3<D, NC, Q>::NQp, SFP = NC * NQp;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        sf[c * NQp + lt] = fval[c];
+        sf[SFP + c * NQp + lt] = fgrad[c][0];
+        sf[2 * SFP + c * NQp + lt] = fgrad[c][1];
+        sf[3 * SFP + c * NQp + lt] = fgrad[c][2];
+      }
+    } else {
+      constexpr int NQp = B2<D, NC, Q>::NQp, SFP = NC * NQp;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        sf[c * NQp + lt] = fval[c];
+        sf[SFP + c * NQp + lt] = fgrad[c][0];
+        sf[2 * SFP + c * NQp + lt] = fgrad[c][1];
+      }
+    }
+  }
+  // phase 1: 3D q2 -> a2 (sf -> t2), line (c, q1, q0); 2D q1 -> a1 (sf -> t1), line (c, q0)
+  static __device__ __forceinline__ void p1(const T* sf, T* t1, T* t2, int lt) {
+    if constexpr (DIM == 3) {
+      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      using LY = B3<D, NC, Q>;
+      constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA, SFP = NC * NQp, T2P = D * SA;
+      for (int n = lt; n < NC * QQ; n += NQ) {
+        const int c = n / QQ, p = n % QQ;
+        T f0[Q], f1[Q], f2[Q], f3[Q];
+#pragma unroll
+        for (int q2 = 0; q2 < Q; ++q2) {
+          const int o = c * NQp + q2 * QQ + p;
+          f0[q2] = sf[o];
+          f1[q2] = sf[SFP + o];
+          f2[q2] = sf[2 * SFP + o];
+          f3[q2] = sf[3 * SFP + o];
+        }
+#pragma unroll
+        for (int a2 = 0; a2 < D; ++a2) {
+          T zbb = 0, zbg = 0, zgb = 0;
+#pragma unroll
+          for (int q2 = 0; q2 < Q; ++q2) {
+            const T b = cB<T, K>(q2, a2), g = cG<T, K>(q2, a2);
+            zgb += b * f1[q2];
+            zbg += b * f2[q2];
+            zbb += b * f0[q2] + g * f3[q2];
+          }
+          const int o = a2 * SA + c * CA + p;
+          t2[o] = zbb;
+          t2[T2P + o] = zbg;
+          t2[2 * T2P + o] = zgb;
+        }
+      }
+    } else {
+      constexpr int NQ = Q * Q;
+      using LY = B2<D, NC, Q>;
+      constexpr int NQp = LY::NQp, R = LY::R, SFP = NC * NQp, T1P = Q * R;
+      for (int n = lt; n < NC * Q; n += NQ) {
+        const int c = n / Q, q0 = n % Q;
+        T f0[Q], f1[Q], f2[Q];
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) {
+          const int o = c * NQp + q1 * Q + q0;
+          f0[q1] = sf[o];
+          f1[q1] = sf[SFP + o];
+          f2[q1] = sf[2 * SFP + o];
+        }
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1) {
+          T yb = 0, yg = 0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
+            yg += b * f1[q1];
+            yb += b * f0[q1] + g * f2[q1];
+          }
+          const int o = q0 * R + c * D + a1;
+          t1[o] = yb;
+          t1[T1P + o] = yg;
+        }
+      }
+      (void)t2;
+    }
+  }
+  // phase 2: 3D q1 -> a1 (t2 -> t1), line (c, a2, q0); 2D q0 -> a0 (t1 -> out), line (c, a1)
+  static __device__ __forceinline__ void p2(T* t1, const T* t2, int lt, T* out) {
+    if constexpr (DIM == 3) {
+      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      using LY = B3<D, NC, Q>;
+      constexpr int CA = LY::CA, SA = LY::SA, RB = LY::RB, T2P = D * SA, T1P = Q * RB;
+      for (int n = lt; n < NM * Q; n += NQ) {
+        const int q0 = n % Q, m = n / Q, c = m / D, a2 = m % D;
+        T zb[Q], zbg[Q], zgb[Q];
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) {
+          const int o = a2 * SA + c * CA + q1 * Q + q0;
+          zb[q1] = t2[o];
+          zbg[q1] = t2[T2P + o];
+          zgb[q1] = t2[2 * T2P + o];
+        }
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1) {
+          T yb = 0, yg = 0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) {
+            const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
+            yg += b * zgb[q1];
+            yb += g * zbg[q1] + b * zb[q1];
+          }
+          const int o = q0 * RB + m * D + a1;
+          t1[o] = yb;
+          t1[T1P + o] = yg;
+        }
+      }
+      (void)out;
+    } else {
+      constexpr int NQ = Q * Q;
+      using LY = B2<D, NC, Q>;
+      constexpr int R = LY::R, T1P = Q * R;
+      for (int r = lt; r < NM; r += NQ) {
+        T yb[Q], yg[Q];
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) {
+          yb[q0] = t1[q0 * R + r];
+          yg[q0] = t1[T1P + q0 * R + r];
+        }
+#pragma unroll
+        for (int a0 = 0; a0 < D; ++a0) {
+          T s = 0;
+#pragma unroll
+          for (int q0 = 0; q0 < Q; ++q0) s += cG<T, K>(q0, a0) * yg[q0] + cB<T, K>(q0, a0) * yb[q0];
+          out[r * D + a0] = s;
+        }
+      }
+      (void)t2;
+    }
+  }
+  // phase 3 (3D only): q0 -> a0 (t1 -> out), line (c, a2, a1)
+  static __device__ __forceinline__ void p3(const T* t1, int lt, T* out) {
+    if constexpr (DIM == 3) {
+      constexpr int NQ = Q * Q * Q;
+      constexpr int RB = B3<D, NC, Q>::RB, T1P = Q * RB;
+      for (int r = lt; r < NM * D; r += NQ) {
+        T yb[Q], yg[Q];
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) {
+          yb[q0] = t1[q0 * RB + r];
+          yg[q0] = t1[T1P + q0 * RB + r];
+        }
+#pragma unroll
+        for (int a0 = 0; a0 < D; ++a0) {
+          T s = 0;
+#pragma unroll
+          for (int q0 = 0; q0 < Q; ++q0) s += cG<T, K>(q0, a0) * yg[q0] + cB<T, K>(q0, a0) * yb[q0];
+          out[r * D + a0] = s;
+        }
+      }
+    }
+  }
+};
+
+// ---- backward, NC fields with L 1D dofs: out[c][j] = sum_q fval phi_j(q)
+template <int DIM, int K, int NC, class T, int L>
+struct L2B {
+  static constexpr int Q = 2 * K, NM = NC * L;
+  static __device__ __forceinline__ void p0(const T (&fval)[NC], T* sf, int lt) {
+    constexpr int NQp = DIM == 3 ? B3<L, NC, Q>::NQp : B2<L, NC, Q>::NQp;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) sf[c * NQp + lt] = fval[c];
+  }
+  static __device__ __forceinline__ void p1(const T* sf, T* t1, T* t2, int lt) {
+    if constexpr (DIM == 3) {
+      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      using LY = B3<L, NC, Q>;
+      constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA;
+      for (int n = lt; n < NC * QQ; n += NQ) {           // q2 -> j2, line (c, q1, q0)
+        const int c = n / QQ, p = n % QQ;
+        T f[Q];
+#pragma unroll
+        for (int q2 = 0; q2 < Q; ++q2) f[q2] = sf[c * NQp + q2 * QQ + p];
+#pragma unroll
+        for (int j2 = 0; j2 < L; ++j2) {
+          T s = 0;
+#pragma unroll
+          for (int q2 = 0; q2 < Q; ++q2) s += cL<T, K, L>(q2, j2) * f[q2];
+          t2[j2 * SA + c * CA + p] = s;
+        }
+      }
+      (void)t1;
+    } else {
+      constexpr int NQ = Q * Q;
+      using LY = B2<L, NC, Q>;
+      constexpr int NQp = LY::NQp, R = LY::R;
+      for (int n = lt; n < NC * Q; n += NQ) {            // q1 -> j1, line (c, q0)
+        const int c = n / Q, q0 = n % Q;
+        T f[Q];
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) f[q1] = sf[c * NQp + q1 * Q + q0];
+#pragma unroll
+        for (int j1 = 0; j1 < L; ++j1) {
+          T s = 0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) s += cL<T, K, L>(q1, j1) * f[q1];
+          t1[q0 * R + c * L + j1] = s;
+        }
+      }
+      (void)t2;
+    }
+  }
+  static __device__ __forceinline__ void p2(T* t1, const T* t2, int lt, T* out) {
+    if constexpr (DIM == 3) {
+      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      using LY = B3<L, NC, Q>;
+      constexpr int CA = LY::CA, SA = LY::SA, RB = LY::RB;
+      for (int n = lt; n < NM * Q; n += NQ) {            // q1 -> j1, line (c, j2, q0)
+        const int q0 = n % Q, m = n / Q, c = m / L, j2 = m % L;
+        T zz[Q];
+#pragma unroll
+        for (int q1 = 0; q1 < Q; ++q1) zz[q1] = t2[j2 * SA + c * CA + q1 * Q + q0];
+#pragma unroll
+        for (int j1 = 0; j1 < L; ++j1) {
+          T s = 0;
+#pragma unroll
+          for (int q1 = 0; q1 < Q; ++q1) s += cL<T, K, L>(q1, j1) * zz[q1];
+          t1[q0 * RB + m * L + j1] = s;
+        }
+      }
+      (void)out;
+    } else {
+      constexpr int NQ = Q * Q, R = B2<L, NC, Q>::R;
+      for (int r = lt; r < NM; r += NQ) {                // q0 -> j0, line (c, j1)
+        T y[Q];
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * R + r];
+#pragma unroll
+        for (int j0 = 0; j0 < L; ++j0) {
+          T s = 0;
+#pragma unroll
+          for (int q0 = 0; q0 < Q; ++q0) s += cL<T, K, L>(q0, j0) * y[q0];
+          out[r * L + j0] = s;
+        }
+      }
+      (void)t2;
+    }
+  }
+  static __device__ __forceinline__ void p3(const T* t1, int lt, T* out) {
+    if constexpr (DIM == 3) {
+      constexpr int NQ = Q * Q * Q, RB = B3<L, NC, Q>::RB;
+      for (int r = lt; r < NM * L; r += NQ) {            // q0 -> j0, line (c, j2, j1)
+        T y[Q];
+#pragma unroll
+        for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * RB + r];
+#pragma unroll
+        for (int j0 = 0; j0 < L; ++j0) {
+          T s = 0;
+#pragma unroll
+          for (int q0 = 0; q0 < Q; ++q0) s += cL<T, K, L>(q0, j0) * y[q0];
+          out[r * L + j0] = s;
+        }
+      }
+    }
+  }
+};
+
+// ---- entry points: the stages with a barrier after each phase
 template <int DIM, int K, int NC, class T, bool VAL = true>
 __device__ __forceinline__ void h1_fwd(const T* __restrict__ in, T* t1, T* t2, const T* B, const T* G,
                                        int lt, T (&val)[NC], T (&grad)[NC][DIM]) {
-  constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  using S = H1F<DIM, K, NC, T>;
+  S::s1(in, t1, lt);
+  __syncthreads();
   if constexpr (DIM == 3) {
-    constexpr int NQ = Q * Q * Q;
-    using LY = F3<D, NC, Q>;
-    constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS, T1P = Q * P1, T2P = Q * Q * MS;
-    for (int r = lt; r < NM * D; r += NQ) {            // a0 -> q0, line (c, a2, a1)
-      T u[D];
-#pragma unroll
-      for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
-      const int o = (r / D) * N1 + r % D;
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) {
-        T sb = 0, sg = 0;
-#pragma unroll
-        for (int a0 = 0; a0 < D; ++a0) {
-          sb += cB<T, K>(q0, a0) * u[a0];
-          sg += cG<T, K>(q0, a0) * u[a0];
-        }
-        t1[q0 * P1 + o] = sb;
-        t1[T1P + q0 * P1 + o] = sg;
-      }
-    }
-    __syncthreads();
-    for (int n = lt; n < Q * NM; n += NQ) {            // a1 -> q1, line (q0, c, a2)
-      const int q0 = n / NM, m = n % NM;
-      T xb[D], xg[D];
-#pragma unroll
-      for (int a1 = 0; a1 < D; ++a1) {
-        xb[a1] = t1[q0 * P1 + m * N1 + a1];
-        xg[a1] = t1[T1P + q0 * P1 + m * N1 + a1];
-      }
-#pragma unroll
-      for (int q1 = 0; q1 < Q; ++q1) {
-        T bb = 0, bg = 0, gb = 0;
-#pragma unroll
-        for (int a1 = 0; a1 < D; ++a1) {
-          const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
-          bb += b * xb[a1];
-          bg += g * xb[a1];
-          gb += b * xg[a1];
-        }
-        const int o = (q1 * Q + q0) * MS + m;
-        t2[o] = bb;
-        t2[T2P + o] = bg;
-        t2[2 * T2P + o] = gb;
-      }
-    }
-    __syncthreads();
-    const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
-    T b2[D], g2[D];
-#pragma unroll
-    for (int a2 = 0; a2 < D; ++a2) {
-      b2[a2] = B[q2 * D + a2];
-      g2[a2] = G[q2 * D + a2];
-    }
-    const int pb = (q1 * Q + q0) * MS;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {                     // a2 -> q2 at this point
-      T v = 0, dx = 0, dy = 0, dz = 0;
-#pragma unroll
-      for (int a2 = 0; a2 < D; ++a2) {
-        const int o = pb + c * D + a2;
-        if constexpr (VAL) v += b2[a2] * t2[o];
-        dy += b2[a2] * t2[T2P + o];
-        dx += b2[a2] * t2[2 * T2P + o];
-        dz += g2[a2] * t2[o];
-      }
-      val[c] = v;
-      grad[c][0] = dx;
-      grad[c][1] = dy;
-      grad[c][2] = dz;
-    }
-    __syncthreads();
-  } else {
-    constexpr int NQ = Q * Q, R = F2<D, NC, Q>::R, T1P = Q * R;
-    for (int r = lt; r < NM; r += NQ) {                // a0 -> q0, line (c, a1)
-      T u[D];
-#pragma unroll
-      for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) {
-        T sb = 0, sg = 0;
-#pragma unroll
-        for (int a0 = 0; a0 < D; ++a0) {
-          sb += cB<T, K>(q0, a0) * u[a0];
-          sg += cG<T, K>(q0, a0) * u[a0];
-        }
-        t1[q0 * R + r] = sb;
-        t1[T1P + q0 * R + r] = sg;
-      }
-    }
-    __syncthreads();
-    const int q0 = lt % Q, q1 = lt / Q;
-    T b1[D], g1[D];
-#pragma unroll
-    for (int a1 = 0; a1 < D; ++a1) {
-      b1[a1] = B[q1 * D + a1];
-      g1[a1] = G[q1 * D + a1];
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {                     // a1 -> q1 at this point
-      T v = 0, dx = 0, dy = 0;
-#pragma unroll
-      for (int a1 = 0; a1 < D; ++a1) {
-        const int o = q0 * R + c * D + a1;
-        v += b1[a1] * t1[o];
-        dx += b1[a1] * t1[T1P + o];
-        dy += g1[a1] * t1[o];
-      }
-      val[c] = v;
-      grad[c][0] = dx;
-      grad[c][1] = dy;
-    }
+    S::s2(t1, t2, lt);
     __syncthreads();
   }
+  S::template s3<VAL>(DIM == 3 ? t2 : t1, B, G, lt, val, grad);
+  __syncthreads();
 }
-
-// out[c][a] = sum_q ( fval[c] w_a(q) + sum_r fgrad[c][r] d_r w_a(q) )   (B^T and G^T)
+template <int DIM, int K, int NC, class T, int L_ = K>
+__device__ __forceinline__ void l2_fwd(const T* __restrict__ in, T* t1, T* t2, const T* Bl, int lt, T (&val)[NC]) {
+  using S = L2F<DIM, K, NC, T, L_>;
+  S::s1(in, t1, lt);
+  __syncthreads();
+  if constexpr (DIM == 3) {
+    S::s2(t1, t2, lt);
+    __syncthreads();
+  }
+  S::s3(DIM == 3 ? t2 : t1, Bl, lt, val);
+  __syncthreads();
+}
 template <int DIM, int K, int NC, class T>
 __device__ __forceinline__ void h1_bwd(const T (&fval)[NC], const T (&fgrad)[NC][DIM], T* sf, T* t1, T* t2,
                                        const T* B, const T* G, int lt, T* out) {
-  constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  using S = H1B<DIM, K, NC, T>;
   (void)B;
   (void)G;
+  S::p0(fval, fgrad, sf, lt);
+  __syncthreads();
+  S::p1(sf, t1, t2, lt);
+  __syncthreads();
+  S::p2(t1, t2, lt, out);
+  __syncthreads();
   if constexpr (DIM == 3) {
-    constexpr int QQ = Q * Q, NQ = QQ * Q;
-    using LY = B3<D, NC, Q>;
-    constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA, RB = LY::RB;
-    constexpr int SFP = NC * NQp, T2P = D * SA, T1P = Q * RB;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      sf[c * NQp + lt] = fval[c];
-      sf[SFP + c * NQp + lt] = fgrad[c][0];
-      sf[2 * SFP + c * NQp + lt] = fgrad[c][1];
-      sf[3 * SFP + c * NQp + lt] = fgrad[c][2];
-    }
-    __syncthreads();
-    for (int n = lt; n < NC * QQ; n += NQ) {           // q2 -> a2, line (c, q1, q0)
-      const int c = n / QQ, p = n % QQ;
-      T f0[Q], f1[Q], f2[Q], f3[Q];
-#pragma unroll
-      for (int q2 = 0; q2 < Q; ++q2) {
-        const int o = c * NQp + q2 * QQ + p;
-        f0[q2] = sf[o];
-        f1[q2] = sf[SFP + o];
-        f2[q2] = sf[2 * SFP + o];
-        f3[q2] = sf[3 * SFP + o];
-      }
-#pragma unroll
-      for (int a2 = 0; a2 < D; ++a2) {
-        T zbb = 0, zbg = 0, zgb = 0;
-#pragma unroll
-        for (int q2 = 0; q2 < Q; ++q2) {
-          const T b = cB<T, K>(q2, a2), g = cG<T, K>(q2, a2);
-          zgb += b * f1[q2];
-          zbg += b * f2[q2];
-          zbb += b * f0[q2] + g * f3[q2];
-        }
-        const int o = a2 * SA + c * CA + p;
-        t2[o] = zbb;
-        t2[T2P + o] = zbg;
-        t2[2 * T2P + o] = zgb;
-      }
-    }
-    __syncthreads();
-    for (int n = lt; n < NM * Q; n += NQ) {            // q1 -> a1, line (c, a2, q0)
-      const int q0 = n % Q, m = n / Q, c = m / D, a2 = m % D;
-      T zb[Q], zbg[Q], zgb[Q];
-#pragma unroll
-      for (int q1 = 0; q1 < Q; ++q1) {
-        const int o = a2 * SA + c * CA + q1 * Q + q0;
-        zb[q1] = t2[o];
-        zbg[q1] = t2[T2P + o];
-        zgb[q1] = t2[2 * T2P + o];
-      }
-#pragma unroll
-      for (int a1 = 0; a1 < D; ++a1) {
-        T yb = 0, yg = 0;
-#pragma unroll
-        for (int q1 = 0; q1 < Q; ++q1) {
-          const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
-          yg += b * zgb[q1];
-          yb += g * zbg[q1] + b * zb[q1];
-        }
-        const int o = q0 * RB + m * D + a1;
-        t1[o] = yb;
-        t1[T1P + o] = yg;
-      }
-    }
-    __syncthreads();
-    for (int r = lt; r < NM * D; r += NQ) {            // q0 -> a0, line (c, a2, a1)
-      T yb[Q], yg[Q];
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) {
-        yb[q0] = t1[q0 * RB + r];
-        yg[q0] = t1[T1P + q0 * RB + r];
-      }
-#pragma unroll
-      for (int a0 = 0; a0 < D; ++a0) {
-        T s = 0;
-#pragma unroll
-        for (int q0 = 0; q0 < Q; ++q0) s += cG<T, K>(q0, a0) * yg[q0] + cB<T, K>(q0, a0) * yb[q0];
-        out[r * D + a0] = s;
-      }
-    }
-    __syncthreads();
-  } else {
-    constexpr int NQ = Q * Q;
-    using LY = B2<D, NC, Q>;
-    constexpr int NQp = LY::NQp, R = LY::R, SFP = NC * NQp, T1P = Q * R;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      sf[c * NQp + lt] = fval[c];
-      sf[SFP + c * NQp + lt] = fgrad[c][0];
-      sf[2 * SFP + c * NQp + lt] = fgrad[c][1];
-    }
-    __syncthreads();
-    for (int n = lt; n < NC * Q; n += NQ) {            // q1 -> a1, line (c, q0)
-      const int c = n / Q, q0 = n % Q;
-      T f0[Q], f1[Q], f2[Q];
-#pragma unroll
-      for (int q1 = 0; q1 < Q; ++q1) {
-        const int o = c * NQp + q1 * Q + q0;
-        f0[q1] = sf[o];
-        f1[q1] = sf[SFP + o];
-        f2[q1] = sf[2 * SFP + o];
-      }
-#pragma unroll
-      for (int a1 = 0; a1 < D; ++a1) {
-        T yb = 0, yg = 0;
-#pragma unroll
-        for (int q1 = 0; q1 < Q; ++q1) {
-          const T b = cB<T, K>(q1, a1), g = cG<T, K>(q1, a1);
-          yg += b * f1[q1];
-          yb += b * f0[q1] + g * f2[q1];
-        }
-        const int o = q0 * R + c * D + a1;
-        t1[o] = yb;
-        t1[T1P + o] = yg;
-      }
-    }
-    __syncthreads();
-    for (int r = lt; r < NM; r += NQ) {                // q0 -> a0, line (c, a1)
-      T yb[Q], yg[Q];
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) {
-        yb[q0] = t1[q0 * R + r];
-        yg[q0] = t1[T1P + q0 * R + r];
-      }
-#pragma unroll
-      for (int a0 = 0; a0 < D; ++a0) {
-        T s = 0;
-#pragma unroll
-        for (int q0 = 0; q0 < Q; ++q0) s += cG<T, K>(q0, a0) * yg[q0] + cB<T, K>(q0, a0) * yb[q0];
-        out[r * D + a0] = s;
-      }
-    }
+    S::p3(t1, lt, out);
     __syncthreads();
   }
 }
-
-// values of NC fields with L_ 1D dofs (default: the L2 basis, L_ = K) at this thread's
-// quadrature point; with L_ = K + 1 and the H1 table it interpolates H1 values only.
-// Bl: that table in shared memory (this thread's row).
-template <int DIM, int K, int NC, class T, int L_ = K>
-__device__ __forceinline__ void l2_fwd(const T* __restrict__ in, T* t1, T* t2, const T* Bl, int lt, T (&val)[NC]) {
-  constexpr int L = L_, Q = 2 * K, NM = NC * L;
-  if constexpr (DIM == 3) {
-    constexpr int NQ = Q * Q * Q;
-    using LY = F3<L, NC, Q>;
-    constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS;
-    for (int r = lt; r < NM * L; r += NQ) {            // j0 -> q0, line (c, j2, j1)
-      T u[L];
-#pragma unroll
-      for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
-      const int o = (r / L) * N1 + r % L;
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) {
-        T s = 0;
-#pragma unroll
-        for (int j0 = 0; j0 < L; ++j0) s += cL<T, K, L>(q0, j0) * u[j0];
-        t1[q0 * P1 + o] = s;
-      }
-    }
-    __syncthreads();
-    for (int n = lt; n < Q * NM; n += NQ) {            // j1 -> q1, line (q0, c, j2)
-      const int q0 = n / NM, m = n % NM;
-      T x[L];
-#pragma unroll
-      for (int j1 = 0; j1 < L; ++j1) x[j1] = t1[q0 * P1 + m * N1 + j1];
-#pragma unroll
-      for (int q1 = 0; q1 < Q; ++q1) {
-        T s = 0;
-#pragma unroll
-        for (int j1 = 0; j1 < L; ++j1) s += cL<T, K, L>(q1, j1) * x[j1];
-        t2[(q1 * Q + q0) * MS + m] = s;
-      }
-    }
-    __syncthreads();
-    const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
-    T b2[L];
-#pragma unroll
-    for (int j2 = 0; j2 < L; ++j2) b2[j2] = Bl[q2 * L + j2];
-    const int pb = (q1 * Q + q0) * MS;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {                     // j2 -> q2 at this point
-      T s = 0;
-#pragma unroll
-      for (int j2 = 0; j2 < L; ++j2) s += b2[j2] * t2[pb + c * L + j2];
-      val[c] = s;
-    }
-    __syncthreads();
-  } else {
-    constexpr int NQ = Q * Q, R = F2<L, NC, Q>::R;
-    for (int r = lt; r < NM; r += NQ) {                // j0 -> q0, line (c, j1)
-      T u[L];
-#pragma unroll
-      for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) {
-        T s = 0;
-#pragma unroll
-        for (int j0 = 0; j0 < L; ++j0) s += cL<T, K, L>(q0, j0) * u[j0];
-        t1[q0 * R + r] = s;
-      }
-    }
-    __syncthreads();
-    const int q0 = lt % Q, q1 = lt / Q;
-    T b1[L];
-#pragma unroll
-    for (int j1 = 0; j1 < L; ++j1) b1[j1] = Bl[q1 * L + j1];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {                     // j1 -> q1 at this point
-      T s = 0;
-#pragma unroll
-      for (int j1 = 0; j1 < L; ++j1) s += b1[j1] * t1[q0 * R + c * L + j1];
-      val[c] = s;
-    }
-    __syncthreads();
-  }
-}
-
-// out[c][j] = sum_q fval[c] phi_j(q)  (L_ as in l2_fwd)
 template <int DIM, int K, int NC, class T, int L_ = K>
 __device__ __forceinline__ void l2_bwd(const T (&fval)[NC], T* sf, T* t1, T* t2, const T* Bl, int lt, T* out) {
-  constexpr int L = L_, Q = 2 * K, NM = NC * L;
+  using S = L2B<DIM, K, NC, T, L_>;
   (void)Bl;
+  S::p0(fval, sf, lt);
+  __syncthreads();
+  S::p1(sf, t1, t2, lt);
+  __syncthreads();
+  S::p2(t1, t2, lt, out);
+  __syncthreads();
   if constexpr (DIM == 3) {
-    constexpr int QQ = Q * Q, NQ = QQ * Q;
-    using LY = B3<L, NC, Q>;
-    constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA, RB = LY::RB;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) sf[c * NQp + lt] = fval[c];
-    __syncthreads();
-    for (int n = lt; n < NC * QQ; n += NQ) {           // q2 -> j2, line (c, q1, q0)
-      const int c = n / QQ, p = n % QQ;
-      T f[Q];
-#pragma unroll
-      for (int q2 = 0; q2 < Q; ++q2) f[q2] = sf[c * NQp + q2 * QQ + p];
-#pragma unroll
-      for (int j2 = 0; j2 < L; ++j2) {
-        T s = 0;
-#pragma unroll
-        for (int q2 = 0; q2 < Q; ++q2) s += cL<T, K, L>(q2, j2) * f[q2];
-        t2[j2 * SA + c * CA + p] = s;
-      }
-    }
-    __syncthreads();
-    for (int n = lt; n < NM * Q; n += NQ) {            // q1 -> j1, line (c, j2, q0)
-      const int q0 = n % Q, m = n / Q, c = m / L, j2 = m % L;
-      T z[Q];
-#pragma unroll
-      for (int q1 = 0; q1 < Q; ++q1) z[q1] = t2[j2 * SA + c * CA + q1 * Q + q0];
-#pragma unroll
-      for (int j1 = 0; j1 < L; ++j1) {
-        T s = 0;
-#pragma unroll
-        for (int q1 = 0; q1 < Q; ++q1) s += cL<T, K, L>(q1, j1) * z[q1];
-        t1[q0 * RB + m * L + j1] = s;
-      }
-    }
-    __syncthreads();
-    for (int r = lt; r < NM * L; r += NQ) {            // q0 -> j0, line (c, j2, j1)
-      T y[Q];
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * RB + r];
-#pragma unroll
-      for (int j0 = 0; j0 < L; ++j0) {
-        T s = 0;
-#pragma unroll
-        for (int q0 = 0; q0 < Q; ++q0) s += cL<T, K, L>(q0, j0) * y[q0];
-        out[r * L + j0] = s;
-      }
-    }
-    __syncthreads();
-  } else {
-    constexpr int NQ = Q * Q;
-    using LY = B2<L, NC, Q>;
-    constexpr int NQp = LY::NQp, R = LY::R;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) sf[c * NQp + lt] = fval[c];
-    __syncthreads();
-    for (int n = lt; n < NC * Q; n += NQ) {            // q1 -> j1, line (c, q0)
-      const int c = n / Q, q0 = n % Q;
-      T f[Q];
-#pragma unroll
-      for (int q1 = 0; q1 < Q; ++q1) f[q1] = sf[c * NQp + q1 * Q + q0];
-#pragma unroll
-      for (int j1 = 0; j1 < L; ++j1) {
-        T s = 0;
-#pragma unroll
-        for (int q1 = 0; q1 < Q; ++q1) s += cL<T, K, L>(q1, j1) * f[q1];
-        t1[q0 * R + c * L + j1] = s;
-      }
-    }
-    __syncthreads();
-    for (int r = lt; r < NM; r += NQ) {                // q0 -> j0, line (c, j1)
-      T y[Q];
-#pragma unroll
-      for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * R + r];
-#pragma unroll
-      for (int j0 = 0; j0 < L; ++j0) {
-        T s = 0;
-#pragma unroll
-        for (int q0 = 0; q0 < Q; ++q0) s += cL<T, K, L>(q0, j0) * y[q0];
-        out[r * L + j0] = s;
-      }
-    }
+    S::p3(t1, lt, out);
     __syncthreads();
   }
 }
+
+// H1 and L2 fields together, each phase of both under one barrier; the L2 stages use their
+// own scratch (u1, u2, sfl: L2Scratch sizes)
+template <int DIM, int K, int NC, int NCL, class T, bool VAL = true>
+__device__ __forceinline__ void h1l2_fwd(const T* __restrict__ in, const T* __restrict__ inl, T* t1, T* t2, T* u1,
+                                         T* u2, const T* B, const T* G, const T* Bl, int lt, T (&val)[NC],
+                                         T (&grad)[NC][DIM], T (&lval)[NCL]) {
+  using S = H1F<DIM, K, NC, T>;
+  using SL = L2F<DIM, K, NCL, T, K>;
+  S::s1(in, t1, lt);
+  SL::s1(inl, u1, lt);
+  __syncthreads();
+  if constexpr (DIM == 3) {
+    S::s2(t1, t2, lt);
+    SL::s2(u1, u2, lt);
+    __syncthreads();
+  }
+  S::template s3<VAL>(DIM == 3 ? t2 : t1, B, G, lt, val, grad);
+  SL::s3(DIM == 3 ? u2 : u1, Bl, lt, lval);
+  __syncthreads();
+}
+template <int DIM, int K, int NC, int NCL, class T>
+__device__ __forceinline__ void h1l2_bwd(const T (&fval)[NC], const T (&fgrad)[NC][DIM], const T (&lval)[NCL],
+                                         T* sf, T* t1, T* t2, T* sfl, T* u1, T* u2, int lt, T* out, T* outl) {
+  using S = H1B<DIM, K, NC, T>;
+  using SL = L2B<DIM, K, NCL, T, K>;
+  S::p0(fval, fgrad, sf, lt);
+  SL::p0(lval, sfl, lt);
+  __syncthreads();
+  S::p1(sf, t1, t2, lt);
+  SL::p1(sfl, u1, u2, lt);
+  __syncthreads();
+  S::p2(t1, t2, lt, out);
+  SL::p2(u1, u2, lt, outl);
+  __syncthreads();
+  if constexpr (DIM == 3) {
+    S::p3(t1, lt, out);
+    SL::p3(u1, lt, outl);
+    __syncthreads();
+  }
+}
+
+// L2 scratch of the fused entry points (entries of T): forward t1, t2 and backward sf, t1, t2
+// for NCL fields with K 1D dofs
+template <int DIM, int K, int NCL>
+struct L2Scratch {
+  static constexpr int Q = 2 * K;
+  static constexpr int U1 = DIM == 3 ? lay::imax(Q * F3<K, NCL, Q>::P1, Q * B3<K, NCL, Q>::RB)
+                                     : lay::imax(Q * F2<K, NCL, Q>::R, Q * B2<K, NCL, Q>::R);
+  static constexpr int U2 = DIM == 3 ? lay::imax(Q * Q * F3<K, NCL, Q>::MS, K * B3<K, NCL, Q>::SA) : 1;
+  static constexpr int SF = NCL * (DIM == 3 ? B3<K, NCL, Q>::NQp : B2<K, NCL, Q>::NQp);
+  static constexpr int ALL = U1 + U2 + SF;
+};
 
 }  // namespace ln
 

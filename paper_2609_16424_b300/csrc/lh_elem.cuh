@@ -16,7 +16,7 @@ namespace lh {
 // read as values only, NCL L2 fields) and the contraction scratch.  The kernel's forward
 // contractions take at most max(NCH, NCV, NCL) fields and its backward ones at most
 // max(NCO, 1); the scratch holds the largest need over those counts.
-template <int DIM, int K, int NCH, int NCV, int NCL, int NCO>
+template <int DIM, int K, int NCH, int NCV, int NCL, int NCO, int XL = 0>
 struct Plan {
   using C = Cfg<DIM, K>;
   static constexpr int NCF = lay::imax(lay::imax(NCH, NCV), lay::imax(NCL, 1)), NCB = lay::imax(NCO, 1);
@@ -26,7 +26,7 @@ struct Plan {
   static constexpr int T1 = lay::imax(NF::T1, NB::T1);
   static constexpr int T2 = lay::imax(NF::T2, NB::T2);
   static constexpr int SF = NB::SF;
-  static constexpr int PER = IN + T1 + T2 + SF;
+  static constexpr int PER = IN + T1 + T2 + SF + XL;   // XL: extra scratch of a fused kernel
   static constexpr int HEAD = ((Tab<K>::SMEM + C::THREADS + 1) / 2) * 2;   // tables + reduction
   static constexpr size_t bytes(size_t szT) { return szT * (size_t)(HEAD + C::EPB * PER); }
 };

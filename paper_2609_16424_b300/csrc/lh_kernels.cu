@@ -298,7 +298,8 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
   constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q;
   constexpr int NCH = 2 * DIM;   // dk_x, dk_v
   constexpr int NR = lin_len<DIM>();
-  using PL = Plan<DIM, K, NCH, 0, 1, DIM>;
+  using L2S = ln::L2Scratch<DIM, K, 1>;   // the L2 stages share the H1 stages' barriers
+  using PL = Plan<DIM, K, NCH, 0, 1, DIM, L2S::ALL>;
   using TB = Tab<K>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* smem = reinterpret_cast<float*>(smem_raw);
@@ -313,6 +314,9 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
   float* t1 = s_l + NL;
   float* t2 = t1 + PL::T1;
   float* sf = t2 + PL::T2;
+  float* u1 = sf + PL::SF;
+  float* u2 = u1 + L2S::U1;
+  float* sfl = u2 + L2S::U2;
   const ElemIdx E = elem_index<DIM, K>(P);
   for (int i = lt; i < NCH * ND; i += NQ) {
     const int comp = i / ND, a = i % ND;
@@ -329,9 +333,8 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
   }
   __syncthreads();
   float hv[NCH], hg[NCH][DIM];
-  h1_fwd<DIM, K, NCH, float, true>(s_h, t1, t2, sB, sG, lt, hv, hg);
   float lq[1];
-  l2_fwd<DIM, K, 1>(s_l, t1, t2, sBl, lt, lq);
+  ln::h1l2_fwd<DIM, K, NCH, 1, float, true>(s_h, s_l, t1, t2, u1, u2, sB, sG, sBl, lt, hv, hg, lq);
   float mq;
   {
     const int q0 = lt % Q, q1 = (lt / Q) % Q, q2 = lt / (Q * Q);
@@ -359,13 +362,12 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
       g -= dW * Lr[O + LF_TGS] + Lr[O + LF_W] * (Lr[O + LF_TGX] * tau * hv[0] + Lr[O + LF_TGY] * tau * hv[1]);
     }
   }
-  h1_bwd<DIM, K, DIM>(fval, fgrad, sf, t1, t2, sB, sG, lt, s_h);
-  if (E.valid)
-    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
   float gv[1] = {g};
-  l2_bwd<DIM, K, 1>(gv, sf, t1, t2, sBl, lt, s_l);
-  if (E.valid)
+  ln::h1l2_bwd<DIM, K, DIM, 1, float>(fval, fgrad, gv, sf, t1, t2, sfl, u1, u2, lt, s_h, s_l);
+  if (E.valid) {
+    for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
     for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = TO(s_l[i]);
+  }
 }
 
 // =====================================================================================
@@ -943,7 +945,7 @@ struct Launch {
   template <class TO>
   static cudaError_t jvp_rec(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
                              float* ev, TO* out, cudaEvent_t* ev2) {
-    using PL = Plan<DIM, K, 2 * DIM, 0, 1, DIM>;
+    using PL = Plan<DIM, K, 2 * DIM, 0, 1, DIM, ln::L2Scratch<DIM, K, 1>::ALL>;
     const size_t by = PL::bytes(sizeof(float));
     cudaError_t e = prep<k_jvp_rec<DIM, K, TO>>(by);
     if (e != cudaSuccess) return e;
