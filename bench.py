@@ -592,7 +592,9 @@ def run_ours(args, rank, world, device):
         rate, reps_c, t_c, _ = oracle_residual_rate(u_np, k_np, tau)
         out["cpu_baseline"] = {"value": round(rate, 6), "unit": "GDoF/s", "cores": 1, "kind": "oracle",
                                "sample": f"oracle residual on the full bench state ({W['name']}, n={n}), "
-                                         f"{reps_c} evaluations, {t_c:.2f} s each, 1 thread"}
+                                         f"{reps_c} evaluations, {t_c:.2f} s each, 1 thread",
+                               "jvp_fd_value": round(rate / 2, 6),
+                               "jvp_fd_note": "directional finite-difference J.w = two oracle residuals"}
         if not args.headline_only:
             ra, procs, cores, reps_a, t_a = oracle_all_cores(u_np, k_np, tau)
             out["cpu_baseline_all_cores"] = {
@@ -600,6 +602,31 @@ def run_ours(args, rank, world, device):
                 "sample": f"{procs} single-threaded oracle processes, each evaluating the residual of the full "
                           f"bench state; {reps_a} evaluations in {t_a:.1f} s"}
     return out
+
+
+def run_cpu_config5(args):
+    """The oracle's residual (and its two-residual finite-difference J.w) on the 48^3 Q2-Q1
+    seeded perturbed state, one thread: one evaluation after the set-up (about a minute of
+    host time, hence not part of the default run)."""
+    import numpy as np
+    import lh_synth
+    from oracle.fem import Mesh as OMesh
+    from oracle.hydro import Hydro, Params
+    from oracle import problems
+    with one_thread():
+        t0 = time.perf_counter()
+        om = OMesh((48, 48, 48), (0.0,) * 3, (1.0,) * 3, 2)
+        hyd = Hydro(om, Params(om, gamma=1.4, visc=True))
+        u = problems.perturbed_state(hyd, lh_synth.perturbed_draws((48, 48, 48), 2, 102))
+        k = np.zeros_like(u)
+        t_setup = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        hyd.residual(u, k, 1e-4)
+        t = time.perf_counter() - t1
+    n = om.n_unknowns
+    return {"metric": "oracle residual at 48^3 Q2-Q1 (config 5, k = 2), one thread", "value": round(n / t / 1e9, 6),
+            "unit": "GDoF/s", "seconds_per_residual": round(t, 2), "setup_s": round(t_setup, 1), "n_unknowns": n,
+            "jvp_fd_value": round(n / (2 * t) / 1e9, 6), "cores": 1, "kind": "oracle"}
 
 
 def tg_fp64_steps():
@@ -1187,6 +1214,7 @@ def main():
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the 48^3, interface and Taylor-Green extras and the all-cores oracle")
     ap.add_argument("--sweep", action="store_true", help="48^3 order sweep of the element kernels")
+    ap.add_argument("--cpu-config5", action="store_true", help="the oracle residual at 48^3 Q2-Q1, one thread")
     ap.add_argument("--orders", type=int, nargs="+", default=[1, 2, 3, 4])
     ap.add_argument("--mlp", action="store_true", help="learned initial guess vs extrapolation")
     ap.add_argument("--mlp-steps", type=int, default=14)
@@ -1218,7 +1246,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.sweep:
+    if args.cpu_config5:
+        out = run_cpu_config5(args)
+    elif args.sweep:
         out = run_sweep(args)
     elif args.mlp:
         out = run_mlp(args)
