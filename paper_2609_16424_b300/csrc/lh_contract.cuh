@@ -11,11 +11,15 @@
 //    forward stage runs per quadrature point, with this thread's table row taken from
 //    shared memory once.  The intermediate layouts are padded so that the lanes of a warp
 //    fall into distinct banks (the padding is chosen at compile time by counting banks for
-//    the first warp).
+//    the first warp).  The line stages take the element's thread count as a stride (NT:
+//    one thread per point, or half of that when each thread holds two points); with two
+//    points per thread the per-point stages (s3x2, p0x2) work on the pair (q0, q1, q2),
+//    (q0 + 1, q1, q2) in paired FP32 operations.
 //  * output-parallel form (FP64 and double-float, bound by arithmetic): the threads of an
 //    element stride over the outputs of each stage, which keeps every lane busy (the line
 //    counts are not multiples of the warp width).
-// Every function ends with __syncthreads() so the caller may reuse the scratch at once.
+// Every entry point ends with a barrier so the caller may reuse the scratch at once; the
+// stage functions themselves have none.
 // In both forms each output is the same sum, in the same order, as the plain definition
 // out = sum_a table(q, a) in(a) along each direction, so they give identical results.
 //
@@ -29,6 +33,7 @@
 #include <mutex>
 #include <vector>
 #include "lh_common.cuh"
+#include "lh_f2.cuh"
 #include "lh_internal.h"
 
 namespace lh {
@@ -354,16 +359,19 @@ namespace ln {
 // stages of one direction in the same barrier phase (disjoint scratch).
 
 // ---- forward, NC H1 fields: values (if VAL) and reference gradients at this point
-template <int DIM, int K, int NC, class T>
+template <int DIM, int K, int NC, class T, int NT = 0>
 struct H1F {
   static constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  static constexpr int NS = NT ? NT : (DIM == 3 ? Q * Q * Q : Q * Q);   // threads per element
   // a0 -> q0, one thread per line (c, a2, a1) [3D] or (c, a1) [2D]
   static __device__ __forceinline__ void s1(const T* __restrict__ in, T* t1, int lt) {
     if constexpr (DIM == 3) {
-      constexpr int NQ = Q * Q * Q;
       using LY = F3<D, NC, Q>;
       constexpr int N1 = LY::N1, P1 = LY::P1, T1P = Q * P1;
-      for (int r = lt; r < NM * D; r += NQ) {
+#pragma unroll
+      for (int it = 0; it < (NM * D + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM * D) break;
         T u[D];
 #pragma unroll
         for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
@@ -381,8 +389,11 @@ struct H1F {
         }
       }
     } else {
-      constexpr int NQ = Q * Q, R = F2<D, NC, Q>::R, T1P = Q * R;
-      for (int r = lt; r < NM; r += NQ) {
+      constexpr int R = F2<D, NC, Q>::R, T1P = Q * R;
+#pragma unroll
+      for (int it = 0; it < (NM + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM) break;
         T u[D];
 #pragma unroll
         for (int a0 = 0; a0 < D; ++a0) u[a0] = in[r * D + a0];
@@ -403,10 +414,12 @@ struct H1F {
   // a1 -> q1 (3D only), one thread per line (q0, c, a2)
   static __device__ __forceinline__ void s2(const T* t1, T* t2, int lt) {
     if constexpr (DIM == 3) {
-      constexpr int NQ = Q * Q * Q;
       using LY = F3<D, NC, Q>;
       constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS, T1P = Q * P1, T2P = Q * Q * MS;
-      for (int n = lt; n < Q * NM; n += NQ) {
+#pragma unroll
+      for (int it = 0; it < (Q * NM + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= Q * NM) break;
         const int q0 = n / NM, m = n % NM;
         T xb[D], xg[D];
 #pragma unroll
@@ -489,18 +502,98 @@ struct H1F {
       }
     }
   }
+  // Paired form of s3 (T = float): this thread's two points differ in q0 only, (q0, q1, q2)
+  // and (q0 + 1, q1, q2) with q0 = 2 (lt % (Q/2)) (pair_points); the last direction's table
+  // row is common to both, the intermediates differ.
+  template <bool VAL>
+  static __device__ __forceinline__ void s3x2(const float* src, const float* B, const float* G, int lt,
+                                              float2 (&val)[NC], float2 (&grad)[NC][DIM]) {
+    constexpr int QH = Q / 2;
+    if constexpr (DIM == 3) {
+      using LY = F3<D, NC, Q>;
+      constexpr int MS = LY::MS, T2P = Q * Q * MS;
+      const int q0 = 2 * (lt % QH), q1 = (lt / QH) % Q, q2 = lt / (QH * Q);
+      float2 b2[D], g2[D];
+#pragma unroll
+      for (int a2 = 0; a2 < D; ++a2) {
+        b2[a2] = f2s(B[q2 * D + a2]);
+        g2[a2] = f2s(G[q2 * D + a2]);
+      }
+      const int pa = (q1 * Q + q0) * MS, pb = pa + MS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float2 v = f2s(0.f), dx = v, dy = v, dz = v;
+#pragma unroll
+        for (int a2 = 0; a2 < D; ++a2) {
+          const int o = c * D + a2;
+          const float2 s0 = make_float2(src[pa + o], src[pb + o]);
+          const float2 s1 = make_float2(src[T2P + pa + o], src[T2P + pb + o]);
+          const float2 s2 = make_float2(src[2 * T2P + pa + o], src[2 * T2P + pb + o]);
+          if (a2 == 0) {
+            if constexpr (VAL) v = f2mul(b2[0], s0);
+            dy = f2mul(b2[0], s1);
+            dx = f2mul(b2[0], s2);
+            dz = f2mul(g2[0], s0);
+          } else {
+            if constexpr (VAL) v = f2fma(b2[a2], s0, v);
+            dy = f2fma(b2[a2], s1, dy);
+            dx = f2fma(b2[a2], s2, dx);
+            dz = f2fma(g2[a2], s0, dz);
+          }
+        }
+        val[c] = v;
+        grad[c][0] = dx;
+        grad[c][1] = dy;
+        grad[c][2] = dz;
+      }
+    } else {
+      constexpr int R = F2<D, NC, Q>::R, T1P = Q * R;
+      const int q0 = 2 * (lt % QH), q1 = lt / QH;
+      float2 b1[D], g1[D];
+#pragma unroll
+      for (int a1 = 0; a1 < D; ++a1) {
+        b1[a1] = f2s(B[q1 * D + a1]);
+        g1[a1] = f2s(G[q1 * D + a1]);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float2 v = f2s(0.f), dx = v, dy = v;
+#pragma unroll
+        for (int a1 = 0; a1 < D; ++a1) {
+          const int o = q0 * R + c * D + a1;
+          const float2 s0 = make_float2(src[o], src[o + R]);
+          const float2 s1 = make_float2(src[T1P + o], src[T1P + o + R]);
+          if (a1 == 0) {
+            v = f2mul(b1[0], s0);
+            dx = f2mul(b1[0], s1);
+            dy = f2mul(g1[0], s0);
+          } else {
+            v = f2fma(b1[a1], s0, v);
+            dx = f2fma(b1[a1], s1, dx);
+            dy = f2fma(g1[a1], s0, dy);
+          }
+        }
+        val[c] = v;
+        grad[c][0] = dx;
+        grad[c][1] = dy;
+      }
+    }
+  }
 };
 
 // ---- forward, NC fields with L 1D dofs: values at this point (table cL<T, K, L>)
-template <int DIM, int K, int NC, class T, int L>
+template <int DIM, int K, int NC, class T, int L, int NT = 0>
 struct L2F {
   static constexpr int Q = 2 * K, NM = NC * L;
+  static constexpr int NS = NT ? NT : (DIM == 3 ? Q * Q * Q : Q * Q);
   static __device__ __forceinline__ void s1(const T* __restrict__ in, T* t1, int lt) {
     if constexpr (DIM == 3) {
-      constexpr int NQ = Q * Q * Q;
       using LY = F3<L, NC, Q>;
       constexpr int N1 = LY::N1, P1 = LY::P1;
-      for (int r = lt; r < NM * L; r += NQ) {            // j0 -> q0, line (c, j2, j1)
+#pragma unroll
+      for (int it = 0; it < (NM * L + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM * L) break;            // j0 -> q0, line (c, j2, j1)
         T u[L];
 #pragma unroll
         for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
@@ -514,8 +607,11 @@ struct L2F {
         }
       }
     } else {
-      constexpr int NQ = Q * Q, R = F2<L, NC, Q>::R;
-      for (int r = lt; r < NM; r += NQ) {                // j0 -> q0, line (c, j1)
+      constexpr int R = F2<L, NC, Q>::R;
+#pragma unroll
+      for (int it = 0; it < (NM + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM) break;                // j0 -> q0, line (c, j1)
         T u[L];
 #pragma unroll
         for (int j0 = 0; j0 < L; ++j0) u[j0] = in[r * L + j0];
@@ -531,10 +627,12 @@ struct L2F {
   }
   static __device__ __forceinline__ void s2(const T* t1, T* t2, int lt) {
     if constexpr (DIM == 3) {
-      constexpr int NQ = Q * Q * Q;
       using LY = F3<L, NC, Q>;
       constexpr int N1 = LY::N1, P1 = LY::P1, MS = LY::MS;
-      for (int n = lt; n < Q * NM; n += NQ) {            // j1 -> q1, line (q0, c, j2)
+#pragma unroll
+      for (int it = 0; it < (Q * NM + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= Q * NM) break;            // j1 -> q1, line (q0, c, j2)
         const int q0 = n / NM, m = n % NM;
         T x[L];
 #pragma unroll
@@ -580,12 +678,46 @@ struct L2F {
       }
     }
   }
+  // paired form of s3 (the points of H1F::s3x2)
+  static __device__ __forceinline__ void s3x2(const float* src, const float* Bl, int lt, float2 (&val)[NC]) {
+    constexpr int QH = Q / 2;
+    if constexpr (DIM == 3) {
+      constexpr int MS = F3<L, NC, Q>::MS;
+      const int q0 = 2 * (lt % QH), q1 = (lt / QH) % Q, q2 = lt / (QH * Q);
+      float2 b2[L];
+#pragma unroll
+      for (int j2 = 0; j2 < L; ++j2) b2[j2] = f2s(Bl[q2 * L + j2]);
+      const int pa = (q1 * Q + q0) * MS, pb = pa + MS;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        float2 v = f2mul(b2[0], make_float2(src[pa + c * L], src[pb + c * L]));
+#pragma unroll
+        for (int j2 = 1; j2 < L; ++j2) v = f2fma(b2[j2], make_float2(src[pa + c * L + j2], src[pb + c * L + j2]), v);
+        val[c] = v;
+      }
+    } else {
+      constexpr int R = F2<L, NC, Q>::R;
+      const int q0 = 2 * (lt % QH), q1 = lt / QH;
+      float2 b1[L];
+#pragma unroll
+      for (int j1 = 0; j1 < L; ++j1) b1[j1] = f2s(Bl[q1 * L + j1]);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const int o = q0 * R + c * L;
+        float2 v = f2mul(b1[0], make_float2(src[o], src[o + R]));
+#pragma unroll
+        for (int j1 = 1; j1 < L; ++j1) v = f2fma(b1[j1], make_float2(src[o + j1], src[o + R + j1]), v);
+        val[c] = v;
+      }
+    }
+  }
 };
 
 // ---- backward, NC H1 fields: out[c][a] = sum_q (fval w_a + fgrad . grad w_a)
-template <int DIM, int K, int NC, class T>
+template <int DIM, int K, int NC, class T, int NT = 0>
 struct H1B {
   static constexpr int D = K + 1, Q = 2 * K, NM = NC * D;
+  static constexpr int NS = NT ? NT : (DIM == 3 ? Q * Q * Q : Q * Q);
   // phase 0: the point values into sf
   static __device__ __forceinline__ void p0(const T (&fval)[NC], const T (&fgrad)[NC][DIM], T* sf, int lt) {
     if constexpr (DIM == 3) {
@@ -607,13 +739,38 @@ struct H1B {
       }
     }
   }
+  // paired form of p0 (the points of H1F::s3x2, adjacent in sf: one 8-byte store per value
+  // when the row stride is even)
+  static __device__ __forceinline__ void p0x2(const float2 (&fval)[NC], const float2 (&fgrad)[NC][DIM], float* sf,
+                                              int lt) {
+    constexpr int QH = Q / 2;
+    constexpr int NQp = DIM == 3 ? B3<D, NC, Q>::NQp : B2<D, NC, Q>::NQp, SFP = NC * NQp;
+    const int p = 2 * (lt % QH) + Q * (lt / QH);
+    auto st = [&](int o, float2 v) {
+      if constexpr (NQp % 2 == 0) {
+        *reinterpret_cast<float2*>(sf + o) = v;
+      } else {
+        sf[o] = v.x;
+        sf[o + 1] = v.y;
+      }
+    };
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      st(c * NQp + p, fval[c]);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) st((d + 1) * SFP + c * NQp + p, fgrad[c][d]);
+    }
+  }
   // phase 1: 3D q2 -> a2 (sf -> t2), line (c, q1, q0); 2D q1 -> a1 (sf -> t1), line (c, q0)
   static __device__ __forceinline__ void p1(const T* sf, T* t1, T* t2, int lt) {
     if constexpr (DIM == 3) {
-      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      constexpr int QQ = Q * Q;
       using LY = B3<D, NC, Q>;
       constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA, SFP = NC * NQp, T2P = D * SA;
-      for (int n = lt; n < NC * QQ; n += NQ) {
+#pragma unroll
+      for (int it = 0; it < (NC * QQ + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= NC * QQ) break;
         const int c = n / QQ, p = n % QQ;
         T f0[Q], f1[Q], f2[Q], f3[Q];
 #pragma unroll
@@ -641,10 +798,12 @@ struct H1B {
         }
       }
     } else {
-      constexpr int NQ = Q * Q;
       using LY = B2<D, NC, Q>;
       constexpr int NQp = LY::NQp, R = LY::R, SFP = NC * NQp, T1P = Q * R;
-      for (int n = lt; n < NC * Q; n += NQ) {
+#pragma unroll
+      for (int it = 0; it < (NC * Q + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= NC * Q) break;
         const int c = n / Q, q0 = n % Q;
         T f0[Q], f1[Q], f2[Q];
 #pragma unroll
@@ -674,10 +833,13 @@ struct H1B {
   // phase 2: 3D q1 -> a1 (t2 -> t1), line (c, a2, q0); 2D q0 -> a0 (t1 -> out), line (c, a1)
   static __device__ __forceinline__ void p2(T* t1, const T* t2, int lt, T* out) {
     if constexpr (DIM == 3) {
-      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      constexpr int QQ = Q * Q;
       using LY = B3<D, NC, Q>;
       constexpr int CA = LY::CA, SA = LY::SA, RB = LY::RB, T2P = D * SA, T1P = Q * RB;
-      for (int n = lt; n < NM * Q; n += NQ) {
+#pragma unroll
+      for (int it = 0; it < (NM * Q + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= NM * Q) break;
         const int q0 = n % Q, m = n / Q, c = m / D, a2 = m % D;
         T zb[Q], zbg[Q], zgb[Q];
 #pragma unroll
@@ -703,10 +865,12 @@ struct H1B {
       }
       (void)out;
     } else {
-      constexpr int NQ = Q * Q;
       using LY = B2<D, NC, Q>;
       constexpr int R = LY::R, T1P = Q * R;
-      for (int r = lt; r < NM; r += NQ) {
+#pragma unroll
+      for (int it = 0; it < (NM + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM) break;
         T yb[Q], yg[Q];
 #pragma unroll
         for (int q0 = 0; q0 < Q; ++q0) {
@@ -727,9 +891,11 @@ struct H1B {
   // phase 3 (3D only): q0 -> a0 (t1 -> out), line (c, a2, a1)
   static __device__ __forceinline__ void p3(const T* t1, int lt, T* out) {
     if constexpr (DIM == 3) {
-      constexpr int NQ = Q * Q * Q;
       constexpr int RB = B3<D, NC, Q>::RB, T1P = Q * RB;
-      for (int r = lt; r < NM * D; r += NQ) {
+#pragma unroll
+      for (int it = 0; it < (NM * D + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM * D) break;
         T yb[Q], yg[Q];
 #pragma unroll
         for (int q0 = 0; q0 < Q; ++q0) {
@@ -749,20 +915,38 @@ struct H1B {
 };
 
 // ---- backward, NC fields with L 1D dofs: out[c][j] = sum_q fval phi_j(q)
-template <int DIM, int K, int NC, class T, int L>
+template <int DIM, int K, int NC, class T, int L, int NT = 0>
 struct L2B {
   static constexpr int Q = 2 * K, NM = NC * L;
+  static constexpr int NS = NT ? NT : (DIM == 3 ? Q * Q * Q : Q * Q);
   static __device__ __forceinline__ void p0(const T (&fval)[NC], T* sf, int lt) {
     constexpr int NQp = DIM == 3 ? B3<L, NC, Q>::NQp : B2<L, NC, Q>::NQp;
 #pragma unroll
     for (int c = 0; c < NC; ++c) sf[c * NQp + lt] = fval[c];
   }
+  static __device__ __forceinline__ void p0x2(const float2 (&fval)[NC], float* sf, int lt) {
+    constexpr int QH = Q / 2;
+    constexpr int NQp = DIM == 3 ? B3<L, NC, Q>::NQp : B2<L, NC, Q>::NQp;
+    const int p = 2 * (lt % QH) + Q * (lt / QH);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if constexpr (NQp % 2 == 0) {
+        *reinterpret_cast<float2*>(sf + c * NQp + p) = fval[c];
+      } else {
+        sf[c * NQp + p] = fval[c].x;
+        sf[c * NQp + p + 1] = fval[c].y;
+      }
+    }
+  }
   static __device__ __forceinline__ void p1(const T* sf, T* t1, T* t2, int lt) {
     if constexpr (DIM == 3) {
-      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      constexpr int QQ = Q * Q;
       using LY = B3<L, NC, Q>;
       constexpr int NQp = LY::NQp, CA = LY::CA, SA = LY::SA;
-      for (int n = lt; n < NC * QQ; n += NQ) {           // q2 -> j2, line (c, q1, q0)
+#pragma unroll
+      for (int it = 0; it < (NC * QQ + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= NC * QQ) break;           // q2 -> j2, line (c, q1, q0)
         const int c = n / QQ, p = n % QQ;
         T f[Q];
 #pragma unroll
@@ -777,10 +961,12 @@ struct L2B {
       }
       (void)t1;
     } else {
-      constexpr int NQ = Q * Q;
       using LY = B2<L, NC, Q>;
       constexpr int NQp = LY::NQp, R = LY::R;
-      for (int n = lt; n < NC * Q; n += NQ) {            // q1 -> j1, line (c, q0)
+#pragma unroll
+      for (int it = 0; it < (NC * Q + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= NC * Q) break;            // q1 -> j1, line (c, q0)
         const int c = n / Q, q0 = n % Q;
         T f[Q];
 #pragma unroll
@@ -798,10 +984,13 @@ struct L2B {
   }
   static __device__ __forceinline__ void p2(T* t1, const T* t2, int lt, T* out) {
     if constexpr (DIM == 3) {
-      constexpr int QQ = Q * Q, NQ = QQ * Q;
+      constexpr int QQ = Q * Q;
       using LY = B3<L, NC, Q>;
       constexpr int CA = LY::CA, SA = LY::SA, RB = LY::RB;
-      for (int n = lt; n < NM * Q; n += NQ) {            // q1 -> j1, line (c, j2, q0)
+#pragma unroll
+      for (int it = 0; it < (NM * Q + NS - 1) / NS; ++it) {
+        const int n = lt + it * NS;
+        if (n >= NM * Q) break;            // q1 -> j1, line (c, j2, q0)
         const int q0 = n % Q, m = n / Q, c = m / L, j2 = m % L;
         T zz[Q];
 #pragma unroll
@@ -816,8 +1005,11 @@ struct L2B {
       }
       (void)out;
     } else {
-      constexpr int NQ = Q * Q, R = B2<L, NC, Q>::R;
-      for (int r = lt; r < NM; r += NQ) {                // q0 -> j0, line (c, j1)
+      constexpr int R = B2<L, NC, Q>::R;
+#pragma unroll
+      for (int it = 0; it < (NM + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM) break;                // q0 -> j0, line (c, j1)
         T y[Q];
 #pragma unroll
         for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * R + r];
@@ -834,8 +1026,11 @@ struct L2B {
   }
   static __device__ __forceinline__ void p3(const T* t1, int lt, T* out) {
     if constexpr (DIM == 3) {
-      constexpr int NQ = Q * Q * Q, RB = B3<L, NC, Q>::RB;
-      for (int r = lt; r < NM * L; r += NQ) {            // q0 -> j0, line (c, j2, j1)
+      constexpr int RB = B3<L, NC, Q>::RB;
+#pragma unroll
+      for (int it = 0; it < (NM * L + NS - 1) / NS; ++it) {
+        const int r = lt + it * NS;
+        if (r >= NM * L) break;            // q0 -> j0, line (c, j2, j1)
         T y[Q];
 #pragma unroll
         for (int q0 = 0; q0 < Q; ++q0) y[q0] = t1[q0 * RB + r];
@@ -948,6 +1143,55 @@ __device__ __forceinline__ void h1l2_bwd(const T (&fval)[NC], const T (&fgrad)[N
     S::p3(t1, lt, out);
     SL::p3(u1, lt, outl);
     __syncthreads();
+  }
+}
+
+// Paired fused entry points (T = float, NT threads per element, two points per thread):
+// the line stages stride over NT threads; SYNC is the barrier between phases (__syncwarp
+// when the element's threads are one warp or part of one, else __syncthreads).
+template <bool WARP>
+__device__ __forceinline__ void esync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+template <int DIM, int K, int NC, int NCL, int NT, bool WARP, bool VAL = true>
+__device__ __forceinline__ void h1l2_fwd_x2(const float* __restrict__ in, const float* __restrict__ inl, float* t1,
+                                            float* t2, float* u1, float* u2, const float* B, const float* G,
+                                            const float* Bl, int lt, float2 (&val)[NC], float2 (&grad)[NC][DIM],
+                                            float2 (&lval)[NCL]) {
+  using S = H1F<DIM, K, NC, float, NT>;
+  using SL = L2F<DIM, K, NCL, float, K, NT>;
+  S::s1(in, t1, lt);
+  SL::s1(inl, u1, lt);
+  esync<WARP>();
+  if constexpr (DIM == 3) {
+    S::s2(t1, t2, lt);
+    SL::s2(u1, u2, lt);
+    esync<WARP>();
+  }
+  S::template s3x2<VAL>(DIM == 3 ? t2 : t1, B, G, lt, val, grad);
+  SL::s3x2(DIM == 3 ? u2 : u1, Bl, lt, lval);
+  esync<WARP>();
+}
+template <int DIM, int K, int NC, int NCL, int NT, bool WARP>
+__device__ __forceinline__ void h1l2_bwd_x2(const float2 (&fval)[NC], const float2 (&fgrad)[NC][DIM],
+                                            const float2 (&lval)[NCL], float* sf, float* t1, float* t2, float* sfl,
+                                            float* u1, float* u2, int lt, float* out, float* outl) {
+  using S = H1B<DIM, K, NC, float, NT>;
+  using SL = L2B<DIM, K, NCL, float, K, NT>;
+  S::p0x2(fval, fgrad, sf, lt);
+  SL::p0x2(lval, sfl, lt);
+  esync<WARP>();
+  S::p1(sf, t1, t2, lt);
+  SL::p1(sfl, u1, u2, lt);
+  esync<WARP>();
+  S::p2(t1, t2, lt, out);
+  SL::p2(u1, u2, lt, outl);
+  esync<WARP>();
+  if constexpr (DIM == 3) {
+    S::p3(t1, lt, out);
+    SL::p3(u1, lt, outl);
+    esync<WARP>();
   }
 }
 

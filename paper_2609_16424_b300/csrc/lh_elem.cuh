@@ -37,12 +37,12 @@ struct ElemIdx {
   bool valid;
 };
 
-template <int DIM, int K>
-__device__ __forceinline__ ElemIdx elem_index(const ElemParams& P) {
-  using C = Cfg<DIM, K>;
+// element of this thread: NTE threads per element, EPB elements per block
+template <int DIM, int NTE, int EPB>
+__device__ __forceinline__ ElemIdx elem_index_nt(const ElemParams& P) {
   ElemIdx r;
-  const int eb = threadIdx.x / C::NQ;
-  r.e = (long long)blockIdx.x * C::EPB + eb;
+  const int eb = threadIdx.x / NTE;
+  r.e = (long long)blockIdx.x * EPB + eb;
   r.valid = r.e < P.NE;
   // 32-bit lattice arithmetic: dim * N_V < 2^31 is checked at mesh creation, so NE fits
   const unsigned e = r.valid ? (unsigned)r.e : 0u, n0 = (unsigned)P.n0, n1 = (unsigned)P.n1;
@@ -58,6 +58,22 @@ __device__ __forceinline__ ElemIdx elem_index(const ElemParams& P) {
   }
   return r;
 }
+template <int DIM, int K>
+__device__ __forceinline__ ElemIdx elem_index(const ElemParams& P) {
+  return elem_index_nt<DIM, Cfg<DIM, K>::NQ, Cfg<DIM, K>::EPB>(P);
+}
+
+// Two quadrature points per thread (the paired element kernels): NT = NQ / 2 threads per
+// element, EPB elements per block of at least 128 threads; WARP: the element's threads lie
+// within one warp, so a warp barrier orders its shared-memory phases.
+template <int DIM, int K>
+struct Cfg2 {
+  using C = Cfg<DIM, K>;
+  static constexpr int NT = C::NQ / 2;
+  static constexpr int EPB = NT >= 128 ? 1 : 128 / NT;
+  static constexpr int THREADS = EPB * NT;
+  static constexpr bool WARP = NT <= 32 && 32 % NT == 0;
+};
 
 // global lattice node of local H1 node a of element (ex, ey, ez)
 template <int DIM, int K>

@@ -13,6 +13,7 @@
 #include "lh_qp.cuh"
 #include "lh_contract.cuh"
 #include "lh_elem.cuh"
+#include "lh_tc.cuh"
 
 namespace lh {
 
@@ -368,6 +369,294 @@ k_jvp_rec(ElemParams P, const float* __restrict__ rec, float tau, const float* _
     for (int i = lt; i < DIM * ND; i += NQ) ev[E.e * (DIM * ND) + i] = s_h[i];
     for (int i = lt; i < NL; i += NQ) oute[E.e * NL + i] = TO(s_l[i]);
   }
+}
+
+// Shared-memory plan of the paired record J.w (units of float): per element the gathered
+// direction, the H1 and L2 scratch of the line stages; every region starts at an even
+// offset so that the paired point stages can store both points with one 8-byte access.
+template <int DIM, int K, int NCH>
+struct PlanX2 {
+  using C = Cfg<DIM, K>;
+  using PL = Plan<DIM, K, NCH, 0, 1, DIM>;
+  using L2S = ln::L2Scratch<DIM, K, 1>;
+  static constexpr int ev(int x) { return (x + 1) & ~1; }
+  static constexpr int OL = NCH * C::ND, OT1 = ev(OL + C::NL), OT2 = ev(OT1 + PL::T1), OSF = ev(OT2 + PL::T2),
+                       OU1 = ev(OSF + PL::SF), OU2 = ev(OU1 + L2S::U1), OSFL = ev(OU2 + L2S::U2),
+                       PER = ev(OSFL + L2S::SF);
+  static constexpr int HEAD = ev(Tab<K>::SMEM);
+  static constexpr size_t bytes() { return sizeof(float) * (size_t)(HEAD + Cfg2<DIM, K>::EPB * PER); }
+};
+
+// The record J.w with two quadrature points per thread (Cfg2): the same stages as k_jvp_rec,
+// with the per-point work (the last forward direction, the linearised point map, the first
+// backward phase) in paired FP32 operations on the two points (q0, q1, q2) and
+// (q0 + 1, q1, q2), q0 = 2 (lt % (Q/2)), whose record entries are adjacent (one 8-byte load
+// per field); the line stages stride over the element's NQ / 2 threads; the gather takes one
+// thread per local node for all components.  The map is linear in the direction, so tau
+// scales W instead of the reference gradients.
+template <int DIM, int K, class TO>
+__global__ void __launch_bounds__(Cfg2<DIM, K>::THREADS)
+k_jvp_rec2(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ dk,
+           float* __restrict__ ev, TO* __restrict__ oute) {
+  using C = Cfg<DIM, K>;
+  using C2 = Cfg2<DIM, K>;
+  constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q, NT = C2::NT, QH = Q / 2;
+  constexpr int NCH = 2 * DIM;   // dk_x, dk_v
+  constexpr int NR = lin_len<DIM>(), O = 2 * DIM * DIM;
+  using PX = PlanX2<DIM, K, NCH>;
+  using TB = Tab<K>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* smem = reinterpret_cast<float*>(smem_raw);
+  const float* sB = smem + TB::B;
+  const float* sG = smem + TB::G;
+  const float* sBl = smem + TB::BL;
+  const float* sW = smem + TB::W;
+  load_tables(P, smem, TB::SMEM);
+  const int eb = threadIdx.x / NT, lt = threadIdx.x % NT;
+  float* s_h = smem + PX::HEAD + eb * PX::PER;
+  float* s_l = s_h + PX::OL;
+  float* t1 = s_h + PX::OT1;
+  float* t2 = s_h + PX::OT2;
+  float* sf = s_h + PX::OSF;
+  float* u1 = s_h + PX::OU1;
+  float* u2 = s_h + PX::OU2;
+  float* sfl = s_h + PX::OSFL;
+  const ElemIdx E = elem_index_nt<DIM, NT, C2::EPB>(P);
+  for (int a = lt; a < ND; a += NT) {
+    const long long nd = node_of<DIM, K>(P, E, a);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) s_h[c * ND + a] = E.valid ? dk[c * P.NV + nd] : 0.f;
+  }
+  for (int i = lt; i < NL; i += NT) s_l[i] = E.valid ? dk[2 * DIM * P.NV + E.e * NL + i] : 0.f;
+  // record of this thread's two points (idle lanes read element 0's: finite, never written)
+  const int p0 = 2 * (lt % QH) + Q * (lt / QH);
+  float2 Lr[NR];
+  {
+    const float2* rq = reinterpret_cast<const float2*>(rec + (E.valid ? E.e : 0) * NR * NQ + p0);
+#pragma unroll
+    for (int f = 0; f < NR; ++f) Lr[f] = rq[f * (NQ / 2)];
+  }
+  __syncthreads();
+  float2 hv[NCH], hg[NCH][DIM], lq[1];
+  ln::h1l2_fwd_x2<DIM, K, NCH, 1, NT, C2::WARP>(s_h, s_l, t1, t2, u1, u2, sB, sG, sBl, lt, hv, hg, lq);
+  float2 mq;
+  {
+    const int q0 = 2 * (lt % QH), q1 = (lt / QH) % Q, q2 = lt / (QH * Q);
+    float2 a = f2mul(make_float2(sW[q0], sW[q0 + 1]), f2s(sW[q1]));
+    if constexpr (DIM == 3) a = f2mul(a, f2s(sW[q2]));
+    mq = f2mul(f2s(P.fmq0[E.valid ? E.e : 0]), a);
+  }
+  float2 dJ[DIM][DIM], dGv[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      dJ[i][r] = hg[i][r];
+      dGv[i][r] = hg[DIM + i][r];
+    }
+  const float2 tW = f2mul(f2s(tau), Lr[O + LF_W]);
+  float2 fgrad[DIM][DIM], dEo, dW;
+  qp_tangent_lin_x2<DIM>(Lr, dJ, dGv, lq[0], tW, P.visc != 0, fgrad, dEo, dW);
+  float2 fval[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) fval[i] = f2mul(mq, hv[DIM + i]);
+  float2 g = f2fma(mq, lq[0], f2neg(dEo));
+  if constexpr (DIM == 2) {
+    if (P.tg) {   // d(W s(x_q)) = dW s + W grad s . dx
+      const float2 dx = f2mul(f2s(tau), f2fma(Lr[O + LF_TGX], hv[0], f2mul(Lr[O + LF_TGY], hv[1])));
+      g = f2add(g, f2neg(f2fma(Lr[O + LF_W], dx, f2mul(dW, Lr[O + LF_TGS]))));
+    }
+  }
+  float2 gv[1] = {g};
+  ln::h1l2_bwd_x2<DIM, K, DIM, 1, NT, C2::WARP>(fval, fgrad, gv, sf, t1, t2, sfl, u1, u2, lt, s_h, s_l);
+  if (E.valid) {
+    for (int i = lt; i < DIM * ND; i += NT) ev[E.e * (DIM * ND) + i] = s_h[i];
+    for (int i = lt; i < NL; i += NT) oute[E.e * NL + i] = TO(s_l[i]);
+  }
+}
+
+// Pipelined record J.w (elements of 64 quadrature points, one warp per element, two points
+// per lane): each warp walks a strided list of elements; the record of its next element
+// (one contiguous block) arrives by a bulk asynchronous copy into the warp's shared-memory
+// slot while the current element's last backward stages and the next forward stages run,
+// and the next element's direction is loaded into registers while the current one
+// computes.  Per-warp slot (floats): record (whose space also holds the first backward
+// phase's point values, dead before the next record is requested) | gathered direction
+// (H1, L2) | line-stage scratch.
+constexpr int kPipeWarps = 8;   // warps (elements in flight) per block
+template <int DIM, int K>
+struct PipeX2 {
+  using C = Cfg<DIM, K>;
+  using PL = Plan<DIM, K, 2 * DIM, 0, 1, DIM>;
+  using L2S = ln::L2Scratch<DIM, K, 1>;
+  static constexpr int ev(int x) { return (x + 1) & ~1; }
+  static constexpr int a4(int x) { return (x + 3) & ~3; }
+  static constexpr int REC = lin_len<DIM>() * C::NQ;   // one element's record
+  static constexpr int OSFL = ev(PL::SF);               // sf at 0, sfl after it, both inside the record
+  static constexpr int OG = a4(REC), OGL = OG + 2 * DIM * C::ND, OT1 = ev(OGL + C::NL), OT2 = ev(OT1 + PL::T1),
+                       OU1 = ev(OT2 + PL::T2), OU2 = ev(OU1 + L2S::U1), SLOT = a4(OU2 + L2S::U2);
+  static constexpr int HEAD = a4(2 * kPipeWarps + Tab<K>::SMEM);   // mbarriers, tables
+  static constexpr size_t bytes() { return sizeof(float) * (size_t)(HEAD + kPipeWarps * SLOT); }
+  static_assert((REC * sizeof(float)) % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(OSFL + L2S::SF <= REC, "the backward point values fit in the record's space");
+};
+constexpr unsigned kPipePolls = 1u << 22;   // mbarrier polls before a record copy is given up
+
+template <int DIM, int K, class TO>
+__global__ void __launch_bounds__(32 * kPipeWarps, 2)
+k_jvp_rec_pipe(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ dk,
+               float* __restrict__ ev, TO* __restrict__ oute) {
+  using C = Cfg<DIM, K>;
+  using PX = PipeX2<DIM, K>;
+  constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q, QH = Q / 2;
+  static_assert(NQ == 64, "one warp per element, two points per lane");
+  constexpr int NCH = 2 * DIM;   // dk_x, dk_v
+  constexpr int NR = lin_len<DIM>(), O = 2 * DIM * DIM, REC = PX::REC;
+  using TB = Tab<K>;
+  using S = ln::H1F<DIM, K, NCH, float, 32>;
+  using SL = ln::L2F<DIM, K, 1, float, K, 32>;
+  using SB = ln::H1B<DIM, K, DIM, float, 32>;
+  using SLB = ln::L2B<DIM, K, 1, float, K, 32>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_raw);
+  float* tab = reinterpret_cast<float*>(smem_raw) + 2 * kPipeWarps;
+  const float* sB = tab + TB::B;
+  const float* sG = tab + TB::G;
+  const float* sBl = tab + TB::BL;
+  const float* sW = tab + TB::W;
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  float* slot = reinterpret_cast<float*>(smem_raw) + PX::HEAD + w * PX::SLOT;
+  float* R = slot;
+  float* G = slot + PX::OG;
+  float* GL = slot + PX::OGL;
+  float* t1 = slot + PX::OT1;
+  float* t2 = slot + PX::OT2;
+  float* sf = R;
+  float* sfl = R + PX::OSFL;
+  float* u1 = slot + PX::OU1;
+  float* u2 = slot + PX::OU2;
+  load_tables(P, tab, TB::SMEM);
+  if (lane == 0) {
+    tc::mbar_init(&mbar[w], 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  const long long TW = (long long)gridDim.x * kPipeWarps;
+  long long e = (long long)blockIdx.x * kPipeWarps + w;
+  if (e >= P.NE) return;
+  // the element's direction: lane a < ND holds node a's NCH components, lane j < NL the
+  // j-th L2 value
+  float gx[NCH], gl = 0.f;
+  auto fetch = [&](long long el) {
+    const unsigned n0 = (unsigned)P.n0, n1 = (unsigned)P.n1, eu = (unsigned)el;
+    const unsigned t = eu / n0, ex = eu - t * n0, ey = t % n1, ez = t / n1;
+    if (lane < ND) {
+      const int a0 = lane % (K + 1), a1 = (lane / (K + 1)) % (K + 1), a2 = lane / ((K + 1) * (K + 1));
+      const unsigned i0 = ex * K + a0, i1 = ey * K + a1, i2 = ez * K + a2;
+      const long long nd = (long long)(i0 + (unsigned)P.N0 * (i1 + (unsigned)P.N1 * i2));
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) gx[c] = dk[c * P.NV + nd];
+    }
+    if (lane < NL) gl = dk[2 * DIM * P.NV + el * NL + lane];
+  };
+  auto place = [&]() {
+    if (lane < ND) {
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) G[c * ND + lane] = gx[c];
+    }
+    if (lane < NL) GL[lane] = gl;
+  };
+  if (lane == 0) {
+    tc::mbar_arrive_expect_tx(&mbar[w], REC * (uint32_t)sizeof(float));
+    tc::bulk_g2s(R, rec + e * REC, REC * (uint32_t)sizeof(float), &mbar[w]);
+  }
+  fetch(e);
+  place();
+  __syncwarp();
+  const int p0 = 2 * (lane % QH) + Q * (lane / QH);
+  uint32_t phase = 0;
+  bool ok = true;
+  for (;;) {
+    const long long en = e + TW;
+    const bool next = en < P.NE;
+    S::s1(G, t1, lane);
+    SL::s1(GL, u1, lane);
+    __syncwarp();
+    if (next) fetch(en);   // G is free until the outputs
+    S::s2(t1, t2, lane);
+    SL::s2(u1, u2, lane);
+    __syncwarp();
+    float2 hv[NCH], hg[NCH][DIM], lq[1];
+    S::template s3x2<true>(DIM == 3 ? t2 : t1, sB, sG, lane, hv, hg);
+    SL::s3x2(DIM == 3 ? u2 : u1, sBl, lane, lq);
+    float2 mq;
+    {
+      const int q0 = 2 * (lane % QH), q1 = (lane / QH) % Q, q2 = lane / (QH * Q);
+      float2 a = f2mul(make_float2(sW[q0], sW[q0 + 1]), f2s(sW[q1]));
+      if constexpr (DIM == 3) a = f2mul(a, f2s(sW[q2]));
+      mq = f2mul(f2s(P.fmq0[e]), a);
+    }
+    if (ok) {
+      ok = tc::mbar_wait(&mbar[w], phase, kPipePolls);
+      if (ok) phase ^= 1u;
+    }
+    float2 Lr[NR];
+#pragma unroll
+    for (int f = 0; f < NR; ++f) Lr[f] = *reinterpret_cast<const float2*>(R + f * NQ + p0);
+    float2 dJ[DIM][DIM], dGv[DIM][DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i)
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        dJ[i][r] = hg[i][r];
+        dGv[i][r] = hg[DIM + i][r];
+      }
+    const float2 tW = f2mul(f2s(tau), Lr[O + LF_W]);
+    float2 fgrad[DIM][DIM], dEo, dW;
+    qp_tangent_lin_x2<DIM>(Lr, dJ, dGv, lq[0], tW, P.visc != 0, fgrad, dEo, dW);
+    float2 fval[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) fval[i] = f2mul(mq, hv[DIM + i]);
+    float2 g = f2fma(mq, lq[0], f2neg(dEo));
+    if constexpr (DIM == 2) {
+      if (P.tg) {   // d(W s(x_q)) = dW s + W grad s . dx
+        const float2 dx = f2mul(f2s(tau), f2fma(Lr[O + LF_TGX], hv[0], f2mul(Lr[O + LF_TGY], hv[1])));
+        g = f2add(g, f2neg(f2fma(Lr[O + LF_W], dx, f2mul(dW, Lr[O + LF_TGS]))));
+      }
+    }
+    __syncwarp();   // every lane has read R and t2
+    float2 gv[1] = {g};
+    SB::p0x2(fval, fgrad, sf, lane);
+    SLB::p0x2(gv, sfl, lane);
+    __syncwarp();
+    SB::p1(sf, t1, t2, lane);
+    SLB::p1(sfl, u1, u2, lane);
+    __syncwarp();   // sf and sfl read: the record's space is free
+    if (next && ok && lane == 0) {   // the next record (async proxy after the generic reads)
+      tc::fence_proxy_async();
+      tc::mbar_arrive_expect_tx(&mbar[w], REC * (uint32_t)sizeof(float));
+      tc::bulk_g2s(R, rec + en * REC, REC * (uint32_t)sizeof(float), &mbar[w]);
+    }
+    SB::p2(t1, t2, lane, G);
+    SLB::p2(u1, u2, lane, GL);
+    __syncwarp();
+    if constexpr (DIM == 3) {
+      SB::p3(t1, lane, G);
+      SLB::p3(u1, lane, GL);
+      __syncwarp();
+    }
+    const float bad = ok ? 1.f : __int_as_float(0x7fc00000);
+    for (int i = lane; i < DIM * ND; i += 32) ev[e * (DIM * ND) + i] = G[i] * bad;
+    if (lane < NL) oute[e * NL + lane] = TO(GL[lane] * bad);
+    if (!next) break;
+    __syncwarp();   // outputs read before G is refilled
+    place();
+    __syncwarp();
+    e = en;
+  }
+  // after a copy was given up on (no later copy is issued) it may still be in flight: wait
+  // once more, bounded, before the block's shared memory is released
+  if (!ok) tc::mbar_wait(&mbar[w], phase, kPipePolls);
 }
 
 // =====================================================================================
@@ -910,10 +1199,36 @@ cudaError_t init_const_tables() {
   return e != cudaSuccess ? e : init_const_tables_explicit();
 }
 
+// blocks of KERN resident on the whole device at the given launch shape (once per device)
+template <auto KERN>
+static cudaError_t resident_blocks(int threads, size_t bytes, int* out) {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int v = cache[dev & 63].load(std::memory_order_acquire);
+  if (v == 0) {
+    int nb = 0, nsm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, KERN, threads, bytes);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (nb < 1) return cudaErrorInvalidConfiguration;
+    v = nb * nsm;
+    cache[dev & 63].store(v, std::memory_order_release);
+  }
+  *out = v;
+  return cudaSuccess;
+}
+
 template <int DIM, int K>
 struct Launch {
   using C = Cfg<DIM, K>;
   static unsigned grid(const ElemParams& P) { return (unsigned)((P.NE + C::EPB - 1) / C::EPB); }
+  // the record J.w in the form measured fastest per order: pipelined (elements of 64
+  // points: 3D Q2, 2D Q4; one warp per element), one point per thread (3D Q1), else paired
+  // (two points per thread)
+  static constexpr bool kPipeRec = (DIM == 3 && K == 2) || (DIM == 2 && K == 4);
+  static constexpr bool kPairRec = !(DIM == 3 && K == 1);
 
   static cudaError_t residual(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                               double* ev, double* Re, double* bmin, double* r, cudaEvent_t* ev2, float* rec) {
@@ -945,12 +1260,32 @@ struct Launch {
   template <class TO>
   static cudaError_t jvp_rec(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
                              float* ev, TO* out, cudaEvent_t* ev2) {
-    using PL = Plan<DIM, K, 2 * DIM, 0, 1, DIM, ln::L2Scratch<DIM, K, 1>::ALL>;
-    const size_t by = PL::bytes(sizeof(float));
-    cudaError_t e = prep<k_jvp_rec<DIM, K, TO>>(by);
-    if (e != cudaSuccess) return e;
-    mark(ev2, 0, s);
-    k_jvp_rec<DIM, K, TO><<<grid(P), C::THREADS, by, s>>>(P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV);
+    if constexpr (kPipeRec) {
+      const size_t by = PipeX2<DIM, K>::bytes();
+      cudaError_t e = prep<k_jvp_rec_pipe<DIM, K, TO>>(by);
+      int resident = 0;
+      if (e == cudaSuccess) e = resident_blocks<k_jvp_rec_pipe<DIM, K, TO>>(32 * kPipeWarps, by, &resident);
+      if (e != cudaSuccess) return e;
+      const long long need = (P.NE + kPipeWarps - 1) / kPipeWarps;
+      mark(ev2, 0, s);
+      k_jvp_rec_pipe<DIM, K, TO><<<(unsigned)(need < resident ? need : resident), 32 * kPipeWarps, by, s>>>(
+          P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV);
+    } else if constexpr (kPairRec) {
+      using C2 = Cfg2<DIM, K>;
+      const size_t by = PlanX2<DIM, K, 2 * DIM>::bytes();
+      cudaError_t e = prep<k_jvp_rec2<DIM, K, TO>>(by);
+      if (e != cudaSuccess) return e;
+      mark(ev2, 0, s);
+      k_jvp_rec2<DIM, K, TO><<<(unsigned)((P.NE + C2::EPB - 1) / C2::EPB), C2::THREADS, by, s>>>(
+          P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV);
+    } else {
+      using PL = Plan<DIM, K, 2 * DIM, 0, 1, DIM, ln::L2Scratch<DIM, K, 1>::ALL>;
+      const size_t by = PL::bytes(sizeof(float));
+      cudaError_t e = prep<k_jvp_rec<DIM, K, TO>>(by);
+      if (e != cudaSuccess) return e;
+      mark(ev2, 0, s);
+      k_jvp_rec<DIM, K, TO><<<grid(P), C::THREADS, by, s>>>(P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV);
+    }
     mark(ev2, 1, s);
     count_launches(2);
     k_assemble_jvp<DIM, K, float, TO><<<asm_grid(P), kAsmX, 0, s>>>(P, dk, tau, ev, out);

@@ -4,6 +4,9 @@
 #pragma once
 #include "lh_common.cuh"
 #include "lh_dd.cuh"
+#if defined(__CUDACC__)
+#include "lh_f2.cuh"
+#endif
 
 namespace lh {
 
@@ -322,6 +325,116 @@ __host__ __device__ __forceinline__ void qp_tangent_lin(const T (&L)[lin_len<DIM
     }
   }
 }
+
+#if defined(__CUDACC__)
+// qp_tangent_lin for two quadrature points at once (paired FP32 operations, lh_f2.cuh), in
+// the form the record J.w uses: dJ and dGv are the reference gradients of the direction's
+// x and v fields (not yet multiplied by tau), de its energy value, and tW = tau W.  The map
+// is linear in (dJ, dGv, de), so scaling W by tau scales every output by tau.  sigma and
+// d sigma are symmetric: only i <= j is formed.
+template <int DIM>
+__device__ __forceinline__ void qp_tangent_lin_x2(const float2 (&L)[lin_len<DIM>()], const float2 (&dJ)[DIM][DIM],
+                                                  const float2 (&dGv)[DIM][DIM], float2 de, float2 tW, bool visc,
+                                                  float2 (&dSo)[DIM][DIM], float2& dEo, float2& dW) {
+  constexpr int O = 2 * DIM * DIM;
+  auto Ji = [&](int i, int j) -> const float2& { return L[i * DIM + j]; };
+  auto Lv = [&](int i, int j) -> const float2& { return L[DIM * DIM + i * DIM + j]; };
+  // theta = tr(J^-1 dJ)
+  float2 th = f2mul(Ji(0, 0), dJ[0][0]);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+      if (i + r > 0) th = f2fma(Ji(i, r), dJ[r][i], th);
+  // d grad v = (dGv - grad v dJ) J^-1
+  float2 dL[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    float2 Y[DIM];
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      float2 y = dGv[i][r];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) y = f2fma(f2neg(Lv(i, b)), dJ[b][r], y);
+      Y[r] = y;
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      float2 v = f2mul(Y[0], Ji(0, j));
+#pragma unroll
+      for (int r = 1; r < DIM; ++r) v = f2fma(Y[r], Ji(r, j), v);
+      dL[i][j] = v;
+    }
+  }
+  const float2 np = f2neg(L[O + LF_P]);
+  const float2 dp = f2fma(np, th, f2mul(L[O + LF_PE], de));
+  float2 mu = f2s(0.f), dmu = f2s(0.f);
+  if (visc) {
+    float2 ddiv = dL[0][0];
+#pragma unroll
+    for (int i = 1; i < DIM; ++i) ddiv = f2add(ddiv, dL[i][i]);
+    mu = L[O + LF_MU];
+    dmu = f2fma(L[O + LF_AE], de, f2fma(L[O + LF_ADIV], ddiv, f2mul(L[O + LF_ATH], th)));
+  }
+  const float2 ndp = f2neg(dp);
+  float2 sg[DIM][DIM], dsg[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = i; j < DIM; ++j) {
+      if (i == j) {
+        sg[i][i] = f2fma(mu, Lv(i, i), np);
+        dsg[i][i] = f2fma(mu, dL[i][i], f2fma(dmu, Lv(i, i), ndp));
+      } else {
+        const float2 ep = f2mul(f2s(0.5f), f2add(Lv(i, j), Lv(j, i)));
+        const float2 dep = f2mul(f2s(0.5f), f2add(dL[i][j], dL[j][i]));
+        sg[i][j] = sg[j][i] = f2mul(mu, ep);
+        dsg[i][j] = dsg[j][i] = f2fma(mu, dep, f2mul(dmu, ep));
+      }
+    }
+  float2 E = f2s(0.f), dE = f2s(0.f);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      E = (i + j == 0) ? f2mul(sg[0][0], Lv(0, 0)) : f2fma(sg[i][j], Lv(i, j), E);
+      dE = (i + j == 0) ? f2mul(dsg[0][0], Lv(0, 0)) : f2fma(dsg[i][j], Lv(i, j), dE);
+      dE = f2fma(sg[i][j], dL[i][j], dE);
+    }
+  dEo = f2mul(tW, f2fma(th, E, dE));
+  dW = f2mul(tW, th);
+  float2 nsg[DIM][DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = i; j < DIM; ++j) nsg[i][j] = nsg[j][i] = f2neg(sg[i][j]);
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    float2 nM[DIM], N[DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {   // -M = -sigma J^-T (row i)
+      float2 v = f2mul(nsg[i][0], Ji(b, 0));
+#pragma unroll
+      for (int k = 1; k < DIM; ++k) v = f2fma(nsg[i][k], Ji(b, k), v);
+      nM[b] = v;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {   // N = theta sigma + d sigma - M dJ^T (row i)
+      float2 v = f2fma(th, sg[i][a], dsg[i][a]);
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) v = f2fma(nM[b], dJ[a][b], v);
+      N[a] = v;
+    }
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      float2 v = f2mul(N[0], Ji(j, 0));
+#pragma unroll
+      for (int a = 1; a < DIM; ++a) v = f2fma(N[a], Ji(j, a), v);
+      dSo[i][j] = f2mul(tW, v);
+    }
+  }
+}
+#endif
 
 // Transpose of qp_tangent_lin (the adjoint of the linearised point map, for the
 // reduced-precision J^T y): given the adjoints Sb of dS, Eb of dE and Wb of dW, returns the

@@ -108,6 +108,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// one arrival that also announces `bytes` of asynchronous copies completing on this phase
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(mbar)), "r"(bytes)
+               : "memory");
+}
+// bulk copy global -> this CTA's shared memory (both 16-byte aligned, bytes a multiple of
+// 16), completing `bytes` on mbar's current phase
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(mbar)) : "memory");
+}
 // wait for completion of the phase with the given parity; gives up after max_iter polls
 // or about 2^31 SM clock cycles (~1 s), whichever comes first, and returns false (the
 // caller records the failure and poisons dependent results)
