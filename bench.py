@@ -188,11 +188,12 @@ def timed_steps(mesh, u_s, k_s, dt, steps, prec, flush, profile=False, arnoldi=1
 
 
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of a launch inside the timed Newton steps of
-# this workload, with the digest of the CUDA sources it was built from.  The figure is
+# (dram__bytes_read.sum + dram__bytes_write.sum) of a launch inside the Newton steps of this
+# workload (the event-instrumented repeat), with the digest of the CUDA sources it was built
+# from.  The figure is
 # reported only while the sources still have that digest (csrc_digest()).
-NCU_TRAFFIC = {"k_jvp_rec<3,2,float>": {"bytes": 91823616 + 351232, "csrc": "ce85d270b921ee85"},
-               "k_residual<3,2>": {"bytes": 13419520 + 40261888, "csrc": "ce85d270b921ee85"}}
+NCU_TRAFFIC = {"k_jvp_rec_pipe<3,2,float>": {"bytes": 91842048 + 102912, "csrc": "eb103cf395251eb4"},
+               "k_residual<3,2>": {"bytes": 13443328 + 40211968, "csrc": "eb103cf395251eb4"}}
 
 
 def csrc_digest():
@@ -224,6 +225,16 @@ def fp32_ops_residual(dim, k, visc=True):
     return 15 * macs + (2 * k) ** dim * (ops.value + 8 * (dim + 4) + 20)
 
 
+def rec_kernel_name(dim, k):
+    """The library's FP32 record J.w kernel for (dim, k): pipelined for elements of 64 points
+    (3D Q2, 2D Q4), one point per thread for 3D Q1, else two points per thread."""
+    if (dim, k) in ((3, 2), (2, 4)):
+        return f"k_jvp_rec_pipe<{dim},{k},float>"
+    if (dim, k) == (3, 1):
+        return f"k_jvp_rec<{dim},{k},float>"
+    return f"k_jvp_rec2<{dim},{k},float>"
+
+
 def dominant_roofline(kind, launch_ms, ne, k, prec, fp64_peak, fp32_peak):
     """Roofline of the step's dominant element kernel (3D, order k).
     residual: float operations of its double-word arithmetic against the FP32 pipe's
@@ -232,8 +243,8 @@ def dominant_roofline(kind, launch_ms, ne, k, prec, fp64_peak, fp32_peak):
     FP32 record J.w: the larger of its FP32-FLOP fraction and its HBM fraction (algorithmic
     bytes: record, direction, element output)."""
     t = launch_ms * 1e-3
-    name = {"residual": "k_residual<3,2>", "jvp_fp64": "k_jvp<3,2,double,double>",
-            "jvp_fp32": "k_jvp_rec<3,2,float>", "jvp_tc": f"k_jvp_tc<3,2,{prec}>"}.get(kind, kind)
+    name = {"residual": f"k_residual<3,{k}>", "jvp_fp64": f"k_jvp<3,{k},double,double>",
+            "jvp_fp32": rec_kernel_name(3, k), "jvp_tc": f"k_jvp_tc<3,{k},{prec}>"}.get(kind, kind)
     out = {"kernel": name, "launch_ms": round(launch_ms, 5), "peak_source": "measured FMA probe (lh_probe_fma) "
            "this run" if kind != "jvp_fp32" else None}
     if kind == "residual":

@@ -3,6 +3,7 @@
 - 3D point-blast mesh 24^3 Q2-Q1 (the benchmark's size): the oracle evaluates the whole
   residual and the complex-step J.w (seconds) and every output is compared.
 - Three-state interface problem 56x24 Q3-Q2 with per-element rho0 / gamma.
+- The record J.w of 64-point elements at sizes where its warps walk element lists.
 - 48^3 meshes (throughput sweep sizes, too large for the dense oracle): properties that hold
   at any size, checked on the GPU outputs alone.
 """
@@ -39,6 +40,23 @@ def test_blast24_residual_and_jvp_full_vector():
         rel = c.rel_blocks(jt, jref32)
         assert rel[0] <= 2e-5 and max(rel[1:]) <= tol, (kind, rel)
     c.gm.tc_status()
+
+
+@pytest.mark.parametrize("dim,n,k", [(2, (56, 48), 4), (3, (17, 15, 11), 2)])
+def test_record_jvp_element_lists(dim, n, k):
+    """The record J.w for elements of 64 points (2D Q4, 3D Q2: one warp per element walking a
+    strided element list, the next record arriving by bulk copy) at sizes with more elements
+    than resident warps (2368 on a B300) and not a multiple of them: warps take one or two
+    elements, each output is compared with the oracle's complex-step J.w."""
+    c = Case(dim, n, k, seed=64)
+    kk = lh_synth.normal_vector(c.gm.n, 65, 0.05)
+    dk = lh_synth.normal_vector(c.gm.n, 66)
+    tau = 1e-3
+    u, kd = c.dev(c.u), c.dev(kk)
+    c.gm.linearize(u, kd, tau)
+    jf = c.gm.jvp(u, kd, tau, c.dev(dk, torch.float32), lin=True).double().cpu().numpy()
+    jref = c.hyd.jvp_complex_step(c.u, kk, tau, dk.astype(np.float32).astype(np.float64))
+    assert max(c.rel_blocks(jf, jref)) <= 2e-5
 
 
 def test_interface_problem_full_size():
