@@ -118,7 +118,11 @@ lh_status lh_residual(lh_mesh* mesh, const double* u, const double* k, double ta
  * and need the record of a preceding lh_linearize(u, k, tau); LH_TF32/LH_BF16 return
  * LH_EINVAL for 3D orders >= 3 (the dense element operator does not fit in shared memory).
  * A tensor-core wait that times out writes NaN into the affected element rows and is
- * reported by the next lh_newton_step (LH_ECUDA) and by lh_tc_status. */
+ * reported by the next lh_newton_step (LH_ECUDA) and by lh_tc_status.  The same holds for
+ * LH_FP32_LIN on elements of 64 points (3D Q2, 2D Q4), whose kernel copies each element's
+ * record into shared memory asynchronously and waits on the copy with a bounded wait
+ * (about 1 s): if that wait runs out, the rows of the warp's later elements are NaN, a
+ * failing lh_newton_step reports LH_ECUDA and lh_tc_status reports it. */
 lh_status lh_jvp(lh_mesh* mesh, const double* u, const double* k, double tau,
                  const void* dk, void* out, lh_prec prec);
 
@@ -137,8 +141,10 @@ lh_status lh_halo_len(const lh_mesh* mesh, int face, long long* len);
 lh_status lh_halo_pack(lh_mesh* mesh, int face, const void* r, void* buf, lh_prec prec);
 lh_status lh_halo_add(lh_mesh* mesh, int face, const void* buf, void* r, lh_prec prec);
 
-/* Status of the tensor-core J.w: LH_OK, or LH_ECUDA if one of its bounded waits on the
- * tensor cores timed out since the mesh was created (synchronises; clears the flag). */
+/* Status of the bounded waits of the tensor-core J.w (on the tensor cores) and of the
+ * LH_FP32_LIN J.w of 64-point elements (on its record copies): LH_OK, or LH_ECUDA if one of
+ * them timed out since the last call or the mesh's creation (synchronises; clears the
+ * flag). */
 lh_status lh_tc_status(lh_mesh* mesh);
 
 /* Poll limit of every bounded wait of the tensor-core J.w on its MMA completions (process

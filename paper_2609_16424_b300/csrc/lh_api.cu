@@ -300,7 +300,7 @@ struct KrylovOp {
   cudaError_t jvp_f32(const float* x, float* y) {
     if (tck < 0)
       return launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, x, reinterpret_cast<float*>(m->d_ev), y,
-                                prof_pair(m, LH_PROF_JVP32));
+                                prof_pair(m, LH_PROF_JVP32), tc_err(m));
     return launch_jvp_tc<float>(m->P, m->stream, tck, m->d_rec, tau, x, reinterpret_cast<float*>(m->d_ev), y,
                                 tc_err(m), prof_pair(m, LH_PROF_JVPTC));
   }
@@ -1141,7 +1141,7 @@ lh_status lh_jvp(lh_mesh* m, const double* u, const double* k, double tau, const
     if (prec == LH_FP32_LIN) {
       LH_CK(m, launch_jvp_rec_f32(m->P, m->stream, m->d_rec, tau, static_cast<const float*>(dk),
                                   reinterpret_cast<float*>(m->d_ev), static_cast<float*>(out),
-                                  prof_pair(m, LH_PROF_JVP32)));
+                                  prof_pair(m, LH_PROF_JVP32), tc_err(m)));
     } else {
       if (!jvp_tc_supported(m->P.dim, m->P.K))
         return fail(m, LH_EINVAL, "lh_jvp: tensor-core J.w supports 2D orders 1-4 and 3D orders 1-2");
@@ -1338,6 +1338,15 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     rec = m->d_rec;
   }
   m->rec_valid = false;   // the record will describe this solve's internal iterates
+  // on a failure of a solve with the record J.w, a bounded wait of that kernel that ran out
+  // (its rows are then NaN) is the cause to report
+  auto wait_status = [&](lh_status failed) {
+    if (f32 && tck < 0) {
+      const lh_status t = lh_tc_status(m);
+      if (t != LH_OK) return t;
+    }
+    return failed;
+  };
   std::memset(&S, 0, sizeof(S));
   const long long n = m->n;
   const int mres = o.restart;
@@ -1400,7 +1409,7 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     if (o.precond >= 2)   // the record describes the current iterate k (its last residual)
       LH_CK(m, launch_jvv_diag(m->P, s, rec, tau, reinterpret_cast<float*>(m->d_ev), m->d_diagMv, m->d_jdiag,
                                kJvvFloor));
-    if (o.precond == 3 && (st = cheb_bounds(m, o, tau, tck, zd)) != LH_OK) return st;
+    if (o.precond == 3 && (st = cheb_bounds(m, o, tau, tck, zd)) != LH_OK) return wait_status(st);
     const double* rhs = r;   // with scaled_norm GMRES solves W J dk = -W r
     if (wsc) {
       LH_CK(m, launch_row_mul<double>(s, wsc, r, rs, n));
@@ -1409,7 +1418,7 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
     if (f32) {
       KrylovOp<float> op{m, o.precond, tck, u, k, tau, zf};
       op.wsc = wsc;
-      if ((st = gmres<float>(m, oi, op, rhs, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return st;
+      if ((st = gmres<float>(m, oi, op, rhs, nr, dk, Vf, wf, uf, zd, wd, S)) != LH_OK) return wait_status(st);
     } else {
       KrylovOp<double> op{m, o.precond, -1, u, k, tau, zd};
       op.wsc = wsc;
@@ -1433,8 +1442,8 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
       lam *= 0.5;
       ++S.backtracks;
     }
-    if (!accepted) return fail(m, LH_ETANGLED, "Newton: line search found no trial with det J > 0 "
-                                               "and a finite residual");
+    if (!accepted) return wait_status(fail(m, LH_ETANGLED, "Newton: line search found no trial with det J > 0 "
+                                                           "and a finite residual"));
     std::swap(k, kt);
     std::swap(r, rt);
     nr = std::sqrt(nr2);
@@ -1454,7 +1463,7 @@ static lh_status newton_solve(lh_mesh* m, const double* u, const double* k_init,
   if (S.min_detj == 0.0) S.min_detj = mind;
   if (tck >= 0 && (st = lh_tc_status(m)) != LH_OK) return st;
   *k_out = k;
-  if (!conv) return fail(m, LH_ENOCONV, "Newton did not converge");
+  if (!conv) return wait_status(fail(m, LH_ENOCONV, "Newton did not converge"));
   return LH_OK;
 }
 
@@ -2110,6 +2119,8 @@ lh_status lh_tc_status(lh_mesh* m) {
   LH_CK(m, cudaStreamSynchronize(m->stream));
   if (flag) {
     LH_CK(m, cudaMemsetAsync(tc_err(m), 0, sizeof(int), m->stream));
+    if (flag & kWaitErrPipe)
+      return fail(m, LH_ECUDA, "record J.w: a bounded wait on the copy of an element's record timed out");
     return fail(m, LH_ECUDA, "tensor-core J.w: a bounded wait on the tensor cores timed out");
   }
   return LH_OK;

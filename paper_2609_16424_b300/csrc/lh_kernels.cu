@@ -505,7 +505,7 @@ constexpr unsigned kPipePolls = 1u << 22;   // mbarrier polls before a record co
 template <int DIM, int K, class TO>
 __global__ void __launch_bounds__(32 * kPipeWarps, 2)
 k_jvp_rec_pipe(ElemParams P, const float* __restrict__ rec, float tau, const float* __restrict__ dk,
-               float* __restrict__ ev, TO* __restrict__ oute) {
+               float* __restrict__ ev, TO* __restrict__ oute, int* __restrict__ err) {
   using C = Cfg<DIM, K>;
   using PX = PipeX2<DIM, K>;
   constexpr int ND = C::ND, NL = C::NL, NQ = C::NQ, Q = C::Q, QH = Q / 2;
@@ -655,8 +655,11 @@ k_jvp_rec_pipe(ElemParams P, const float* __restrict__ rec, float tau, const flo
     e = en;
   }
   // after a copy was given up on (no later copy is issued) it may still be in flight: wait
-  // once more, bounded, before the block's shared memory is released
-  if (!ok) tc::mbar_wait(&mbar[w], phase, kPipePolls);
+  // once more, bounded, before the block's shared memory is released; the flag tells the host
+  if (!ok) {
+    tc::mbar_wait(&mbar[w], phase, kPipePolls);
+    if (err && lane == 0) atomicOr(err, kWaitErrPipe);
+  }
 }
 
 // =====================================================================================
@@ -1259,7 +1262,7 @@ struct Launch {
   }
   template <class TO>
   static cudaError_t jvp_rec(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
-                             float* ev, TO* out, cudaEvent_t* ev2) {
+                             float* ev, TO* out, cudaEvent_t* ev2, int* err) {
     if constexpr (kPipeRec) {
       const size_t by = PipeX2<DIM, K>::bytes();
       cudaError_t e = prep<k_jvp_rec_pipe<DIM, K, TO>>(by);
@@ -1269,7 +1272,7 @@ struct Launch {
       const long long need = (P.NE + kPipeWarps - 1) / kPipeWarps;
       mark(ev2, 0, s);
       k_jvp_rec_pipe<DIM, K, TO><<<(unsigned)(need < resident ? need : resident), 32 * kPipeWarps, by, s>>>(
-          P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV);
+          P, rec, (float)tau, dk, ev, out + 2 * DIM * P.NV, err);
     } else if constexpr (kPairRec) {
       using C2 = Cfg2<DIM, K>;
       const size_t by = PlanX2<DIM, K, 2 * DIM>::bytes();
@@ -1398,12 +1401,12 @@ cudaError_t launch_residual(const ElemParams& P, cudaStream_t s, const double* u
   LH_DISPATCH(P, residual(P, s, u, k, tau, ev, Re, bmin, r, ev2, rec))
 }
 cudaError_t launch_jvp_rec_f32(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
-                               float* ev, float* out, cudaEvent_t* ev2) {
-  LH_DISPATCH(P, template jvp_rec<float>(P, s, rec, tau, dk, ev, out, ev2))
+                               float* ev, float* out, cudaEvent_t* ev2, int* err) {
+  LH_DISPATCH(P, template jvp_rec<float>(P, s, rec, tau, dk, ev, out, ev2, err))
 }
 cudaError_t launch_jvp_rec_f64out(const ElemParams& P, cudaStream_t s, const float* rec, double tau,
-                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2) {
-  LH_DISPATCH(P, template jvp_rec<double>(P, s, rec, tau, dk, ev, out, ev2))
+                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2, int* err) {
+  LH_DISPATCH(P, template jvp_rec<double>(P, s, rec, tau, dk, ev, out, ev2, err))
 }
 template <class TO>
 cudaError_t launch_assemble_jvp(const ElemParams& P, cudaStream_t s, const float* dk, double tau, const float* ev,

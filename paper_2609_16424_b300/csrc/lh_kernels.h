@@ -19,11 +19,15 @@ cudaError_t init_const_tables_explicit();
 cudaError_t launch_residual(const ElemParams& P, cudaStream_t s, const double* u, const double* k, double tau,
                             double* ev, double* blockmin, double* r, cudaEvent_t* ev2 = nullptr,
                             float* rec = nullptr);
-// FP32 J.w from the linearisation record (float or double output)
+// FP32 J.w from the linearisation record (float or double output).  err (device int, may be
+// NULL): the pipelined form (elements of 64 points) ORs in kWaitErrPipe when a bounded wait
+// on its record copy runs out (the element rows of that warp are then NaN).
+constexpr int kWaitErrTc = 1, kWaitErrPipe = 2;
 cudaError_t launch_jvp_rec_f32(const ElemParams& P, cudaStream_t s, const float* rec, double tau, const float* dk,
-                               float* ev, float* out, cudaEvent_t* ev2 = nullptr);
+                               float* ev, float* out, cudaEvent_t* ev2 = nullptr, int* err = nullptr);
 cudaError_t launch_jvp_rec_f64out(const ElemParams& P, cudaStream_t s, const float* rec, double tau,
-                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2 = nullptr);
+                                  const float* dk, float* ev, double* out, cudaEvent_t* ev2 = nullptr,
+                                  int* err = nullptr);
 // node-centric assembly of a float J.w from its element scratch (x rows from dk)
 template <class TO>
 cudaError_t launch_assemble_jvp(const ElemParams& P, cudaStream_t s, const float* dk, double tau, const float* ev,
